@@ -1,0 +1,227 @@
+"""Pins of the oracle's solvers: Jacobi-PCG, Chebyshev smoothing, Lanczos
+bounds, the p-multigrid transfers and V-cycle, and flexible CG (CPU only).
+
+Anchors: numpy's dense LAPACK solve and eigensolver on tiny meshes, the closed
+form of the Chebyshev error polynomial, exactness of polynomial interpolation,
+the adjoint identity between prolongation and restriction, the spectral
+convergence of the manufactured problem, and iteration counts that stay flat
+as the mesh is refined.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2110_01716_gb300 import inputs
+
+DIR, NEU = 0, 1
+
+
+def level(orc, ex, ey, ez, N, bc, seed=3):
+    return orc.Level(ex, ey, ez, N, bc, inputs.box_vertices(ex, ey, ez, 0.1, seed))
+
+
+def dense_unique(L, apply):
+    ids = L.ids
+    rep = np.full(L.ng, -1)
+    for l in range(ids.size - 1, -1, -1):
+        rep[ids[l]] = l
+    M = np.zeros((L.ng, L.ng))
+    for g in range(L.ng):
+        M[:, g] = apply((ids == g).astype(np.float64))[rep]
+    return M, rep
+
+
+def manufactured(L):
+    X = L.X
+    x, y, z = X[:, 0].ravel(), X[:, 1].ravel(), X[:, 2].ravel()
+    us = np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+    return us, L.assembled_rhs(3 * np.pi ** 2 * us)
+
+
+def test_pcg_matches_dense_solve_dirichlet(orc):
+    L = level(orc, 2, 2, 2, 4, DIR)
+    A, rep = dense_unique(L, L.ax)
+    keep = L.mask[rep] == 1.0
+    b = L.gs(inputs.random_field(L.nl, 4)) * L.mask
+    x, info = L.pcg(b, tol=1e-14, maxit=1000)
+    assert info["status"] == 0
+    ref = np.zeros(L.ng)
+    ref[keep] = np.linalg.solve(A[np.ix_(keep, keep)], b[rep][keep])
+    assert np.max(np.abs(x - ref[L.ids])) < 1e-10 * np.max(np.abs(ref))
+    # the converged residual, recomputed, meets the stopping rule
+    r = b - L.ax(x)
+    assert np.sqrt(L.dot(r, r)) <= 1e-13 * np.sqrt(L.dot(b, b))
+
+
+def test_pcg_neumann_matches_least_squares(orc):
+    L = level(orc, 2, 2, 2, 3, NEU)
+    A, rep = dense_unique(L, L.ax)
+    g = L.gs(inputs.random_field(L.nl, 8))
+    b_u = g[rep] - g[rep].mean()  # mean-zero over unique dofs
+    b = b_u[L.ids]
+    x, info = L.pcg(b, tol=1e-13, maxit=1000)
+    assert info["status"] == 0
+    ref = np.linalg.lstsq(A, b_u, rcond=None)[0]
+    xu = x[rep]
+    np.testing.assert_allclose(xu - xu.mean(), ref - ref.mean(), atol=1e-10 * np.abs(ref).max())
+
+
+def test_pcg_plain_cg_and_zero_rhs(orc):
+    L = level(orc, 2, 1, 2, 3, DIR)
+    x, info = L.pcg(np.zeros(L.nl), x0=np.ones(L.nl) * L.mask, tol=1e-10)
+    # b = 0: the stopping rule is reached only at x = 0
+    assert info["res0"] > 0
+    b = L.gs(inputs.random_field(L.nl, 2)) * L.mask
+    x1, i1 = L.pcg(b, tol=1e-12, precond=True)
+    x2, i2 = L.pcg(b, tol=1e-12, precond=False)
+    assert i1["status"] == 0 and i2["status"] == 0
+    np.testing.assert_allclose(x1, x2, atol=1e-9 * np.abs(x1).max())
+
+
+def test_pcg_reports_nonconvergence(orc):
+    L = level(orc, 2, 2, 2, 5, DIR)
+    _, b = manufactured(L)
+    x, info = L.pcg(b, tol=1e-12, maxit=3)
+    assert info["status"] == 1 and info["iters"] == 3
+
+
+def test_manufactured_solution_converges_spectrally(orc):
+    errs = []
+    for N in range(2, 10):
+        L = level(orc, 2, 2, 2, N, DIR, seed=1)
+        us, b = manufactured(L)
+        u, info = L.pcg(b, tol=1e-13, maxit=3000)
+        assert info["status"] == 0
+        errs.append(np.max(np.abs(u - us * L.mask)))
+    errs = np.array(errs)
+    # error falls geometrically with N at fixed mesh (exponential convergence)
+    assert np.all(errs[1:] < errs[:-1] / 5), errs
+    assert errs[-1] < 1e-10
+
+
+def test_manufactured_solution_at_8cube_order7(orc):
+    L = level(orc, 8, 8, 8, 7, DIR, seed=1)
+    us, b = manufactured(L)
+    u, info = L.pcg(b, tol=1e-10, maxit=2000)
+    assert info["status"] == 0
+    assert np.max(np.abs(u - us)) < 1e-9
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_chebyshev_error_polynomial_closed_form(orc, k):
+    # diagonal operator with a known spectrum; Jacobi scaling d
+    n = 40
+    rng = np.random.Generator(np.random.PCG64(k))
+    d = rng.uniform(0.5, 2.0, n)
+    lam = np.linspace(0.05, 1.0, n)  # spectrum of D^-1 A
+    a = lam * d
+    lo, hi = 0.1, 1.1
+    e0 = rng.standard_normal(n)
+    xstar = rng.standard_normal(n)
+    b = a * xstar
+    x0 = xstar - e0
+    x = orc.cheb(n, lambda v: a * v, 1.0 / d, b, x0, k, lo, hi, x_zero=False)
+    theta, delta = (hi + lo) / 2, (hi - lo) / 2
+    T = np.polynomial.chebyshev.Chebyshev.basis(k)
+    factor = T((theta - lam) / delta) / T(theta / delta)
+    np.testing.assert_allclose(xstar - x, factor * e0, atol=1e-12)
+    # starting from zero gives the same as x0 = 0 with x_zero=False
+    xa = orc.cheb(n, lambda v: a * v, 1.0 / d, b, np.zeros(n), k, lo, hi, x_zero=True)
+    xb = orc.cheb(n, lambda v: a * v, 1.0 / d, b, np.zeros(n), k, lo, hi, x_zero=False)
+    np.testing.assert_allclose(xa, xb, atol=1e-13)
+
+
+@pytest.mark.parametrize("bc", [DIR, NEU])
+def test_lanczos_estimate_of_largest_eigenvalue(orc, bc):
+    L = level(orc, 2, 2, 2, 4, bc)
+    A, rep = dense_unique(L, L.ax)
+    d = L.diag()[rep]
+    keep = L.mask[rep] == 1.0
+    As = A[np.ix_(keep, keep)] / np.sqrt(np.outer(d[keep], d[keep]))
+    lmax = np.linalg.eigvalsh(As)[-1]
+    est, steps = L.lanczos_max(20, seed=5)
+    assert steps == 20
+    assert est <= lmax * (1 + 1e-12)
+    assert est >= 0.97 * lmax
+
+
+@pytest.mark.parametrize("Nf,Nc", [(7, 3), (3, 1), (5, 2)])
+def test_prolongation_exact_and_restriction_is_its_transpose(orc, Nf, Nc):
+    v = inputs.box_vertices(2, 3, 2, 0.1, 6)
+    F = orc.Level(2, 3, 2, Nf, NEU, v)
+    Cl = orc.Level(2, 3, 2, Nc, NEU, v)
+    J = orc.interp(Nf, Nc)
+    # physical coordinates are trilinear in (r,s,t): interpolation reproduces them,
+    # and products of two coordinates when Nc >= 2
+    Xc, Xf = Cl.X, F.X
+    fields = [(Xc[:, 0], Xf[:, 0]), (Xc[:, 2], Xf[:, 2])]
+    if Nc >= 2:
+        fields.append((Xc[:, 0] * Xc[:, 1], Xf[:, 0] * Xf[:, 1]))
+    for fc, ff in fields:
+        got = orc.interp3(F.E, Nf + 1, Nc + 1, J, fc.ravel())
+        np.testing.assert_allclose(got, ff.ravel(), atol=1e-13)
+    # <P u_c, v_f>_f = <u_c, R v_f>_c with R v = gs_c(J^T (v / mult_f))
+    uc = Cl.gs(inputs.random_field(Cl.nl, 1)) / Cl.mult
+    vf = F.gs(inputs.random_field(F.nl, 2)) / F.mult
+    Pu = orc.interp3(F.E, Nf + 1, Nc + 1, J, uc)
+    Rv = Cl.gs(orc.interp3(F.E, Nf + 1, Nc + 1, J, vf / F.mult, transpose=True))
+    lhs, rhs = F.dot(Pu, vf), Cl.dot(uc, Rv)
+    assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+
+
+def test_two_level_vcycle_with_exact_coarse_solve(orc):
+    v = inputs.box_vertices(2, 2, 2, 0.1, 2)
+    P = orc.PMG(2, 2, 2, [4, 2], DIR, v, cheb_degree=2, coarse_tol=1e-15, coarse_maxit=5000)
+    L = P.levels[0]
+    M, rep = dense_unique(L, P.vcycle)
+    A, _ = dense_unique(L, L.ax)
+    keep = L.mask[rep] == 1.0
+    M = M[np.ix_(keep, keep)]
+    A = A[np.ix_(keep, keep)]
+    # exact coarse solve and equal pre/post smoothing: M is symmetric
+    assert np.max(np.abs(M - M.T)) < 1e-9 * np.max(np.abs(M))
+    Eprop = np.eye(A.shape[0]) - M @ A
+    rho = np.max(np.abs(np.linalg.eigvals(Eprop)))
+    assert rho < 0.5, rho
+    # the smoothing interval brackets the estimate
+    lo, hi = P.lam(0)
+    assert 0 < lo < hi
+
+
+def test_flexcg_with_jacobi_equals_pcg(orc):
+    v = inputs.box_vertices(3, 2, 2, 0.1, 4)
+    P = orc.PMG(3, 2, 2, [5, 1], DIR, v)
+    L = P.levels[0]
+    _, b = manufactured(L)
+    for its in (1, 5, 17):
+        xf, fi = P.flexpcg(b, tol=0.0, maxit=its, precond=False)
+        xp, pi = L.pcg(b, tol=0.0, maxit=its)
+        assert fi["iters"] == pi["iters"] == its
+        np.testing.assert_allclose(xf, xp, atol=1e-11 * np.abs(xp).max())
+
+
+@pytest.mark.parametrize("bc", [DIR, NEU])
+def test_pmg_flexcg_iterations_flat_under_refinement(orc, bc):
+    iters = []
+    for e in (2, 4):
+        v = inputs.box_vertices(e, e, e, 0.1, 3)
+        P = orc.PMG(e, e, e, [7, 3, 1], bc, v, cheb_degree=2, coarse_tol=1e-2,
+                    coarse_maxit=50)
+        L = P.levels[0]
+        if bc == DIR:
+            _, b = manufactured(L)
+        else:
+            a, k, phi = inputs.fourier_modes(3)
+            X = L.X
+            f = sum(a[m] * np.cos(2 * np.pi * (k[m, 0] * X[:, 0] + k[m, 1] * X[:, 1]
+                                               + k[m, 2] * X[:, 2]) + phi[m])
+                    for m in range(len(a))).ravel()
+            b = L.gs(L.B * f)
+            b -= L.dot(b, np.ones(L.nl)) / L.dot(np.ones(L.nl), np.ones(L.nl))
+        x, info = P.flexpcg(b, tol=1e-8, maxit=200)
+        assert info["status"] == 0
+        r = b - L.ax(x)
+        assert np.sqrt(L.dot(r, r)) <= 1.01e-8 * np.sqrt(L.dot(b, b))
+        iters.append(info["iters"])
+    assert iters[1] <= iters[0] + 4, iters
+    assert iters[1] < 40, iters
