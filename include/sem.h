@@ -1,0 +1,195 @@
+/*
+ * sem.h -- C ABI of the GB300 spectral-element pressure-Poisson library.
+ *
+ * The library solves the pressure-Poisson problem of a semi-implicit spectral
+ * element (SEM) Navier-Stokes step (Fischer et al., "Highly Optimized
+ * Full-Core Reactor Simulations on Summit", Sec. 2-3) on one GPU:
+ * matrix-free tensor-product stiffness operator on deformed hexahedra, direct
+ * stiffness summation (gather-scatter), p-multigrid preconditioning with
+ * Chebyshev-accelerated Jacobi smoothing, Jacobi-PCG and flexible CG.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Mesh: a box of ex*ey*ez hexahedra on a vertex lattice of
+ *   (ex+1)(ey+1)(ez+1) points, each element mapped trilinearly from [-1,1]^3
+ *   (the isoparametric map of Sec. 2 with straight edges).  Element
+ *   e = ix + ex*(iy + ey*iz).
+ * - Fields are "E-layout" vectors: E*(N+1)^3 values, element-major, point
+ *   (i,j,k) of an element at i + (N+1)*(j + (N+1)*k), i along r (Sec. 2, Eq. 2:
+ *   nodal values u^e_ijk on Gauss-Lobatto-Legendre points).  A field is
+ *   "continuous" when all local copies of a shared node hold the same value.
+ * - Vectors passed to the library are caller-owned DEVICE memory unless the
+ *   entry point says HOST.  The library never frees them.  The library owns
+ *   everything reachable from a handle (geometry, numbering, workspaces) and
+ *   frees it in the matching *_destroy.
+ * - All device work is enqueued on the caller's CUDA stream (`stream`, a
+ *   cudaStream_t passed as void*; NULL = the legacy default stream).  Entry
+ *   points that return values to the host synchronise that stream.
+ * - Every entry point returns a sem_status; on failure sem_last_error() holds a
+ *   message (thread-local) and outputs are unspecified.  No C++ exception
+ *   crosses this boundary.  Arguments are validated before any device work.
+ * - Handles are not thread-safe: one host thread at a time per handle.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SEM_OK = 0,
+  SEM_EINVAL = 1,    /* bad argument, size, null pointer, folded element */
+  SEM_ENOMEM = 2,    /* device or host allocation failed */
+  SEM_ECUDA = 3,     /* a CUDA runtime call failed */
+  SEM_ENOTCONV = 4,  /* solver hit max_iter before the tolerance */
+  SEM_ENUMERIC = 5,  /* NaN or Inf met in a solver */
+  SEM_EAGAIN = 6,    /* request still pending (sem_poll) */
+  SEM_EBUSY = 7,     /* no free slot or memory for a request (sem_submit) */
+  SEM_ETIMEOUT = 8   /* a bounded wait ran out */
+} sem_status;
+
+typedef enum { SEM_F64 = 0, SEM_F32 = 1, SEM_F16 = 2, SEM_BF16 = 3 } sem_dtype;
+
+enum { SEM_DIRICHLET = 0, SEM_NEUMANN = 1 };
+enum { SEM_GEOM_STORED = 0, SEM_GEOM_TRILINEAR = 1 };
+
+typedef struct sem_mesh sem_mesh;
+typedef struct sem_pmg sem_pmg;
+
+/* Mesh description.  verts (HOST, may be NULL): vertex lattice
+ * [(ex+1)(ey+1)(ez+1)][3], vertex (a,b,c) at a + (ex+1)(b + (ey+1)c); it is
+ * copied during sem_mesh_create.  When NULL the library builds the unit-cube
+ * lattice and moves every vertex strictly inside the cube by
+ * (2u-1)*jitter/(ex,ey,ez) per coordinate, u = top 53 bits of
+ * splitmix64(seed + (3*vertex + coordinate + 1) * 0x9E3779B97F4A7C15) * 2^-53.
+ * bc: SEM_DIRICHLET (u = 0 on the box boundary) or SEM_NEUMANN.
+ * geom: SEM_GEOM_STORED keeps the six geometric factors per point in HBM;
+ * SEM_GEOM_TRILINEAR keeps only the 8 vertices per element and recomputes
+ * the factors inside the operator kernel. */
+typedef struct {
+  int32_t ex, ey, ez;  /* elements per direction, each >= 1 */
+  int32_t N;           /* polynomial order, 1 <= N <= SEM_MAX_ORDER */
+  double jitter;       /* built-in generator only */
+  uint64_t seed;       /* built-in generator only */
+  int32_t bc;
+  int32_t geom;
+  const double *verts;
+} sem_mesh_desc;
+
+#define SEM_MAX_ORDER 11
+
+/* Build the mesh, its geometric factors (Sec. 2: isoparametric map, six
+ * symmetric factors G = w det(J) J^-1 J^-T per GLL point, mass B = w det(J)),
+ * the shared-node numbering for gather-scatter (Sec. 3: global vertex ids)
+ * and the Jacobi diagonal.  Synchronises `stream`.
+ * Errors: SEM_EINVAL (sizes, order, det(J) <= 0, more than 2^31-1 local
+ * points), SEM_ENOMEM, SEM_ECUDA. */
+sem_status sem_mesh_create(const sem_mesh_desc *desc, void *stream, sem_mesh **out);
+sem_status sem_mesh_destroy(sem_mesh *mesh);
+
+/* n_local = E (N+1)^3, n_global = (ex N+1)(ey N+1)(ez N+1) unique nodes,
+ * dev_bytes = device memory owned by the mesh.  Any output may be NULL. */
+sem_status sem_mesh_info(const sem_mesh *mesh, int64_t *n_local, int64_t *n_global,
+                         size_t *dev_bytes);
+
+enum {
+  SEM_FIELD_X = 0, SEM_FIELD_Y = 1, SEM_FIELD_Z = 2, /* physical coordinates */
+  SEM_FIELD_MASS = 3,  /* B = w_i w_j w_k det(J), unassembled */
+  SEM_FIELD_MULT = 4,  /* number of local copies of each node */
+  SEM_FIELD_MASK = 5,  /* 0 on Dirichlet boundary nodes, else 1 */
+  SEM_FIELD_DINV = 6   /* mask / assembled diagonal of A (Jacobi) */
+};
+/* Write one per-point field of the mesh, FP64 E-layout, into out (device,
+ * n_local doubles). */
+sem_status sem_mesh_field(sem_mesh *mesh, int32_t which, double *out, void *stream);
+
+enum { SEM_AX_LOCAL = 0, SEM_AX_ASSEMBLED = 1 };
+/* Stiffness operator (Sec. 2, footnote 1: u_r = Dhat u along each direction,
+ * then w = sum_d Dhat_d^T sum_e G_de u_e).
+ * SEM_AX_LOCAL:     w = A_L u, element by element (no summation).
+ * SEM_AX_ASSEMBLED: w = mask * gs(A_L u).
+ * dtype: SEM_F64 (u, w double) or SEM_F32 (u, w float; factors rounded to
+ * float once at mesh creation).  u and w are E-layout device vectors of
+ * n_local elements and must not overlap. */
+sem_status sem_ax(sem_mesh *mesh, sem_dtype dtype, const void *u, void *w, int32_t flags,
+                  void *stream);
+
+/* Direct stiffness summation in place (Sec. 2: C0 continuity; Sec. 3: gs):
+ * every local copy of a node receives the sum over its copies.  All copies end
+ * bit-identical.  dtype SEM_F64 or SEM_F32. */
+sem_status sem_gs(sem_mesh *mesh, sem_dtype dtype, void *u, void *stream);
+
+/* Inner product over unique nodes of two FP64 E-layout vectors,
+ * sum_l u_l v_l / mult_l (equal to the Euclidean product of the unique values
+ * when u and v are continuous).  Writes *result (HOST); synchronises. */
+sem_status sem_dot(sem_mesh *mesh, const double *u, const double *v, double *result,
+                   void *stream);
+
+/* p-multigrid description (Sec. 3, pMG: levels of decreasing order, tensor
+ * interpolation between them, Chebyshev-accelerated point-Jacobi smoothing,
+ * preconditioner arithmetic optionally in 32-bit). */
+typedef struct {
+  int32_t nlevels;          /* 1..8; orders[0] must equal the mesh order */
+  int32_t orders[8];        /* strictly decreasing, e.g. {7, 3, 1} */
+  int32_t cheb_degree;      /* Chebyshev degree per smoothing, >= 1 */
+  int32_t lanczos_steps;    /* steps of the lambda_max estimate, >= 2 */
+  uint64_t seed;            /* start vector of the lambda_max estimate */
+  int32_t smoother_dtype;   /* sem_dtype of the smoothed levels: F64 or F32 */
+  double coarse_tol;        /* coarsest level: FP64 Jacobi-PCG relative tol */
+  int32_t coarse_maxit;     /* ... and iteration cap (tol <= 0: exactly maxit) */
+} sem_pmg_desc;
+
+/* Build the hierarchy on the mesh's vertices and boundary condition.
+ * Chebyshev interval per smoothed level: [lambda_hi/10, lambda_hi] with
+ * lambda_hi = 1.1 * (Lanczos estimate of lambda_max(D^-1 A)).
+ * The pMG handle refers to the mesh, which must outlive it.  Synchronises. */
+sem_status sem_pmg_setup(sem_mesh *mesh, const sem_pmg_desc *desc, void *stream,
+                         sem_pmg **out);
+sem_status sem_pmg_destroy(sem_pmg *pmg);
+/* Chebyshev interval of level l (HOST outputs). */
+sem_status sem_pmg_info(const sem_pmg *pmg, int32_t level, double *lam_lo, double *lam_hi);
+/* One V-cycle z = M r on the finest level (FP64 E-layout device vectors). */
+sem_status sem_pmg_vcycle(sem_pmg *pmg, const double *r, double *z, void *stream);
+
+enum { SEM_SOLVER_PCG = 0, SEM_SOLVER_FLEXCG = 1 };
+typedef struct {
+  int32_t solver;    /* SEM_SOLVER_PCG (Jacobi, Sec. 3) or SEM_SOLVER_FLEXCG */
+  double tol;        /* stop when ||r|| <= tol ||b|| (unique-dof 2-norm) */
+  int32_t max_iter;
+  int32_t check_every; /* read the residual norm every k iterations (>= 1) */
+} sem_solve_desc;
+
+typedef struct {
+  int32_t iters;
+  int32_t status;      /* sem_status of the solve */
+  double res0, res;    /* initial and final residual norms */
+  double bnorm;
+  double time_ms;      /* device time of the solve (CUDA events) */
+} sem_solve_info;
+
+/* Solve A x = b (FP64 outer iteration).  b: assembled right-hand side
+ * (continuous, masked under Dirichlet; mean-free under Neumann: SEM_EINVAL if
+ * |sum b / mult| > 1e-10 * ||b||_1 / mult).  x: initial guess in, solution
+ * out.  pmg: NULL for Jacobi-PCG; required for SEM_SOLVER_FLEXCG.
+ * Returns SEM_OK, SEM_ENOTCONV (max_iter reached; x and info hold the last
+ * iterate) or SEM_ENUMERIC (NaN/Inf).  Synchronises. */
+sem_status sem_solve(sem_mesh *mesh, sem_pmg *pmg, const double *b, double *x,
+                     const sem_solve_desc *desc, sem_solve_info *info, void *stream);
+
+/* As sem_solve with b and x in HOST memory: copies b (and the guess x) to the
+ * device, solves, copies x back.  Device vectors are owned by the mesh. */
+sem_status sem_solve_host(sem_mesh *mesh, sem_pmg *pmg, const double *b_host, double *x_host,
+                          const sem_solve_desc *desc, sem_solve_info *info, void *stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *sem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_H */

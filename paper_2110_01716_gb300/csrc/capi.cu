@@ -1,0 +1,364 @@
+// capi.cu -- the C ABI of include/sem.h: argument checks, error reporting,
+// mesh and pMG handles, and the host loops of the Krylov solvers.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "pmg.cuh"
+
+namespace sem {
+
+static thread_local std::string g_error;
+
+void set_error_message(const char *msg) { g_error = msg ? msg : ""; }
+
+[[noreturn]] void fail(sem_status st, const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_error = buf;
+  throw Failure{st};
+}
+
+template <typename F>
+static sem_status guarded(F &&f) {
+  try {
+    f();
+    return SEM_OK;
+  } catch (const Failure &e) {
+    return e.status;
+  } catch (const std::bad_alloc &) {
+    g_error = "host allocation failed";
+    return SEM_ENOMEM;
+  } catch (...) {
+    g_error = "unexpected internal error";
+    return SEM_ECUDA;
+  }
+}
+
+// Unit-cube lattice with interior vertices moved by splitmix64 offsets
+// (see sem_mesh_desc).
+static std::vector<double> builtin_vertices(int ex, int ey, int ez, double jitter, uint64_t seed) {
+  const size_t nv = (size_t)(ex + 1) * (ey + 1) * (ez + 1);
+  std::vector<double> v(3 * nv);
+  const int cnt[3] = {ex, ey, ez};
+  for (int c = 0; c <= ez; ++c)
+    for (int b = 0; b <= ey; ++b)
+      for (int a = 0; a <= ex; ++a) {
+        const size_t id = a + (size_t)(ex + 1) * (b + (size_t)(ey + 1) * c);
+        const int idx[3] = {a, b, c};
+        const bool interior = a > 0 && a < ex && b > 0 && b < ey && c > 0 && c < ez;
+        for (int m = 0; m < 3; ++m) {
+          double x = (double)idx[m] / (double)cnt[m];
+          if (interior) {
+            uint64_t z = seed + (uint64_t)(3 * id + m + 1) * 0x9E3779B97F4A7C15ull;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+            double off = ((2.0 * u - 1.0) * jitter) / (double)cnt[m];
+            x = x + off;
+          }
+          v[3 * id + m] = x;
+        }
+      }
+  return v;
+}
+
+static void ensure_work(sem_mesh *M) {
+  if (M->work.p) return;
+  M->work.alloc(4 * (size_t)M->fine.t.nl);
+}
+
+static double *slot(sem_mesh *M, int s) { return M->scal.p + s; }
+
+static void read_scalars(sem_mesh *M, int count, cudaStream_t st) {
+  SEM_CHECK_CUDA(cudaMemcpyAsync(M->pinned, M->scal.p, count * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+  SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+// Jacobi-PCG (Sec. 3) or flexible CG with one pMG V-cycle per iteration
+// (Sec. 3).  Scalar slots: 0 bb, 1 rr, 2/3 rho (alternating), 4 pw, 5 zw,
+// 6 sum of b, 7 unused output.
+static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
+                            const sem_solve_desc &d, sem_solve_info &info, cudaStream_t st) {
+  const Level &L = M->fine;
+  const Topo &t = L.t;
+  const bool flex = d.solver == SEM_SOLVER_FLEXCG;
+  ensure_work(M);
+  double *r = M->work.p, *z = r + t.nl, *p = z + t.nl, *w = p + t.nl;
+  cudaEvent_t e0, e1;
+  SEM_CHECK_CUDA(cudaEventCreate(&e0));
+  SEM_CHECK_CUDA(cudaEventCreate(&e1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } guard{e0, e1};
+  SEM_CHECK_CUDA(cudaEventRecord(e0, st));
+  if (t.bc == SEM_NEUMANN) {
+    launch_sum(t, M->red, b, slot(M, 6), st);
+    launch_dot(t, M->red, b, b, slot(M, 0), st);
+    read_scalars(M, 8, st);
+    double s = M->pinned[6], bb = M->pinned[0];
+    SEM_REQUIRE(std::fabs(s) <= 1e-10 * std::sqrt((double)t.ng) * std::sqrt(bb) || bb == 0.0,
+                "Neumann right-hand side is not mean-free (sum %.3e, norm %.3e)", s,
+                std::sqrt(bb));
+  }
+  apply_assembled<double>(L, x, w, st);
+  launch_cg_start(t, M->red, b, w, flex ? nullptr : L.dinv64.p, r, z, p, slot(M, 0), slot(M, 1),
+                  slot(M, 2), st);
+  read_scalars(M, 8, st);
+  const double bb = M->pinned[0];
+  double rr = M->pinned[1];
+  info.bnorm = std::sqrt(bb);
+  info.res0 = std::sqrt(rr);
+  info.iters = 0;
+  sem_status status = SEM_ENOTCONV;
+  const double tol2 = d.tol * d.tol * bb;
+  if (!(rr == rr) || !(bb == bb)) status = SEM_ENUMERIC;
+  else if (rr <= tol2) status = SEM_OK;
+  if (status == SEM_ENOTCONV && flex) {
+    pmg_vcycle(P, r, z, st);
+    launch_convert<double, double>(t.nl, z, p, st);
+    launch_dot(t, M->red, r, z, slot(M, 2), st);
+  }
+  const int every = d.check_every < 1 ? 1 : d.check_every;
+  for (int it = 1; status == SEM_ENOTCONV && it <= d.max_iter; ++it) {
+    const int cur = 2 + ((it - 1) & 1), nxt = 2 + (it & 1);
+    apply_assembled<double>(L, p, w, st);
+    launch_dot(t, M->red, p, w, slot(M, 4), st);
+    launch_cg_update(t, M->red, slot(M, cur), slot(M, 4), p, w, flex ? nullptr : L.dinv64.p, x, r,
+                     z, slot(M, 1), flex ? slot(M, 7) : slot(M, nxt), nullptr, st);
+    info.iters = it;
+    if (it % every == 0 || it == d.max_iter) {
+      read_scalars(M, 8, st);
+      rr = M->pinned[1];
+      if (!(rr == rr) || std::isinf(rr)) { status = SEM_ENUMERIC; break; }
+      if (rr <= tol2) { status = SEM_OK; break; }
+    }
+    if (it == d.max_iter) break;
+    if (flex) {
+      pmg_vcycle(P, r, z, st);
+      launch_flex_dots(t, M->red, z, r, w, slot(M, nxt), slot(M, 5), st);
+      launch_cg_direction(t.nl, slot(M, 5), slot(M, 4), -1.0, z, p, nullptr, st);
+    } else {
+      launch_cg_direction(t.nl, slot(M, nxt), slot(M, cur), 1.0, z, p, nullptr, st);
+    }
+  }
+  SEM_CHECK_CUDA(cudaEventRecord(e1, st));
+  read_scalars(M, 8, st);
+  rr = M->pinned[1];
+  info.res = std::sqrt(rr);
+  if (status == SEM_ENOTCONV && rr <= tol2) status = SEM_OK;
+  float ms = 0.f;
+  SEM_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  info.time_ms = ms;
+  info.status = status;
+  if (status == SEM_ENOTCONV)
+    set_error_message("solver reached max_iter before the tolerance");
+  else if (status == SEM_ENUMERIC)
+    set_error_message("NaN or Inf in the solver residual");
+  return status;
+}
+
+}  // namespace sem
+
+using namespace sem;
+
+static cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+extern "C" {
+
+const char *sem_last_error(void) { return g_error.c_str(); }
+
+sem_status sem_mesh_create(const sem_mesh_desc *desc, void *stream, sem_mesh **out) {
+  return guarded([&] {
+    SEM_REQUIRE(desc != nullptr && out != nullptr, "null desc or out");
+    *out = nullptr;
+    SEM_REQUIRE(desc->ex >= 1 && desc->ey >= 1 && desc->ez >= 1,
+                "element counts must be >= 1");
+    SEM_REQUIRE((int64_t)desc->ex * desc->ey * desc->ez <= (1ll << 31),
+                "too many elements");
+    std::vector<double> verts;
+    const double *v = desc->verts;
+    if (!v) {
+      SEM_REQUIRE(desc->jitter >= 0.0 && desc->jitter < 0.5, "jitter must be in [0, 0.5)");
+      verts = builtin_vertices(desc->ex, desc->ey, desc->ez, desc->jitter, desc->seed);
+      v = verts.data();
+    }
+    std::unique_ptr<sem_mesh> M(new sem_mesh());
+    cudaStream_t st = as_stream(stream);
+    M->stream = st;
+    build_level(M->fine, desc->ex, desc->ey, desc->ez, desc->N, desc->bc, desc->geom, v, false, st);
+    M->red.init(kVecMaxBlocks, 4);
+    M->scal.alloc(16);
+    SEM_CHECK_CUDA(cudaMemsetAsync(M->scal.p, 0, 16 * sizeof(double), st));
+    SEM_CHECK_CUDA(cudaMallocHost(&M->pinned, 16 * sizeof(double)));
+    SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+    *out = M.release();
+  });
+}
+
+sem_status sem_mesh_destroy(sem_mesh *mesh) {
+  return guarded([&] {
+    if (!mesh) return;
+    if (mesh->pinned) cudaFreeHost(mesh->pinned);
+    delete mesh;
+  });
+}
+
+sem_status sem_mesh_info(const sem_mesh *mesh, int64_t *n_local, int64_t *n_global,
+                         size_t *dev_bytes) {
+  return guarded([&] {
+    SEM_REQUIRE(mesh != nullptr, "null mesh");
+    if (n_local) *n_local = mesh->fine.t.nl;
+    if (n_global) *n_global = mesh->fine.t.ng;
+    if (dev_bytes)
+      *dev_bytes = mesh->fine.device_bytes() + mesh->work.bytes() + mesh->red.partials.bytes() +
+                   mesh->scal.bytes() + mesh->host_b.bytes() + mesh->host_x.bytes();
+  });
+}
+
+sem_status sem_mesh_field(sem_mesh *mesh, int32_t which, double *out, void *stream) {
+  return guarded([&] {
+    SEM_REQUIRE(mesh != nullptr && out != nullptr, "null mesh or output");
+    SEM_REQUIRE(which >= SEM_FIELD_X && which <= SEM_FIELD_DINV, "unknown field %d", which);
+    launch_field(mesh->fine, which, out, as_stream(stream));
+  });
+}
+
+sem_status sem_ax(sem_mesh *mesh, sem_dtype dtype, const void *u, void *w, int32_t flags,
+                  void *stream) {
+  return guarded([&] {
+    SEM_REQUIRE(mesh != nullptr && u != nullptr && w != nullptr, "null mesh or vector");
+    SEM_REQUIRE(u != w, "u and w must not alias");
+    SEM_REQUIRE(flags == SEM_AX_LOCAL || flags == SEM_AX_ASSEMBLED, "unknown flags %d", flags);
+    cudaStream_t st = as_stream(stream);
+    if (dtype == SEM_F64) {
+      launch_ax<double>(mesh->fine, (const double *)u, (double *)w, st);
+      if (flags == SEM_AX_ASSEMBLED) {
+        launch_gs<double>(mesh->fine, (double *)w, st);
+        launch_mask<double>(mesh->fine, (double *)w, st);
+      }
+    } else if (dtype == SEM_F32) {
+      if (!mesh->fine.dinv32.p) level_ensure_f32(mesh->fine, st);
+      launch_ax<float>(mesh->fine, (const float *)u, (float *)w, st);
+      if (flags == SEM_AX_ASSEMBLED) {
+        launch_gs<float>(mesh->fine, (float *)w, st);
+        launch_mask<float>(mesh->fine, (float *)w, st);
+      }
+    } else {
+      fail(SEM_EINVAL, "sem_ax supports SEM_F64 and SEM_F32");
+    }
+  });
+}
+
+sem_status sem_gs(sem_mesh *mesh, sem_dtype dtype, void *u, void *stream) {
+  return guarded([&] {
+    SEM_REQUIRE(mesh != nullptr && u != nullptr, "null mesh or vector");
+    if (dtype == SEM_F64) launch_gs<double>(mesh->fine, (double *)u, as_stream(stream));
+    else if (dtype == SEM_F32) launch_gs<float>(mesh->fine, (float *)u, as_stream(stream));
+    else fail(SEM_EINVAL, "sem_gs supports SEM_F64 and SEM_F32");
+  });
+}
+
+sem_status sem_dot(sem_mesh *mesh, const double *u, const double *v, double *result,
+                   void *stream) {
+  return guarded([&] {
+    SEM_REQUIRE(mesh && u && v && result, "null argument");
+    cudaStream_t st = as_stream(stream);
+    launch_dot(mesh->fine.t, mesh->red, u, v, mesh->scal.p + 15, st);
+    SEM_CHECK_CUDA(cudaMemcpyAsync(result, mesh->scal.p + 15, sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
+    SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+sem_status sem_pmg_setup(sem_mesh *mesh, const sem_pmg_desc *desc, void *stream, sem_pmg **out) {
+  return guarded([&] {
+    SEM_REQUIRE(mesh && desc && out, "null argument");
+    *out = nullptr;
+    std::unique_ptr<sem_pmg> P(new sem_pmg());
+    pmg_build(P.get(), mesh, *desc, as_stream(stream));
+    *out = P.release();
+  });
+}
+
+sem_status sem_pmg_destroy(sem_pmg *pmg) {
+  return guarded([&] { delete pmg; });
+}
+
+sem_status sem_pmg_info(const sem_pmg *pmg, int32_t level, double *lam_lo, double *lam_hi) {
+  return guarded([&] {
+    SEM_REQUIRE(pmg != nullptr, "null pmg");
+    SEM_REQUIRE(level >= 0 && level < (int)pmg->levp.size(), "level %d out of range", level);
+    if (lam_lo) *lam_lo = pmg->levp[level]->lam_lo;
+    if (lam_hi) *lam_hi = pmg->levp[level]->lam_hi;
+  });
+}
+
+sem_status sem_pmg_vcycle(sem_pmg *pmg, const double *r, double *z, void *stream) {
+  return guarded([&] {
+    SEM_REQUIRE(pmg && r && z, "null argument");
+    SEM_REQUIRE(r != z, "r and z must not alias");
+    pmg_vcycle(pmg, r, z, as_stream(stream));
+  });
+}
+
+static void check_solve_args(sem_mesh *mesh, sem_pmg *pmg, const sem_solve_desc *desc,
+                             sem_solve_info *info) {
+  SEM_REQUIRE(mesh && desc && info, "null argument");
+  SEM_REQUIRE(desc->solver == SEM_SOLVER_PCG || desc->solver == SEM_SOLVER_FLEXCG,
+              "unknown solver %d", desc->solver);
+  SEM_REQUIRE(desc->solver == SEM_SOLVER_PCG || pmg != nullptr,
+              "SEM_SOLVER_FLEXCG needs a pMG preconditioner");
+  SEM_REQUIRE(pmg == nullptr || pmg->mesh == mesh, "pmg was built on another mesh");
+  SEM_REQUIRE(desc->tol >= 0.0 && desc->max_iter >= 0, "negative tol or max_iter");
+}
+
+sem_status sem_solve(sem_mesh *mesh, sem_pmg *pmg, const double *b, double *x,
+                     const sem_solve_desc *desc, sem_solve_info *info, void *stream) {
+  sem_status result = SEM_OK;
+  sem_status st = guarded([&] {
+    check_solve_args(mesh, pmg, desc, info);
+    SEM_REQUIRE(b && x && b != (const double *)x, "null or aliased b and x");
+    std::memset(info, 0, sizeof(*info));
+    result = run_solve(mesh, pmg, b, x, *desc, *info, as_stream(stream));
+  });
+  return st != SEM_OK ? st : result;
+}
+
+sem_status sem_solve_host(sem_mesh *mesh, sem_pmg *pmg, const double *b_host, double *x_host,
+                          const sem_solve_desc *desc, sem_solve_info *info, void *stream) {
+  sem_status result = SEM_OK;
+  sem_status st = guarded([&] {
+    check_solve_args(mesh, pmg, desc, info);
+    SEM_REQUIRE(b_host && x_host, "null host vector");
+    std::memset(info, 0, sizeof(*info));
+    const size_t n = (size_t)mesh->fine.t.nl;
+    if (!mesh->host_b.p) {
+      mesh->host_b.alloc(n);
+      mesh->host_x.alloc(n);
+    }
+    cudaStream_t s = as_stream(stream);
+    SEM_CHECK_CUDA(cudaMemcpyAsync(mesh->host_b.p, b_host, n * sizeof(double),
+                                   cudaMemcpyHostToDevice, s));
+    SEM_CHECK_CUDA(cudaMemcpyAsync(mesh->host_x.p, x_host, n * sizeof(double),
+                                   cudaMemcpyHostToDevice, s));
+    result = run_solve(mesh, pmg, mesh->host_b.p, mesh->host_x.p, *desc, *info, s);
+    SEM_CHECK_CUDA(cudaMemcpyAsync(x_host, mesh->host_x.p, n * sizeof(double),
+                                   cudaMemcpyDeviceToHost, s));
+    SEM_CHECK_CUDA(cudaStreamSynchronize(s));
+  });
+  return st != SEM_OK ? st : result;
+}
+
+}  // extern "C"

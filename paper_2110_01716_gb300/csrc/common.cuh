@@ -1,0 +1,205 @@
+// common.cuh -- internal declarations shared by the library's translation units.
+//
+// Nothing here is part of the C ABI (include/sem.h).  Errors inside the library
+// are raised as sem::Failure and turned into a sem_status at the ABI boundary.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <string>
+#include <vector>
+
+#include "sem.h"
+
+namespace sem {
+
+// ------------------------------------------------------------------ errors
+struct Failure {
+  sem_status status;
+};
+[[noreturn]] void fail(sem_status st, const char *fmt, ...);
+void set_error_message(const char *msg);
+
+#define SEM_CHECK_CUDA(call)                                                              \
+  do {                                                                                    \
+    cudaError_t err_ = (call);                                                            \
+    if (err_ != cudaSuccess)                                                              \
+      ::sem::fail(err_ == cudaErrorMemoryAllocation ? SEM_ENOMEM : SEM_ECUDA, "%s:%d: %s: %s", \
+                  __FILE__, __LINE__, #call, cudaGetErrorString(err_));                   \
+  } while (0)
+
+#define SEM_REQUIRE(cond, ...)                       \
+  do {                                               \
+    if (!(cond)) ::sem::fail(SEM_EINVAL, __VA_ARGS__); \
+  } while (0)
+
+// Device allocation owned by a library object; freed in the destructor.
+template <typename T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) return;
+    SEM_CHECK_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    n = count;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+};
+
+// ------------------------------------------------------------------ fast division
+// Division of non-negative 32-bit integers below 2^31 by a runtime constant d
+// with one high multiply (Granlund and Montgomery, PLDI 1994):
+//   s = ceil(log2 d),  m = floor(2^32 (2^s - d) / d) + 1,
+//   n / d = (umulhi(n, m) + n) >> s.
+struct FastDiv {
+  uint32_t d = 1, m = 0, s = 0;
+  FastDiv() = default;
+  explicit FastDiv(uint32_t div) : d(div) {
+    s = 0;
+    while ((1ull << s) < div) ++s;
+    m = (uint32_t)((((1ull << s) - div) << 32) / div + 1);
+  }
+  __host__ __device__ __forceinline__ uint32_t div(uint32_t n) const {
+#ifdef __CUDA_ARCH__
+    return (__umulhi(n, m) + n) >> s;
+#else
+    return (uint32_t)((((uint64_t)n * m >> 32) + n) >> s);
+#endif
+  }
+};
+
+// ------------------------------------------------------------------ topology
+// Structural description of a box mesh of order N.  Every quantity that
+// depends only on where a local point sits (multiplicity, Dirichlet mask,
+// copies of a shared node) is computed from indices on the fly, so no
+// per-point integer arrays live in HBM.
+struct Topo {
+  int32_t ex, ey, ez, N, Np, Np3;
+  int32_t bc;        // SEM_DIRICHLET / SEM_NEUMANN
+  int64_t E, nl, ng; // elements, local points, unique nodes
+  FastDiv div_np3, div_np, div_ex, div_ey;
+};
+
+// Six face bits of a point inside its element and of an element inside the box:
+// bit 0: -r face (i = 0 / ix = 0), 1: +r, 2: -s, 3: +s, 4: -t, 5: +t.
+__device__ __forceinline__ uint32_t point_face_bits(int i, int j, int k, int N) {
+  return (i == 0) | ((i == N) << 1) | ((j == 0) << 2) | ((j == N) << 3) | ((k == 0) << 4) |
+         ((k == N) << 5);
+}
+__device__ __forceinline__ uint32_t elem_face_bits(int ix, int iy, int iz, const Topo &t) {
+  return (ix == 0) | ((ix == t.ex - 1) << 1) | ((iy == 0) << 2) | ((iy == t.ey - 1) << 3) |
+         ((iz == 0) << 4) | ((iz == t.ez - 1) << 5);
+}
+
+struct PointInfo {
+  uint32_t e, p;         // element, point in element
+  int i, j, k;           // point indices
+  int ix, iy, iz;        // element indices
+  float inv_mult;        // 1 / number of copies (exact: 1, 1/2, 1/4, 1/8)
+  float mask;            // 0 on the Dirichlet boundary, else 1
+};
+
+__device__ __forceinline__ PointInfo point_info(uint32_t l, const Topo &t) {
+  PointInfo q;
+  q.e = t.div_np3.div(l);
+  q.p = l - q.e * (uint32_t)t.Np3;
+  uint32_t jk = t.div_np.div(q.p);
+  q.i = (int)(q.p - jk * (uint32_t)t.Np);
+  q.k = (int)t.div_np.div(jk);
+  q.j = (int)(jk - (uint32_t)q.k * t.Np);
+  uint32_t yz = t.div_ex.div(q.e);
+  q.ix = (int)(q.e - yz * (uint32_t)t.ex);
+  q.iz = (int)t.div_ey.div(yz);
+  q.iy = (int)(yz - (uint32_t)q.iz * t.ey);
+  uint32_t pf = point_face_bits(q.i, q.j, q.k, t.N);
+  uint32_t ef = elem_face_bits(q.ix, q.iy, q.iz, t);
+  q.inv_mult = 1.0f / (float)(1u << __popc(pf & ~ef));
+  q.mask = (t.bc == SEM_DIRICHLET && (pf & ef)) ? 0.0f : 1.0f;
+  return q;
+}
+
+// ------------------------------------------------------------------ basis tables
+constexpr int kMaxNp = SEM_MAX_ORDER + 1;
+
+// GLL nodes, weights and derivative matrix of one order (Sec. 2, footnote 1),
+// small enough to travel to kernels as a parameter.
+struct Basis {
+  int N;
+  double xi[kMaxNp];
+  double w[kMaxNp];
+  double D[kMaxNp * kMaxNp];  // D[i*Np + l] = h_l'(xi_i)
+  float D32[kMaxNp * kMaxNp];
+};
+Basis make_basis(int N);
+
+// ------------------------------------------------------------------ levels
+// One discretisation of the box at order N: geometry, numbering and the
+// Jacobi diagonal, in the precisions its users need.
+struct Level {
+  Topo t{};
+  Basis basis{};
+  int32_t geom = SEM_GEOM_STORED;
+  std::vector<double> verts_host;  // lattice [(ex+1)(ey+1)(ez+1)][3]
+  DevBuf<double> verts;            // per element [E][8][3], corner (a,b,c) at a+2b+4c
+  DevBuf<double> G64;              // [E][6][Np3]  (rr, rs, rt, ss, st, tt)
+  DevBuf<float> G32;               // [E][6][Np3]
+  DevBuf<int32_t> shared_nodes;    // unique ids of nodes with more than one copy
+  int64_t n_shared = 0;
+  DevBuf<double> dinv64;           // mask / assembled diagonal
+  DevBuf<float> dinv32;
+  size_t device_bytes() const {
+    return verts.bytes() + G64.bytes() + G32.bytes() + shared_nodes.bytes() + dinv64.bytes() +
+           dinv32.bytes();
+  }
+};
+
+// ------------------------------------------------------------------ basis (host)
+void gll_points(int N, double *xi, double *w);
+void derivative_matrix(int N, const double *xi, double *D);
+void interpolation_matrix(int Nf, int Nc, double *J);
+
+// ------------------------------------------------------------------ launches
+void build_level(Level &L, int ex, int ey, int ez, int N, int bc, int geom,
+                 const double *verts_host, bool want_g32, cudaStream_t st);
+void level_ensure_f32(Level &L, cudaStream_t st);
+
+template <typename T>
+void launch_ax(const Level &L, const T *u, T *w, cudaStream_t st);
+template <typename T>
+void launch_gs(const Level &L, T *u, cudaStream_t st);
+template <typename T>
+void launch_mask(const Level &L, T *u, cudaStream_t st);
+void launch_field(const Level &L, int which, double *out, cudaStream_t st);
+
+// Deterministic reductions into device scalars (see vec.cu).
+struct Reducer {
+  DevBuf<double> partials;  // [nblocks][nsums]
+  DevBuf<unsigned int> counter;
+  int nblocks = 0;
+  void init(int blocks, int max_sums);
+};
+
+}  // namespace sem
+
+// Opaque handles of the ABI.
+struct sem_mesh {
+  sem::Level fine;
+  cudaStream_t stream = nullptr;
+  sem::Reducer red;
+  sem::DevBuf<double> scal;   // device scalars of the solvers
+  sem::DevBuf<double> work;   // solver work vectors
+  sem::DevBuf<double> host_b, host_x;  // device copies for sem_solve_host
+  double *pinned = nullptr;   // host-pinned scalars
+};

@@ -1,0 +1,136 @@
+// gs.cu -- direct stiffness summation and Dirichlet masking on the box.
+//
+// Sec. 2: C0 continuity makes the SEM exchange a unit-depth stencil: a node
+// on an element face, edge or vertex has 2, 4 or 8 local copies, and the
+// gather-scatter (gs) replaces every copy by the sum of all copies.  Sec. 3
+// builds that exchange from global vertex ids; on the box the ids are the
+// lattice coordinates, so each thread takes one shared node from a table of
+// unique ids and finds its copies arithmetically (no CSR index arrays).
+// Copies are summed in a fixed order (x fastest, lower element first), so all
+// copies end bit-identical and the result does not depend on scheduling.
+#include "common.cuh"
+
+namespace sem {
+
+struct GsGeom {
+  Topo t;
+  FastDiv div_nx, div_nxy, div_N;
+  uint32_t nx, nxy;
+};
+
+static GsGeom gs_geom(const Topo &t) {
+  GsGeom g;
+  g.t = t;
+  g.nx = (uint32_t)(t.ex * t.N + 1);
+  g.nxy = g.nx * (uint32_t)(t.ey * t.N + 1);
+  g.div_nx = FastDiv(g.nx);
+  g.div_nxy = FastDiv(g.nxy);
+  g.div_N = FastDiv((uint32_t)t.N);
+  return g;
+}
+
+// Copies of lattice coordinate c along one direction with ne elements:
+// (element index, local index) pairs, lower element first.
+__device__ __forceinline__ int copies_1d(uint32_t c, int ne, int N, const FastDiv &dN, int *el,
+                                         int *lo) {
+  int q = (int)dN.div(c);
+  int r = (int)c - q * N;
+  if (r == 0 && q > 0 && q < ne) {
+    el[0] = q - 1; lo[0] = N;
+    el[1] = q;     lo[1] = 0;
+    return 2;
+  }
+  if (q == ne) { el[0] = ne - 1; lo[0] = N; return 1; }
+  el[0] = q; lo[0] = r;
+  return 1;
+}
+
+template <typename T>
+__global__ void gs_kernel(GsGeom g, const int32_t *__restrict__ nodes, int64_t nsh,
+                          T *__restrict__ u) {
+  const Topo &t = g.t;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nsh;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t id = (uint32_t)nodes[s];
+    uint32_t gz = g.div_nxy.div(id);
+    uint32_t rem = id - gz * g.nxy;
+    uint32_t gy = g.div_nx.div(rem);
+    uint32_t gx = rem - gy * g.nx;
+    int ex_[2], ix_[2], ey_[2], iy_[2], ez_[2], iz_[2];
+    int cx = copies_1d(gx, t.ex, t.N, g.div_N, ex_, ix_);
+    int cy = copies_1d(gy, t.ey, t.N, g.div_N, ey_, iy_);
+    int cz = copies_1d(gz, t.ez, t.N, g.div_N, ez_, iz_);
+    size_t idx[8];
+    int n = 0;
+    for (int c = 0; c < cz; ++c)
+      for (int b = 0; b < cy; ++b)
+        for (int a = 0; a < cx; ++a) {
+          size_t e = (size_t)ex_[a] + (size_t)t.ex * ((size_t)ey_[b] + (size_t)t.ey * ez_[c]);
+          idx[n++] = e * t.Np3 + ix_[a] + t.Np * (iy_[b] + t.Np * iz_[c]);
+        }
+    T sum = u[idx[0]];
+    for (int q = 1; q < n; ++q) sum += u[idx[q]];
+    for (int q = 0; q < n; ++q) u[idx[q]] = sum;
+  }
+}
+
+// Zero the Dirichlet boundary: the points of element faces lying on the box
+// boundary.  One thread per (boundary face, face point).
+template <typename T>
+__global__ void mask_faces_kernel(Topo t, int64_t nfaces, T *__restrict__ u) {
+  const int Np = t.Np, Np2 = Np * Np;
+  const int64_t fx = (int64_t)t.ey * t.ez, fy = (int64_t)t.ex * t.ez;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nfaces * Np2;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    int64_t f = s / Np2;
+    int q = (int)(s - f * Np2);
+    int a = q % Np, b = q / Np;
+    int ix, iy, iz, i, j, k;
+    int side = (int)(f & 1);
+    int64_t h = f >> 1;
+    if (h < fx) {  // x = 0 or x = 1 faces
+      iy = (int)(h % t.ey); iz = (int)(h / t.ey);
+      ix = side ? t.ex - 1 : 0; i = side ? t.N : 0; j = a; k = b;
+    } else if (h < fx + fy) {
+      h -= fx;
+      ix = (int)(h % t.ex); iz = (int)(h / t.ex);
+      iy = side ? t.ey - 1 : 0; j = side ? t.N : 0; i = a; k = b;
+    } else {
+      h -= fx + fy;
+      ix = (int)(h % t.ex); iy = (int)(h / t.ex);
+      iz = side ? t.ez - 1 : 0; k = side ? t.N : 0; i = a; j = b;
+    }
+    size_t e = (size_t)ix + (size_t)t.ex * ((size_t)iy + (size_t)t.ey * iz);
+    u[e * t.Np3 + i + Np * (j + Np * k)] = T(0);
+  }
+}
+
+static int grid_1d(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  const int64_t cap = 152 * 8;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <typename T>
+void launch_gs(const Level &L, T *u, cudaStream_t st) {
+  if (L.n_shared == 0) return;
+  gs_kernel<T><<<grid_1d(L.n_shared, 256), 256, 0, st>>>(gs_geom(L.t), L.shared_nodes.p,
+                                                          L.n_shared, u);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_mask(const Level &L, T *u, cudaStream_t st) {
+  if (L.t.bc != SEM_DIRICHLET) return;
+  const Topo &t = L.t;
+  int64_t nfaces = 2 * ((int64_t)t.ey * t.ez + (int64_t)t.ex * t.ez + (int64_t)t.ex * t.ey);
+  mask_faces_kernel<T><<<grid_1d(nfaces * t.Np * t.Np, 256), 256, 0, st>>>(t, nfaces, u);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+template void launch_gs<double>(const Level &, double *, cudaStream_t);
+template void launch_gs<float>(const Level &, float *, cudaStream_t);
+template void launch_mask<double>(const Level &, double *, cudaStream_t);
+template void launch_mask<float>(const Level &, float *, cudaStream_t);
+
+}  // namespace sem

@@ -1,0 +1,42 @@
+// kernels.cuh -- launchers of the vector, smoother and transfer kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace sem {
+
+constexpr int kVecThreads = 256;
+constexpr int kVecMaxBlocks = 152 * 8;  // grid of every reduction (fixed per size)
+
+int vec_grid(int64_t n);
+
+void launch_dot(const Topo &t, Reducer &R, const double *u, const double *v, double *out,
+                cudaStream_t st);
+void launch_dot_skip(const Topo &t, Reducer &R, const double *u, const double *v, double *out,
+                     const int *skip, cudaStream_t st);
+void launch_sum(const Topo &t, Reducer &R, const double *u, double *out, cudaStream_t st);
+void launch_remove_mean(const Topo &t, Reducer &R, double *u, double *scratch, cudaStream_t st);
+void launch_cg_start(const Topo &t, Reducer &R, const double *b, const double *w,
+                     const double *dinv, double *r, double *z, double *p, double *bb, double *rr,
+                     double *rz, cudaStream_t st);
+void launch_cg_update(const Topo &t, Reducer &R, const double *rho, const double *pw,
+                      const double *p, const double *w, const double *dinv, double *x, double *r,
+                      double *z, double *rr, double *rz, const int *skip, cudaStream_t st);
+void launch_cg_direction(int64_t n, const double *num, const double *den, double sign,
+                         const double *z, double *p, const int *skip, cudaStream_t st);
+void launch_flex_dots(const Topo &t, Reducer &R, const double *z, const double *r,
+                      const double *w, double *zr, double *zw, cudaStream_t st);
+void launch_stop_test(const double *rr, const double *bb, double tol2, int it, int maxit,
+                      int *skip, int *iters, cudaStream_t st);
+template <typename A, typename B>
+void launch_convert(int64_t n, const A *a, B *b, cudaStream_t st);
+
+// Assembled operator on a level: w = mask * gs(A_L u).
+template <typename T>
+inline void apply_assembled(const Level &L, const T *u, T *w, cudaStream_t st) {
+  launch_ax<T>(L, u, w, st);
+  launch_gs<T>(L, w, st);
+  launch_mask<T>(L, w, st);
+}
+
+}  // namespace sem

@@ -1,0 +1,440 @@
+// pmg.cu -- p-multigrid preconditioner (Sec. 3, pMG paragraph).
+//
+// Levels of decreasing polynomial order on the same trilinear geometry;
+// coarse-to-fine interpolation u_f = (J x J x J) u_c with one 1D matrix J per
+// level pair; restriction is its transpose on unique dofs,
+// r_c = mask_c gs_c((J^T x J^T x J^T)(r_f / mult_f)); Chebyshev-accelerated
+// point-Jacobi smoothing in FP64 or FP32 (the paper runs all of pMG in 32-bit);
+// the coarsest level is solved by FP64 Jacobi-PCG on the device (the paper
+// used an algebraic multigrid on the host there).  One V-cycle: pre-smooth
+// from zero, residual, restrict, recurse, prolong and correct, post-smooth.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "pmg.cuh"
+
+namespace sem {
+
+// ------------------------------------------------------------------ Chebyshev
+// Start of a Chebyshev smoothing: r = b - w (w = A x assembled, or r = b when
+// w is null and x = 0), d = dinv r / theta, x = d (x_zero) or x += d.
+template <typename T>
+__global__ void cheb_start_kernel(int64_t n, const T *__restrict__ b, const T *__restrict__ w,
+                                  const T *__restrict__ dinv, T *__restrict__ r, T *__restrict__ d,
+                                  T *__restrict__ x, T inv_theta, int x_zero) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    T rl = w ? b[l] - w[l] : b[l];
+    r[l] = rl;
+    T dl = dinv[l] * rl * inv_theta;
+    d[l] = dl;
+    x[l] = x_zero ? dl : x[l] + dl;
+  }
+}
+
+// One Chebyshev step after w = A d (assembled):
+// r -= w;  d = c1 d + c2 dinv r;  x += d.
+template <typename T>
+__global__ void cheb_step_kernel(int64_t n, const T *__restrict__ w, const T *__restrict__ dinv,
+                                 T *__restrict__ r, T *__restrict__ d, T *__restrict__ x, T c1,
+                                 T c2) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    T rl = r[l] - w[l];
+    r[l] = rl;
+    T dl = c1 * d[l] + c2 * dinv[l] * rl;
+    d[l] = dl;
+    x[l] += dl;
+  }
+}
+
+// ------------------------------------------------------------------ transfers
+struct TransferParams {
+  Topo tf;      // fine level
+  int npf, npc; // points per direction
+  double J[kMaxNp * kMaxNp];  // J[i*npc + a]: coarse basis a at fine node i
+};
+
+// Restriction of the fine residual b - w, weighted by 1/mult, to unassembled
+// coarse values: out_e = (J^T x J^T x J^T) ((b - w)/mult)_e.  One CTA per element.
+template <typename Tf, typename Tc>
+__global__ void restrict_kernel(TransferParams tp, const Tf *__restrict__ b,
+                                const Tf *__restrict__ w, Tc *__restrict__ out) {
+  extern __shared__ double sm[];
+  const int nf = tp.npf, nc = tp.npc;
+  const int nf3 = nf * nf * nf;
+  double *s0 = sm;                    // nf^3
+  double *s1 = s0 + nf3;              // nc nf nf
+  double *s2 = s1 + nc * nf * nf;     // nc nc nf
+  for (int64_t e = blockIdx.x; e < tp.tf.E; e += gridDim.x) {
+    for (int q = threadIdx.x; q < nf3; q += blockDim.x) {
+      uint32_t l = (uint32_t)(e * nf3 + q);
+      PointInfo pi = point_info(l, tp.tf);
+      s0[q] = ((double)b[l] - (double)w[l]) * (double)pi.inv_mult;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc * nf * nf; q += blockDim.x) {
+      int a = q % nc, jk = q / nc;
+      double s = 0.0;
+      for (int i = 0; i < nf; ++i) s += tp.J[i * nc + a] * s0[i + nf * jk];
+      s1[q] = s;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc * nc * nf; q += blockDim.x) {
+      int a = q % nc, bk = q / nc, bb = bk % nc, k = bk / nc;
+      double s = 0.0;
+      for (int j = 0; j < nf; ++j) s += tp.J[j * nc + bb] * s1[a + nc * (j + nf * k)];
+      s2[q] = s;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc * nc * nc; q += blockDim.x) {
+      int ab = q % (nc * nc), c = q / (nc * nc);
+      double s = 0.0;
+      for (int k = 0; k < nf; ++k) s += tp.J[k * nc + c] * s2[ab + nc * nc * k];
+      out[e * nc * nc * nc + q] = (Tc)s;
+    }
+    __syncthreads();
+  }
+}
+
+// Prolongation and correction: x_f += (J x J x J) x_c.  One CTA per element.
+template <typename Tc, typename Tf>
+__global__ void prolong_kernel(TransferParams tp, const Tc *__restrict__ xc, Tf *__restrict__ xf) {
+  extern __shared__ double sm[];
+  const int nf = tp.npf, nc = tp.npc;
+  const int nc3 = nc * nc * nc, nf3 = nf * nf * nf;
+  double *s0 = sm;                // nc^3
+  double *s1 = s0 + nc3;          // nf nc nc
+  double *s2 = s1 + nf * nc * nc; // nf nf nc
+  for (int64_t e = blockIdx.x; e < tp.tf.E; e += gridDim.x) {
+    for (int q = threadIdx.x; q < nc3; q += blockDim.x) s0[q] = (double)xc[e * nc3 + q];
+    __syncthreads();
+    for (int q = threadIdx.x; q < nf * nc * nc; q += blockDim.x) {
+      int i = q % nf, bc = q / nf;
+      double s = 0.0;
+      for (int a = 0; a < nc; ++a) s += tp.J[i * nc + a] * s0[a + nc * bc];
+      s1[q] = s;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nf * nf * nc; q += blockDim.x) {
+      int i = q % nf, jc = q / nf, j = jc % nf, c = jc / nf;
+      double s = 0.0;
+      for (int b = 0; b < nc; ++b) s += tp.J[j * nc + b] * s1[i + nf * (b + nc * c)];
+      s2[q] = s;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nf3; q += blockDim.x) {
+      int ij = q % (nf * nf), k = q / (nf * nf);
+      double s = 0.0;
+      for (int c = 0; c < nc; ++c) s += tp.J[k * nc + c] * s2[ij + nf * nf * c];
+      xf[e * nf3 + q] = (Tf)((double)xf[e * nf3 + q] + s);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ Lanczos start vector
+// splitmix64 (Steele, Lea and Flood 2014) keyed by the node's unique id:
+// v = 2 u - 1 with u the top 53 bits times 2^-53; masked.
+__global__ void random_start_kernel(Topo t, uint64_t seed, double *__restrict__ v) {
+  const uint64_t nx = (uint64_t)t.ex * t.N + 1, ny = (uint64_t)t.ey * t.N + 1;
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
+       l += gridDim.x * blockDim.x) {
+    PointInfo q = point_info(l, t);
+    uint64_t gx = (uint64_t)q.ix * t.N + q.i, gy = (uint64_t)q.iy * t.N + q.j,
+             gz = (uint64_t)q.iz * t.N + q.k;
+    uint64_t id = gx + nx * (gy + ny * gz);
+    uint64_t z = seed + (id + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    v[l] = (2.0 * u - 1.0) * (double)q.mask;
+  }
+}
+
+// Largest eigenvalue of the symmetric tridiagonal (diag a, off-diagonal b) by
+// bisection: the number of negative pivots of the LDL^T factorisation of
+// T - mu I counts the eigenvalues below mu (Sylvester's law of inertia).
+static double tridiag_lambda_max(const std::vector<double> &a, const std::vector<double> &b) {
+  const int m = (int)a.size();
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < m; ++i) {
+    double rad = 0.0;
+    if (i > 0) rad += std::fabs(b[i - 1]);
+    if (i + 1 < m) rad += std::fabs(b[i]);
+    lo = std::min(lo, a[i] - rad);
+    hi = std::max(hi, a[i] + rad);
+  }
+  auto below = [&](double mu) {
+    int neg = 0;
+    double piv = a[0] - mu;
+    if (piv < 0) ++neg;
+    for (int i = 1; i < m; ++i) {
+      if (piv == 0.0) piv = 1e-300;
+      piv = (a[i] - mu) - b[i - 1] * b[i - 1] / piv;
+      if (piv < 0) ++neg;
+    }
+    return neg;
+  };
+  for (int it = 0; it < 300 && hi - lo > 1e-15 * std::fabs(hi); ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (below(mid) == m) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+// lambda_max(D^-1 A) from the Lanczos tridiagonal of m steps of Jacobi-PCG on
+// A y = v (alpha_j, beta_j give T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+// T_j,j+1 = sqrt(beta_j)/alpha_j).
+static double lanczos_lambda_max(Level &L, Reducer &R, int m, uint64_t seed, cudaStream_t st) {
+  const Topo &t = L.t;
+  DevBuf<double> v, r, z, p, w, x, sc;
+  v.alloc(t.nl); r.alloc(t.nl); z.alloc(t.nl); p.alloc(t.nl); w.alloc(t.nl); x.alloc(t.nl);
+  sc.alloc(8);
+  random_start_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, seed, v.p);
+  SEM_CHECK_CUDA(cudaGetLastError());
+  if (t.bc == SEM_NEUMANN) launch_remove_mean(t, R, v.p, sc.p + 7, st);
+  SEM_CHECK_CUDA(cudaMemsetAsync(x.p, 0, t.nl * sizeof(double), st));
+  // slots: 0 bb, 1 rr, 2 rho_a, 3 rho_b, 4 pw
+  launch_cg_start(t, R, v.p, nullptr, L.dinv64.p, r.p, z.p, p.p, sc.p + 0, sc.p + 1, sc.p + 2, st);
+  std::vector<double> alpha, beta;
+  double h[8];
+  SEM_CHECK_CUDA(cudaMemcpyAsync(h, sc.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+  double rho0 = h[2], rho = h[2];
+  for (int j = 0; j < m; ++j) {
+    int cur = 2 + (j & 1), nxt = 2 + ((j + 1) & 1);
+    apply_assembled<double>(L, p.p, w.p, st);
+    launch_dot(t, R, p.p, w.p, sc.p + 4, st);
+    launch_cg_update(t, R, sc.p + cur, sc.p + 4, p.p, w.p, L.dinv64.p, x.p, r.p, z.p, sc.p + 1,
+                     sc.p + nxt, nullptr, st);
+    SEM_CHECK_CUDA(cudaMemcpyAsync(h, sc.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+    double pw = h[4], rho1 = h[nxt];
+    double a = rho / pw, bta = rho1 / rho;
+    alpha.push_back(a);
+    beta.push_back(bta);
+    rho = rho1;
+    if (!(rho1 > 1e-28 * rho0)) break;
+    launch_cg_direction(t.nl, sc.p + nxt, sc.p + cur, 1.0, z.p, p.p, nullptr, st);
+  }
+  const int k = (int)alpha.size();
+  std::vector<double> ta(k), tb(k > 1 ? k - 1 : 0);
+  for (int j = 0; j < k; ++j) {
+    ta[j] = 1.0 / alpha[j] + (j > 0 ? beta[j - 1] / alpha[j - 1] : 0.0);
+    if (j + 1 < k) tb[j] = std::sqrt(beta[j]) / alpha[j];
+  }
+  return tridiag_lambda_max(ta, tb);
+}
+
+// ------------------------------------------------------------------ setup
+static int grid_elems(int64_t E) { return (int)std::min<int64_t>(E, 152 * 16); }
+
+template <typename T>
+static T *vec_of(PmgLevel &P, int which) {
+  if constexpr (sizeof(T) == 8) return P.v64[which].p;
+  else return P.v32[which].p;
+}
+
+void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t st) {
+  SEM_REQUIRE(d.nlevels >= 1 && d.nlevels <= 8, "nlevels=%d outside [1,8]", d.nlevels);
+  SEM_REQUIRE(d.orders[0] == mesh->fine.t.N, "orders[0]=%d differs from the mesh order %d",
+              d.orders[0], mesh->fine.t.N);
+  for (int l = 1; l < d.nlevels; ++l)
+    SEM_REQUIRE(d.orders[l] >= 1 && d.orders[l] < d.orders[l - 1],
+                "orders must be strictly decreasing and >= 1");
+  SEM_REQUIRE(d.cheb_degree >= 1 && d.cheb_degree <= 16, "cheb_degree=%d outside [1,16]",
+              d.cheb_degree);
+  SEM_REQUIRE(d.lanczos_steps >= 2 && d.lanczos_steps <= 200, "lanczos_steps outside [2,200]");
+  SEM_REQUIRE(d.smoother_dtype == SEM_F64 || d.smoother_dtype == SEM_F32,
+              "smoother_dtype must be SEM_F64 or SEM_F32");
+  SEM_REQUIRE(d.coarse_maxit >= 0 && d.coarse_maxit <= 100000, "coarse_maxit out of range");
+  P->mesh = mesh;
+  P->desc = d;
+  const Level &F = mesh->fine;
+  P->red.init(kVecMaxBlocks, 4);
+  P->scal.alloc(32);
+  P->flags.alloc(4);
+  P->levp.clear();
+  for (int l = 0; l < d.nlevels; ++l) P->levp.emplace_back(new PmgLevel());
+  for (int l = 0; l < d.nlevels; ++l) {
+    PmgLevel &Q = *P->levp[l];
+    const bool coarsest = (l == d.nlevels - 1);
+    Q.dtype = coarsest ? SEM_F64 : d.smoother_dtype;
+    if (l == 0) {
+      Q.L = &mesh->fine;
+    } else {
+      Q.own.reset(new Level());
+      build_level(*Q.own, F.t.ex, F.t.ey, F.t.ez, d.orders[l], F.t.bc, SEM_GEOM_STORED,
+                  F.verts_host.data(), Q.dtype == SEM_F32, st);
+      Q.L = Q.own.get();
+    }
+    if (Q.dtype == SEM_F32) level_ensure_f32(*Q.L, st);
+    const int64_t n = Q.L->t.nl;
+    // vectors: 0 b, 1 x, 2 r, 3 d, 4 w
+    for (int v = 0; v < 5; ++v) {
+      if (Q.dtype == SEM_F32) Q.v32[v].alloc(n);
+      else Q.v64[v].alloc(n);
+    }
+    if (!coarsest) {
+      double est = lanczos_lambda_max(*Q.L, P->red, d.lanczos_steps, d.seed, st);
+      Q.lam_hi = 1.1 * est;
+      Q.lam_lo = Q.lam_hi / 10.0;
+      Q.J.resize((size_t)(d.orders[l] + 1) * (d.orders[l + 1] + 1));
+      interpolation_matrix(d.orders[l], d.orders[l + 1], Q.J.data());
+    }
+  }
+  // coarse-solve Krylov vectors (FP64)
+  const int64_t nc = (*P->levp.back()).L->t.nl;
+  P->cz.alloc(nc); P->cp.alloc(nc); P->cw.alloc(nc);
+  P->z64.alloc(F.t.nl);
+  SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------------------ V-cycle
+template <typename T>
+static void smooth(sem_pmg *P, int l, bool x_zero, cudaStream_t st) {
+  PmgLevel &Q = (*P->levp[l]);
+  const Level &L = *Q.L;
+  const int64_t n = L.t.nl;
+  T *b = vec_of<T>(Q, 0), *x = vec_of<T>(Q, 1), *r = vec_of<T>(Q, 2), *d = vec_of<T>(Q, 3),
+    *w = vec_of<T>(Q, 4);
+  const T *dinv;
+  if constexpr (sizeof(T) == 8) dinv = L.dinv64.p;
+  else dinv = L.dinv32.p;
+  const double theta = 0.5 * (Q.lam_hi + Q.lam_lo), delta = 0.5 * (Q.lam_hi - Q.lam_lo);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  if (!x_zero) apply_assembled<T>(L, x, w, st);
+  cheb_start_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(n, b, x_zero ? nullptr : w, dinv, r,
+                                                            d, x, (T)(1.0 / theta), x_zero);
+  SEM_CHECK_CUDA(cudaGetLastError());
+  for (int it = 2; it <= P->desc.cheb_degree; ++it) {
+    apply_assembled<T>(L, d, w, st);
+    double rho1 = 1.0 / (2.0 * sigma - rho);
+    cheb_step_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(n, w, dinv, r, d, x,
+                                                             (T)(rho1 * rho), (T)(2.0 * rho1 / delta));
+    SEM_CHECK_CUDA(cudaGetLastError());
+    rho = rho1;
+  }
+}
+
+static TransferParams transfer_params(const PmgLevel &F, const PmgLevel &C) {
+  TransferParams tp;
+  std::memset(&tp, 0, sizeof(tp));
+  tp.tf = F.L->t;
+  tp.npf = F.L->t.Np;
+  tp.npc = C.L->t.Np;
+  std::copy(F.J.begin(), F.J.end(), tp.J);
+  return tp;
+}
+
+template <typename Tf, typename Tc>
+static void restrict_to(sem_pmg *P, int l, cudaStream_t st) {
+  PmgLevel &F = (*P->levp[l]), &C = (*P->levp[l + 1]);
+  TransferParams tp = transfer_params(F, C);
+  size_t shm = sizeof(double) * ((size_t)tp.npf * tp.npf * tp.npf + (size_t)tp.npc * tp.npf * tp.npf +
+                                 (size_t)tp.npc * tp.npc * tp.npf);
+  restrict_kernel<Tf, Tc><<<grid_elems(tp.tf.E), 128, shm, st>>>(tp, vec_of<Tf>(F, 0),
+                                                                  vec_of<Tf>(F, 4), vec_of<Tc>(C, 0));
+  SEM_CHECK_CUDA(cudaGetLastError());
+  launch_gs<Tc>(*C.L, vec_of<Tc>(C, 0), st);
+  launch_mask<Tc>(*C.L, vec_of<Tc>(C, 0), st);
+}
+
+template <typename Tc, typename Tf>
+static void prolong_from(sem_pmg *P, int l, cudaStream_t st) {
+  PmgLevel &F = (*P->levp[l]), &C = (*P->levp[l + 1]);
+  TransferParams tp = transfer_params(F, C);
+  size_t shm = sizeof(double) * ((size_t)tp.npc * tp.npc * tp.npc + (size_t)tp.npf * tp.npc * tp.npc +
+                                 (size_t)tp.npf * tp.npf * tp.npc);
+  prolong_kernel<Tc, Tf><<<grid_elems(tp.tf.E), 128, shm, st>>>(tp, vec_of<Tc>(C, 1),
+                                                                 vec_of<Tf>(F, 1));
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+// Coarsest level: FP64 Jacobi-PCG from zero with a device-side stopping test,
+// so the launch sequence is fixed (capturable) and no host round trip occurs.
+static void coarse_solve(sem_pmg *P, cudaStream_t st) {
+  PmgLevel &Q = (*P->levp.back());
+  Level &L = *Q.L;
+  const Topo &t = L.t;
+  double *b = Q.v64[0].p, *x = Q.v64[1].p, *r = Q.v64[2].p;
+  double *z = P->cz.p, *p = P->cp.p, *w = P->cw.p;
+  double *sc = P->scal.p;  // 0 bb, 1 rr, 2/3 rho, 4 pw, 5 mean scratch
+  int *skip = P->flags.p, *iters = P->flags.p + 1;
+  if (t.bc == SEM_NEUMANN) launch_remove_mean(t, P->red, b, sc + 5, st);
+  SEM_CHECK_CUDA(cudaMemsetAsync(x, 0, t.nl * sizeof(double), st));
+  SEM_CHECK_CUDA(cudaMemsetAsync(skip, 0, 2 * sizeof(int), st));
+  launch_cg_start(t, P->red, b, nullptr, L.dinv64.p, r, z, p, sc + 0, sc + 1, sc + 2, st);
+  const double tol = P->desc.coarse_tol;
+  const double tol2 = tol > 0 ? tol * tol : 0.0;
+  const int maxit = P->desc.coarse_maxit;
+  launch_stop_test(sc + 1, sc + 0, tol2, 0, maxit, skip, iters, st);
+  for (int it = 1; it <= maxit; ++it) {
+    const int cur = 2 + ((it - 1) & 1), nxt = 2 + (it & 1);
+    launch_ax<double>(L, p, w, st);
+    launch_gs<double>(L, w, st);
+    launch_mask<double>(L, w, st);
+    launch_dot_skip(t, P->red, p, w, sc + 4, skip, st);
+    launch_cg_update(t, P->red, sc + cur, sc + 4, p, w, L.dinv64.p, x, r, z, sc + 1, sc + nxt, skip,
+                     st);
+    launch_stop_test(sc + 1, sc + 0, tol2, it, maxit, skip, iters, st);
+    launch_cg_direction(t.nl, sc + nxt, sc + cur, 1.0, z, p, skip, st);
+  }
+}
+
+template <typename T, typename Tn>
+static void vcycle_level(sem_pmg *P, int l, cudaStream_t st);
+
+template <typename T>
+static void vcycle_dispatch(sem_pmg *P, int l, cudaStream_t st) {
+  const int last = (int)P->levp.size() - 1;
+  if (l == last) {
+    coarse_solve(P, st);
+    return;
+  }
+  if ((*P->levp[l + 1]).dtype == SEM_F32) vcycle_level<T, float>(P, l, st);
+  else vcycle_level<T, double>(P, l, st);
+}
+
+template <typename T, typename Tn>
+static void vcycle_level(sem_pmg *P, int l, cudaStream_t st) {
+  PmgLevel &Q = (*P->levp[l]);
+  const Level &L = *Q.L;
+  smooth<T>(P, l, true, st);
+  // residual w = A x (assembled); the restriction forms (b - w) / mult
+  apply_assembled<T>(L, vec_of<T>(Q, 1), vec_of<T>(Q, 4), st);
+  restrict_to<T, Tn>(P, l, st);
+  vcycle_dispatch<Tn>(P, l + 1, st);
+  prolong_from<Tn, T>(P, l, st);
+  smooth<T>(P, l, false, st);
+}
+
+void pmg_vcycle(sem_pmg *P, const double *r, double *z, cudaStream_t st) {
+  PmgLevel &Q = (*P->levp[0]);
+  const int64_t n = Q.L->t.nl;
+  if (P->levp.size() == 1) {
+    // a single level: the coarse solver itself
+    launch_convert<double, double>(n, r, Q.v64[0].p, st);
+    coarse_solve(P, st);
+    launch_convert<double, double>(n, Q.v64[1].p, z, st);
+    return;
+  }
+  if (Q.dtype == SEM_F32) {
+    launch_convert<double, float>(n, r, Q.v32[0].p, st);
+    vcycle_dispatch<float>(P, 0, st);
+    launch_convert<float, double>(n, Q.v32[1].p, z, st);
+  } else {
+    launch_convert<double, double>(n, r, Q.v64[0].p, st);
+    vcycle_dispatch<double>(P, 0, st);
+    launch_convert<double, double>(n, Q.v64[1].p, z, st);
+  }
+}
+
+}  // namespace sem

@@ -1,0 +1,34 @@
+// pmg.cuh -- p-multigrid hierarchy (internal).
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sem {
+
+struct PmgLevel {
+  Level *L = nullptr;          // level 0 is the mesh's own fine level
+  std::unique_ptr<Level> own;  // coarser levels are owned here
+  int dtype = SEM_F64;         // arithmetic of the level's smoother
+  double lam_lo = 0.0, lam_hi = 0.0;
+  DevBuf<double> v64[5];       // b, x, r, d, w in FP64 ...
+  DevBuf<float> v32[5];        // ... or FP32
+  std::vector<double> J;       // (N_l+1) x (N_{l+1}+1) interpolation to this level
+};
+
+void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t st);
+void pmg_vcycle(sem_pmg *P, const double *r, double *z, cudaStream_t st);
+
+}  // namespace sem
+
+struct sem_pmg {
+  sem_mesh *mesh = nullptr;
+  sem_pmg_desc desc{};
+  std::vector<std::unique_ptr<sem::PmgLevel>> levp;
+  sem::Reducer red;
+  sem::DevBuf<double> scal;
+  sem::DevBuf<int> flags;
+  sem::DevBuf<double> cz, cp, cw, z64;
+};

@@ -1,0 +1,314 @@
+// vec.cu -- fused vector updates and deterministic reductions of the Krylov
+// solvers (Sec. 3: Jacobi-PCG for the Stokes substep, flexible CG for the
+// pMG-preconditioned pressure solve).
+//
+// Inner products are over unique nodes: sum_l u_l v_l / mult_l, with the
+// multiplicity computed from the point's position (no stored weights).
+// Reductions are deterministic: each CTA of a fixed-size grid reduces its
+// share in a fixed order (warp shuffles, then warps in order), writes one
+// partial per sum, and the last CTA to finish (ticket counter) adds the
+// partials in CTA order.  The same n gives the same bits on every run.
+// Scalars live in device memory, so an iteration needs no host round trip.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace sem {
+
+void Reducer::init(int blocks, int max_sums) {
+  nblocks = blocks;
+  partials.alloc((size_t)blocks * max_sums);
+  counter.alloc(1);
+  SEM_CHECK_CUDA(cudaMemset(counter.p, 0, sizeof(unsigned int)));
+}
+
+int vec_grid(int64_t n) {
+  int64_t b = (n + kVecThreads - 1) / kVecThreads;
+  return (int)(b < 1 ? 1 : (b > kVecMaxBlocks ? kVecMaxBlocks : b));
+}
+
+// Reduce NS per-thread values over the grid; the last CTA writes out[s].
+template <int NS>
+__device__ void grid_reduce(double (&v)[NS], double *__restrict__ partials,
+                            unsigned int *__restrict__ counter, double *const *out) {
+  __shared__ double sh[NS][kVecThreads / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double x = v[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[s][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double x = 0.0;
+      for (int q = 0; q < kVecThreads / 32; ++q) x += sh[s][q];
+      partials[(size_t)blockIdx.x * NS + s] = x;
+    }
+    __threadfence();
+    unsigned int ticket = atomicAdd(counter, 1u);
+    last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double x = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      x += __ldcg(&partials[(size_t)b * NS + s]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[s][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double x = 0.0;
+      for (int q = 0; q < kVecThreads / 32; ++q) x += sh[s][q];
+      *out[s] = x;
+    }
+    *counter = 0u;
+  }
+}
+
+template <int NS>
+struct OutPtrs {
+  double *p[NS];
+};
+
+// ------------------------------------------------------------------ dots
+// out = sum u v / mult (optionally a second pair)
+__global__ void __launch_bounds__(kVecThreads)
+    dot_kernel(Topo t, const double *__restrict__ u, const double *__restrict__ v,
+               double *partials, unsigned int *counter, OutPtrs<1> out) {
+  double acc[1] = {0.0};
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
+       l += gridDim.x * blockDim.x) {
+    PointInfo q = point_info(l, t);
+    acc[0] += u[l] * v[l] * (double)q.inv_mult;
+  }
+  grid_reduce<1>(acc, partials, counter, out.p);
+}
+
+void launch_dot(const Topo &t, Reducer &R, const double *u, const double *v, double *out,
+                cudaStream_t st) {
+  OutPtrs<1> o{{out}};
+  dot_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, u, v, R.partials.p, R.counter.p, o);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ CG start
+// r = b - mask(w) (w = A x assembled, or r = b when w == null),
+// z = dinv r (Jacobi) or z untouched (flexible: z comes from the V-cycle),
+// p = z;  sums: bb = <b,b>, rr = <r,r>, rz = <r,z>.
+__global__ void __launch_bounds__(kVecThreads)
+    cg_start_kernel(Topo t, const double *__restrict__ b, const double *__restrict__ w,
+                    const double *__restrict__ dinv, double *__restrict__ r,
+                    double *__restrict__ z, double *__restrict__ p, double *partials,
+                    unsigned int *counter, OutPtrs<3> out) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
+       l += gridDim.x * blockDim.x) {
+    PointInfo q = point_info(l, t);
+    double bl = b[l];
+    double rl = bl - (w ? (double)q.mask * w[l] : 0.0);
+    r[l] = rl;
+    double im = (double)q.inv_mult;
+    acc[0] += bl * bl * im;
+    acc[1] += rl * rl * im;
+    if (dinv) {
+      double zl = dinv[l] * rl;
+      z[l] = zl;
+      p[l] = zl;
+      acc[2] += rl * zl * im;
+    }
+  }
+  grid_reduce<3>(acc, partials, counter, out.p);
+}
+
+void launch_cg_start(const Topo &t, Reducer &R, const double *b, const double *w,
+                     const double *dinv, double *r, double *z, double *p, double *bb, double *rr,
+                     double *rz, cudaStream_t st) {
+  OutPtrs<3> o{{bb, rr, rz}};
+  cg_start_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, b, w, dinv, r, z, p, R.partials.p,
+                                                          R.counter.p, o);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ CG iteration
+// alpha = rho / pw;  x += alpha p;  r -= alpha mask(w);  rr = <r,r>;
+// Jacobi: z = dinv r and rz = <r,z>.  skip != null: the whole kernel is a
+// no-op once *skip is set (device-side stop of the coarse solve).
+__global__ void __launch_bounds__(kVecThreads)
+    cg_update_kernel(Topo t, const double *__restrict__ rho, const double *__restrict__ pw,
+                     const double *__restrict__ p, const double *__restrict__ w,
+                     const double *__restrict__ dinv, double *__restrict__ x,
+                     double *__restrict__ r, double *__restrict__ z, double *partials,
+                     unsigned int *counter, OutPtrs<2> out, const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  const double alpha = *rho / *pw;
+  double acc[2] = {0.0, 0.0};
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
+       l += gridDim.x * blockDim.x) {
+    PointInfo q = point_info(l, t);
+    x[l] += alpha * p[l];
+    double rl = r[l] - alpha * (double)q.mask * w[l];
+    r[l] = rl;
+    double im = (double)q.inv_mult;
+    acc[0] += rl * rl * im;
+    if (dinv) {
+      double zl = dinv[l] * rl;
+      z[l] = zl;
+      acc[1] += rl * zl * im;
+    }
+  }
+  grid_reduce<2>(acc, partials, counter, out.p);
+}
+
+void launch_cg_update(const Topo &t, Reducer &R, const double *rho, const double *pw,
+                      const double *p, const double *w, const double *dinv, double *x, double *r,
+                      double *z, double *rr, double *rz, const int *skip, cudaStream_t st) {
+  OutPtrs<2> o{{rr, rz}};
+  cg_update_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, rho, pw, p, w, dinv, x, r, z,
+                                                           R.partials.p, R.counter.p, o, skip);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+// p = z + beta p with beta = num / den (Fletcher-Reeves: rz_new / rz_old) or
+// beta = -num / den (flexible: -<z,w> / <p,w>).
+__global__ void __launch_bounds__(kVecThreads)
+    cg_direction_kernel(int64_t n, const double *__restrict__ num, const double *__restrict__ den,
+                        double sign, const double *__restrict__ z, double *__restrict__ p,
+                        const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  const double beta = sign * *num / *den;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x)
+    p[l] = z[l] + beta * p[l];
+}
+
+void launch_cg_direction(int64_t n, const double *num, const double *den, double sign,
+                         const double *z, double *p, const int *skip, cudaStream_t st) {
+  cg_direction_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(n, num, den, sign, z, p, skip);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+// Flexible CG after the preconditioner: zr = <z, r>, zw = <z, mask(w)>.
+__global__ void __launch_bounds__(kVecThreads)
+    flex_dots_kernel(Topo t, const double *__restrict__ z, const double *__restrict__ r,
+                     const double *__restrict__ w, double *partials, unsigned int *counter,
+                     OutPtrs<2> out) {
+  double acc[2] = {0.0, 0.0};
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
+       l += gridDim.x * blockDim.x) {
+    PointInfo q = point_info(l, t);
+    double zl = z[l] * (double)q.inv_mult;
+    acc[0] += zl * r[l];
+    acc[1] += zl * (double)q.mask * w[l];
+  }
+  grid_reduce<2>(acc, partials, counter, out.p);
+}
+
+void launch_flex_dots(const Topo &t, Reducer &R, const double *z, const double *r,
+                      const double *w, double *zr, double *zw, cudaStream_t st) {
+  OutPtrs<2> o{{zr, zw}};
+  flex_dots_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, z, r, w, R.partials.p,
+                                                           R.counter.p, o);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+// <p, w> with a device-side skip flag (coarse solve).
+__global__ void __launch_bounds__(kVecThreads)
+    dot_skip_kernel(Topo t, const double *__restrict__ u, const double *__restrict__ v,
+                    double *partials, unsigned int *counter, OutPtrs<1> out,
+                    const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  double acc[1] = {0.0};
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
+       l += gridDim.x * blockDim.x) {
+    PointInfo q = point_info(l, t);
+    acc[0] += u[l] * v[l] * (double)q.inv_mult;
+  }
+  grid_reduce<1>(acc, partials, counter, out.p);
+}
+
+void launch_dot_skip(const Topo &t, Reducer &R, const double *u, const double *v, double *out,
+                     const int *skip, cudaStream_t st) {
+  OutPtrs<1> o{{out}};
+  dot_skip_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, u, v, R.partials.p, R.counter.p, o,
+                                                          skip);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+// Device-side stopping test of the coarse solve: skip = (rr <= tol^2 bb) or
+// (iteration count reached).  One thread.
+__global__ void stop_test_kernel(const double *__restrict__ rr, const double *__restrict__ bb,
+                                 double tol2, int it, int maxit, int *skip, int *iters) {
+  if (*skip) return;
+  *iters = it;
+  if (it >= maxit || !(*rr > tol2 * *bb)) *skip = 1;
+}
+
+void launch_stop_test(const double *rr, const double *bb, double tol2, int it, int maxit,
+                      int *skip, int *iters, cudaStream_t st) {
+  stop_test_kernel<<<1, 1, 0, st>>>(rr, bb, tol2, it, maxit, skip, iters);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ conversions
+template <typename A, typename B>
+__global__ void convert_kernel(int64_t n, const A *__restrict__ a, B *__restrict__ b) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x)
+    b[l] = (B)a[l];
+}
+
+template <typename A, typename B>
+void launch_convert(int64_t n, const A *a, B *b, cudaStream_t st) {
+  convert_kernel<A, B><<<vec_grid(n), kVecThreads, 0, st>>>(n, a, b);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+template void launch_convert<double, float>(int64_t, const double *, float *, cudaStream_t);
+template void launch_convert<float, double>(int64_t, const float *, double *, cudaStream_t);
+template void launch_convert<double, double>(int64_t, const double *, double *, cudaStream_t);
+
+// Neumann: subtract the unique-dof mean, u -= (sum u/mult) / (sum 1/mult).
+__global__ void sub_mean_kernel(Topo t, const double *__restrict__ sum, double *__restrict__ u) {
+  const double mean = *sum / (double)t.ng;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < t.nl;
+       l += (int64_t)gridDim.x * blockDim.x)
+    u[l] -= mean;
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+    sum_kernel(Topo t, const double *__restrict__ u, double *partials, unsigned int *counter,
+               OutPtrs<1> out) {
+  double acc[1] = {0.0};
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
+       l += gridDim.x * blockDim.x) {
+    PointInfo q = point_info(l, t);
+    acc[0] += u[l] * (double)q.inv_mult;
+  }
+  grid_reduce<1>(acc, partials, counter, out.p);
+}
+
+void launch_remove_mean(const Topo &t, Reducer &R, double *u, double *scratch, cudaStream_t st) {
+  OutPtrs<1> o{{scratch}};
+  sum_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, u, R.partials.p, R.counter.p, o);
+  SEM_CHECK_CUDA(cudaGetLastError());
+  sub_mean_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, scratch, u);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+void launch_sum(const Topo &t, Reducer &R, const double *u, double *out, cudaStream_t st) {
+  OutPtrs<1> o{{out}};
+  sum_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, u, R.partials.p, R.counter.p, o);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+}  // namespace sem

@@ -1,0 +1,260 @@
+"""ctypes binding of the C ABI in ``include/sem.h``.
+
+Argument marshalling only: every computation runs in the CUDA library
+``_build/libsem.so``.  Device vectors are torch CUDA tensors (the binding
+passes their data pointers); streams are torch CUDA streams (their raw
+``cudaStream_t``).  Importing this module does not load the library; the first
+call does, and raises if it was not built (there is no fallback path).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsem.so")
+
+SEM_OK, SEM_EINVAL, SEM_ENOMEM, SEM_ECUDA, SEM_ENOTCONV, SEM_ENUMERIC, SEM_EAGAIN, SEM_EBUSY, \
+    SEM_ETIMEOUT = range(9)
+STATUS_NAMES = ["SEM_OK", "SEM_EINVAL", "SEM_ENOMEM", "SEM_ECUDA", "SEM_ENOTCONV", "SEM_ENUMERIC",
+                "SEM_EAGAIN", "SEM_EBUSY", "SEM_ETIMEOUT"]
+SEM_F64, SEM_F32, SEM_F16, SEM_BF16 = range(4)
+SEM_DIRICHLET, SEM_NEUMANN = 0, 1
+SEM_GEOM_STORED, SEM_GEOM_TRILINEAR = 0, 1
+SEM_AX_LOCAL, SEM_AX_ASSEMBLED = 0, 1
+SEM_FIELD_X, SEM_FIELD_Y, SEM_FIELD_Z, SEM_FIELD_MASS, SEM_FIELD_MULT, SEM_FIELD_MASK, \
+    SEM_FIELD_DINV = range(7)
+SEM_SOLVER_PCG, SEM_SOLVER_FLEXCG = 0, 1
+SEM_MAX_ORDER = 11
+
+EXPORTED = ["sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_field", "sem_ax",
+            "sem_gs", "sem_dot", "sem_pmg_setup", "sem_pmg_destroy", "sem_pmg_info",
+            "sem_pmg_vcycle", "sem_solve", "sem_solve_host", "sem_last_error"]
+
+
+class SemError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 9 else status}: {msg}")
+
+
+class sem_mesh_desc(C.Structure):
+    _fields_ = [("ex", C.c_int32), ("ey", C.c_int32), ("ez", C.c_int32), ("N", C.c_int32),
+                ("jitter", C.c_double), ("seed", C.c_uint64), ("bc", C.c_int32),
+                ("geom", C.c_int32), ("verts", C.c_void_p)]
+
+
+class sem_pmg_desc(C.Structure):
+    _fields_ = [("nlevels", C.c_int32), ("orders", C.c_int32 * 8), ("cheb_degree", C.c_int32),
+                ("lanczos_steps", C.c_int32), ("seed", C.c_uint64), ("smoother_dtype", C.c_int32),
+                ("coarse_tol", C.c_double), ("coarse_maxit", C.c_int32)]
+
+
+class sem_solve_desc(C.Structure):
+    _fields_ = [("solver", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
+                ("check_every", C.c_int32)]
+
+
+class sem_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("res0", C.c_double),
+                ("res", C.c_double), ("bnorm", C.c_double), ("time_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libsem.so (raises when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run paper_2110_01716_gb300.build.build())")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    L.sem_last_error.restype = C.c_char_p
+    L.sem_mesh_create.argtypes = [C.POINTER(sem_mesh_desc), vp, C.POINTER(vp)]
+    L.sem_mesh_destroy.argtypes = [vp]
+    L.sem_mesh_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_size_t)]
+    L.sem_mesh_field.argtypes = [vp, i32, vp, vp]
+    L.sem_ax.argtypes = [vp, i32, vp, vp, i32, vp]
+    L.sem_gs.argtypes = [vp, i32, vp, vp]
+    L.sem_dot.argtypes = [vp, vp, vp, C.POINTER(d), vp]
+    L.sem_pmg_setup.argtypes = [vp, C.POINTER(sem_pmg_desc), vp, C.POINTER(vp)]
+    L.sem_pmg_destroy.argtypes = [vp]
+    L.sem_pmg_info.argtypes = [vp, i32, C.POINTER(d), C.POINTER(d)]
+    L.sem_pmg_vcycle.argtypes = [vp, vp, vp, vp]
+    L.sem_solve.argtypes = [vp, vp, vp, vp, C.POINTER(sem_solve_desc), C.POINTER(sem_solve_info),
+                            vp]
+    L.sem_solve_host.argtypes = L.sem_solve.argtypes
+    for name in EXPORTED:
+        if name != "sem_last_error":
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return lib().sem_last_error().decode()
+
+
+def check(status: int):
+    if status != SEM_OK:
+        raise SemError(status, last_error())
+    return status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------- handles
+class Mesh:
+    """Owning wrapper of a sem_mesh handle."""
+
+    def __init__(self, ex, ey, ez, N, bc=SEM_DIRICHLET, geom=SEM_GEOM_STORED, verts=None,
+                 jitter=0.1, seed=1, stream=None):
+        import numpy as np
+
+        self._verts = None
+        vptr = None
+        if verts is not None:
+            self._verts = np.ascontiguousarray(verts, dtype=np.float64)
+            vptr = self._verts.ctypes.data
+        desc = sem_mesh_desc(ex, ey, ez, N, float(jitter), int(seed), bc, geom, vptr)
+        h = C.c_void_p()
+        check(lib().sem_mesh_create(C.byref(desc), _stream(stream), C.byref(h)))
+        self.h = h
+        self.ex, self.ey, self.ez, self.N, self.bc, self.geom = ex, ey, ez, N, bc, geom
+        nl, ng, nb = C.c_int64(), C.c_int64(), C.c_size_t()
+        check(lib().sem_mesh_info(self.h, C.byref(nl), C.byref(ng), C.byref(nb)))
+        self.n_local, self.n_global = nl.value, ng.value
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().sem_mesh_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        nl, ng, nb = C.c_int64(), C.c_int64(), C.c_size_t()
+        check(lib().sem_mesh_info(self.h, C.byref(nl), C.byref(ng), C.byref(nb)))
+        return {"n_local": nl.value, "n_global": ng.value, "dev_bytes": nb.value}
+
+
+def sem_mesh_field(mesh: Mesh, which: int, out, stream=None):
+    check(lib().sem_mesh_field(mesh.h, which, _ptr(out), _stream(stream)))
+    return out
+
+
+def sem_ax(mesh: Mesh, dtype: int, u, w, flags=SEM_AX_ASSEMBLED, stream=None):
+    check(lib().sem_ax(mesh.h, dtype, _ptr(u), _ptr(w), flags, _stream(stream)))
+    return w
+
+
+def sem_gs(mesh: Mesh, dtype: int, u, stream=None):
+    check(lib().sem_gs(mesh.h, dtype, _ptr(u), _stream(stream)))
+    return u
+
+
+def sem_dot(mesh: Mesh, u, v, stream=None) -> float:
+    out = C.c_double()
+    check(lib().sem_dot(mesh.h, _ptr(u), _ptr(v), C.byref(out), _stream(stream)))
+    return out.value
+
+
+class Pmg:
+    """Owning wrapper of a sem_pmg handle (keeps its mesh alive)."""
+
+    def __init__(self, mesh: Mesh, orders=(7, 3, 1), cheb_degree=2, lanczos_steps=20, seed=0,
+                 smoother_dtype=SEM_F32, coarse_tol=1e-2, coarse_maxit=50, stream=None):
+        desc = sem_pmg_desc()
+        desc.nlevels = len(orders)
+        for i, o in enumerate(orders):
+            desc.orders[i] = int(o)
+        desc.cheb_degree = cheb_degree
+        desc.lanczos_steps = lanczos_steps
+        desc.seed = int(seed)
+        desc.smoother_dtype = smoother_dtype
+        desc.coarse_tol = float(coarse_tol)
+        desc.coarse_maxit = int(coarse_maxit)
+        h = C.c_void_p()
+        check(lib().sem_pmg_setup(mesh.h, C.byref(desc), _stream(stream), C.byref(h)))
+        self.h = h
+        self.mesh = mesh
+        self.orders = tuple(orders)
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().sem_pmg_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lam(self, level):
+        lo, hi = C.c_double(), C.c_double()
+        check(lib().sem_pmg_info(self.h, level, C.byref(lo), C.byref(hi)))
+        return lo.value, hi.value
+
+
+def sem_pmg_vcycle(pmg: Pmg, r, z, stream=None):
+    check(lib().sem_pmg_vcycle(pmg.h, _ptr(r), _ptr(z), _stream(stream)))
+    return z
+
+
+def sem_solve(mesh: Mesh, pmg, b, x, solver=SEM_SOLVER_PCG, tol=1e-8, max_iter=1000,
+              check_every=1, stream=None, raise_on_notconv=False):
+    """Solve in place (x: initial guess in, solution out); returns the info dict."""
+    desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every))
+    info = sem_solve_info()
+    st = lib().sem_solve(mesh.h, pmg.h if pmg is not None else None, _ptr(b), _ptr(x),
+                         C.byref(desc), C.byref(info), _stream(stream))
+    if st not in (SEM_OK, SEM_ENOTCONV) or (raise_on_notconv and st != SEM_OK):
+        raise SemError(st, last_error())
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+def sem_solve_host(mesh: Mesh, pmg, b_host, x_host, solver=SEM_SOLVER_PCG, tol=1e-8,
+                   max_iter=1000, check_every=1, stream=None):
+    """As sem_solve with host (CPU tensor or numpy) b and x; x is updated in place."""
+    desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every))
+    info = sem_solve_info()
+    bp = b_host.ctypes.data if hasattr(b_host, "ctypes") else b_host.data_ptr()
+    xp = x_host.ctypes.data if hasattr(x_host, "ctypes") else x_host.data_ptr()
+    st = lib().sem_solve_host(mesh.h, pmg.h if pmg is not None else None, bp, xp, C.byref(desc),
+                              C.byref(info), _stream(stream))
+    if st not in (SEM_OK, SEM_ENOTCONV):
+        raise SemError(st, last_error())
+    d = info.as_dict()
+    d["status"] = st
+    return d

@@ -1,0 +1,72 @@
+"""The C ABI library builds, loads and exports what include/sem.h declares;
+argument errors come back as status codes before any device work (CPU only)."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libsem():
+    from paper_2110_01716_gb300 import build, sem
+
+    build.build()
+    return sem
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "sem.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:sem_status|const char \*)\s*(sem_\w+)\(", text, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ["sem_mesh_create", "sem_ax", "sem_gs", "sem_pmg_setup", "sem_solve"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(libsem):
+    L = libsem.lib()
+    missing = [n for n in declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(declared_symbols()) <= set(libsem.EXPORTED) | {"sem_last_error"}
+
+
+def test_invalid_arguments_return_einval_without_device_work(libsem):
+    L = libsem.lib()
+    h = C.c_void_p()
+    # null descriptor
+    assert L.sem_mesh_create(None, None, C.byref(h)) == libsem.SEM_EINVAL
+    assert "null" in libsem.last_error()
+    for bad in [dict(ex=0), dict(N=0), dict(N=libsem.SEM_MAX_ORDER + 1), dict(bc=7),
+                dict(geom=5), dict(jitter=0.7)]:
+        args = dict(ex=2, ey=2, ez=2, N=3, jitter=0.1, seed=1, bc=0, geom=0, verts=None)
+        args.update(bad)
+        desc = libsem.sem_mesh_desc(**args)
+        st = L.sem_mesh_create(C.byref(desc), None, C.byref(h))
+        assert st == libsem.SEM_EINVAL, (bad, st)
+        assert libsem.last_error()
+        assert not h.value
+    # null handles are rejected
+    assert L.sem_ax(None, 0, None, None, 0, None) == libsem.SEM_EINVAL
+    assert L.sem_gs(None, 0, None, None) == libsem.SEM_EINVAL
+    assert L.sem_pmg_setup(None, None, None, C.byref(h)) == libsem.SEM_EINVAL
+    info = libsem.sem_solve_info()
+    desc = libsem.sem_solve_desc(0, 1e-8, 10, 1)
+    assert L.sem_solve(None, None, None, None, C.byref(desc), C.byref(info), None) == \
+        libsem.SEM_EINVAL
+    assert L.sem_mesh_destroy(None) == libsem.SEM_OK
+    assert L.sem_pmg_destroy(None) == libsem.SEM_OK
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2110_01716_gb300 import sem
+
+    monkeypatch.setattr(sem, "_lib", None)
+    monkeypatch.setattr(sem, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        sem.lib()

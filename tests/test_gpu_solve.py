@@ -1,0 +1,173 @@
+"""GPU parity of the solvers against the FP64 oracle, through the C ABI.
+
+* Jacobi-PCG: the residual of the GPU solution, recomputed by the oracle,
+  meets the tolerance; the solution matches the oracle's solution.
+* pMG V-cycle with an FP64 smoother and a fixed number of coarse iterations
+  is a fixed linear map: it matches the oracle's V-cycle to 1e-10.
+* FlexCG + pMG (FP64 and FP32 smoothers) reaches 1e-8; the final error against
+  the oracle's solution is reported and bounded.
+* Status codes: SEM_ENOTCONV at max_iter, SEM_EINVAL for a Neumann right-hand
+  side that is not mean-free.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_01716_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2110_01716_gb300 import sem  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_2110_01716_gb300 import build
+
+    build.build()
+    oracle.build()
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def manufactured(L):
+    X = L.X
+    us = (np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2])).ravel()
+    return us, L.assembled_rhs(3 * np.pi ** 2 * us)
+
+
+def fourier_rhs(L, seed=3):
+    a, k, phi = inputs.fourier_modes(seed)
+    X = L.X
+    f = sum(a[m] * np.cos(2 * np.pi * (k[m, 0] * X[:, 0] + k[m, 1] * X[:, 1] + k[m, 2] * X[:, 2])
+                          + phi[m]) for m in range(len(a))).ravel()
+    b = L.gs(L.B * f)
+    return b - L.dot(b, np.ones(L.nl)) / L.ng
+
+
+def residual(L, b, x):
+    r = b - L.ax(x)
+    return np.sqrt(L.dot(r, r)) / np.sqrt(L.dot(b, b))
+
+
+@pytest.mark.parametrize("e,N", [(8, 7), (3, 5), (2, 1)])
+def test_jacobi_pcg_manufactured(e, N):
+    v = inputs.box_vertices(e, e, e, 0.1, 1)
+    m = sem.Mesh(e, e, e, N, sem.SEM_DIRICHLET, verts=v)
+    L = oracle.Level(e, e, e, N, 0, v)
+    us, b = manufactured(L)
+    bd = torch.tensor(b, device=DEV)
+    xd = torch.zeros_like(bd)
+    info = sem.sem_solve(m, None, bd, xd, sem.SEM_SOLVER_PCG, tol=1e-10, max_iter=2000)
+    assert info["status"] == sem.SEM_OK, info
+    x = xd.cpu().numpy()
+    assert residual(L, b, x) <= 1.05e-10
+    xo, io = L.pcg(b, tol=1e-10, maxit=2000)
+    assert abs(info["iters"] - io["iters"]) <= 2
+    assert rel(x, xo) < 1e-8
+    if (e, N) == (8, 7):
+        assert np.max(np.abs(x - us)) < 1e-9  # discretisation error of the config-1 problem
+
+
+def test_pcg_check_every_and_host_buffers():
+    v = inputs.box_vertices(4, 4, 4, 0.1, 1)
+    m = sem.Mesh(4, 4, 4, 6, 0, verts=v)
+    L = oracle.Level(4, 4, 4, 6, 0, v)
+    _, b = manufactured(L)
+    x_host = np.zeros(L.nl)
+    info = sem.sem_solve_host(m, None, b.copy(), x_host, sem.SEM_SOLVER_PCG, tol=1e-9,
+                              max_iter=1000, check_every=8)
+    assert info["status"] == sem.SEM_OK
+    assert info["iters"] % 8 == 0
+    assert residual(L, b, x_host) <= 1.05e-9
+
+
+def test_pcg_not_converged_status():
+    m = sem.Mesh(3, 3, 3, 5, 0, jitter=0.1, seed=2)
+    L = oracle.Level(3, 3, 3, 5, 0, inputs.box_vertices(3, 3, 3, 0.1, 2))
+    _, b = manufactured(L)
+    bd = torch.tensor(b, device=DEV)
+    xd = torch.zeros_like(bd)
+    info = sem.sem_solve(m, None, bd, xd, sem.SEM_SOLVER_PCG, tol=1e-12, max_iter=3)
+    assert info["status"] == sem.SEM_ENOTCONV and info["iters"] == 3
+    xo, io = L.pcg(b, tol=0.0, maxit=3)
+    assert rel(xd.cpu().numpy(), xo) < 1e-10  # same three iterates
+
+
+def test_neumann_rhs_must_be_mean_free():
+    m = sem.Mesh(2, 2, 2, 3, sem.SEM_NEUMANN, jitter=0.1, seed=1)
+    bd = torch.ones(m.n_local, device=DEV, dtype=torch.float64)
+    xd = torch.zeros_like(bd)
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_solve(m, None, bd, xd, sem.SEM_SOLVER_PCG, tol=1e-8, max_iter=10)
+    assert ei.value.status == sem.SEM_EINVAL
+
+
+@pytest.mark.parametrize("bc,orders", [(0, (5, 3, 1)), (1, (7, 3, 1)), (0, (4, 2)), (1, (3, 1))])
+def test_vcycle_fp64_matches_oracle(bc, orders):
+    e = (3, 2, 4)
+    v = inputs.box_vertices(*e, 0.1, 5)
+    m = sem.Mesh(*e, orders[0], bc, verts=v)
+    P = sem.Pmg(m, orders=orders, smoother_dtype=sem.SEM_F64, coarse_tol=0.0, coarse_maxit=12,
+                seed=4)
+    Po = oracle.PMG(*e, list(orders), bc, v, cheb_degree=2, lanczos_steps=20, seed=4,
+                    coarse_tol=0.0, coarse_maxit=12)
+    for lvl in range(len(orders) - 1):
+        lo, hi = P.lam(lvl)
+        olo, ohi = Po.lam(lvl)
+        assert abs(hi - ohi) < 1e-10 * ohi and abs(lo - olo) < 1e-10 * olo
+    L = Po.levels[0]
+    r = L.gs(inputs.random_field(L.nl, 8)) * L.mask
+    if bc == 1:
+        r -= L.dot(r, np.ones(L.nl)) / L.ng
+    zd = torch.empty(L.nl, device=DEV, dtype=torch.float64)
+    sem.sem_pmg_vcycle(P, torch.tensor(r, device=DEV), zd)
+    assert rel(zd.cpu().numpy(), Po.vcycle(r)) < 1e-10
+
+
+def test_vcycle_fp32_close_to_fp64_oracle():
+    e = (4, 3, 3)
+    v = inputs.box_vertices(*e, 0.1, 6)
+    m = sem.Mesh(*e, 7, 0, verts=v)
+    P = sem.Pmg(m, orders=(7, 3, 1), smoother_dtype=sem.SEM_F32, coarse_tol=0.0, coarse_maxit=20)
+    Po = oracle.PMG(*e, [7, 3, 1], 0, v, coarse_tol=0.0, coarse_maxit=20)
+    L = Po.levels[0]
+    _, b = manufactured(L)
+    zd = torch.empty(L.nl, device=DEV, dtype=torch.float64)
+    sem.sem_pmg_vcycle(P, torch.tensor(b, device=DEV), zd)
+    err = rel(zd.cpu().numpy(), Po.vcycle(b))
+    assert err < 1e-4, err  # single precision smoothing, stated tolerance
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("dtype", [sem.SEM_F64, sem.SEM_F32])
+def test_flexcg_pmg_reaches_1e8(bc, dtype):
+    e = 6
+    v = inputs.box_vertices(e, e, e, 0.1, 3)
+    m = sem.Mesh(e, e, e, 7, bc, verts=v)
+    L = oracle.Level(e, e, e, 7, bc, v)
+    b = manufactured(L)[1] if bc == 0 else fourier_rhs(L)
+    P = sem.Pmg(m, orders=(7, 3, 1), smoother_dtype=dtype, coarse_tol=1e-2, coarse_maxit=50)
+    bd = torch.tensor(b, device=DEV)
+    xd = torch.zeros_like(bd)
+    info = sem.sem_solve(m, P, bd, xd, sem.SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=100)
+    assert info["status"] == sem.SEM_OK, info
+    x = xd.cpu().numpy()
+    assert residual(L, b, x) <= 1.05e-8
+    Po = oracle.PMG(e, e, e, [7, 3, 1], bc, v, coarse_tol=1e-2, coarse_maxit=50)
+    xo, io = Po.flexpcg(b, tol=1e-8, maxit=100)
+    if bc == 1:
+        x = x - L.dot(x, np.ones(L.nl)) / L.ng
+        xo = xo - L.dot(xo, np.ones(L.nl)) / L.ng
+    err = rel(x, xo)
+    assert err < 1e-6, err
+    assert info["iters"] <= io["iters"] + 3
