@@ -1,0 +1,430 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 SEM pressure-Poisson solve.
+
+One step = one full pressure-type Poisson solve from a zero guess: the whole
+hot path (operator, gather-scatter, masking, Chebyshev-Jacobi smoothing in
+FP32, tensor-product transfers, FP64 coarse Jacobi-PCG, FP64 flexible CG
+with its inner products) on the mixed-precision workload
+
+    box of 48^3 = 110,592 trilinear hexahedra, N = 7, vertices jittered
+    +-10% of h (seed 3), Neumann, smooth random mean-free right-hand side,
+    p-multigrid 7-3-1, Chebyshev degree 2, FP32 smoother, FlexCG in FP64 to
+    a relative residual of 1e-8.
+
+value = unique dofs solved per second (GDOF/s, whole job over all ranks).
+The working set (about 6 GB) is far larger than the 129 MB L2, so no L2 flush
+is needed between steps.  Besides the headline line the JSON carries the
+dominant kernel's roofline (measured live with CUDA events on the launching
+stream inside the timed region), an end-to-end number through the host-buffer
+entry point, the CPU oracle's throughput on a bounded sample, the FP64/FP32
+operator throughput at 64^3 elements (HBM roofline), SM clocks sampled during
+the timed region and the number of library kernels launched.
+
+--impl reference times the CPU oracle (the only reference there is) on a
+bounded sample of the same workload.  With torchrun, every rank runs an
+independent replica (the solve is not sharded: replicas only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Poisson solve time to 1e-8 (GDOF/s) & Ax GB/s vs HBM roofline; p50/p99 latency"
+E_SIDE, ORDER, MESH_SEED, RHS_SEED = 48, 7, 3, 3
+TOL = 1e-8
+WORKLOAD = ("mixed-precision Neumann pressure solve: E=48^3=110592 jittered hexes (+-10% h, "
+            "seed 3), N=7, pMG 7-3-1, Chebyshev(2)-Jacobi smoother in FP32, FP64 coarse "
+            "Jacobi-PCG (tol 1e-2, <=50 it), FP64 FlexCG to 1e-8 from x=0")
+# Fallback peaks of the recipe, used only when MEASURED_PEAKS.json is absent.
+FALLBACK_HBM_GBS = 6800.0
+# FP64 pipe: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (the part's
+# nominal 1.25 TFLOP/s; an FMA-chain probe on this machine measured 1.195).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM traffic of one fine-level FP64 operator launch from an ncu capture
+# (profiles/ax_f64_N7.txt), valid while the kernel source is unchanged.
+AX_TRAFFIC = {"source_sha256": None, "bytes_per_point": None}
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--side", type=int, default=E_SIDE, help="elements per direction")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the operator sweep, e2e and CPU-baseline legs")
+    p.add_argument("--breakdown", action="store_true",
+                   help="after the timed region, time every kernel class of one more solve")
+    return p.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def rhs_on_device(sem, torch, mesh, dev):
+    """Neumann right-hand side b = gs(B f) minus its unique-dof mean, with f the
+    seeded smooth random field of the input module, evaluated on the mesh's own
+    GLL coordinates."""
+    from paper_2110_01716_gb300 import inputs
+
+    n = mesh.n_local
+    X = [torch.empty(n, device=dev, dtype=torch.float64) for _ in range(3)]
+    for d in range(3):
+        sem.sem_mesh_field(mesh, d, X[d])
+    Bm = torch.empty(n, device=dev, dtype=torch.float64)
+    sem.sem_mesh_field(mesh, sem.SEM_FIELD_MASS, Bm)
+    a, k, phi = inputs.fourier_modes(RHS_SEED)
+    f = torch.zeros(n, device=dev, dtype=torch.float64)
+    for m in range(len(a)):
+        f += float(a[m]) * torch.cos(2 * torch.pi * (float(k[m, 0]) * X[0] + float(k[m, 1]) * X[1]
+                                                     + float(k[m, 2]) * X[2]) + float(phi[m]))
+    b = Bm * f
+    sem.sem_gs(mesh, sem.SEM_F64, b)
+    ones = torch.ones_like(b)
+    mean = sem.sem_dot(mesh, b, ones) / mesh.n_global
+    b -= mean
+    del X, Bm, f, ones
+    return b
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def ax_source_sha():
+    with open(os.path.join(ROOT, "paper_2110_01716_gb300", "csrc", "ax.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def operator_sweep(sem, torch, dev, hbm):
+    """FP64 / FP32 operator throughput at 64^3 elements, N=7 (stored and
+    recomputed geometry), median of 20 launches after 3 warm-ups."""
+    from paper_2110_01716_gb300 import inputs
+
+    out = {}
+    k = 64
+    N = ORDER
+    for geom, gname in ((sem.SEM_GEOM_STORED, "stored"), (sem.SEM_GEOM_TRILINEAR, "trilinear")):
+        mesh = sem.Mesh(k, k, k, N, sem.SEM_DIRICHLET, geom,
+                        verts=inputs.box_vertices(k, k, k, 0.1, 2 + k))
+        n = mesh.n_local
+        for dt, tdt, name in ((sem.SEM_F64, torch.float64, "f64"), (sem.SEM_F32, torch.float32,
+                                                                      "f32")):
+            u = torch.rand(n, device=dev, dtype=tdt, generator=torch.Generator(dev).manual_seed(5))
+            w = torch.empty_like(u)
+            st = torch.cuda.current_stream()
+            for _ in range(3):
+                sem.sem_ax(mesh, dt, u, w, sem.SEM_AX_LOCAL)
+            times = []
+            for _ in range(20):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                sem.sem_ax(mesh, dt, u, w, sem.SEM_AX_LOCAL)
+                e1.record(st)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = statistics.median(times)
+            esz = 8 if name == "f64" else 4
+            bpp = 2 * esz + (6 * esz if gname == "stored" else 0)
+            bytes_alg = n * bpp + (mesh.ex * mesh.ey * mesh.ez * 24 * 8 if gname != "stored" else 0)
+            flops = n * (12 * (N + 1) + 15)
+            out[f"{name}_{gname}"] = {
+                "E": k ** 3, "ms": round(ms, 4), "gdofs_local": round(n / ms / 1e6, 3),
+                "GB_s": round(bytes_alg / ms / 1e6, 1), "hbm_frac": round(bytes_alg / ms / 1e6 / hbm, 4),
+                "TFLOP_s": round(flops / ms / 1e9, 3)}
+            del u, w
+        mesh.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def oracle_sample_solve(side=12):
+    """One oracle FlexCG + pMG solve on a side^3 box of the same recipe.
+    Returns (seconds, unique dofs, iterations, threads)."""
+    import numpy as np
+
+    import oracle
+    from paper_2110_01716_gb300 import inputs
+
+    oracle.build()
+    v = inputs.box_vertices(side, side, side, 0.1, MESH_SEED)
+    P = oracle.PMG(side, side, side, [7, 3, 1], 1, v, cheb_degree=2, lanczos_steps=20, seed=0,
+                   coarse_tol=1e-2, coarse_maxit=50)
+    L = P.levels[0]
+    a, k, phi = inputs.fourier_modes(RHS_SEED)
+    X = L.X
+    f = sum(a[m] * np.cos(2 * np.pi * (k[m, 0] * X[:, 0] + k[m, 1] * X[:, 1] + k[m, 2] * X[:, 2])
+                          + phi[m]) for m in range(len(a))).ravel()
+    b = L.gs(L.B * f)
+    b -= L.dot(b, np.ones(L.nl)) / L.ng
+    t0 = time.perf_counter()
+    x, info = P.flexpcg(b, tol=TOL, maxit=200)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dt, L.ng, info["iters"], threads
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    side = 12
+    for _ in range(args.warmup):
+        oracle_sample_solve(side)
+    times, ng, iters, threads = [], 0, 0, 1
+    for _ in range(args.steps):
+        dt, ng, iters, threads = oracle_sample_solve(side)
+        times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = ng / (ms / 1e3) / 1e9
+    sample = (f"oracle FlexCG+pMG 7-3-1 solve to 1e-8 on a {side}^3-element box of the same "
+              f"recipe (N=7, Neumann, {ng} unique dofs, {iters} iterations), setup excluded")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference_sample": sample},
+            "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+
+    from paper_2110_01716_gb300 import build, inputs, sem
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    build.build()
+    hbm, hbm_src = measured_peaks()
+
+    side = args.side
+    verts = inputs.box_vertices(side, side, side, 0.1, MESH_SEED)
+    mesh = sem.Mesh(side, side, side, ORDER, sem.SEM_NEUMANN, sem.SEM_GEOM_STORED, verts=verts)
+    pmg = sem.Pmg(mesh, orders=(7, 3, 1), cheb_degree=2, lanczos_steps=20, seed=0,
+                  smoother_dtype=sem.SEM_F32, coarse_tol=1e-2, coarse_maxit=50)
+    b = rhs_on_device(sem, torch, mesh, dev)
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        x.zero_()
+        return sem.sem_solve(mesh, pmg, b, x, sem.SEM_SOLVER_FLEXCG, tol=TOL, max_iter=200,
+                             check_every=1)
+
+    for _ in range(max(args.warmup, 0)):
+        info = step()
+    # timed region
+    sem.sem_trace_enable(True, f"ax_f64_N{ORDER}")
+    sem.sem_trace_read(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    infos = []
+    for s in range(args.steps):
+        infos.append(step())
+        ev[s + 1].record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    trace = sem.sem_trace_read(reset=True)
+    sem.sem_trace_enable(False, "")
+    step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if pg:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    ng = mesh.n_global
+    value = world * ng / (ms_per_step / 1e3) / 1e9
+    for inf in infos:
+        if inf["status"] != sem.SEM_OK:
+            raise SystemExit(f"solve did not converge: {inf}")
+
+    # dominant kernel: fine-level FP64 operator (FP64-pipe bound on GB300)
+    key = f"ax_f64_N{ORDER}"
+    ax = trace.get(key, {"launches": 0, "timed": 0, "total_ms": 0.0})
+    ax_ms = ax["total_ms"] / max(ax["timed"], 1)
+    nl = mesh.n_local
+    flops_pt = 12 * (ORDER + 1) + 15
+    ax_tflops = nl * flops_pt / (ax_ms / 1e3) / 1e12 if ax_ms > 0 else None
+    traffic = None
+    if AX_TRAFFIC["source_sha256"] == ax_source_sha() and AX_TRAFFIC["bytes_per_point"]:
+        traffic = AX_TRAFFIC["bytes_per_point"] * nl
+    launches = sum(v["launches"] for v in trace.values())
+    ax_share = ax["total_ms"] / total_ms if total_ms > 0 else None
+    roofline = {"bound": "alu", "achieved": ax_tflops, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": (ax_tflops / FP64_PEAK_TFLOPS) if ax_tflops else None,
+                "traffic": traffic, "kernel": key,
+                "per_launch_ms": ax_ms, "launches_timed": ax["timed"],
+                "share_of_step": ax_share,
+                "algorithmic": f"{flops_pt} flop/pt x {nl} local pts per launch; "
+                               f"64 B/pt x {nl} = {64 * nl / 1e9:.2f} GB",
+                "hbm_GB_s": (64 * nl / (ax_ms / 1e3) / 1e9) if ax_ms > 0 else None,
+                "hbm_frac": (64 * nl / (ax_ms / 1e3) / 1e9 / hbm) if ax_ms > 0 else None,
+                "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz; "
+                               f"HBM {hbm} GB/s {hbm_src}"}
+
+    line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "E": side ** 3, "N": ORDER, "n_local": nl,
+                       "n_global": ng, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (working set ~6 GB), no flush"},
+            "iters": [inf["iters"] for inf in infos],
+            "final_rel_res": max(inf["res"] / inf["bnorm"] for inf in infos),
+            "latency_ms": {"p50": statistics.median(step_ms),
+                           "p99": sorted(step_ms)[min(len(step_ms) - 1,
+                                                      int(0.99 * len(step_ms)))]},
+            "roofline": roofline, "gpu_launches": launches,
+            "trace_classes": {k: v["launches"] for k, v in sorted(trace.items())},
+            "clocks": clk}
+
+    if args.breakdown:
+        # one untimed solve with every launch bracketed by events (Table-1 style)
+        sem.sem_trace_enable(True, "*")
+        sem.sem_trace_read(reset=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bd = sem.sem_trace_read(reset=True)
+        sem.sem_trace_enable(False, "")
+        tot = e0.elapsed_time(e1)
+        line["breakdown"] = {"solve_ms": tot, "kernel_ms": sum(v["total_ms"] for v in bd.values()),
+                             "classes": {k: [v["launches"], round(v["total_ms"], 3)]
+                                         for k, v in sorted(bd.items(),
+                                                            key=lambda kv: -kv[1]["total_ms"])}}
+
+    if not args.no_extras and rank == 0:
+        # end to end through the host-buffer entry point (pinned host memory)
+        bh = b.cpu().pin_memory()
+        xh = torch.zeros(nl, dtype=torch.float64).pin_memory()
+        for _ in range(1):
+            xh.zero_()
+            sem.sem_solve_host(mesh, pmg, bh, xh, sem.SEM_SOLVER_FLEXCG, tol=TOL, max_iter=200)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            xh.zero_()
+            sem.sem_solve_host(mesh, pmg, bh, xh, sem.SEM_SOLVER_FLEXCG, tol=TOL, max_iter=200)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        line["e2e"] = {"value": ng / e2e_s / 1e9, "unit": "GDOF/s",
+                       "h2d_bytes_per_step": 2 * nl * 8, "d2h_bytes_per_step": nl * 8}
+        del bh, xh
+        pmg.close()
+        mesh.close()
+        del b, x
+        torch.cuda.empty_cache()
+        line["ax_sweep_64cube"] = operator_sweep(sem, torch, dev, hbm)
+        if world == 1:
+            dt, ng_s, it_s, threads = oracle_sample_solve(12)
+            line["cpu_baseline"] = {
+                "value": ng_s / dt / 1e9, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
+                "sample": f"oracle FlexCG+pMG 7-3-1 solve to 1e-8 on a 12^3-element box of the "
+                          f"same recipe ({ng_s} unique dofs, {it_s} iterations, {dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

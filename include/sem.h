@@ -185,6 +185,23 @@ sem_status sem_solve(sem_mesh *mesh, sem_pmg *pmg, const double *b, double *x,
 sem_status sem_solve_host(sem_mesh *mesh, sem_pmg *pmg, const double *b_host, double *x_host,
                           const sem_solve_desc *desc, sem_solve_info *info, void *stream);
 
+/* Tracing (Sec. 4 reports timing breakdowns from CUDA events): while enabled,
+ * every kernel launch of the library is counted under a class name such as
+ * "ax_f64_N7" or "gs_f32_N3"; launches of classes whose name contains
+ * `timed_filter` (NULL or "" = none, "*" = all) are also bracketed by CUDA events on
+ * their stream.  sem_trace_read synchronises on the pending events and fills
+ * up to max_entries entries (HOST array); *n_entries receives the number of
+ * classes.  reset != 0 clears the counters afterwards. */
+typedef struct {
+  char name[48];
+  int64_t launches;  /* launches counted */
+  int64_t timed;     /* launches timed with events */
+  double total_ms;   /* summed device time of the timed launches */
+} sem_trace_entry;
+sem_status sem_trace_enable(int32_t enable, const char *timed_filter);
+sem_status sem_trace_read(sem_trace_entry *out, int32_t max_entries, int32_t *n_entries,
+                          int32_t reset);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *sem_last_error(void);
 

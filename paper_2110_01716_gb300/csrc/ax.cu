@@ -14,6 +14,7 @@
 // the r and s fluxes.
 #include "common.cuh"
 #include "device_basis.cuh"
+#include "trace.cuh"
 
 namespace sem {
 
@@ -131,6 +132,9 @@ template <typename T, int NP>
 static void ax_dispatch_geom(const Level &L, const T *u, T *w, cudaStream_t st) {
   using S = AxShape<NP>;
   const T *G = nullptr;
+  const bool f64 = sizeof(T) == 8;
+  const bool tri = L.geom != SEM_GEOM_STORED;
+  TraceScope ts(tri ? (f64 ? "ax_f64_tri" : "ax_f32_tri") : (f64 ? "ax_f64" : "ax_f32"), L.t.N, st);
   if (L.geom == SEM_GEOM_STORED) {
     if constexpr (sizeof(T) == 8) G = (const T *)L.G64.p;
     else G = (const T *)L.G32.p;

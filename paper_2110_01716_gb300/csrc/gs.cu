@@ -9,6 +9,7 @@
 // Copies are summed in a fixed order (x fastest, lower element first), so all
 // copies end bit-identical and the result does not depend on scheduling.
 #include "common.cuh"
+#include "trace.cuh"
 
 namespace sem {
 
@@ -114,6 +115,7 @@ static int grid_1d(int64_t n, int threads) {
 template <typename T>
 void launch_gs(const Level &L, T *u, cudaStream_t st) {
   if (L.n_shared == 0) return;
+  TraceScope ts(sizeof(T) == 8 ? "gs_f64" : "gs_f32", L.t.N, st);
   gs_kernel<T><<<grid_1d(L.n_shared, 256), 256, 0, st>>>(gs_geom(L.t), L.shared_nodes.p,
                                                           L.n_shared, u);
   SEM_CHECK_CUDA(cudaGetLastError());
@@ -124,6 +126,7 @@ void launch_mask(const Level &L, T *u, cudaStream_t st) {
   if (L.t.bc != SEM_DIRICHLET) return;
   const Topo &t = L.t;
   int64_t nfaces = 2 * ((int64_t)t.ey * t.ez + (int64_t)t.ex * t.ez + (int64_t)t.ex * t.ey);
+  TraceScope ts(sizeof(T) == 8 ? "mask_f64" : "mask_f32", t.N, st);
   mask_faces_kernel<T><<<grid_1d(nfaces * t.Np * t.Np, 256), 256, 0, st>>>(t, nfaces, u);
   SEM_CHECK_CUDA(cudaGetLastError());
 }

@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "pmg.cuh"
+#include "trace.cuh"
 
 namespace sem {
 
@@ -196,8 +197,11 @@ static double lanczos_lambda_max(Level &L, Reducer &R, int m, uint64_t seed, cud
   DevBuf<double> v, r, z, p, w, x, sc;
   v.alloc(t.nl); r.alloc(t.nl); z.alloc(t.nl); p.alloc(t.nl); w.alloc(t.nl); x.alloc(t.nl);
   sc.alloc(8);
+  {
+  TraceScope ts("lanczos_start", t.N, st);
   random_start_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, seed, v.p);
   SEM_CHECK_CUDA(cudaGetLastError());
+  }
   if (t.bc == SEM_NEUMANN) launch_remove_mean(t, R, v.p, sc.p + 7, st);
   SEM_CHECK_CUDA(cudaMemsetAsync(x.p, 0, t.nl * sizeof(double), st));
   // slots: 0 bb, 1 rr, 2 rho_a, 3 rho_b, 4 pw
@@ -311,12 +315,17 @@ static void smooth(sem_pmg *P, int l, bool x_zero, cudaStream_t st) {
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
   if (!x_zero) apply_assembled<T>(L, x, w, st);
+  const bool f64 = sizeof(T) == 8;
+  {
+  TraceScope ts(f64 ? "cheb_start_f64" : "cheb_start_f32", L.t.N, st);
   cheb_start_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(n, b, x_zero ? nullptr : w, dinv, r,
                                                             d, x, (T)(1.0 / theta), x_zero);
   SEM_CHECK_CUDA(cudaGetLastError());
+  }
   for (int it = 2; it <= P->desc.cheb_degree; ++it) {
     apply_assembled<T>(L, d, w, st);
     double rho1 = 1.0 / (2.0 * sigma - rho);
+    TraceScope ts(f64 ? "cheb_step_f64" : "cheb_step_f32", L.t.N, st);
     cheb_step_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(n, w, dinv, r, d, x,
                                                              (T)(rho1 * rho), (T)(2.0 * rho1 / delta));
     SEM_CHECK_CUDA(cudaGetLastError());
@@ -340,9 +349,12 @@ static void restrict_to(sem_pmg *P, int l, cudaStream_t st) {
   TransferParams tp = transfer_params(F, C);
   size_t shm = sizeof(double) * ((size_t)tp.npf * tp.npf * tp.npf + (size_t)tp.npc * tp.npf * tp.npf +
                                  (size_t)tp.npc * tp.npc * tp.npf);
+  {
+  TraceScope ts("restrict", F.L->t.N, st);
   restrict_kernel<Tf, Tc><<<grid_elems(tp.tf.E), 128, shm, st>>>(tp, vec_of<Tf>(F, 0),
                                                                   vec_of<Tf>(F, 4), vec_of<Tc>(C, 0));
   SEM_CHECK_CUDA(cudaGetLastError());
+  }
   launch_gs<Tc>(*C.L, vec_of<Tc>(C, 0), st);
   launch_mask<Tc>(*C.L, vec_of<Tc>(C, 0), st);
 }
@@ -353,6 +365,7 @@ static void prolong_from(sem_pmg *P, int l, cudaStream_t st) {
   TransferParams tp = transfer_params(F, C);
   size_t shm = sizeof(double) * ((size_t)tp.npc * tp.npc * tp.npc + (size_t)tp.npf * tp.npc * tp.npc +
                                  (size_t)tp.npf * tp.npf * tp.npc);
+  TraceScope ts("prolong", F.L->t.N, st);
   prolong_kernel<Tc, Tf><<<grid_elems(tp.tf.E), 128, shm, st>>>(tp, vec_of<Tc>(C, 1),
                                                                  vec_of<Tf>(F, 1));
   SEM_CHECK_CUDA(cudaGetLastError());

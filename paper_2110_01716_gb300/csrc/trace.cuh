@@ -1,0 +1,27 @@
+// trace.cuh -- per-class launch counters and event timers (see trace.cu).
+#pragma once
+
+#include <string>
+
+#include "common.cuh"
+
+namespace sem {
+
+// Counts one launch of class "<name>_N<order>" and, when the class matches
+// the timing filter, brackets it with CUDA events on `st`.  Construct it just
+// before the launch; it records the closing event when it goes out of scope.
+class TraceScope {
+ public:
+  TraceScope(const char *name, int N, cudaStream_t st);
+  ~TraceScope();
+  TraceScope(const TraceScope &) = delete;
+  TraceScope &operator=(const TraceScope &) = delete;
+
+ private:
+  cudaStream_t st_;
+  cudaEvent_t e0_{}, e1_{};
+  bool active_ = false;
+  std::string key_;
+};
+
+}  // namespace sem

@@ -11,6 +11,7 @@
 // Scalars live in device memory, so an iteration needs no host round trip.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "trace.cuh"
 
 namespace sem {
 
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(kVecThreads)
 void launch_dot(const Topo &t, Reducer &R, const double *u, const double *v, double *out,
                 cudaStream_t st) {
   OutPtrs<1> o{{out}};
+  TraceScope ts("dot", t.N, st);
   dot_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, u, v, R.partials.p, R.counter.p, o);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
@@ -135,6 +137,7 @@ void launch_cg_start(const Topo &t, Reducer &R, const double *b, const double *w
                      const double *dinv, double *r, double *z, double *p, double *bb, double *rr,
                      double *rz, cudaStream_t st) {
   OutPtrs<3> o{{bb, rr, rz}};
+  TraceScope ts("cg_start", t.N, st);
   cg_start_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, b, w, dinv, r, z, p, R.partials.p,
                                                           R.counter.p, o);
   SEM_CHECK_CUDA(cudaGetLastError());
@@ -174,6 +177,7 @@ void launch_cg_update(const Topo &t, Reducer &R, const double *rho, const double
                       const double *p, const double *w, const double *dinv, double *x, double *r,
                       double *z, double *rr, double *rz, const int *skip, cudaStream_t st) {
   OutPtrs<2> o{{rr, rz}};
+  TraceScope ts("cg_update", t.N, st);
   cg_update_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, rho, pw, p, w, dinv, x, r, z,
                                                            R.partials.p, R.counter.p, o, skip);
   SEM_CHECK_CUDA(cudaGetLastError());
@@ -194,6 +198,7 @@ __global__ void __launch_bounds__(kVecThreads)
 
 void launch_cg_direction(int64_t n, const double *num, const double *den, double sign,
                          const double *z, double *p, const int *skip, cudaStream_t st) {
+  TraceScope ts("cg_direction", 0, st);
   cg_direction_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(n, num, den, sign, z, p, skip);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
@@ -217,6 +222,7 @@ __global__ void __launch_bounds__(kVecThreads)
 void launch_flex_dots(const Topo &t, Reducer &R, const double *z, const double *r,
                       const double *w, double *zr, double *zw, cudaStream_t st) {
   OutPtrs<2> o{{zr, zw}};
+  TraceScope ts("flex_dots", t.N, st);
   flex_dots_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, z, r, w, R.partials.p,
                                                            R.counter.p, o);
   SEM_CHECK_CUDA(cudaGetLastError());
@@ -240,6 +246,7 @@ __global__ void __launch_bounds__(kVecThreads)
 void launch_dot_skip(const Topo &t, Reducer &R, const double *u, const double *v, double *out,
                      const int *skip, cudaStream_t st) {
   OutPtrs<1> o{{out}};
+  TraceScope ts("dot", t.N, st);
   dot_skip_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, u, v, R.partials.p, R.counter.p, o,
                                                           skip);
   SEM_CHECK_CUDA(cudaGetLastError());
@@ -256,6 +263,7 @@ __global__ void stop_test_kernel(const double *__restrict__ rr, const double *__
 
 void launch_stop_test(const double *rr, const double *bb, double tol2, int it, int maxit,
                       int *skip, int *iters, cudaStream_t st) {
+  TraceScope ts("stop_test", 0, st);
   stop_test_kernel<<<1, 1, 0, st>>>(rr, bb, tol2, it, maxit, skip, iters);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
@@ -270,6 +278,7 @@ __global__ void convert_kernel(int64_t n, const A *__restrict__ a, B *__restrict
 
 template <typename A, typename B>
 void launch_convert(int64_t n, const A *a, B *b, cudaStream_t st) {
+  TraceScope ts("convert", 0, st);
   convert_kernel<A, B><<<vec_grid(n), kVecThreads, 0, st>>>(n, a, b);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
@@ -299,6 +308,7 @@ __global__ void __launch_bounds__(kVecThreads)
 
 void launch_remove_mean(const Topo &t, Reducer &R, double *u, double *scratch, cudaStream_t st) {
   OutPtrs<1> o{{scratch}};
+  TraceScope ts("mean", t.N, st);
   sum_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, u, R.partials.p, R.counter.p, o);
   SEM_CHECK_CUDA(cudaGetLastError());
   sub_mean_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, scratch, u);
@@ -307,6 +317,7 @@ void launch_remove_mean(const Topo &t, Reducer &R, double *u, double *scratch, c
 
 void launch_sum(const Topo &t, Reducer &R, const double *u, double *out, cudaStream_t st) {
   OutPtrs<1> o{{out}};
+  TraceScope ts("sum", t.N, st);
   sum_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, u, R.partials.p, R.counter.p, o);
   SEM_CHECK_CUDA(cudaGetLastError());
 }

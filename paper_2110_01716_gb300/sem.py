@@ -30,7 +30,8 @@ SEM_MAX_ORDER = 11
 
 EXPORTED = ["sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_field", "sem_ax",
             "sem_gs", "sem_dot", "sem_pmg_setup", "sem_pmg_destroy", "sem_pmg_info",
-            "sem_pmg_vcycle", "sem_solve", "sem_solve_host", "sem_last_error"]
+            "sem_pmg_vcycle", "sem_solve", "sem_solve_host", "sem_trace_enable",
+            "sem_trace_read", "sem_last_error"]
 
 
 class SemError(RuntimeError):
@@ -54,6 +55,11 @@ class sem_pmg_desc(C.Structure):
 class sem_solve_desc(C.Structure):
     _fields_ = [("solver", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("check_every", C.c_int32)]
+
+
+class sem_trace_entry(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("timed", C.c_int64),
+                ("total_ms", C.c_double)]
 
 
 class sem_solve_info(C.Structure):
@@ -92,6 +98,8 @@ def lib():
     L.sem_solve.argtypes = [vp, vp, vp, vp, C.POINTER(sem_solve_desc), C.POINTER(sem_solve_info),
                             vp]
     L.sem_solve_host.argtypes = L.sem_solve.argtypes
+    L.sem_trace_enable.argtypes = [i32, C.c_char_p]
+    L.sem_trace_read.argtypes = [C.POINTER(sem_trace_entry), i32, C.POINTER(i32), i32]
     for name in EXPORTED:
         if name != "sem_last_error":
             getattr(L, name).restype = C.c_int
@@ -258,3 +266,17 @@ def sem_solve_host(mesh: Mesh, pmg, b_host, x_host, solver=SEM_SOLVER_PCG, tol=1
     d = info.as_dict()
     d["status"] = st
     return d
+
+
+def sem_trace_enable(enable: bool, timed_filter: str = ""):
+    check(lib().sem_trace_enable(int(bool(enable)), timed_filter.encode()))
+
+
+def sem_trace_read(reset: bool = True):
+    """{class name: {"launches", "timed", "total_ms"}} of the launches traced so far."""
+    n = C.c_int32()
+    check(lib().sem_trace_read(None, 0, C.byref(n), 0))
+    arr = (sem_trace_entry * max(n.value, 1))()
+    check(lib().sem_trace_read(arr, n.value, C.byref(n), int(bool(reset))))
+    return {e.name.decode(): {"launches": e.launches, "timed": e.timed, "total_ms": e.total_ms}
+            for e in arr[:n.value]}
