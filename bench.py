@@ -51,6 +51,11 @@ FALLBACK_HBM_GBS = 6800.0
 # FP64 pipe: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (the part's
 # nominal 1.25 TFLOP/s; an FMA-chain probe on this machine measured 1.195).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# The FP64 operator runs in FP32-pair arithmetic: one FP64-equivalent FMA
+# costs 12 FP32-pipe instructions, so its ALU roof is the FP32 issue rate
+# (152 SMs x 128 lanes x 2.07 GHz) / 12 x 2 flop.
+PAIR_INSTR_PER_FMA = 12
+PAIR_PEAK_TFLOPS = 152 * 128 * 2.07e9 / PAIR_INSTR_PER_FMA * 2 / 1e12
 # DRAM traffic of one fine-level FP64 operator launch from an ncu capture
 # (profiles/ax_f64_N7.txt), valid while the kernel source is unchanged.
 AX_TRAFFIC = {"source_sha256": None, "bytes_per_point": None}
@@ -172,12 +177,16 @@ def operator_sweep(sem, torch, dev, hbm):
     out = {}
     k = 64
     N = ORDER
-    for geom, gname in ((sem.SEM_GEOM_STORED, "stored"), (sem.SEM_GEOM_TRILINEAR, "trilinear")):
+    for geom, gname, arith in ((sem.SEM_GEOM_STORED, "stored", sem.SEM_ARITH_PAIR),
+                               (sem.SEM_GEOM_STORED, "stored_native", sem.SEM_ARITH_NATIVE),
+                               (sem.SEM_GEOM_TRILINEAR, "trilinear", sem.SEM_ARITH_NATIVE)):
         mesh = sem.Mesh(k, k, k, N, sem.SEM_DIRICHLET, geom,
-                        verts=inputs.box_vertices(k, k, k, 0.1, 2 + k))
+                        verts=inputs.box_vertices(k, k, k, 0.1, 2 + k), f64_arith=arith)
         n = mesh.n_local
-        for dt, tdt, name in ((sem.SEM_F64, torch.float64, "f64"), (sem.SEM_F32, torch.float32,
-                                                                      "f32")):
+        kinds = ((sem.SEM_F64, torch.float64, "f64"), (sem.SEM_F32, torch.float32, "f32"))
+        if gname == "stored_native":
+            kinds = kinds[:1]
+        for dt, tdt, name in kinds:
             u = torch.rand(n, device=dev, dtype=tdt, generator=torch.Generator(dev).manual_seed(5))
             w = torch.empty_like(u)
             st = torch.cuda.current_stream()
@@ -194,8 +203,9 @@ def operator_sweep(sem, torch, dev, hbm):
                 times.append(e0.elapsed_time(e1))
             ms = statistics.median(times)
             esz = 8 if name == "f64" else 4
-            bpp = 2 * esz + (6 * esz if gname == "stored" else 0)
-            bytes_alg = n * bpp + (mesh.ex * mesh.ey * mesh.ez * 24 * 8 if gname != "stored" else 0)
+            stored = gname.startswith("stored")
+            bpp = 2 * esz + (6 * esz if stored else 0)
+            bytes_alg = n * bpp + (mesh.ex * mesh.ey * mesh.ez * 24 * 8 if not stored else 0)
             flops = n * (12 * (N + 1) + 15)
             out[f"{name}_{gname}"] = {
                 "E": k ** 3, "ms": round(ms, 4), "gdofs_local": round(n / ms / 1e6, 3),
@@ -300,7 +310,7 @@ def main():
     for _ in range(max(args.warmup, 0)):
         info = step()
     # timed region
-    sem.sem_trace_enable(True, f"ax_f64_N{ORDER}")
+    sem.sem_trace_enable(True, f"ax_f64pair_N{ORDER}")
     sem.sem_trace_read(reset=True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -332,8 +342,9 @@ def main():
         if inf["status"] != sem.SEM_OK:
             raise SystemExit(f"solve did not converge: {inf}")
 
-    # dominant kernel: fine-level FP64 operator (FP64-pipe bound on GB300)
-    key = f"ax_f64_N{ORDER}"
+    # dominant kernel: fine-level FP64 operator in FP32-pair arithmetic
+    # (FP32-pipe bound on GB300)
+    key = f"ax_f64pair_N{ORDER}"
     ax = trace.get(key, {"launches": 0, "timed": 0, "total_ms": 0.0})
     ax_ms = ax["total_ms"] / max(ax["timed"], 1)
     nl = mesh.n_local
@@ -344,8 +355,8 @@ def main():
         traffic = AX_TRAFFIC["bytes_per_point"] * nl
     launches = sum(v["launches"] for v in trace.values())
     ax_share = ax["total_ms"] / total_ms if total_ms > 0 else None
-    roofline = {"bound": "alu", "achieved": ax_tflops, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": (ax_tflops / FP64_PEAK_TFLOPS) if ax_tflops else None,
+    roofline = {"bound": "alu", "achieved": ax_tflops, "peak": PAIR_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": (ax_tflops / PAIR_PEAK_TFLOPS) if ax_tflops else None,
                 "traffic": traffic, "kernel": key,
                 "per_launch_ms": ax_ms, "launches_timed": ax["timed"],
                 "share_of_step": ax_share,
@@ -353,7 +364,9 @@ def main():
                                f"64 B/pt x {nl} = {64 * nl / 1e9:.2f} GB",
                 "hbm_GB_s": (64 * nl / (ax_ms / 1e3) / 1e9) if ax_ms > 0 else None,
                 "hbm_frac": (64 * nl / (ax_ms / 1e3) / 1e9 / hbm) if ax_ms > 0 else None,
-                "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz; "
+                "peak_source": "derived: FP32 issue 152 SM x 128 lanes x 2.07 GHz / "
+                               f"{PAIR_INSTR_PER_FMA} instr per FP64-equivalent FMA x 2 flop "
+                               f"(native FP64 pipe: {FP64_PEAK_TFLOPS:.3f}); "
                                f"HBM {hbm} GB/s {hbm_src}"}
 
     line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,

@@ -56,6 +56,12 @@ typedef enum { SEM_F64 = 0, SEM_F32 = 1, SEM_F16 = 2, SEM_BF16 = 3 } sem_dtype;
 
 enum { SEM_DIRICHLET = 0, SEM_NEUMANN = 1 };
 enum { SEM_GEOM_STORED = 0, SEM_GEOM_TRILINEAR = 1 };
+/* How FP64 operator applications are computed (results agree to ~1e-14):
+ * SEM_ARITH_PAIR   FP32-pair ("double-float") arithmetic on the FP32 pipes,
+ *                  geometric factors stored as hi/lo float pairs (default);
+ * SEM_ARITH_NATIVE native FP64 instructions, factors stored as doubles.
+ * Recomputed (trilinear) geometry always uses native FP64. */
+enum { SEM_ARITH_PAIR = 0, SEM_ARITH_NATIVE = 1 };
 
 typedef struct sem_mesh sem_mesh;
 typedef struct sem_pmg sem_pmg;
@@ -78,6 +84,7 @@ typedef struct {
   int32_t bc;
   int32_t geom;
   const double *verts;
+  int32_t f64_arith;   /* SEM_ARITH_PAIR or SEM_ARITH_NATIVE */
 } sem_mesh_desc;
 
 #define SEM_MAX_ORDER 11

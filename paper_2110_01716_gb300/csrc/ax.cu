@@ -150,6 +150,12 @@ static void ax_dispatch_geom(const Level &L, const T *u, T *w, cudaStream_t st) 
 
 template <typename T>
 void launch_ax(const Level &L, const T *u, T *w, cudaStream_t st) {
+  if constexpr (sizeof(T) == 8) {
+    if (L.geom == SEM_GEOM_STORED && L.arith == SEM_ARITH_PAIR) {
+      launch_ax_pair(L, u, w, st);
+      return;
+    }
+  }
   switch (L.t.Np) {
     case 2: ax_dispatch_geom<T, 2>(L, u, w, st); break;
     case 3: ax_dispatch_geom<T, 3>(L, u, w, st); break;

@@ -197,7 +197,8 @@ sem_status sem_mesh_create(const sem_mesh_desc *desc, void *stream, sem_mesh **o
     std::unique_ptr<sem_mesh> M(new sem_mesh());
     cudaStream_t st = as_stream(stream);
     M->stream = st;
-    build_level(M->fine, desc->ex, desc->ey, desc->ez, desc->N, desc->bc, desc->geom, v, false, st);
+    build_level(M->fine, desc->ex, desc->ey, desc->ez, desc->N, desc->bc, desc->geom,
+                desc->f64_arith, v, false, st);
     M->red.init(kVecMaxBlocks, 4);
     M->scal.alloc(16);
     SEM_CHECK_CUDA(cudaMemsetAsync(M->scal.p, 0, 16 * sizeof(double), st));

@@ -107,9 +107,18 @@ struct PointInfo {
   uint32_t e, p;         // element, point in element
   int i, j, k;           // point indices
   int ix, iy, iz;        // element indices
+  int log2_mult;         // number of copies = 2^log2_mult (0..3)
   float inv_mult;        // 1 / number of copies (exact: 1, 1/2, 1/4, 1/8)
   float mask;            // 0 on the Dirichlet boundary, else 1
 };
+
+// v / 2^k for k in 0..3 through the exponent field (integer instructions only,
+// which keeps the scarce FP64 pipe free); values too small to scale become 0.
+__device__ __forceinline__ double scale_pow2_down(double v, int k) {
+  long long b = __double_as_longlong(v);
+  long long ex = (b >> 52) & 0x7FF;
+  return ex > k ? __longlong_as_double(b - ((long long)k << 52)) : 0.0;
+}
 
 __device__ __forceinline__ PointInfo point_info(uint32_t l, const Topo &t) {
   PointInfo q;
@@ -125,7 +134,8 @@ __device__ __forceinline__ PointInfo point_info(uint32_t l, const Topo &t) {
   q.iy = (int)(yz - (uint32_t)q.iz * t.ey);
   uint32_t pf = point_face_bits(q.i, q.j, q.k, t.N);
   uint32_t ef = elem_face_bits(q.ix, q.iy, q.iz, t);
-  q.inv_mult = 1.0f / (float)(1u << __popc(pf & ~ef));
+  q.log2_mult = __popc(pf & ~ef);
+  q.inv_mult = 1.0f / (float)(1u << q.log2_mult);
   q.mask = (t.bc == SEM_DIRICHLET && (pf & ef)) ? 0.0f : 1.0f;
   return q;
 }
@@ -151,17 +161,19 @@ struct Level {
   Topo t{};
   Basis basis{};
   int32_t geom = SEM_GEOM_STORED;
+  int32_t arith = SEM_ARITH_PAIR;  // FP64 operator arithmetic (stored geometry)
   std::vector<double> verts_host;  // lattice [(ex+1)(ey+1)(ez+1)][3]
   DevBuf<double> verts;            // per element [E][8][3], corner (a,b,c) at a+2b+4c
   DevBuf<double> G64;              // [E][6][Np3]  (rr, rs, rt, ss, st, tt)
   DevBuf<float> G32;               // [E][6][Np3]
+  DevBuf<float2> G2;               // [E][6][Np3] FP64 factors split into float pairs
   DevBuf<int32_t> shared_nodes;    // unique ids of nodes with more than one copy
   int64_t n_shared = 0;
   DevBuf<double> dinv64;           // mask / assembled diagonal
   DevBuf<float> dinv32;
   size_t device_bytes() const {
-    return verts.bytes() + G64.bytes() + G32.bytes() + shared_nodes.bytes() + dinv64.bytes() +
-           dinv32.bytes();
+    return verts.bytes() + G64.bytes() + G32.bytes() + G2.bytes() + shared_nodes.bytes() +
+           dinv64.bytes() + dinv32.bytes();
   }
 };
 
@@ -171,8 +183,9 @@ void derivative_matrix(int N, const double *xi, double *D);
 void interpolation_matrix(int Nf, int Nc, double *J);
 
 // ------------------------------------------------------------------ launches
-void build_level(Level &L, int ex, int ey, int ez, int N, int bc, int geom,
+void build_level(Level &L, int ex, int ey, int ez, int N, int bc, int geom, int arith,
                  const double *verts_host, bool want_g32, cudaStream_t st);
+void launch_ax_pair(const Level &L, const double *u, double *w, cudaStream_t st);
 void level_ensure_f32(Level &L, cudaStream_t st);
 
 template <typename T>

@@ -60,42 +60,65 @@ struct TransferParams {
   double J[kMaxNp * kMaxNp];  // J[i*npc + a]: coarse basis a at fine node i
 };
 
+// Arithmetic of a transfer: FP32 when either level smooths in FP32 (the data
+// carries single precision then), FP64 otherwise.
+template <typename A, typename B>
+struct TransferCompute {
+  using type = double;
+};
+template <>
+struct TransferCompute<float, float> {
+  using type = float;
+};
+template <>
+struct TransferCompute<float, double> {
+  using type = float;
+};
+template <>
+struct TransferCompute<double, float> {
+  using type = float;
+};
+
 // Restriction of the fine residual b - w, weighted by 1/mult, to unassembled
 // coarse values: out_e = (J^T x J^T x J^T) ((b - w)/mult)_e.  One CTA per element.
 template <typename Tf, typename Tc>
 __global__ void restrict_kernel(TransferParams tp, const Tf *__restrict__ b,
                                 const Tf *__restrict__ w, Tc *__restrict__ out) {
-  extern __shared__ double sm[];
+  using R = typename TransferCompute<Tf, Tc>::type;
+  extern __shared__ double sm_raw[];
+  R *sm = reinterpret_cast<R *>(sm_raw);
+  __shared__ R sJ[kMaxNp * kMaxNp];
   const int nf = tp.npf, nc = tp.npc;
   const int nf3 = nf * nf * nf;
-  double *s0 = sm;                    // nf^3
-  double *s1 = s0 + nf3;              // nc nf nf
-  double *s2 = s1 + nc * nf * nf;     // nc nc nf
+  R *s0 = sm;                    // nf^3
+  R *s1 = s0 + nf3;              // nc nf nf
+  R *s2 = s1 + nc * nf * nf;     // nc nc nf
+  for (int q = threadIdx.x; q < nf * nc; q += blockDim.x) sJ[q] = (R)tp.J[q];
   for (int64_t e = blockIdx.x; e < tp.tf.E; e += gridDim.x) {
     for (int q = threadIdx.x; q < nf3; q += blockDim.x) {
       uint32_t l = (uint32_t)(e * nf3 + q);
       PointInfo pi = point_info(l, tp.tf);
-      s0[q] = ((double)b[l] - (double)w[l]) * (double)pi.inv_mult;
+      s0[q] = ((R)b[l] - (R)w[l]) * (R)pi.inv_mult;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nc * nf * nf; q += blockDim.x) {
       int a = q % nc, jk = q / nc;
-      double s = 0.0;
-      for (int i = 0; i < nf; ++i) s += tp.J[i * nc + a] * s0[i + nf * jk];
+      R s = 0;
+      for (int i = 0; i < nf; ++i) s += sJ[i * nc + a] * s0[i + nf * jk];
       s1[q] = s;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nc * nc * nf; q += blockDim.x) {
       int a = q % nc, bk = q / nc, bb = bk % nc, k = bk / nc;
-      double s = 0.0;
-      for (int j = 0; j < nf; ++j) s += tp.J[j * nc + bb] * s1[a + nc * (j + nf * k)];
+      R s = 0;
+      for (int j = 0; j < nf; ++j) s += sJ[j * nc + bb] * s1[a + nc * (j + nf * k)];
       s2[q] = s;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nc * nc * nc; q += blockDim.x) {
       int ab = q % (nc * nc), c = q / (nc * nc);
-      double s = 0.0;
-      for (int k = 0; k < nf; ++k) s += tp.J[k * nc + c] * s2[ab + nc * nc * k];
+      R s = 0;
+      for (int k = 0; k < nf; ++k) s += sJ[k * nc + c] * s2[ab + nc * nc * k];
       out[e * nc * nc * nc + q] = (Tc)s;
     }
     __syncthreads();
@@ -105,34 +128,38 @@ __global__ void restrict_kernel(TransferParams tp, const Tf *__restrict__ b,
 // Prolongation and correction: x_f += (J x J x J) x_c.  One CTA per element.
 template <typename Tc, typename Tf>
 __global__ void prolong_kernel(TransferParams tp, const Tc *__restrict__ xc, Tf *__restrict__ xf) {
-  extern __shared__ double sm[];
+  using R = typename TransferCompute<Tf, Tc>::type;
+  extern __shared__ double sm_raw[];
+  R *sm = reinterpret_cast<R *>(sm_raw);
+  __shared__ R sJ[kMaxNp * kMaxNp];
   const int nf = tp.npf, nc = tp.npc;
   const int nc3 = nc * nc * nc, nf3 = nf * nf * nf;
-  double *s0 = sm;                // nc^3
-  double *s1 = s0 + nc3;          // nf nc nc
-  double *s2 = s1 + nf * nc * nc; // nf nf nc
+  R *s0 = sm;                // nc^3
+  R *s1 = s0 + nc3;          // nf nc nc
+  R *s2 = s1 + nf * nc * nc; // nf nf nc
+  for (int q = threadIdx.x; q < nf * nc; q += blockDim.x) sJ[q] = (R)tp.J[q];
   for (int64_t e = blockIdx.x; e < tp.tf.E; e += gridDim.x) {
-    for (int q = threadIdx.x; q < nc3; q += blockDim.x) s0[q] = (double)xc[e * nc3 + q];
+    for (int q = threadIdx.x; q < nc3; q += blockDim.x) s0[q] = (R)xc[e * nc3 + q];
     __syncthreads();
     for (int q = threadIdx.x; q < nf * nc * nc; q += blockDim.x) {
       int i = q % nf, bc = q / nf;
-      double s = 0.0;
-      for (int a = 0; a < nc; ++a) s += tp.J[i * nc + a] * s0[a + nc * bc];
+      R s = 0;
+      for (int a = 0; a < nc; ++a) s += sJ[i * nc + a] * s0[a + nc * bc];
       s1[q] = s;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nf * nf * nc; q += blockDim.x) {
       int i = q % nf, jc = q / nf, j = jc % nf, c = jc / nf;
-      double s = 0.0;
-      for (int b = 0; b < nc; ++b) s += tp.J[j * nc + b] * s1[i + nf * (b + nc * c)];
+      R s = 0;
+      for (int b = 0; b < nc; ++b) s += sJ[j * nc + b] * s1[i + nf * (b + nc * c)];
       s2[q] = s;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nf3; q += blockDim.x) {
       int ij = q % (nf * nf), k = q / (nf * nf);
-      double s = 0.0;
-      for (int c = 0; c < nc; ++c) s += tp.J[k * nc + c] * s2[ij + nf * nf * c];
-      xf[e * nf3 + q] = (Tf)((double)xf[e * nf3 + q] + s);
+      R s = 0;
+      for (int c = 0; c < nc; ++c) s += sJ[k * nc + c] * s2[ij + nf * nf * c];
+      xf[e * nf3 + q] = (Tf)((R)xf[e * nf3 + q] + s);
     }
     __syncthreads();
   }
@@ -274,7 +301,9 @@ void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t s
       Q.L = &mesh->fine;
     } else {
       Q.own.reset(new Level());
-      build_level(*Q.own, F.t.ex, F.t.ey, F.t.ez, d.orders[l], F.t.bc, SEM_GEOM_STORED,
+      // the N = 1 coarsest level keeps FP64 factors for its element matrices
+      const int arith = (coarsest && d.orders[l] == 1) ? SEM_ARITH_NATIVE : F.arith;
+      build_level(*Q.own, F.t.ex, F.t.ey, F.t.ez, d.orders[l], F.t.bc, SEM_GEOM_STORED, arith,
                   F.verts_host.data(), Q.dtype == SEM_F32, st);
       Q.L = Q.own.get();
     }
@@ -293,9 +322,15 @@ void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t s
       interpolation_matrix(d.orders[l], d.orders[l + 1], Q.J.data());
     }
   }
-  // coarse-solve Krylov vectors (FP64)
-  const int64_t nc = (*P->levp.back()).L->t.nl;
-  P->cz.alloc(nc); P->cp.alloc(nc); P->cw.alloc(nc);
+  // coarse solve: one persistent kernel at N = 1, launch-based Jacobi-PCG otherwise
+  PmgLevel &Cl = *P->levp.back();
+  P->persistent_coarse = Cl.L->t.N == 1 && Cl.L->G64.p != nullptr;
+  if (P->persistent_coarse) {
+    coarse_setup(P->coarse, *Cl.L, st);
+  } else {
+    const int64_t nc = Cl.L->t.nl;
+    P->cz.alloc(nc); P->cp.alloc(nc); P->cw.alloc(nc);
+  }
   P->z64.alloc(F.t.nl);
   SEM_CHECK_CUDA(cudaStreamSynchronize(st));
 }
@@ -376,6 +411,11 @@ static void prolong_from(sem_pmg *P, int l, cudaStream_t st) {
 static void coarse_solve(sem_pmg *P, cudaStream_t st) {
   PmgLevel &Q = (*P->levp.back());
   Level &L = *Q.L;
+  if (P->persistent_coarse) {
+    coarse_solve_persistent(P->coarse, L, Q.v64[0].p, Q.v64[1].p, P->desc.coarse_tol,
+                            P->desc.coarse_maxit, st);
+    return;
+  }
   const Topo &t = L.t;
   double *b = Q.v64[0].p, *x = Q.v64[1].p, *r = Q.v64[2].p;
   double *z = P->cz.p, *p = P->cp.p, *w = P->cw.p;

@@ -4,6 +4,7 @@
 #include <memory>
 #include <vector>
 
+#include "coarse.cuh"
 #include "common.cuh"
 
 namespace sem {
@@ -31,4 +32,6 @@ struct sem_pmg {
   sem::DevBuf<double> scal;
   sem::DevBuf<int> flags;
   sem::DevBuf<double> cz, cp, cw, z64;
+  sem::CoarseSolver coarse;   // persistent solver when the coarsest order is 1
+  bool persistent_coarse = false;
 };

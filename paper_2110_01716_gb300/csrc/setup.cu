@@ -107,7 +107,7 @@ Basis make_basis(int N) {
 // Geometric factors of every point from the element's 8 vertices (setup).
 __global__ void geometry_kernel(Topo t, Basis bs, const double *__restrict__ verts,
                                 double *__restrict__ G64, float *__restrict__ G32,
-                                int *__restrict__ bad) {
+                                float2 *__restrict__ G2, int *__restrict__ bad) {
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
        l += gridDim.x * blockDim.x) {
     uint32_t e = t.div_np3.div(l);
@@ -128,6 +128,10 @@ __global__ void geometry_kernel(Topo t, Basis bs, const double *__restrict__ ver
     for (int f = 0; f < 6; ++f) {
       if (G64) G64[base + (size_t)f * t.Np3] = g[f];
       if (G32) G32[base + (size_t)f * t.Np3] = (float)g[f];
+      if (G2) {
+        const float hi = (float)g[f];
+        G2[base + (size_t)f * t.Np3] = make_float2(hi, (float)(g[f] - (double)hi));
+      }
     }
   }
 }
@@ -256,7 +260,7 @@ static std::vector<int32_t> shared_node_table(const Topo &t) {
   return out;
 }
 
-void build_level(Level &L, int ex, int ey, int ez, int N, int bc, int geom,
+void build_level(Level &L, int ex, int ey, int ez, int N, int bc, int geom, int arith,
                  const double *verts_host, bool want_g32, cudaStream_t st) {
   SEM_REQUIRE(ex >= 1 && ey >= 1 && ez >= 1, "element counts must be >= 1 (got %d %d %d)", ex,
               ey, ez);
@@ -264,12 +268,15 @@ void build_level(Level &L, int ex, int ey, int ez, int N, int bc, int geom,
   SEM_REQUIRE(bc == SEM_DIRICHLET || bc == SEM_NEUMANN, "unknown boundary condition %d", bc);
   SEM_REQUIRE(geom == SEM_GEOM_STORED || geom == SEM_GEOM_TRILINEAR, "unknown geometry mode %d",
               geom);
+  SEM_REQUIRE(arith == SEM_ARITH_PAIR || arith == SEM_ARITH_NATIVE, "unknown FP64 arithmetic %d",
+              arith);
   Topo t = make_topo(ex, ey, ez, N, bc);
   SEM_REQUIRE(t.nl <= 0x7fffffffLL && t.ng <= 0x7fffffffLL,
               "mesh too large: %lld local points (limit 2^31-1)", (long long)t.nl);
   L.t = t;
   L.basis = make_basis(N);
   L.geom = geom;
+  L.arith = arith;
   size_t nv = (size_t)(ex + 1) * (ey + 1) * (ez + 1);
   L.verts_host.assign(verts_host, verts_host + 3 * nv);
   // per-element corners
@@ -294,15 +301,17 @@ void build_level(Level &L, int ex, int ey, int ez, int N, int bc, int geom,
   // geometric factors: always computed once (they also give the diagonal)
   DevBuf<double> Gtmp;
   double *G = nullptr;
-  if (geom == SEM_GEOM_STORED) {
+  if (geom == SEM_GEOM_STORED && arith == SEM_ARITH_NATIVE) {
     L.G64.alloc((size_t)t.E * 6 * t.Np3);
     G = L.G64.p;
   } else {
     Gtmp.alloc((size_t)t.E * 6 * t.Np3);
     G = Gtmp.p;
   }
+  if (geom == SEM_GEOM_STORED && arith == SEM_ARITH_PAIR) L.G2.alloc((size_t)t.E * 6 * t.Np3);
   if (want_g32) L.G32.alloc((size_t)t.E * 6 * t.Np3);
-  geometry_kernel<<<grid_for(t.nl, 256), 256, 0, st>>>(t, L.basis, L.verts.p, G, L.G32.p, bad.p);
+  geometry_kernel<<<grid_for(t.nl, 256), 256, 0, st>>>(t, L.basis, L.verts.p, G, L.G32.p, L.G2.p,
+                                                       bad.p);
   SEM_CHECK_CUDA(cudaGetLastError());
   int hbad = 0;
   SEM_CHECK_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -330,26 +339,26 @@ void build_level(Level &L, int ex, int ey, int ez, int N, int bc, int geom,
 
 void level_ensure_f32(Level &L, cudaStream_t st) {
   const Topo &t = L.t;
+  const bool need_g32 = L.geom == SEM_GEOM_STORED && !L.G32.p;
+  if (L.dinv32.p && !need_g32) return;
+  // FP64 factors again (temporarily): they give the FP32 copies and the diagonal
+  DevBuf<int> bad;
+  bad.alloc(1);
+  SEM_CHECK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+  DevBuf<double> g;
+  g.alloc((size_t)t.E * 6 * t.Np3);
+  if (need_g32) L.G32.alloc((size_t)t.E * 6 * t.Np3);
+  geometry_kernel<<<grid_for(t.nl, 256), 256, 0, st>>>(t, L.basis, L.verts.p, g.p,
+                                                       need_g32 ? L.G32.p : nullptr, nullptr, bad.p);
+  SEM_CHECK_CUDA(cudaGetLastError());
   if (!L.dinv32.p) {
     L.dinv32.alloc(t.nl);
     DevBuf<double> d;
     d.alloc(t.nl);
-    // recover the assembled diagonal from its inverse is lossy at masked
-    // points; recompute it instead
-    local_diag_kernel<<<grid_for(t.nl, 256), 256, 0, st>>>(t, L.basis, L.G64.p, L.verts.p, d.p);
+    local_diag_kernel<<<grid_for(t.nl, 256), 256, 0, st>>>(t, L.basis, g.p, L.verts.p, d.p);
     SEM_CHECK_CUDA(cudaGetLastError());
     launch_gs<double>(L, d.p, st);
     invert_diag_kernel<<<grid_for(t.nl, 256), 256, 0, st>>>(t, d.p, nullptr, L.dinv32.p);
-    SEM_CHECK_CUDA(cudaGetLastError());
-  }
-  if (L.geom == SEM_GEOM_STORED && !L.G32.p) {
-    L.G32.alloc((size_t)t.E * 6 * t.Np3);
-    DevBuf<int> bad;
-    bad.alloc(1);
-    SEM_CHECK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
-    DevBuf<double> g;
-    g.alloc((size_t)t.E * 6 * t.Np3);
-    geometry_kernel<<<grid_for(t.nl, 256), 256, 0, st>>>(t, L.basis, L.verts.p, g.p, L.G32.p, bad.p);
     SEM_CHECK_CUDA(cudaGetLastError());
   }
   SEM_CHECK_CUDA(cudaStreamSynchronize(st));

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kVecThreads)
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
        l += gridDim.x * blockDim.x) {
     PointInfo q = point_info(l, t);
-    acc[0] += u[l] * v[l] * (double)q.inv_mult;
+    acc[0] = fma(scale_pow2_down(u[l], q.log2_mult), v[l], acc[0]);
   }
   grid_reduce<1>(acc, partials, counter, out.p);
 }
@@ -105,7 +105,7 @@ void launch_dot(const Topo &t, Reducer &R, const double *u, const double *v, dou
 }
 
 // ------------------------------------------------------------------ CG start
-// r = b - mask(w) (w = A x assembled, or r = b when w == null),
+// r = b - w (w = A x assembled and masked, or r = b when w == null),
 // z = dinv r (Jacobi) or z untouched (flexible: z comes from the V-cycle),
 // p = z;  sums: bb = <b,b>, rr = <r,r>, rz = <r,z>.
 __global__ void __launch_bounds__(kVecThreads)
@@ -118,16 +118,16 @@ __global__ void __launch_bounds__(kVecThreads)
        l += gridDim.x * blockDim.x) {
     PointInfo q = point_info(l, t);
     double bl = b[l];
-    double rl = bl - (w ? (double)q.mask * w[l] : 0.0);
+    double rl = w ? bl - w[l] : bl;
     r[l] = rl;
-    double im = (double)q.inv_mult;
-    acc[0] += bl * bl * im;
-    acc[1] += rl * rl * im;
+    double rs = scale_pow2_down(rl, q.log2_mult);
+    acc[0] = fma(scale_pow2_down(bl, q.log2_mult), bl, acc[0]);
+    acc[1] = fma(rs, rl, acc[1]);
     if (dinv) {
       double zl = dinv[l] * rl;
       z[l] = zl;
       p[l] = zl;
-      acc[2] += rl * zl * im;
+      acc[2] = fma(rs, zl, acc[2]);
     }
   }
   grid_reduce<3>(acc, partials, counter, out.p);
@@ -144,7 +144,7 @@ void launch_cg_start(const Topo &t, Reducer &R, const double *b, const double *w
 }
 
 // ------------------------------------------------------------------ CG iteration
-// alpha = rho / pw;  x += alpha p;  r -= alpha mask(w);  rr = <r,r>;
+// alpha = rho / pw;  x += alpha p;  r -= alpha w (w masked);  rr = <r,r>;
 // Jacobi: z = dinv r and rz = <r,z>.  skip != null: the whole kernel is a
 // no-op once *skip is set (device-side stop of the coarse solve).
 __global__ void __launch_bounds__(kVecThreads)
@@ -159,15 +159,15 @@ __global__ void __launch_bounds__(kVecThreads)
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
        l += gridDim.x * blockDim.x) {
     PointInfo q = point_info(l, t);
-    x[l] += alpha * p[l];
-    double rl = r[l] - alpha * (double)q.mask * w[l];
+    x[l] = fma(alpha, p[l], x[l]);
+    double rl = fma(-alpha, w[l], r[l]);
     r[l] = rl;
-    double im = (double)q.inv_mult;
-    acc[0] += rl * rl * im;
+    double rs = scale_pow2_down(rl, q.log2_mult);
+    acc[0] = fma(rs, rl, acc[0]);
     if (dinv) {
       double zl = dinv[l] * rl;
       z[l] = zl;
-      acc[1] += rl * zl * im;
+      acc[1] = fma(rs, zl, acc[1]);
     }
   }
   grid_reduce<2>(acc, partials, counter, out.p);
@@ -203,7 +203,7 @@ void launch_cg_direction(int64_t n, const double *num, const double *den, double
   SEM_CHECK_CUDA(cudaGetLastError());
 }
 
-// Flexible CG after the preconditioner: zr = <z, r>, zw = <z, mask(w)>.
+// Flexible CG after the preconditioner: zr = <z, r>, zw = <z, w> (w masked).
 __global__ void __launch_bounds__(kVecThreads)
     flex_dots_kernel(Topo t, const double *__restrict__ z, const double *__restrict__ r,
                      const double *__restrict__ w, double *partials, unsigned int *counter,
@@ -212,9 +212,9 @@ __global__ void __launch_bounds__(kVecThreads)
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
        l += gridDim.x * blockDim.x) {
     PointInfo q = point_info(l, t);
-    double zl = z[l] * (double)q.inv_mult;
-    acc[0] += zl * r[l];
-    acc[1] += zl * (double)q.mask * w[l];
+    double zl = scale_pow2_down(z[l], q.log2_mult);
+    acc[0] = fma(zl, r[l], acc[0]);
+    acc[1] = fma(zl, w[l], acc[1]);
   }
   grid_reduce<2>(acc, partials, counter, out.p);
 }
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kVecThreads)
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
        l += gridDim.x * blockDim.x) {
     PointInfo q = point_info(l, t);
-    acc[0] += u[l] * v[l] * (double)q.inv_mult;
+    acc[0] = fma(scale_pow2_down(u[l], q.log2_mult), v[l], acc[0]);
   }
   grid_reduce<1>(acc, partials, counter, out.p);
 }
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kVecThreads)
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
        l += gridDim.x * blockDim.x) {
     PointInfo q = point_info(l, t);
-    acc[0] += u[l] * (double)q.inv_mult;
+    acc[0] += scale_pow2_down(u[l], q.log2_mult);
   }
   grid_reduce<1>(acc, partials, counter, out.p);
 }

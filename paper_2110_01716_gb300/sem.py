@@ -22,6 +22,7 @@ STATUS_NAMES = ["SEM_OK", "SEM_EINVAL", "SEM_ENOMEM", "SEM_ECUDA", "SEM_ENOTCONV
 SEM_F64, SEM_F32, SEM_F16, SEM_BF16 = range(4)
 SEM_DIRICHLET, SEM_NEUMANN = 0, 1
 SEM_GEOM_STORED, SEM_GEOM_TRILINEAR = 0, 1
+SEM_ARITH_PAIR, SEM_ARITH_NATIVE = 0, 1
 SEM_AX_LOCAL, SEM_AX_ASSEMBLED = 0, 1
 SEM_FIELD_X, SEM_FIELD_Y, SEM_FIELD_Z, SEM_FIELD_MASS, SEM_FIELD_MULT, SEM_FIELD_MASK, \
     SEM_FIELD_DINV = range(7)
@@ -43,7 +44,7 @@ class SemError(RuntimeError):
 class sem_mesh_desc(C.Structure):
     _fields_ = [("ex", C.c_int32), ("ey", C.c_int32), ("ez", C.c_int32), ("N", C.c_int32),
                 ("jitter", C.c_double), ("seed", C.c_uint64), ("bc", C.c_int32),
-                ("geom", C.c_int32), ("verts", C.c_void_p)]
+                ("geom", C.c_int32), ("verts", C.c_void_p), ("f64_arith", C.c_int32)]
 
 
 class sem_pmg_desc(C.Structure):
@@ -140,7 +141,7 @@ class Mesh:
     """Owning wrapper of a sem_mesh handle."""
 
     def __init__(self, ex, ey, ez, N, bc=SEM_DIRICHLET, geom=SEM_GEOM_STORED, verts=None,
-                 jitter=0.1, seed=1, stream=None):
+                 jitter=0.1, seed=1, stream=None, f64_arith=SEM_ARITH_PAIR):
         import numpy as np
 
         self._verts = None
@@ -148,11 +149,12 @@ class Mesh:
         if verts is not None:
             self._verts = np.ascontiguousarray(verts, dtype=np.float64)
             vptr = self._verts.ctypes.data
-        desc = sem_mesh_desc(ex, ey, ez, N, float(jitter), int(seed), bc, geom, vptr)
+        desc = sem_mesh_desc(ex, ey, ez, N, float(jitter), int(seed), bc, geom, vptr, f64_arith)
         h = C.c_void_p()
         check(lib().sem_mesh_create(C.byref(desc), _stream(stream), C.byref(h)))
         self.h = h
         self.ex, self.ey, self.ez, self.N, self.bc, self.geom = ex, ey, ez, N, bc, geom
+        self.f64_arith = f64_arith
         nl, ng, nb = C.c_int64(), C.c_int64(), C.c_size_t()
         check(lib().sem_mesh_info(self.h, C.byref(nl), C.byref(ng), C.byref(nb)))
         self.n_local, self.n_global = nl.value, ng.value

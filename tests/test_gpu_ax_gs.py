@@ -41,9 +41,16 @@ def _build():
     oracle.build()
 
 
-def make(ex, ey, ez, N, bc=0, geom=sem.SEM_GEOM_STORED, seed=3):
+def make(ex, ey, ez, N, bc=0, geom=sem.SEM_GEOM_STORED, seed=3, arith=sem.SEM_ARITH_PAIR):
     v = inputs.box_vertices(ex, ey, ez, 0.1, seed)
-    return sem.Mesh(ex, ey, ez, N, bc, geom, verts=v), oracle.Level(ex, ey, ez, N, bc, v), v
+    return (sem.Mesh(ex, ey, ez, N, bc, geom, verts=v, f64_arith=arith),
+            oracle.Level(ex, ey, ez, N, bc, v), v)
+
+
+# (geometry, FP64 arithmetic): stored factors with FP32-pair or native FP64
+# arithmetic, and recomputed trilinear factors (native FP64)
+MODES = [(sem.SEM_GEOM_STORED, sem.SEM_ARITH_PAIR), (sem.SEM_GEOM_STORED, sem.SEM_ARITH_NATIVE),
+         (sem.SEM_GEOM_TRILINEAR, sem.SEM_ARITH_NATIVE)]
 
 
 CASES = [(1, 1, 1, 1), (2, 3, 2, 2), (3, 2, 4, 3), (5, 3, 2, 4), (2, 2, 3, 5), (3, 4, 2, 6),
@@ -51,9 +58,9 @@ CASES = [(1, 1, 1, 1), (2, 3, 2, 2), (3, 2, 4, 3), (5, 3, 2, 4), (2, 2, 3, 5), (
 
 
 @pytest.mark.parametrize("ex,ey,ez,N", CASES)
-@pytest.mark.parametrize("geom", [sem.SEM_GEOM_STORED, sem.SEM_GEOM_TRILINEAR])
-def test_ax_fp64_matches_oracle(ex, ey, ez, N, geom):
-    m, L, _ = make(ex, ey, ez, N, geom=geom)
+@pytest.mark.parametrize("geom,arith", MODES)
+def test_ax_fp64_matches_oracle(ex, ey, ez, N, geom, arith):
+    m, L, _ = make(ex, ey, ez, N, geom=geom, arith=arith)
     u = inputs.random_field(L.nl, 11)
     ud = torch.tensor(u, device=DEV)
     wd = torch.empty_like(ud)
@@ -85,6 +92,35 @@ def test_ax_dirichlet_and_neumann_masks():
         wd = torch.empty_like(ud)
         sem.sem_ax(m, sem.SEM_F64, ud, wd, sem.SEM_AX_ASSEMBLED)
         assert rel(wd.cpu().numpy(), L.ax(u)) < TOL64
+
+
+def test_ax_pair_arithmetic_on_wide_dynamic_range():
+    """FP32-pair arithmetic keeps FP64 accuracy for inputs spanning many
+    decades, signed zeros and exact zeros."""
+    m, L, _ = make(3, 2, 2, 6)
+    rng = np.random.Generator(np.random.PCG64(77))
+    u = rng.uniform(-1, 1, L.nl) * 10.0 ** rng.uniform(-30, 30, L.nl)
+    u[::17] = 0.0
+    u[5::19] = -0.0
+    ud = torch.tensor(u, device=DEV)
+    wd = torch.empty_like(ud)
+    sem.sem_ax(m, sem.SEM_F64, ud, wd, sem.SEM_AX_LOCAL)
+    assert rel(wd.cpu().numpy(), L.ax_local(u)) < TOL64
+    for scale in (1e-20, 1e20):
+        v = inputs.random_field(L.nl, 4) * scale
+        sem.sem_ax(m, sem.SEM_F64, torch.tensor(v, device=DEV), wd, sem.SEM_AX_LOCAL)
+        assert rel(wd.cpu().numpy(), L.ax_local(v)) < TOL64
+
+
+def test_ax_nan_propagates():
+    m, L, _ = make(2, 2, 2, 3)
+    for arith in (sem.SEM_ARITH_PAIR, sem.SEM_ARITH_NATIVE):
+        m, L, _ = make(2, 2, 2, 3, arith=arith)
+        u = inputs.random_field(L.nl, 4)
+        u[10] = np.nan
+        wd = torch.empty(L.nl, device=DEV, dtype=torch.float64)
+        sem.sem_ax(m, sem.SEM_F64, torch.tensor(u, device=DEV), wd, sem.SEM_AX_LOCAL)
+        assert torch.isnan(wd).any()
 
 
 def test_ax_grid_stride_many_elements():
@@ -176,13 +212,15 @@ def _element_vertices(v, ex, ey, e):
     return out
 
 
-@pytest.mark.parametrize("k,geom", [(64, sem.SEM_GEOM_STORED), (48, sem.SEM_GEOM_TRILINEAR)])
-def test_ax_full_size_sampled_elements(k, geom):
-    """Config-2 sizes in the benchmark's launch configuration: the local
+@pytest.mark.parametrize("k,geom,arith", [(64, sem.SEM_GEOM_STORED, sem.SEM_ARITH_PAIR),
+                                          (64, sem.SEM_GEOM_STORED, sem.SEM_ARITH_NATIVE),
+                                          (48, sem.SEM_GEOM_TRILINEAR, sem.SEM_ARITH_NATIVE)])
+def test_ax_full_size_sampled_elements(k, geom, arith):
+    """Operator-sweep sizes in the benchmark's launch configuration: the local
     operator of sampled elements against the oracle run on those elements."""
     N = 7
     v = inputs.box_vertices(k, k, k, 0.1, seed=2 + k)
-    m = sem.Mesh(k, k, k, N, 0, geom, verts=v)
+    m = sem.Mesh(k, k, k, N, 0, geom, verts=v, f64_arith=arith)
     Np3 = (N + 1) ** 3
     u = inputs.random_field(m.n_local, 100 + k)
     ud = torch.tensor(u, device=DEV)

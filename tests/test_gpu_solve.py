@@ -112,11 +112,15 @@ def test_neumann_rhs_must_be_mean_free():
     assert ei.value.status == sem.SEM_EINVAL
 
 
-@pytest.mark.parametrize("bc,orders", [(0, (5, 3, 1)), (1, (7, 3, 1)), (0, (4, 2)), (1, (3, 1))])
-def test_vcycle_fp64_matches_oracle(bc, orders):
+@pytest.mark.parametrize("bc,orders,arith", [(0, (5, 3, 1), sem.SEM_ARITH_PAIR),
+                                             (1, (7, 3, 1), sem.SEM_ARITH_PAIR),
+                                             (1, (7, 3, 1), sem.SEM_ARITH_NATIVE),
+                                             (0, (4, 2), sem.SEM_ARITH_PAIR),
+                                             (1, (3, 1), sem.SEM_ARITH_NATIVE)])
+def test_vcycle_fp64_matches_oracle(bc, orders, arith):
     e = (3, 2, 4)
     v = inputs.box_vertices(*e, 0.1, 5)
-    m = sem.Mesh(*e, orders[0], bc, verts=v)
+    m = sem.Mesh(*e, orders[0], bc, verts=v, f64_arith=arith)
     P = sem.Pmg(m, orders=orders, smoother_dtype=sem.SEM_F64, coarse_tol=0.0, coarse_maxit=12,
                 seed=4)
     Po = oracle.PMG(*e, list(orders), bc, v, cheb_degree=2, lanczos_steps=20, seed=4,
