@@ -43,9 +43,10 @@ if ROOT not in sys.path:
 METRIC = "Poisson solve time to 1e-8 (GDOF/s) & Ax GB/s vs HBM roofline; p50/p99 latency"
 E_SIDE, ORDER, MESH_SEED, RHS_SEED = 48, 7, 3, 3
 TOL = 1e-8
+CHEB_DEGREE, COARSE_TOL, COARSE_MAXIT = 3, 1e-2, 100
 WORKLOAD = ("mixed-precision Neumann pressure solve: E=48^3=110592 jittered hexes (+-10% h, "
-            "seed 3), N=7, pMG 7-3-1, Chebyshev(2)-Jacobi smoother in FP32, FP64 coarse "
-            "Jacobi-PCG (tol 1e-2, <=50 it), FP64 FlexCG to 1e-8 from x=0")
+            "seed 3), N=7, pMG 7-3-1, Chebyshev(3)-Jacobi smoother in FP32, FP64 coarse "
+            "Jacobi-PCG (tol 1e-2, <=100 it), FP64 FlexCG to 1e-8 from x=0")
 # Fallback peaks of the recipe, used only when MEASURED_PEAKS.json is absent.
 FALLBACK_HBM_GBS = 6800.0
 # FP64 pipe: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (the part's
@@ -56,9 +57,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # (152 SMs x 128 lanes x 2.07 GHz) / 12 x 2 flop.
 PAIR_INSTR_PER_FMA = 12
 PAIR_PEAK_TFLOPS = 152 * 128 * 2.07e9 / PAIR_INSTR_PER_FMA * 2 / 1e12
-# DRAM traffic of one fine-level FP64 operator launch from an ncu capture
-# (profiles/ax_f64_N7.txt), valid while the kernel source is unchanged.
-AX_TRAFFIC = {"source_sha256": None, "bytes_per_point": None}
+# DRAM traffic of one fine-level FP64 operator launch per local point, from an
+# ncu capture (profiles/ax_f64pair_N7.md), valid while the source is unchanged.
+AX_TRAFFIC = {"source_sha256": "ab9460908abee14bcf8f1dbe80d2dc039a0c47229b82a9a9bf9600553313fc7e",
+              "bytes_per_point": 62.66}
 
 
 def parse_args():
@@ -72,6 +74,9 @@ def parse_args():
                    help="skip the operator sweep, e2e and CPU-baseline legs")
     p.add_argument("--breakdown", action="store_true",
                    help="after the timed region, time every kernel class of one more solve")
+    p.add_argument("--coarse-maxit", type=int, default=COARSE_MAXIT)
+    p.add_argument("--coarse-tol", type=float, default=COARSE_TOL)
+    p.add_argument("--cheb-degree", type=int, default=CHEB_DEGREE)
     return p.parse_args()
 
 
@@ -165,7 +170,7 @@ class ClockSampler:
 
 
 def ax_source_sha():
-    with open(os.path.join(ROOT, "paper_2110_01716_gb300", "csrc", "ax.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2110_01716_gb300", "csrc", "ax_pair.cu"), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()
 
 
@@ -296,8 +301,9 @@ def main():
     side = args.side
     verts = inputs.box_vertices(side, side, side, 0.1, MESH_SEED)
     mesh = sem.Mesh(side, side, side, ORDER, sem.SEM_NEUMANN, sem.SEM_GEOM_STORED, verts=verts)
-    pmg = sem.Pmg(mesh, orders=(7, 3, 1), cheb_degree=2, lanczos_steps=20, seed=0,
-                  smoother_dtype=sem.SEM_F32, coarse_tol=1e-2, coarse_maxit=50)
+    pmg = sem.Pmg(mesh, orders=(7, 3, 1), cheb_degree=args.cheb_degree, lanczos_steps=20, seed=0,
+                  smoother_dtype=sem.SEM_F32, coarse_tol=args.coarse_tol,
+                  coarse_maxit=args.coarse_maxit)
     b = rhs_on_device(sem, torch, mesh, dev)
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
@@ -374,6 +380,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "E": side ** 3, "N": ORDER, "n_local": nl,
+                       "cheb_degree": args.cheb_degree, "coarse_tol": args.coarse_tol,
+                       "coarse_maxit": args.coarse_maxit,
                        "n_global": ng, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (working set ~6 GB), no flush"},
             "iters": [inf["iters"] for inf in infos],

@@ -84,17 +84,28 @@ struct PairShape {
   static constexpr int NP3 = NP2 * NP;
   static constexpr int NE = (256 / NP2) < 1 ? 1 : (256 / NP2);
   static constexpr int THREADS = NE * NP2;
+  // two CTAs per SM when the register budget allows (16 warps hide latency)
+  static constexpr int MIN_CTAS = THREADS >= 128 ? 2 : 4;
 };
 
+// Three phases per element, with one barrier before the last:
+//  A: u_r, u_s (shared) and u_t (registers) for the whole (i,j) column;
+//  B: pointwise geometric mix in place (each thread reads and writes only its
+//     own points), G streamed from HBM;
+//  C: transposed contractions reading the fluxes of the whole element.
+// Keeping the fluxes in shared memory instead of registers lets two CTAs
+// share an SM.
 template <int NP>
-__global__ void __launch_bounds__(PairShape<NP>::THREADS)
+__global__ void __launch_bounds__(PairShape<NP>::THREADS, PairShape<NP>::MIN_CTAS)
     ax_pair_kernel(int64_t E, Basis bs, const double *__restrict__ u, double *__restrict__ w,
                    const float2 *__restrict__ G2) {
   using S = PairShape<NP>;
   constexpr int NP2 = S::NP2, NP3 = S::NP3, NE = S::NE;
-  __shared__ float2 sD[NP][NP + 1];
-  __shared__ float2 sA[NE][NP3];
-  __shared__ float2 sB[NE][NP3];
+  extern __shared__ float2 smem_pair[];
+  float2(*sD)[NP + 1] = reinterpret_cast<float2(*)[NP + 1]>(smem_pair);
+  float2(*sU)[NP3] = reinterpret_cast<float2(*)[NP3]>(smem_pair + NP * (NP + 1));
+  float2(*sR)[NP3] = sU + NE;
+  float2(*sS)[NP3] = sR + NE;
 
   const int le = threadIdx.x / NP2;
   const int ij = threadIdx.x - le * NP2;
@@ -108,62 +119,69 @@ __global__ void __launch_bounds__(PairShape<NP>::THREADS)
   for (int64_t e0 = (int64_t)blockIdx.x * NE; e0 < E; e0 += (int64_t)gridDim.x * NE) {
     const int64_t e = e0 + le;
     const bool active = e < E;
-    float2 ru[NP];
+    float2 rt[NP];
     if (active) {
       const double *ue = u + e * NP3;
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
-        ru[k] = split_f64(ue[ij + k * NP2]);
-        sA[le][ij + k * NP2] = ru[k];
+        rt[k] = split_f64(ue[ij + k * NP2]);
+        sU[le][ij + k * NP2] = rt[k];
       }
     }
     __syncthreads();
-    float2 wr[NP], ws[NP], wt[NP];
     if (active) {
+      // A: reference gradients; u_t overwrites the column of u in registers
+      float ts[NP], tc[NP];
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        ts[k] = 0.f;
+        tc[k] = 0.f;
+#pragma unroll
+        for (int l = 0; l < NP; ++l) pair_fma(sD[k][l], rt[l], ts[k], tc[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        float rs = 0.f, rc = 0.f, ss = 0.f, sc = 0.f;
+#pragma unroll
+        for (int l = 0; l < NP; ++l) {
+          pair_fma(sD[i][l], sU[le][l + j * NP + k * NP2], rs, rc);
+          pair_fma(sD[j][l], sU[le][i + l * NP + k * NP2], ss, sc);
+        }
+        sR[le][ij + k * NP2] = pair_norm(rs, rc);
+        sS[le][ij + k * NP2] = pair_norm(ss, sc);
+        rt[k] = pair_norm(ts[k], tc[k]);
+      }
+      // B: W = G (u_r, u_s, u_t), in place
       const float2 *Ge = G2 + e * 6 * NP3 + ij;
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
-        float rs = 0.f, rc = 0.f, ss = 0.f, sc = 0.f, ts = 0.f, tc = 0.f;
-#pragma unroll
-        for (int l = 0; l < NP; ++l) {
-          pair_fma(sD[i][l], sA[le][l + j * NP + k * NP2], rs, rc);
-          pair_fma(sD[j][l], sA[le][i + l * NP + k * NP2], ss, sc);
-          pair_fma(sD[k][l], ru[l], ts, tc);
-        }
-        const float2 ur = pair_norm(rs, rc), us = pair_norm(ss, sc), ut = pair_norm(ts, tc);
         float2 g[6];
 #pragma unroll
-        for (int f = 0; f < 6; ++f) g[f] = Ge[f * NP3 + k * NP2];
+        for (int f = 0; f < 6; ++f) g[f] = __ldg(&Ge[f * NP3 + k * NP2]);
+        const float2 ur = sR[le][ij + k * NP2], us = sS[le][ij + k * NP2], ut = rt[k];
         float a = 0.f, b = 0.f;
         pair_fma(g[0], ur, a, b); pair_fma(g[1], us, a, b); pair_fma(g[2], ut, a, b);
-        wr[k] = pair_norm(a, b);
+        sR[le][ij + k * NP2] = pair_norm(a, b);
         a = 0.f; b = 0.f;
         pair_fma(g[1], ur, a, b); pair_fma(g[3], us, a, b); pair_fma(g[4], ut, a, b);
-        ws[k] = pair_norm(a, b);
+        sS[le][ij + k * NP2] = pair_norm(a, b);
         a = 0.f; b = 0.f;
         pair_fma(g[2], ur, a, b); pair_fma(g[4], us, a, b); pair_fma(g[5], ut, a, b);
-        wt[k] = pair_norm(a, b);
+        rt[k] = pair_norm(a, b);
       }
     }
     __syncthreads();
     if (active) {
-#pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        sA[le][ij + k * NP2] = wr[k];
-        sB[le][ij + k * NP2] = ws[k];
-      }
-    }
-    __syncthreads();
-    if (active) {
+      // C: w = D^T W_r + D^T W_s + D^T W_t
       double *we = w + e * NP3;
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
         float s = 0.f, c = 0.f;
 #pragma unroll
         for (int l = 0; l < NP; ++l) {
-          pair_fma(sD[l][i], sA[le][l + j * NP + k * NP2], s, c);
-          pair_fma(sD[l][j], sB[le][i + l * NP + k * NP2], s, c);
-          pair_fma(sD[l][k], wt[l], s, c);
+          pair_fma(sD[l][i], sR[le][l + j * NP + k * NP2], s, c);
+          pair_fma(sD[l][j], sS[le][i + l * NP + k * NP2], s, c);
+          pair_fma(sD[l][k], rt[l], s, c);
         }
         const float2 r = pair_norm(s, c);
         we[ij + k * NP2] = widen_f32(r.x) + widen_f32(r.y);
@@ -179,8 +197,17 @@ static void launch_pair_np(const Level &L, const double *u, double *w, cudaStrea
   int64_t blocks = (L.t.E + S::NE - 1) / S::NE;
   const int64_t cap = 152 * 16;
   int grid = (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
+  const size_t shm = sizeof(float2) * ((size_t)NP * (NP + 1) + 3 * (size_t)S::NE * S::NP3);
+  static bool attr_set[64] = {};  // the attribute is per function and device
+  int dev = 0;
+  SEM_CHECK_CUDA(cudaGetDevice(&dev));
+  if (dev >= 64 || !attr_set[dev]) {
+    SEM_CHECK_CUDA(cudaFuncSetAttribute(ax_pair_kernel<NP>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    if (dev < 64) attr_set[dev] = true;
+  }
   TraceScope ts("ax_f64pair", L.t.N, st);
-  ax_pair_kernel<NP><<<grid, S::THREADS, 0, st>>>(L.t.E, L.basis, u, w, L.G2.p);
+  ax_pair_kernel<NP><<<grid, S::THREADS, shm, st>>>(L.t.E, L.basis, u, w, L.G2.p);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
 

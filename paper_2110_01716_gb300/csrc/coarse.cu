@@ -4,14 +4,17 @@
 // The paper solves its N = 1 coarse grid with algebraic multigrid on the host
 // (Sec. 4, Table 1 discussion).  On one GPU the coarse problem is small
 // (about one unique node per element) and latency bound, so the whole CG
-// iteration runs inside one launch: vectors live in unique-node layout
-// (no duplicated copies), the operator is applied node by node from
-// precomputed 8x8 element matrices (each node sums the rows of the at most 8
-// elements that contain it, in a fixed order, so no atomics are needed), and
-// the inner products use a two-stage grid reduction in which every CTA adds
-// the per-CTA partials in the same order -- all CTAs obtain bit-identical
-// scalars and take the same stopping decision.  Three grid barriers per
-// iteration.
+// iteration runs inside one launch:
+//  * vectors live in unique-node layout (no duplicated copies);
+//  * the operator is the assembled 27-point stencil of the trilinear N = 1
+//    discretisation, stored structure-of-arrays [27][nodes] in FP64 and built
+//    once from the 8x8 element matrices in a fixed order (no atomics);
+//  * the Krylov method is Jacobi-preconditioned CG in the Chronopoulos-Gear
+//    arrangement (one fused reduction of (r,z), (Az,z), (r,r) per iteration,
+//    s = A p carried by recurrence), so an iteration needs two grid barriers;
+//  * reductions are two-stage: per-CTA partials, then every CTA adds all
+//    partials in the same order, so all CTAs hold bit-identical scalars and
+//    take the same stopping decision.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -24,39 +27,56 @@ namespace cg = cooperative_groups;
 
 namespace sem {
 
-constexpr int kCoarseThreads = 256;
+// CTA size and the number of CTAs per SM of the persistent coarse kernel
+// (grid barriers cost more with more CTAs; more CTAs hide more latency).
+#ifndef SEM_COARSE_THREADS
+#define SEM_COARSE_THREADS 256
+#endif
+#ifndef SEM_COARSE_CTAS_PER_SM
+#define SEM_COARSE_CTAS_PER_SM 1
+#endif
+constexpr int kCoarseThreads = SEM_COARSE_THREADS;
 
+// All index arithmetic is 32-bit with multiplicative division: 64-bit
+// integer division is emulated and would compete for the scarce FP64 pipe.
 struct CoarseArgs {
   int ex, ey, ez;
-  int nx, ny;  // lattice points along x and y
+  int nx, ny, nz;  // lattice points per direction
+  FastDiv div_nx, div_nxy, div_ex, div_ey;
   int64_t ng;
   int bc;
-  const double *Ae;    // [E][64]
+  const double *S;     // [27][ng] assembled stencil
   const double *dinv;  // [ng]
   const double *b_local;
   double *x_local;
-  double *x, *r, *z, *p, *w;
-  // Four partial-sum regions of grid*4 doubles: the mean, the initial sums,
-  // <p,w> and (rr, rz).  Consecutive reductions use different regions, so a
-  // CTA that races ahead never overwrites partials another CTA still reads.
-  double *partM, *partI, *partA, *partB;
+  double *x, *r, *z, *p, *s, *w;
+  // Three partial-sum regions of grid*4 doubles (mean, start, iteration);
+  // every reduction write is separated by a grid barrier from the reads of
+  // the previous reduction in the same region.
+  double *partM, *partI, *partK;
   int *iters;
   double tol2;
   int maxit;
 };
 
-__device__ __forceinline__ void node_coords(int64_t g, int nx, int ny, int &gx, int &gy, int &gz) {
-  int64_t nxy = (int64_t)nx * ny;
-  gz = (int)(g / nxy);
-  int64_t rem = g - (int64_t)gz * nxy;
-  gy = (int)(rem / nx);
-  gx = (int)(rem - (int64_t)gy * nx);
+__device__ __forceinline__ void node_coords(const CoarseArgs &A, int64_t g, int &gx, int &gy,
+                                            int &gz) {
+  const uint32_t u = (uint32_t)g;
+  gz = (int)A.div_nxy.div(u);
+  const uint32_t rem = u - (uint32_t)gz * (uint32_t)(A.nx * A.ny);
+  gy = (int)A.div_nx.div(rem);
+  gx = (int)(rem - (uint32_t)gy * (uint32_t)A.nx);
 }
 
-// Block sum of NS values, then grid-wide sum identical in every CTA.
+// Block sum of NS values, then grid-wide sum identical in every CTA.  FP64
+// additions are scarce on this part, so only warp 0 of each CTA reduces the
+// per-warp partials and, after the grid barrier, the per-CTA partials (in
+// CTA order, lane-strided, then a fixed shuffle tree); the result is
+// broadcast through shared memory.
 template <int NS>
 __device__ void coop_sum(double (&v)[NS], double *part, cg::grid_group &grid) {
   __shared__ double sh[NS][kCoarseThreads / 32];
+  __shared__ double res[NS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
@@ -66,43 +86,66 @@ __device__ void coop_sum(double (&v)[NS], double *part, cg::grid_group &grid) {
     if (lane == 0) sh[s][warp] = x;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      double x = 0.0;
-      for (int q = 0; q < kCoarseThreads / 32; ++q) x += sh[s][q];
-      part[(size_t)blockIdx.x * NS + s] = x;
+      double x = lane < kCoarseThreads / 32 ? sh[s][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) part[(size_t)blockIdx.x * NS + s] = x;
     }
   }
   grid.sync();
+  if (warp == 0) {
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    double x = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-      x += __ldcg(&part[(size_t)b * NS + s]);
+    for (int s = 0; s < NS; ++s) {
+      double x = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) x += __ldcg(&part[(size_t)b * NS + s]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    __syncthreads();
-    if (lane == 0) sh[s][warp] = x;
-    __syncthreads();
-    double t = 0.0;
-    for (int q = 0; q < kCoarseThreads / 32; ++q) t += sh[s][q];
-    v[s] = t;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) res[s] = x;
+    }
   }
   __syncthreads();
+#pragma unroll
+  for (int s = 0; s < NS; ++s) v[s] = res[s];
+}
+
+// (A v)_g from the 27-point stencil; Dirichlet boundary rows are zero.
+__device__ __forceinline__ double stencil_apply(const CoarseArgs &A, int64_t g,
+                                                const double *__restrict__ v) {
+  int gx, gy, gz;
+  node_coords(A, g, gx, gy, gz);
+  if (A.bc == SEM_DIRICHLET &&
+      (gx == 0 || gy == 0 || gz == 0 || gx == A.nx - 1 || gy == A.ny - 1 || gz == A.nz - 1))
+    return 0.0;
+  double acc = 0.0;
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int x = gx + dx, y = gy + dy, z = gz + dz;
+        if (x < 0 || y < 0 || z < 0 || x >= A.nx || y >= A.ny || z >= A.nz) continue;
+        const int d = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+        const int64_t nb = g + dx + (int64_t)A.nx * (dy + (int64_t)A.ny * dz);
+        acc = fma(A.S[(int64_t)d * A.ng + g], v[nb], acc);
+      }
+  return acc;
 }
 
 __global__ void __launch_bounds__(kCoarseThreads) coarse_cg_kernel(CoarseArgs A) {
   cg::grid_group grid = cg::this_grid();
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-  const int ex = A.ex, ey = A.ey, ez = A.ez;
+  const int ex = A.ex, ey = A.ey;
   // ---- right-hand side to unique layout (owner copy), x = 0
   double v1[1] = {0.0};
   for (int64_t g = tid; g < A.ng; g += nth) {
     int gx, gy, gz;
-    node_coords(g, A.nx, A.ny, gx, gy, gz);
-    int ix = min(gx, ex - 1), iy = min(gy, ey - 1), iz = min(gz, ez - 1);
+    node_coords(A, g, gx, gy, gz);
+    int ix = min(gx, ex - 1), iy = min(gy, ey - 1), iz = min(gz, A.ez - 1);
     int64_t e = ix + (int64_t)ex * (iy + (int64_t)ey * iz);
     int a = (gx - ix) + 2 * (gy - iy) + 4 * (gz - iz);
     double bg = A.b_local[e * 8 + a];
@@ -116,78 +159,68 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cg_kernel(CoarseArgs A)
     const double mean = v1[0] / (double)A.ng;
     for (int64_t g = tid; g < A.ng; g += nth) A.r[g] -= mean;
   }
-  double v3[3] = {0.0, 0.0, 0.0};  // bb, rr, rz
+  for (int64_t g = tid; g < A.ng; g += nth) A.z[g] = A.dinv[g] * A.r[g];
+  grid.sync();
+  // ---- w = A z;  rho = (r,z), mu = (w,z), rr = (r,r)
+  double v3[3] = {0.0, 0.0, 0.0};
   for (int64_t g = tid; g < A.ng; g += nth) {
-    double rg = A.r[g];
-    double zg = A.dinv[g] * rg;
-    A.z[g] = zg;
-    A.p[g] = zg;
-    v3[0] = fma(rg, rg, v3[0]);
-    v3[2] = fma(rg, zg, v3[2]);
+    const double wg = stencil_apply(A, g, A.z);
+    A.w[g] = wg;
+    const double rg = A.r[g], zg = A.z[g];
+    v3[0] = fma(rg, zg, v3[0]);
+    v3[1] = fma(wg, zg, v3[1]);
+    v3[2] = fma(rg, rg, v3[2]);
   }
-  v3[1] = v3[0];
-  coop_sum<3>(v3, A.partI, grid);  // also orders the p writes before the first product
-  const double bb = v3[0];
-  double rr = v3[1], rho = v3[2];
+  coop_sum<3>(v3, A.partI, grid);
+  const double bb = v3[2];
+  double rho = v3[0], alpha = v3[0] / v3[1];
   int it = 0;
-  bool done = !(rr > A.tol2 * bb) || A.maxit <= 0;
-  while (!done) {
-    ++it;
-    // ---- w = A p, node by node; pw = <p, w>
-    double v[1] = {0.0};
+  if (v3[2] > A.tol2 * bb && A.maxit > 0 && rho != 0.0) {
     for (int64_t g = tid; g < A.ng; g += nth) {
-      int gx, gy, gz;
-      node_coords(g, A.nx, A.ny, gx, gy, gz);
-      double acc = 0.0;
-      const bool bnd = A.bc == SEM_DIRICHLET &&
-                       (gx == 0 || gy == 0 || gz == 0 || gx == ex || gy == ey || gz == ez);
-      if (!bnd) {
-        for (int iz = max(gz - 1, 0); iz <= min(gz, ez - 1); ++iz)
-          for (int iy = max(gy - 1, 0); iy <= min(gy, ey - 1); ++iy)
-            for (int ix = max(gx - 1, 0); ix <= min(gx, ex - 1); ++ix) {
-              const int64_t e = ix + (int64_t)ex * (iy + (int64_t)ey * iz);
-              const int a = (gx - ix) + 2 * (gy - iy) + 4 * (gz - iz);
-              const double *row = A.Ae + e * 64 + a * 8;
-              const int64_t base = ix + (int64_t)A.nx * (iy + (int64_t)A.ny * iz);
-#pragma unroll
-              for (int b = 0; b < 8; ++b) {
-                const int64_t nb = base + (b & 1) + (int64_t)A.nx * (((b >> 1) & 1) +
-                                                                    (int64_t)A.ny * (b >> 2));
-                acc = fma(row[b], A.p[nb], acc);
-              }
-            }
+      A.p[g] = A.z[g];
+      A.s[g] = A.w[g];
+    }
+    for (;;) {
+      ++it;
+      // x += alpha p, r -= alpha s, z = Dinv r   (own nodes only)
+      for (int64_t g = tid; g < A.ng; g += nth) {
+        A.x[g] = fma(alpha, A.p[g], A.x[g]);
+        const double rg = fma(-alpha, A.s[g], A.r[g]);
+        A.r[g] = rg;
+        A.z[g] = A.dinv[g] * rg;
       }
-      A.w[g] = acc;
-      v[0] = fma(A.p[g], acc, v[0]);
+      grid.sync();
+      double v[3] = {0.0, 0.0, 0.0};
+      for (int64_t g = tid; g < A.ng; g += nth) {
+        const double wg = stencil_apply(A, g, A.z);
+        A.w[g] = wg;
+        const double rg = A.r[g], zg = A.z[g];
+        v[0] = fma(rg, zg, v[0]);
+        v[1] = fma(wg, zg, v[1]);
+        v[2] = fma(rg, rg, v[2]);
+      }
+      coop_sum<3>(v, A.partK, grid);
+      const double rr = v[2];
+      if (!(rr > A.tol2 * bb) || it >= A.maxit || !(rr == rr) || v[0] == 0.0) break;
+      const double beta = v[0] / rho;
+      alpha = v[0] / (v[1] - beta * v[0] / alpha);
+      rho = v[0];
+      for (int64_t g = tid; g < A.ng; g += nth) {
+        A.p[g] = fma(beta, A.p[g], A.z[g]);
+        A.s[g] = fma(beta, A.s[g], A.w[g]);
+      }
     }
-    coop_sum<1>(v, A.partA, grid);
-    const double alpha = rho / v[0];
-    // ---- x += alpha p, r -= alpha w, z = Dinv r;  rr, rz
-    double u[2] = {0.0, 0.0};
-    for (int64_t g = tid; g < A.ng; g += nth) {
-      A.x[g] = fma(alpha, A.p[g], A.x[g]);
-      double rg = fma(-alpha, A.w[g], A.r[g]);
-      A.r[g] = rg;
-      double zg = A.dinv[g] * rg;
-      A.z[g] = zg;
-      u[0] = fma(rg, rg, u[0]);
-      u[1] = fma(rg, zg, u[1]);
-    }
-    coop_sum<2>(u, A.partB, grid);
-    rr = u[0];
-    if (!(rr > A.tol2 * bb) || it >= A.maxit || !(rr == rr)) break;
-    const double beta = u[1] / rho;
-    rho = u[1];
-    for (int64_t g = tid; g < A.ng; g += nth) A.p[g] = fma(beta, A.p[g], A.z[g]);
-    grid.sync();
   }
   grid.sync();
   // ---- solution back to E-layout
-  const int64_t nloc = (int64_t)ex * ey * ez * 8;
+  const int64_t nloc = (int64_t)ex * ey * A.ez * 8;
   for (int64_t l = tid; l < nloc; l += nth) {
-    const int64_t e = l >> 3;
+    const uint32_t e = (uint32_t)(l >> 3);
     const int a = (int)(l & 7);
-    const int64_t ix = e % ex, iy = (e / ex) % ey, iz = e / ((int64_t)ex * ey);
+    const uint32_t yz = A.div_ex.div(e);
+    const int64_t ix = e - yz * (uint32_t)ex;
+    const int64_t iz = A.div_ey.div(yz);
+    const int64_t iy = yz - (uint32_t)iz * (uint32_t)ey;
     const int64_t g = (ix + (a & 1)) + (int64_t)A.nx * ((iy + ((a >> 1) & 1)) +
                                                        (int64_t)A.ny * (iz + (a >> 2)));
     A.x_local[l] = A.x[g];
@@ -227,13 +260,37 @@ __global__ void coarse_element_matrices(int64_t E, Basis bs, const double *__res
   }
 }
 
+// Assembled stencil S[d][g] = sum over elements e containing g of
+// A_e[a(g)][b] for the node b of e at offset d from g; elements in a fixed
+// order, so the assembly is deterministic.
+__global__ void coarse_stencil_assemble(CoarseArgs A, const double *__restrict__ Ae,
+                                        double *__restrict__ S) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < A.ng;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    int gx, gy, gz;
+    node_coords(A, g, gx, gy, gz);
+    for (int d = 0; d < 27; ++d) S[(int64_t)d * A.ng + g] = 0.0;
+    for (int iz = max(gz - 1, 0); iz <= min(gz, A.ez - 1); ++iz)
+      for (int iy = max(gy - 1, 0); iy <= min(gy, A.ey - 1); ++iy)
+        for (int ix = max(gx - 1, 0); ix <= min(gx, A.ex - 1); ++ix) {
+          const int64_t e = ix + (int64_t)A.ex * (iy + (int64_t)A.ey * iz);
+          const int a = (gx - ix) + 2 * (gy - iy) + 4 * (gz - iz);
+          for (int b = 0; b < 8; ++b) {
+            const int dx = ix + (b & 1) - gx, dy = iy + ((b >> 1) & 1) - gy, dz = iz + (b >> 2) - gz;
+            const int d = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+            S[(int64_t)d * A.ng + g] += Ae[e * 64 + a * 8 + b];
+          }
+        }
+  }
+}
+
 // Unique-layout Jacobi inverse from the E-layout one (owner copy).
 __global__ void coarse_unique_dinv(CoarseArgs A, const double *__restrict__ dinv_local,
                                    double *__restrict__ out) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < A.ng;
        g += (int64_t)gridDim.x * blockDim.x) {
     int gx, gy, gz;
-    node_coords(g, A.nx, A.ny, gx, gy, gz);
+    node_coords(A, g, gx, gy, gz);
     int ix = min(gx, A.ex - 1), iy = min(gy, A.ey - 1), iz = min(gz, A.ez - 1);
     int64_t e = ix + (int64_t)A.ex * (iy + (int64_t)A.ey * iz);
     int a = (gx - ix) + 2 * (gy - iy) + 4 * (gz - iz);
@@ -244,16 +301,20 @@ __global__ void coarse_unique_dinv(CoarseArgs A, const double *__restrict__ dinv
 static CoarseArgs base_args(const CoarseSolver &C, const Level &L) {
   CoarseArgs A{};
   A.ex = L.t.ex; A.ey = L.t.ey; A.ez = L.t.ez;
-  A.nx = L.t.ex + 1; A.ny = L.t.ey + 1;
+  A.nx = L.t.ex + 1; A.ny = L.t.ey + 1; A.nz = L.t.ez + 1;
+  A.div_nx = FastDiv((uint32_t)A.nx);
+  A.div_nxy = FastDiv((uint32_t)(A.nx * A.ny));
+  A.div_ex = FastDiv((uint32_t)A.ex);
+  A.div_ey = FastDiv((uint32_t)A.ey);
   A.ng = L.t.ng;
   A.bc = L.t.bc;
-  A.Ae = C.Ae.p;
+  A.S = C.S.p;
   A.dinv = C.dinv.p;
-  A.x = C.vec.p; A.r = A.x + A.ng; A.z = A.r + A.ng; A.p = A.z + A.ng; A.w = A.p + A.ng;
+  A.x = C.vec.p; A.r = A.x + A.ng; A.z = A.r + A.ng; A.p = A.z + A.ng; A.s = A.p + A.ng;
+  A.w = A.s + A.ng;
   A.partM = C.part.p;
   A.partI = A.partM + (size_t)C.grid * 4;
-  A.partA = A.partI + (size_t)C.grid * 4;
-  A.partB = A.partA + (size_t)C.grid * 4;
+  A.partK = A.partI + (size_t)C.grid * 4;
   A.iters = C.iters.p;
   return A;
 }
@@ -262,9 +323,11 @@ void coarse_setup(CoarseSolver &C, const Level &L, cudaStream_t st) {
   SEM_REQUIRE(L.t.N == 1, "the persistent coarse solver needs N = 1");
   SEM_REQUIRE(L.G64.p != nullptr, "coarse level needs stored FP64 factors");
   const int64_t E = L.t.E, ng = L.t.ng;
-  C.Ae.alloc((size_t)E * 64);
+  DevBuf<double> Ae;
+  Ae.alloc((size_t)E * 64);
+  C.S.alloc((size_t)27 * ng);
   C.dinv.alloc(ng);
-  C.vec.alloc((size_t)5 * ng);
+  C.vec.alloc((size_t)6 * ng);
   C.iters.alloc(1);
   int dev = 0, sms = 0, per_sm = 0;
   SEM_CHECK_CUDA(cudaGetDevice(&dev));
@@ -276,17 +339,22 @@ void coarse_setup(CoarseSolver &C, const Level &L, cudaStream_t st) {
                                                                kCoarseThreads, 0));
   SEM_REQUIRE(per_sm >= 1, "coarse kernel cannot be resident");
   const int64_t want = (ng + kCoarseThreads - 1) / kCoarseThreads;
+  per_sm = std::min(per_sm, SEM_COARSE_CTAS_PER_SM);
   C.grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
-  C.part.alloc((size_t)C.grid * 16);
+  C.part.alloc((size_t)C.grid * 12);
   {
     TraceScope ts("coarse_setup", 1, st);
     int blocks = (int)std::min<int64_t>((E * 64 + 255) / 256, 152 * 16);
-    coarse_element_matrices<<<blocks, 256, 0, st>>>(E, L.basis, L.G64.p, C.Ae.p);
+    coarse_element_matrices<<<blocks, 256, 0, st>>>(E, L.basis, L.G64.p, Ae.p);
     SEM_CHECK_CUDA(cudaGetLastError());
     CoarseArgs A = base_args(C, L);
+    coarse_stencil_assemble<<<(int)std::min<int64_t>((ng + 255) / 256, 152 * 16), 256, 0, st>>>(
+        A, Ae.p, C.S.p);
+    SEM_CHECK_CUDA(cudaGetLastError());
     coarse_unique_dinv<<<(int)std::min<int64_t>((ng + 255) / 256, 152 * 16), 256, 0, st>>>(
         A, L.dinv64.p, C.dinv.p);
     SEM_CHECK_CUDA(cudaGetLastError());
+    SEM_CHECK_CUDA(cudaStreamSynchronize(st));  // before the element matrices are freed
   }
 }
 

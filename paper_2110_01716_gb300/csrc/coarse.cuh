@@ -6,9 +6,9 @@
 namespace sem {
 
 struct CoarseSolver {
-  DevBuf<double> Ae;    // [E][8][8] element matrices
+  DevBuf<double> S;     // [27][ng] assembled stencil
   DevBuf<double> dinv;  // [ng] Jacobi inverse, unique layout (0 on Dirichlet nodes)
-  DevBuf<double> vec;   // x, r, z, p, w in unique layout
+  DevBuf<double> vec;   // x, r, z, p, s, w in unique layout
   DevBuf<double> part;  // grid reduction partials
   DevBuf<int> iters;    // iterations of the last solve
   int grid = 0;

@@ -77,29 +77,34 @@ __global__ void gs_kernel(GsGeom g, const int32_t *__restrict__ nodes, int64_t n
 
 // Zero the Dirichlet boundary: the points of element faces lying on the box
 // boundary.  One thread per (boundary face, face point).
+// 32-bit index arithmetic with multiplicative division throughout (64-bit
+// integer division is emulated and competes for the FP64 pipe).
 template <typename T>
-__global__ void mask_faces_kernel(Topo t, int64_t nfaces, T *__restrict__ u) {
-  const int Np = t.Np, Np2 = Np * Np;
-  const int64_t fx = (int64_t)t.ey * t.ez, fy = (int64_t)t.ex * t.ez;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nfaces * Np2;
-       s += (int64_t)gridDim.x * blockDim.x) {
-    int64_t f = s / Np2;
-    int q = (int)(s - f * Np2);
-    int a = q % Np, b = q / Np;
+__global__ void mask_faces_kernel(Topo t, uint32_t nfaces, FastDiv div_np2, T *__restrict__ u) {
+  const uint32_t Np = (uint32_t)t.Np, Np2 = Np * Np;
+  const uint32_t fx = (uint32_t)(t.ey * t.ez), fy = (uint32_t)(t.ex * t.ez);
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nfaces * Np2;
+       s += gridDim.x * blockDim.x) {
+    const uint32_t f = div_np2.div(s);
+    const uint32_t q = s - f * Np2;
+    const uint32_t b = t.div_np.div(q), a = q - b * Np;
     int ix, iy, iz, i, j, k;
-    int side = (int)(f & 1);
-    int64_t h = f >> 1;
+    const int side = (int)(f & 1);
+    uint32_t h = f >> 1;
     if (h < fx) {  // x = 0 or x = 1 faces
-      iy = (int)(h % t.ey); iz = (int)(h / t.ey);
-      ix = side ? t.ex - 1 : 0; i = side ? t.N : 0; j = a; k = b;
+      const uint32_t zz = t.div_ey.div(h);
+      iy = (int)(h - zz * (uint32_t)t.ey); iz = (int)zz;
+      ix = side ? t.ex - 1 : 0; i = side ? t.N : 0; j = (int)a; k = (int)b;
     } else if (h < fx + fy) {
       h -= fx;
-      ix = (int)(h % t.ex); iz = (int)(h / t.ex);
-      iy = side ? t.ey - 1 : 0; j = side ? t.N : 0; i = a; k = b;
+      const uint32_t zz = t.div_ex.div(h);
+      ix = (int)(h - zz * (uint32_t)t.ex); iz = (int)zz;
+      iy = side ? t.ey - 1 : 0; j = side ? t.N : 0; i = (int)a; k = (int)b;
     } else {
       h -= fx + fy;
-      ix = (int)(h % t.ex); iy = (int)(h / t.ex);
-      iz = side ? t.ez - 1 : 0; k = side ? t.N : 0; i = a; j = b;
+      const uint32_t yy = t.div_ex.div(h);
+      ix = (int)(h - yy * (uint32_t)t.ex); iy = (int)yy;
+      iz = side ? t.ez - 1 : 0; k = side ? t.N : 0; i = (int)a; j = (int)b;
     }
     size_t e = (size_t)ix + (size_t)t.ex * ((size_t)iy + (size_t)t.ey * iz);
     u[e * t.Np3 + i + Np * (j + Np * k)] = T(0);
@@ -127,7 +132,8 @@ void launch_mask(const Level &L, T *u, cudaStream_t st) {
   const Topo &t = L.t;
   int64_t nfaces = 2 * ((int64_t)t.ey * t.ez + (int64_t)t.ex * t.ez + (int64_t)t.ex * t.ey);
   TraceScope ts(sizeof(T) == 8 ? "mask_f64" : "mask_f32", t.N, st);
-  mask_faces_kernel<T><<<grid_1d(nfaces * t.Np * t.Np, 256), 256, 0, st>>>(t, nfaces, u);
+  mask_faces_kernel<T><<<grid_1d(nfaces * t.Np * t.Np, 256), 256, 0, st>>>(
+      t, (uint32_t)nfaces, FastDiv((uint32_t)(t.Np * t.Np)), u);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
 

@@ -14,6 +14,8 @@ void launch_dot(const Topo &t, Reducer &R, const double *u, const double *v, dou
                 cudaStream_t st);
 void launch_dot_skip(const Topo &t, Reducer &R, const double *u, const double *v, double *out,
                      const int *skip, cudaStream_t st);
+void launch_dot_local(const Topo &t, Reducer &R, const double *u, const double *v, double *out,
+                      const int *skip, cudaStream_t st);
 void launch_sum(const Topo &t, Reducer &R, const double *u, double *out, cudaStream_t st);
 void launch_remove_mean(const Topo &t, Reducer &R, double *u, double *scratch, cudaStream_t st);
 void launch_cg_start(const Topo &t, Reducer &R, const double *b, const double *w,

@@ -21,14 +21,14 @@
 namespace sem {
 
 // ------------------------------------------------------------------ Chebyshev
-// Start of a Chebyshev smoothing: r = b - w (w = A x assembled, or r = b when
-// w is null and x = 0), d = dinv r / theta, x = d (x_zero) or x += d.
+// Start of a Chebyshev smoothing: r = b - w (w = A x assembled and masked, or
+// r = b when w is null and x = 0), d = dinv r / theta, x = d (x_zero) or x += d.
 template <typename T>
-__global__ void cheb_start_kernel(int64_t n, const T *__restrict__ b, const T *__restrict__ w,
+__global__ void cheb_start_kernel(Topo t, const T *__restrict__ b, const T *__restrict__ w,
                                   const T *__restrict__ dinv, T *__restrict__ r, T *__restrict__ d,
                                   T *__restrict__ x, T inv_theta, int x_zero) {
-  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
-       l += (int64_t)gridDim.x * blockDim.x) {
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
+       l += gridDim.x * blockDim.x) {
     T rl = w ? b[l] - w[l] : b[l];
     r[l] = rl;
     T dl = dinv[l] * rl * inv_theta;
@@ -37,14 +37,14 @@ __global__ void cheb_start_kernel(int64_t n, const T *__restrict__ b, const T *_
   }
 }
 
-// One Chebyshev step after w = A d (assembled):
+// One Chebyshev step after w = A d (assembled and masked):
 // r -= w;  d = c1 d + c2 dinv r;  x += d.
 template <typename T>
-__global__ void cheb_step_kernel(int64_t n, const T *__restrict__ w, const T *__restrict__ dinv,
+__global__ void cheb_step_kernel(Topo t, const T *__restrict__ w, const T *__restrict__ dinv,
                                  T *__restrict__ r, T *__restrict__ d, T *__restrict__ x, T c1,
                                  T c2) {
-  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
-       l += (int64_t)gridDim.x * blockDim.x) {
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
+       l += gridDim.x * blockDim.x) {
     T rl = r[l] - w[l];
     r[l] = rl;
     T dl = c1 * d[l] + c2 * dinv[l] * rl;
@@ -79,8 +79,9 @@ struct TransferCompute<double, float> {
   using type = float;
 };
 
-// Restriction of the fine residual b - w, weighted by 1/mult, to unassembled
-// coarse values: out_e = (J^T x J^T x J^T) ((b - w)/mult)_e.  One CTA per element.
+// Restriction of the fine residual b - w (w = A x assembled and masked),
+// weighted by 1/mult, to unassembled coarse values:
+// out_e = (J^T x J^T x J^T) ((b - w)/mult)_e.  One CTA per element.
 template <typename Tf, typename Tc>
 __global__ void restrict_kernel(TransferParams tp, const Tf *__restrict__ b,
                                 const Tf *__restrict__ w, Tc *__restrict__ out) {
@@ -353,15 +354,15 @@ static void smooth(sem_pmg *P, int l, bool x_zero, cudaStream_t st) {
   const bool f64 = sizeof(T) == 8;
   {
   TraceScope ts(f64 ? "cheb_start_f64" : "cheb_start_f32", L.t.N, st);
-  cheb_start_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(n, b, x_zero ? nullptr : w, dinv, r,
-                                                            d, x, (T)(1.0 / theta), x_zero);
+  cheb_start_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(L.t, b, x_zero ? nullptr : w, dinv,
+                                                            r, d, x, (T)(1.0 / theta), x_zero);
   SEM_CHECK_CUDA(cudaGetLastError());
   }
   for (int it = 2; it <= P->desc.cheb_degree; ++it) {
     apply_assembled<T>(L, d, w, st);
     double rho1 = 1.0 / (2.0 * sigma - rho);
     TraceScope ts(f64 ? "cheb_step_f64" : "cheb_step_f32", L.t.N, st);
-    cheb_step_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(n, w, dinv, r, d, x,
+    cheb_step_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(L.t, w, dinv, r, d, x,
                                                              (T)(rho1 * rho), (T)(2.0 * rho1 / delta));
     SEM_CHECK_CUDA(cudaGetLastError());
     rho = rho1;

@@ -144,7 +144,7 @@ void launch_cg_start(const Topo &t, Reducer &R, const double *b, const double *w
 }
 
 // ------------------------------------------------------------------ CG iteration
-// alpha = rho / pw;  x += alpha p;  r -= alpha w (w masked);  rr = <r,r>;
+// alpha = rho / pw;  x += alpha p;  r -= alpha w (w = A p assembled, masked);  rr = <r,r>;
 // Jacobi: z = dinv r and rz = <r,z>.  skip != null: the whole kernel is a
 // no-op once *skip is set (device-side stop of the coarse solve).
 __global__ void __launch_bounds__(kVecThreads)
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kVecThreads)
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
        l += gridDim.x * blockDim.x) {
     PointInfo q = point_info(l, t);
-    double zl = scale_pow2_down(z[l], q.log2_mult);
+    const double zl = scale_pow2_down(z[l], q.log2_mult);
     acc[0] = fma(zl, r[l], acc[0]);
     acc[1] = fma(zl, w[l], acc[1]);
   }
@@ -225,6 +225,29 @@ void launch_flex_dots(const Topo &t, Reducer &R, const double *z, const double *
   TraceScope ts("flex_dots", t.N, st);
   flex_dots_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, z, r, w, R.partials.p,
                                                            R.counter.p, o);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+// <p, mask gs(w)> for a continuous masked p and w = A_L p unassembled: the
+// plain sum over local points (no weights, no gather); optional skip flag.
+__global__ void __launch_bounds__(kVecThreads)
+    dot_local_kernel(Topo t, const double *__restrict__ u, const double *__restrict__ v,
+                     double *partials, unsigned int *counter, OutPtrs<1> out,
+                     const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  double acc[1] = {0.0};
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
+       l += gridDim.x * blockDim.x)
+    acc[0] = fma(u[l], v[l], acc[0]);
+  grid_reduce<1>(acc, partials, counter, out.p);
+}
+
+void launch_dot_local(const Topo &t, Reducer &R, const double *u, const double *v, double *out,
+                      const int *skip, cudaStream_t st) {
+  OutPtrs<1> o{{out}};
+  TraceScope ts("dot_local", t.N, st);
+  dot_local_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, u, v, R.partials.p, R.counter.p, o,
+                                                           skip);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
 
