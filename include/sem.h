@@ -136,6 +136,22 @@ sem_status sem_gs(sem_mesh *mesh, sem_dtype dtype, void *u, void *stream);
 sem_status sem_dot(sem_mesh *mesh, const double *u, const double *v, double *result,
                    void *stream);
 
+/* The inner product of sem_dot for callers that cannot let the library
+ * allocate device memory (a fixed device-memory budget, or a loop that must
+ * not pay for the device synchronisation of cudaMalloc/cudaFree).  The paper
+ * has no counterpart; this is a service of the library.  The reduction
+ * scratch (64 KiB: one partial per CTA of 8192 points plus a counter) is a
+ * static device array that every GPU which loads the library keeps until the
+ * process exits; nothing is allocated per call.  result is DEVICE memory (one
+ * double); the call does not synchronise the stream.  Meshes of more than
+ * 67,092,480 local points return SEM_EINVAL (use sem_dot).  The first call on
+ * a device looks up the scratch address; make it before any stream capture.
+ * All calls share the one scratch array, so calls whose kernels may overlap
+ * on the GPU (different streams without ordering) race and must not be
+ * issued. */
+sem_status sem_dot_noalloc(const sem_mesh *mesh, const double *u, const double *v,
+                           double *result, void *stream);
+
 /* p-multigrid description (Sec. 3, pMG: levels of decreasing order, tensor
  * interpolation between them, Chebyshev-accelerated point-Jacobi smoothing,
  * preconditioner arithmetic optionally in 32-bit). */

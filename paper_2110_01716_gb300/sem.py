@@ -32,7 +32,7 @@ SEM_MAX_ORDER = 11
 EXPORTED = ["sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_field", "sem_ax",
             "sem_gs", "sem_dot", "sem_pmg_setup", "sem_pmg_destroy", "sem_pmg_info",
             "sem_pmg_vcycle", "sem_solve", "sem_solve_host", "sem_trace_enable",
-            "sem_trace_read", "sem_last_error"]
+            "sem_trace_read", "sem_dot_noalloc", "sem_last_error"]
 
 
 class SemError(RuntimeError):
@@ -92,6 +92,7 @@ def lib():
     L.sem_ax.argtypes = [vp, i32, vp, vp, i32, vp]
     L.sem_gs.argtypes = [vp, i32, vp, vp]
     L.sem_dot.argtypes = [vp, vp, vp, C.POINTER(d), vp]
+    L.sem_dot_noalloc.argtypes = [vp, vp, vp, vp, vp]
     L.sem_pmg_setup.argtypes = [vp, C.POINTER(sem_pmg_desc), vp, C.POINTER(vp)]
     L.sem_pmg_destroy.argtypes = [vp]
     L.sem_pmg_info.argtypes = [vp, i32, C.POINTER(d), C.POINTER(d)]
@@ -195,6 +196,13 @@ def sem_dot(mesh: Mesh, u, v, stream=None) -> float:
     out = C.c_double()
     check(lib().sem_dot(mesh.h, _ptr(u), _ptr(v), C.byref(out), _stream(stream)))
     return out.value
+
+
+def sem_dot_noalloc(mesh: Mesh, u, v, result, stream=None):
+    """Unique-node inner product into ``result`` (a one-element device tensor)
+    for callers that cannot have the library allocate; see include/sem.h."""
+    check(lib().sem_dot_noalloc(mesh.h, _ptr(u), _ptr(v), _ptr(result), _stream(stream)))
+    return result
 
 
 class Pmg:
