@@ -43,10 +43,10 @@ if ROOT not in sys.path:
 METRIC = "Poisson solve time to 1e-8 (GDOF/s) & Ax GB/s vs HBM roofline; p50/p99 latency"
 E_SIDE, ORDER, MESH_SEED, RHS_SEED = 48, 7, 3, 3
 TOL = 1e-8
-CHEB_DEGREE, COARSE_TOL, COARSE_MAXIT = 3, 1e-2, 100
+CHEB_DEGREE, COARSE_TOL, COARSE_MAXIT, COARSE_MODE = 3, 1e-1, 30, 1
 WORKLOAD = ("mixed-precision Neumann pressure solve: E=48^3=110592 jittered hexes (+-10% h, "
-            "seed 3), N=7, pMG 7-3-1, Chebyshev(3)-Jacobi smoother in FP32, FP64 coarse "
-            "Jacobi-PCG (tol 1e-2, <=100 it), FP64 FlexCG to 1e-8 from x=0")
+            "seed 3), N=7, pMG 7-3-1, Chebyshev(3)-Jacobi smoother in FP32, FP64 coarse solve "
+            "(CG + lattice multigrid V(2,2), tol 1e-1, <=30 it), FP64 FlexCG to 1e-8 from x=0")
 # Fallback peaks of the recipe, used only when MEASURED_PEAKS.json is absent.
 FALLBACK_HBM_GBS = 6800.0
 # FP64 pipe: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (the part's
@@ -77,6 +77,8 @@ def parse_args():
     p.add_argument("--coarse-maxit", type=int, default=COARSE_MAXIT)
     p.add_argument("--coarse-tol", type=float, default=COARSE_TOL)
     p.add_argument("--cheb-degree", type=int, default=CHEB_DEGREE)
+    p.add_argument("--coarse-mode", type=int, default=COARSE_MODE,
+                   help="0: Jacobi-PCG, 1: multigrid-preconditioned CG on the N=1 lattice")
     return p.parse_args()
 
 
@@ -303,7 +305,7 @@ def main():
     mesh = sem.Mesh(side, side, side, ORDER, sem.SEM_NEUMANN, sem.SEM_GEOM_STORED, verts=verts)
     pmg = sem.Pmg(mesh, orders=(7, 3, 1), cheb_degree=args.cheb_degree, lanczos_steps=20, seed=0,
                   smoother_dtype=sem.SEM_F32, coarse_tol=args.coarse_tol,
-                  coarse_maxit=args.coarse_maxit)
+                  coarse_maxit=args.coarse_maxit, coarse_mode=args.coarse_mode)
     b = rhs_on_device(sem, torch, mesh, dev)
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
@@ -381,7 +383,7 @@ def main():
             "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "E": side ** 3, "N": ORDER, "n_local": nl,
                        "cheb_degree": args.cheb_degree, "coarse_tol": args.coarse_tol,
-                       "coarse_maxit": args.coarse_maxit,
+                       "coarse_maxit": args.coarse_maxit, "coarse_mode": args.coarse_mode,
                        "n_global": ng, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (working set ~6 GB), no flush"},
             "iters": [inf["iters"] for inf in infos],

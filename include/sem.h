@@ -164,7 +164,16 @@ typedef struct {
   int32_t smoother_dtype;   /* sem_dtype of the smoothed levels: F64 or F32 */
   double coarse_tol;        /* coarsest level: FP64 Jacobi-PCG relative tol */
   int32_t coarse_maxit;     /* ... and iteration cap (tol <= 0: exactly maxit) */
+  int32_t coarse_mode;      /* SEM_COARSE_JACOBI or SEM_COARSE_MG (below) */
 } sem_pmg_desc;
+
+/* Coarsest-level solver (the coarsest order must be 1 for SEM_COARSE_MG).
+ * SEM_COARSE_JACOBI: FP64 Jacobi-PCG (the default).
+ * SEM_COARSE_MG: FP64 flexible CG preconditioned by one geometric multigrid
+ * V(2,2) cycle on the N = 1 vertex lattice (Galerkin 27-point operators,
+ * Chebyshev-Jacobi smoothing, dense bottom solve); same tolerance and cap.
+ * The paper solves its coarse grid with algebraic multigrid (Sec. 4). */
+enum { SEM_COARSE_JACOBI = 0, SEM_COARSE_MG = 1 };
 
 /* Build the hierarchy on the mesh's vertices and boundary condition.
  * Chebyshev interval per smoothed level: [lambda_hi/10, lambda_hi] with

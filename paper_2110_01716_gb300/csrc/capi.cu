@@ -72,9 +72,12 @@ static std::vector<double> builtin_vertices(int ex, int ey, int ez, double jitte
   return v;
 }
 
+// Work vectors of the outer solver, each starting on a 256-byte boundary.
+static size_t work_stride(const sem_mesh *M) { return ((size_t)M->fine.t.nl + 31) / 32 * 32; }
+
 static void ensure_work(sem_mesh *M) {
   if (M->work.p) return;
-  M->work.alloc(4 * (size_t)M->fine.t.nl);
+  M->work.alloc(4 * work_stride(M));
 }
 
 static double *slot(sem_mesh *M, int s) { return M->scal.p + s; }
@@ -94,7 +97,8 @@ static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
   const Topo &t = L.t;
   const bool flex = d.solver == SEM_SOLVER_FLEXCG;
   ensure_work(M);
-  double *r = M->work.p, *z = r + t.nl, *p = z + t.nl, *w = p + t.nl;
+  const size_t ws = work_stride(M);
+  double *r = M->work.p, *z = r + ws, *p = z + ws, *w = p + ws;
   cudaEvent_t e0, e1;
   SEM_CHECK_CUDA(cudaEventCreate(&e0));
   SEM_CHECK_CUDA(cudaEventCreate(&e1));

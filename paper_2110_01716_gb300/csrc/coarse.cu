@@ -310,24 +310,32 @@ static CoarseArgs base_args(const CoarseSolver &C, const Level &L) {
   A.bc = L.t.bc;
   A.S = C.S.p;
   A.dinv = C.dinv.p;
-  A.x = C.vec.p; A.r = A.x + A.ng; A.z = A.r + A.ng; A.p = A.z + A.ng; A.s = A.p + A.ng;
-  A.w = A.s + A.ng;
+  const size_t vs = C.vec_stride;
+  A.x = C.vec.p; A.r = A.x + vs; A.z = A.r + vs; A.p = A.z + vs; A.s = A.p + vs; A.w = A.s + vs;
+  const size_t ps = (size_t)((C.grid * 4 + 31) / 32 * 32);
   A.partM = C.part.p;
-  A.partI = A.partM + (size_t)C.grid * 4;
-  A.partK = A.partI + (size_t)C.grid * 4;
+  A.partI = A.partM + ps;
+  A.partK = A.partI + ps;
   A.iters = C.iters.p;
   return A;
 }
 
 void coarse_setup(CoarseSolver &C, const Level &L, cudaStream_t st) {
   SEM_REQUIRE(L.t.N == 1, "the persistent coarse solver needs N = 1");
-  SEM_REQUIRE(L.G64.p != nullptr, "coarse level needs stored FP64 factors");
+  DevBuf<double> Gtmp;
+  const double *G = L.G64.p;
+  if (!G) {
+    level_fp64_factors(L, Gtmp, st);
+    G = Gtmp.p;
+  }
   const int64_t E = L.t.E, ng = L.t.ng;
   DevBuf<double> Ae;
   Ae.alloc((size_t)E * 64);
   C.S.alloc((size_t)27 * ng);
   C.dinv.alloc(ng);
-  C.vec.alloc((size_t)6 * ng);
+  // vectors start on 256-byte boundaries (see coarse_mg.cu)
+  C.vec_stride = (size_t)((ng + 31) / 32 * 32);
+  C.vec.alloc(6 * C.vec_stride);
   C.iters.alloc(1);
   int dev = 0, sms = 0, per_sm = 0;
   SEM_CHECK_CUDA(cudaGetDevice(&dev));
@@ -341,11 +349,11 @@ void coarse_setup(CoarseSolver &C, const Level &L, cudaStream_t st) {
   const int64_t want = (ng + kCoarseThreads - 1) / kCoarseThreads;
   per_sm = std::min(per_sm, SEM_COARSE_CTAS_PER_SM);
   C.grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
-  C.part.alloc((size_t)C.grid * 12);
+  C.part.alloc(3 * (size_t)((C.grid * 4 + 31) / 32 * 32));
   {
     TraceScope ts("coarse_setup", 1, st);
     int blocks = (int)std::min<int64_t>((E * 64 + 255) / 256, 152 * 16);
-    coarse_element_matrices<<<blocks, 256, 0, st>>>(E, L.basis, L.G64.p, Ae.p);
+    coarse_element_matrices<<<blocks, 256, 0, st>>>(E, L.basis, G, Ae.p);
     SEM_CHECK_CUDA(cudaGetLastError());
     CoarseArgs A = base_args(C, L);
     coarse_stencil_assemble<<<(int)std::min<int64_t>((ng + 255) / 256, 152 * 16), 256, 0, st>>>(

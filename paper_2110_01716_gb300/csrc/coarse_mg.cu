@@ -1,0 +1,676 @@
+// coarse_mg.cu -- multigrid-preconditioned coarse solve on the N = 1 lattice.
+//
+// The paper treats its N = 1 coarse grid with algebraic multigrid (Sec. 4,
+// Table 1: the coarse grid falls from 45% to 11% of the run once it is
+// handled well).  Here the coarse problem is the 27-point trilinear stencil
+// on the (ex+1)(ey+1)(ez+1) lattice, and plain Jacobi-PCG needs O(lattice
+// size) iterations, each limited by grid-wide latency.  This mode instead
+// runs flexible CG (FP64) preconditioned by one geometric multigrid V(2,2)
+// cycle per iteration, inside one persistent cooperative kernel:
+//  * levels: lattice coarsened by two per direction (even indices plus the
+//    last), index-space trilinear prolongation P = Pz x Py x Px, restriction
+//    P^T, Galerkin operators P^T A P (27-point stencils, built on the host in
+//    FP64, in a fixed order);
+//  * smoother: degree-2 Chebyshev-Jacobi on [lambda/10, lambda], lambda =
+//    1.1 x a power-iteration estimate of lambda_max(D^-1 A);
+//  * bottom: dense inverse (Neumann: of A + c 1 1^T, exact on mean-free data);
+//  * Dirichlet nodes are eliminated on every level (rows and unknowns zero).
+// The iterations stop at the same relative tolerance and cap as the Jacobi
+// mode, which remains the default.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "coarse.cuh"
+#include "trace.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace sem {
+
+constexpr int kMgThreads = 256;
+constexpr int kMgMaxBottom = 128;
+
+__device__ __forceinline__ void mg_coords(const MgLevelDev &L, int g, int &gx, int &gy, int &gz) {
+  const uint32_t u = (uint32_t)g;
+  gz = (int)L.div_nxy.div(u);
+  const uint32_t rem = u - (uint32_t)gz * (uint32_t)(L.nx * L.ny);
+  gy = (int)L.div_nx.div(rem);
+  gx = (int)(rem - (uint32_t)gy * (uint32_t)L.nx);
+}
+
+__device__ __forceinline__ double mg_apply(const MgLevelDev &L, int g, const double *__restrict__ v) {
+  if (!L.keep[g]) return 0.0;
+  int gx, gy, gz;
+  mg_coords(L, g, gx, gy, gz);
+  double acc = 0.0;
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int x = gx + dx, y = gy + dy, z = gz + dz;
+        if (x < 0 || y < 0 || z < 0 || x >= L.nx || y >= L.ny || z >= L.nz) continue;
+        const int d = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+        acc = fma(L.S[(int64_t)d * L.n + g], v[g + dx + L.nx * (dy + L.ny * dz)], acc);
+      }
+  return acc;
+}
+
+// Grid-wide sums identical in every CTA (warp 0 reduces; see coarse.cu).
+template <int NS>
+__device__ void mg_sum(double (&v)[NS], double *part, cg::grid_group &grid) {
+  __shared__ double sh[NS][kMgThreads / 32];
+  __shared__ double res[NS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double x = v[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[s][warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double x = lane < kMgThreads / 32 ? sh[s][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) part[(size_t)blockIdx.x * NS + s] = x;
+    }
+  }
+  grid.sync();
+  if (warp == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double x = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) x += __ldcg(&part[(size_t)b * NS + s]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) res[s] = x;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < NS; ++s) v[s] = res[s];
+}
+
+// One V(2,2) cycle: level-0 right-hand side b0, result x0 (both level-0
+// vectors, b0 read only).  Every phase maps node g to the same thread, so
+// pointwise dependencies need no barrier; a barrier precedes every phase
+// that reads neighbours or another level.
+__device__ void mg_vcycle(const MgArgs &A, const double *__restrict__ b0, double *__restrict__ x0,
+                          cg::grid_group &grid, int tid, int nth) {
+  for (int l = 0; l < A.nlev - 1; ++l) {
+    const MgLevelDev &L = A.L[l];
+    const double *b = l == 0 ? b0 : L.b;
+    double *x = l == 0 ? x0 : L.x;
+    // pre-smoothing from zero: d = Dinv b / theta, x = d, r = b; one more step
+    for (int g = tid; g < L.n; g += nth) {
+      const double rg = b[g];
+      L.r[g] = rg;
+      const double d = L.dinv[g] * rg * L.inv_theta;
+      L.da[g] = d;
+      x[g] = d;
+    }
+    grid.sync();
+    for (int g = tid; g < L.n; g += nth) {
+      const double rg = L.r[g] - mg_apply(L, g, L.da);
+      L.r[g] = rg;
+      const double d = L.c1 * L.da[g] + L.c2 * L.dinv[g] * rg;
+      L.db[g] = d;
+      x[g] += d;
+    }
+    grid.sync();
+    // residual and restriction to the next level
+    for (int g = tid; g < L.n; g += nth) L.r[g] = b[g] - mg_apply(L, g, x);
+    grid.sync();
+    const MgLevelDev &C = A.L[l + 1];
+    for (int G = tid; G < C.n; G += nth) {
+      double acc = 0.0;
+      if (C.keep[G]) {
+        int Gx, Gy, Gz;
+        mg_coords(C, G, Gx, Gy, Gz);
+        for (int c = 0; c < 3; ++c) {
+          const int fz = L.ri[2][3 * Gz + c];
+          if (fz < 0) continue;
+          const double wz = L.rw[2][3 * Gz + c];
+          for (int b2 = 0; b2 < 3; ++b2) {
+            const int fy = L.ri[1][3 * Gy + b2];
+            if (fy < 0) continue;
+            const double wyz = wz * L.rw[1][3 * Gy + b2];
+            for (int a = 0; a < 3; ++a) {
+              const int fx = L.ri[0][3 * Gx + a];
+              if (fx < 0) continue;
+              acc = fma(wyz * L.rw[0][3 * Gx + a], L.r[fx + L.nx * (fy + L.ny * fz)], acc);
+            }
+          }
+        }
+      }
+      C.b[G] = acc;
+    }
+    grid.sync();
+  }
+  // bottom: dense inverse, one row per thread across the grid
+  {
+    const MgLevelDev &B = A.L[A.nlev - 1];
+    const double *b = A.nlev == 1 ? b0 : B.b;
+    double *x = A.nlev == 1 ? x0 : B.x;
+    for (int i = tid; i < A.nbottom; i += nth) {
+      double acc = 0.0;
+      for (int j = 0; j < A.nbottom; ++j) acc = fma(A.bottom_inv[(size_t)i * A.nbottom + j], b[j], acc);
+      x[i] = acc;
+    }
+    grid.sync();
+  }
+  for (int l = A.nlev - 2; l >= 0; --l) {
+    const MgLevelDev &L = A.L[l];
+    const MgLevelDev &C = A.L[l + 1];
+    const double *b = l == 0 ? b0 : L.b;
+    double *x = l == 0 ? x0 : L.x;
+    // prolongation and correction
+    for (int g = tid; g < L.n; g += nth) {
+      if (!L.keep[g]) continue;
+      int gx, gy, gz;
+      mg_coords(L, g, gx, gy, gz);
+      double acc = 0.0;
+      for (int c = 0; c < 2; ++c) {
+        const int Cz = L.pi[2][2 * gz + c];
+        if (Cz < 0) continue;
+        const double wz = L.pw[2][2 * gz + c];
+        for (int b2 = 0; b2 < 2; ++b2) {
+          const int Cy = L.pi[1][2 * gy + b2];
+          if (Cy < 0) continue;
+          const double wyz = wz * L.pw[1][2 * gy + b2];
+          for (int a = 0; a < 2; ++a) {
+            const int Cx = L.pi[0][2 * gx + a];
+            if (Cx < 0) continue;
+            acc = fma(wyz * L.pw[0][2 * gx + a], C.x[Cx + C.nx * (Cy + C.ny * Cz)], acc);
+          }
+        }
+      }
+      x[g] += acc;
+    }
+    grid.sync();
+    // post-smoothing: r = b - A x; d = Dinv r / theta; x += d; one more step
+    for (int g = tid; g < L.n; g += nth) L.r[g] = b[g] - mg_apply(L, g, x);
+    grid.sync();
+    for (int g = tid; g < L.n; g += nth) {
+      const double d = L.dinv[g] * L.r[g] * L.inv_theta;
+      L.da[g] = d;
+      x[g] += d;
+    }
+    grid.sync();
+    for (int g = tid; g < L.n; g += nth) {
+      const double rg = L.r[g] - mg_apply(L, g, L.da);
+      L.r[g] = rg;
+      const double d = L.c1 * L.da[g] + L.c2 * L.dinv[g] * rg;
+      x[g] += d;
+    }
+    grid.sync();
+  }
+}
+
+__global__ void __launch_bounds__(kMgThreads) coarse_mgcg_kernel(MgArgs A) {
+  cg::grid_group grid = cg::this_grid();
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  const MgLevelDev &L0 = A.L[0];
+  // right-hand side to unique layout (owner copy), x = 0
+  double v1[1] = {0.0};
+  for (int g = tid; g < L0.n; g += nth) {
+    int gx, gy, gz;
+    mg_coords(L0, g, gx, gy, gz);
+    const int ix = min(gx, A.ex - 1), iy = min(gy, A.ey - 1), iz = min(gz, A.ez - 1);
+    const int64_t e = ix + (int64_t)A.ex * (iy + (int64_t)A.ey * iz);
+    const int a = (gx - ix) + 2 * (gy - iy) + 4 * (gz - iz);
+    const double bg = A.b_local[e * 8 + a];
+    A.r[g] = bg;
+    A.x[g] = 0.0;
+    v1[0] += bg;
+  }
+  if (A.bc == SEM_NEUMANN) {
+    mg_sum<1>(v1, A.partM, grid);
+    const double mean = v1[0] / (double)L0.n;
+    for (int g = tid; g < L0.n; g += nth) A.r[g] -= mean;
+  }
+  grid.sync();
+  mg_vcycle(A, A.r, A.z, grid, tid, nth);
+  double v2[2] = {0.0, 0.0};  // rho = (r,z), rr = (r,r)
+  for (int g = tid; g < L0.n; g += nth) {
+    const double rg = A.r[g];
+    v2[0] = fma(rg, A.z[g], v2[0]);
+    v2[1] = fma(rg, rg, v2[1]);
+    A.p[g] = A.z[g];
+  }
+  mg_sum<2>(v2, A.partI, grid);
+  const double bb = v2[1];
+  double rho = v2[0];
+  int it = 0;
+  if (bb > 0.0 && A.maxit > 0 && rho != 0.0) {
+    for (;;) {
+      ++it;
+      double v[1] = {0.0};
+      for (int g = tid; g < L0.n; g += nth) {
+        const double wg = mg_apply(L0, g, A.p);
+        A.w[g] = wg;
+        v[0] = fma(A.p[g], wg, v[0]);
+      }
+      mg_sum<1>(v, A.partA, grid);
+      const double pw = v[0];
+      const double alpha = rho / pw;
+      for (int g = tid; g < L0.n; g += nth) {
+        A.x[g] = fma(alpha, A.p[g], A.x[g]);
+        A.r[g] = fma(-alpha, A.w[g], A.r[g]);
+      }
+      grid.sync();
+      mg_vcycle(A, A.r, A.z, grid, tid, nth);
+      double u[3] = {0.0, 0.0, 0.0};  // (r,z), (z,w), (r,r)
+      for (int g = tid; g < L0.n; g += nth) {
+        const double rg = A.r[g], zg = A.z[g];
+        u[0] = fma(rg, zg, u[0]);
+        u[1] = fma(zg, A.w[g], u[1]);
+        u[2] = fma(rg, rg, u[2]);
+      }
+      mg_sum<3>(u, A.partK, grid);
+      if (!(u[2] > A.tol2 * bb) || it >= A.maxit || !(u[2] == u[2]) || u[0] == 0.0) break;
+      // flexible (Polak-Ribiere) coefficient: (z_new, r_new - r_old) / rho
+      const double beta = -alpha * u[1] / rho;
+      rho = u[0];
+      for (int g = tid; g < L0.n; g += nth) A.p[g] = fma(beta, A.p[g], A.z[g]);
+      grid.sync();  // the next product reads the neighbours' p
+    }
+  }
+  grid.sync();
+  const int64_t nloc = (int64_t)A.ex * A.ey * A.ez * 8;
+  for (int64_t l = tid; l < nloc; l += nth) {
+    const uint32_t e = (uint32_t)(l >> 3);
+    const int a = (int)(l & 7);
+    const uint32_t yz = A.div_ex.div(e);
+    const int ix = (int)(e - yz * (uint32_t)A.ex);
+    const int iz = (int)A.div_ey.div(yz);
+    const int iy = (int)(yz - (uint32_t)iz * (uint32_t)A.ey);
+    const int g = (ix + (a & 1)) + L0.nx * ((iy + ((a >> 1) & 1)) + L0.ny * (iz + (a >> 2)));
+    A.x_local[l] = A.x[g];
+  }
+  if (tid == 0) *A.iters = it;
+}
+
+// ------------------------------------------------------------------ host setup
+namespace {
+
+struct HostLevel {
+  int nx, ny, nz, n;
+  std::vector<double> S;            // [27][n]
+  std::vector<unsigned char> keep;  // unknowns
+  std::vector<double> dinv;
+  double lam_hi = 0.0;
+};
+
+// Coarse points of a 1D lattice of n points: the even indices and the last.
+std::vector<int> coarse_points(int n) {
+  std::vector<int> c;
+  for (int i = 0; i < n; i += 2) c.push_back(i);
+  if (c.back() != n - 1) c.push_back(n - 1);
+  return c;
+}
+
+// Prolongation rows (fine index -> up to two (coarse index, weight)).
+void prolong_1d(int n, std::vector<int> &pi, std::vector<double> &pw, std::vector<int> &ri,
+                std::vector<double> &rw, int &nc) {
+  const std::vector<int> c = coarse_points(n);
+  nc = (int)c.size();
+  std::vector<int> cidx(n, -1);
+  for (int k = 0; k < nc; ++k) cidx[c[k]] = k;
+  pi.assign(2 * n, -1);
+  pw.assign(2 * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    if (cidx[i] >= 0) {
+      pi[2 * i] = cidx[i];
+      pw[2 * i] = 1.0;
+    } else {
+      pi[2 * i] = cidx[i - 1];
+      pw[2 * i] = 0.5;
+      pi[2 * i + 1] = cidx[i + 1];
+      pw[2 * i + 1] = 0.5;
+    }
+  }
+  ri.assign(3 * nc, -1);
+  rw.assign(3 * nc, 0.0);
+  std::vector<int> cnt(nc, 0);
+  for (int i = 0; i < n; ++i)
+    for (int q = 0; q < 2; ++q)
+      if (pi[2 * i + q] >= 0) {
+        const int k = pi[2 * i + q];
+        ri[3 * k + cnt[k]] = i;
+        rw[3 * k + cnt[k]] = pw[2 * i + q];
+        ++cnt[k];
+      }
+}
+
+double apply_host(const HostLevel &L, int g, const std::vector<double> &v) {
+  if (!L.keep[g]) return 0.0;
+  const int gx = g % L.nx, gy = (g / L.nx) % L.ny, gz = g / (L.nx * L.ny);
+  double acc = 0.0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int x = gx + dx, y = gy + dy, z = gz + dz;
+        if (x < 0 || y < 0 || z < 0 || x >= L.nx || y >= L.ny || z >= L.nz) continue;
+        const int nb = x + L.nx * (y + L.ny * z);
+        if (!L.keep[nb]) continue;
+        acc += L.S[(size_t)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)) * L.n + g] * v[nb];
+      }
+  return acc;
+}
+
+// lambda_max(D^-1 A) by 30 power iterations from a fixed start vector.
+double power_lambda(const HostLevel &L) {
+  std::vector<double> v(L.n), w(L.n);
+  for (int g = 0; g < L.n; ++g) v[g] = L.keep[g] ? 1.0 + 0.5 * std::sin(0.7 * g + 0.3) : 0.0;
+  double lam = 0.0;
+  for (int it = 0; it < 30; ++it) {
+    double nv = 0.0;
+    for (double a : v) nv += a * a;
+    nv = std::sqrt(nv);
+    if (nv == 0.0) return 1.0;
+    for (double &a : v) a /= nv;
+    for (int g = 0; g < L.n; ++g) w[g] = L.dinv[g] * apply_host(L, g, v);
+    double num = 0.0;
+    for (int g = 0; g < L.n; ++g) num += v[g] * w[g];
+    lam = num;
+    v.swap(w);
+  }
+  return lam;
+}
+
+}  // namespace
+
+void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st) {
+  const int nx0 = Lv.t.ex + 1, ny0 = Lv.t.ey + 1, nz0 = Lv.t.ez + 1;
+  const int n0 = nx0 * ny0 * nz0;
+  std::unique_ptr<CoarseMg> M(new CoarseMg());
+  std::vector<HostLevel> H(1);
+  H[0].nx = nx0; H[0].ny = ny0; H[0].nz = nz0; H[0].n = n0;
+  H[0].S.resize((size_t)27 * n0);
+  SEM_CHECK_CUDA(cudaMemcpyAsync(H[0].S.data(), C.S.p, H[0].S.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+  SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+  const bool dir = Lv.t.bc == SEM_DIRICHLET;
+  auto boundary = [&](int x, int y, int z, int nx, int ny, int nz) {
+    return dir && (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1);
+  };
+  auto finish_level = [&](HostLevel &L) {
+    L.keep.assign(L.n, 1);
+    L.dinv.assign(L.n, 0.0);
+    for (int g = 0; g < L.n; ++g) {
+      const int x = g % L.nx, y = (g / L.nx) % L.ny, z = g / (L.nx * L.ny);
+      if (boundary(x, y, z, L.nx, L.ny, L.nz)) L.keep[g] = 0;
+    }
+    for (int g = 0; g < L.n; ++g) {
+      const double dg = L.S[(size_t)13 * L.n + g];
+      L.dinv[g] = L.keep[g] && dg != 0.0 ? 1.0 / dg : 0.0;
+    }
+  };
+  finish_level(H[0]);
+  // transfer tables and Galerkin operators
+  std::vector<std::vector<int>> PI[3], RI[3];
+  std::vector<std::vector<double>> PW[3], RW[3];
+  while ((int)H.size() < kMgMaxLevels && H.back().n > kMgMaxBottom &&
+         std::min({H.back().nx, H.back().ny, H.back().nz}) > 3) {
+    const HostLevel &F = H.back();
+    int ncd[3];
+    std::vector<int> pi[3], ri[3];
+    std::vector<double> pw[3], rw[3];
+    const int nf[3] = {F.nx, F.ny, F.nz};
+    for (int d = 0; d < 3; ++d) prolong_1d(nf[d], pi[d], pw[d], ri[d], rw[d], ncd[d]);
+    HostLevel Cl;
+    Cl.nx = ncd[0]; Cl.ny = ncd[1]; Cl.nz = ncd[2];
+    Cl.n = Cl.nx * Cl.ny * Cl.nz;
+    Cl.S.assign((size_t)27 * Cl.n, 0.0);
+    // A_c[I][J] = sum_f sum_g P[f][I] A[f][g] P[g][J], fine unknowns only
+    for (int f = 0; f < F.n; ++f) {
+      if (!F.keep[f]) continue;
+      const int fx = f % F.nx, fy = (f / F.nx) % F.ny, fz = f / (F.nx * F.ny);
+      for (int d = 0; d < 27; ++d) {
+        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        const int gx = fx + dx, gy = fy + dy, gz = fz + dz;
+        if (gx < 0 || gy < 0 || gz < 0 || gx >= F.nx || gy >= F.ny || gz >= F.nz) continue;
+        const int gidx = gx + F.nx * (gy + F.ny * gz);
+        if (!F.keep[gidx]) continue;
+        const double a = F.S[(size_t)d * F.n + f];
+        if (a == 0.0) continue;
+        for (int c1 = 0; c1 < 2; ++c1) {
+          const int Iz = pi[2][2 * fz + c1];
+          if (Iz < 0) continue;
+          for (int b1 = 0; b1 < 2; ++b1) {
+            const int Iy = pi[1][2 * fy + b1];
+            if (Iy < 0) continue;
+            for (int a1 = 0; a1 < 2; ++a1) {
+              const int Ix = pi[0][2 * fx + a1];
+              if (Ix < 0) continue;
+              const double wI = pw[2][2 * fz + c1] * pw[1][2 * fy + b1] * pw[0][2 * fx + a1];
+              const int I = Ix + Cl.nx * (Iy + Cl.ny * Iz);
+              for (int c2 = 0; c2 < 2; ++c2) {
+                const int Jz = pi[2][2 * gz + c2];
+                if (Jz < 0) continue;
+                for (int b2 = 0; b2 < 2; ++b2) {
+                  const int Jy = pi[1][2 * gy + b2];
+                  if (Jy < 0) continue;
+                  for (int a2 = 0; a2 < 2; ++a2) {
+                    const int Jx = pi[0][2 * gx + a2];
+                    if (Jx < 0) continue;
+                    const double wJ = pw[2][2 * gz + c2] * pw[1][2 * gy + b2] * pw[0][2 * gx + a2];
+                    const int od = (Jx - Ix + 1) + 3 * (Jy - Iy + 1) + 9 * (Jz - Iz + 1);
+                    SEM_REQUIRE(Jx - Ix >= -1 && Jx - Ix <= 1 && Jy - Iy >= -1 && Jy - Iy <= 1 &&
+                                    Jz - Iz >= -1 && Jz - Iz <= 1,
+                                "coarse stencil exceeds 27 points");
+                    Cl.S[(size_t)od * Cl.n + I] += wI * a * wJ;
+                  }
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    finish_level(Cl);
+    for (int d = 0; d < 3; ++d) {
+      PI[d].push_back(pi[d]); PW[d].push_back(pw[d]);
+      RI[d].push_back(ri[d]); RW[d].push_back(rw[d]);
+    }
+    H.push_back(std::move(Cl));
+  }
+  SEM_REQUIRE(H.back().n <= kMgMaxBottom, "coarse lattice too elongated for the multigrid mode");
+  // bottom: dense (Dirichlet rows -> identity; Neumann: + c 1 1^T)
+  const HostLevel &B = H.back();
+  const int nb = B.n;
+  std::vector<double> Ad((size_t)nb * nb, 0.0), inv((size_t)nb * nb, 0.0);
+  {
+    std::vector<double> e(nb, 0.0);
+    for (int j = 0; j < nb; ++j) {
+      std::fill(e.begin(), e.end(), 0.0);
+      e[j] = 1.0;
+      for (int i = 0; i < nb; ++i) Ad[(size_t)i * nb + j] = apply_host(B, i, e);
+    }
+    double dmean = 0.0;
+    for (int i = 0; i < nb; ++i) dmean += Ad[(size_t)i * nb + i];
+    dmean /= nb;
+    for (int i = 0; i < nb; ++i)
+      if (!B.keep[i]) {
+        for (int j = 0; j < nb; ++j) Ad[(size_t)i * nb + j] = Ad[(size_t)j * nb + i] = 0.0;
+        Ad[(size_t)i * nb + i] = 1.0;
+      }
+    if (!dir)
+      for (size_t q = 0; q < Ad.size(); ++q) Ad[q] += dmean / nb;
+    // Gauss-Jordan with partial pivoting
+    std::vector<double> a = Ad;
+    for (int i = 0; i < nb; ++i) inv[(size_t)i * nb + i] = 1.0;
+    for (int col = 0; col < nb; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < nb; ++r)
+        if (std::fabs(a[(size_t)r * nb + col]) > std::fabs(a[(size_t)piv * nb + col])) piv = r;
+      SEM_REQUIRE(a[(size_t)piv * nb + col] != 0.0, "singular bottom-level operator");
+      if (piv != col)
+        for (int k = 0; k < nb; ++k) {
+          std::swap(a[(size_t)piv * nb + k], a[(size_t)col * nb + k]);
+          std::swap(inv[(size_t)piv * nb + k], inv[(size_t)col * nb + k]);
+        }
+      const double d = 1.0 / a[(size_t)col * nb + col];
+      for (int k = 0; k < nb; ++k) {
+        a[(size_t)col * nb + k] *= d;
+        inv[(size_t)col * nb + k] *= d;
+      }
+      for (int r = 0; r < nb; ++r) {
+        if (r == col) continue;
+        const double f = a[(size_t)r * nb + col];
+        if (f == 0.0) continue;
+        for (int k = 0; k < nb; ++k) {
+          a[(size_t)r * nb + k] -= f * a[(size_t)col * nb + k];
+          inv[(size_t)r * nb + k] -= f * inv[(size_t)col * nb + k];
+        }
+      }
+    }
+    for (int i = 0; i < nb; ++i)
+      if (!B.keep[i])
+        for (int j = 0; j < nb; ++j) inv[(size_t)i * nb + j] = 0.0;
+  }
+  // Chebyshev bounds (smoothed levels)
+  for (size_t l = 0; l + 1 < H.size(); ++l) H[l].lam_hi = 1.1 * power_lambda(H[l]);
+  // Device buffers.  Every array carved out of the three buffers starts on a
+  // 256-byte boundary: the unrolled gathers read neighbouring table entries,
+  // which the compiler may merge into vector loads that need that alignment.
+  auto up = [](size_t n, size_t q) { return (n + q - 1) / q * q; };
+  const int nlev = (int)H.size();
+  size_t dbl = up((size_t)nb * nb, 32), ints = 0;
+  for (int l = 0; l < nlev; ++l) {
+    dbl += up((size_t)27 * H[l].n, 32) + up(H[l].n, 32) + (l == 0 ? 4 : 6) * up(H[l].n, 32);
+    if (l + 1 < nlev)
+      for (int d = 0; d < 3; ++d) {
+        dbl += up(PW[d][l].size(), 32) + up(RW[d][l].size(), 32);
+        ints += up(PI[d][l].size(), 64) + up(RI[d][l].size(), 64);
+      }
+  }
+  size_t keeps = 0;
+  for (int l = 0; l < nlev; ++l) keeps += up(H[l].n, 256);
+  M->dbuf.alloc(dbl);
+  M->ibuf.alloc(ints > 0 ? ints : 1);
+  M->kbuf.alloc(keeps);
+  std::vector<double> hd(dbl, 0.0);
+  std::vector<int> hi(ints > 0 ? ints : 1, -1);
+  std::vector<unsigned char> hk(keeps, 0);
+  size_t od = 0, oi = 0, ok = 0;
+  MgArgs &A = M->args;
+  std::memset(&A, 0, sizeof(A));
+  A.nlev = nlev;
+  for (int l = 0; l < nlev; ++l) {
+    const HostLevel &L = H[l];
+    MgLevelDev &D = A.L[l];
+    D.nx = L.nx; D.ny = L.ny; D.nz = L.nz; D.n = L.n;
+    D.div_nx = FastDiv((uint32_t)L.nx);
+    D.div_nxy = FastDiv((uint32_t)(L.nx * L.ny));
+    const size_t nv = up(L.n, 32);
+    std::copy(L.S.begin(), L.S.end(), hd.begin() + od);
+    D.S = M->dbuf.p + od; od += up(L.S.size(), 32);
+    std::copy(L.dinv.begin(), L.dinv.end(), hd.begin() + od);
+    D.dinv = M->dbuf.p + od; od += nv;
+    std::copy(L.keep.begin(), L.keep.end(), hk.begin() + ok);
+    D.keep = M->kbuf.p + ok; ok += up(L.n, 256);
+    if (l > 0) { D.x = M->dbuf.p + od; od += nv; D.b = M->dbuf.p + od; od += nv; }
+    D.r = M->dbuf.p + od; od += nv;
+    D.w = M->dbuf.p + od; od += nv;
+    D.da = M->dbuf.p + od; od += nv;
+    D.db = M->dbuf.p + od; od += nv;
+    if (l + 1 < nlev) {
+      const double theta = 0.5 * (L.lam_hi + L.lam_hi / 10.0);
+      const double delta = 0.5 * (L.lam_hi - L.lam_hi / 10.0);
+      const double sigma = theta / delta, rho0 = 1.0 / sigma;
+      const double rho1 = 1.0 / (2.0 * sigma - rho0);
+      D.inv_theta = 1.0 / theta;
+      D.c1 = rho1 * rho0;
+      D.c2 = 2.0 * rho1 / delta;
+      for (int d = 0; d < 3; ++d) {
+        std::copy(PI[d][l].begin(), PI[d][l].end(), hi.begin() + oi);
+        D.pi[d] = M->ibuf.p + oi; oi += up(PI[d][l].size(), 64);
+        std::copy(RI[d][l].begin(), RI[d][l].end(), hi.begin() + oi);
+        D.ri[d] = M->ibuf.p + oi; oi += up(RI[d][l].size(), 64);
+        std::copy(PW[d][l].begin(), PW[d][l].end(), hd.begin() + od);
+        D.pw[d] = M->dbuf.p + od; od += up(PW[d][l].size(), 32);
+        std::copy(RW[d][l].begin(), RW[d][l].end(), hd.begin() + od);
+        D.rw[d] = M->dbuf.p + od; od += up(RW[d][l].size(), 32);
+      }
+    }
+  }
+  std::copy(inv.begin(), inv.end(), hd.begin() + od);
+  A.bottom_inv = M->dbuf.p + od; od += up(inv.size(), 32);
+  A.nbottom = nb;
+  SEM_REQUIRE(od <= dbl && oi <= hi.size() && ok <= keeps, "multigrid buffer layout overflow");
+  // guard: every device array of the hierarchy is 256-byte aligned
+  auto aligned = [](const void *p) { return ((uintptr_t)p & 255u) == 0; };
+  for (int l = 0; l < nlev; ++l) {
+    const MgLevelDev &D = A.L[l];
+    bool ok_al = aligned(D.S) && aligned(D.dinv) && aligned(D.keep) && aligned(D.r) &&
+                 aligned(D.w) && aligned(D.da) && aligned(D.db) && (l == 0 || (aligned(D.x) &&
+                                                                              aligned(D.b)));
+    if (l + 1 < nlev)
+      for (int d = 0; d < 3; ++d)
+        ok_al = ok_al && aligned(D.pi[d]) && aligned(D.pw[d]) && aligned(D.ri[d]) &&
+                aligned(D.rw[d]);
+    SEM_REQUIRE(ok_al, "multigrid arrays are not 256-byte aligned");
+  }
+  SEM_REQUIRE(aligned(A.bottom_inv), "multigrid arrays are not 256-byte aligned");
+  SEM_CHECK_CUDA(cudaMemcpyAsync(M->dbuf.p, hd.data(), hd.size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, st));
+  SEM_CHECK_CUDA(cudaMemcpyAsync(M->ibuf.p, hi.data(), hi.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, st));
+  SEM_CHECK_CUDA(cudaMemcpyAsync(M->kbuf.p, hk.data(), hk.size(), cudaMemcpyHostToDevice, st));
+  // the level-0 dinv comes from the coarse solver's unique-layout inverse
+  A.L[0].dinv = C.dinv.p;
+  A.ex = Lv.t.ex; A.ey = Lv.t.ey; A.ez = Lv.t.ez; A.bc = Lv.t.bc;
+  A.div_ex = FastDiv((uint32_t)Lv.t.ex);
+  A.div_ey = FastDiv((uint32_t)Lv.t.ey);
+  const size_t s0 = C.vec_stride;
+  A.x = C.vec.p; A.r = A.x + s0; A.z = A.r + s0; A.p = A.z + s0; A.w = A.p + s0;
+  // grid: one CTA per SM (grid barriers dominate; see coarse.cu)
+  int dev = 0, sms = 0, per_sm = 0;
+  SEM_CHECK_CUDA(cudaGetDevice(&dev));
+  SEM_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SEM_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_mgcg_kernel,
+                                                               kMgThreads, 0));
+  SEM_REQUIRE(per_sm >= 1, "multigrid coarse kernel cannot be resident");
+#ifndef SEM_MG_CTAS_PER_SM
+#define SEM_MG_CTAS_PER_SM 1
+#endif
+  M->grid = std::max(1, std::min(sms * std::min(per_sm, SEM_MG_CTAS_PER_SM),
+                                 (n0 + kMgThreads - 1) / kMgThreads));
+  const size_t ps = up((size_t)M->grid * 4, 32);
+  M->part.alloc(4 * ps);
+  A.partM = M->part.p;
+  A.partI = A.partM + ps;
+  A.partA = A.partI + ps;
+  A.partK = A.partA + ps;
+  A.iters = C.iters.p;
+  M->levels = nlev;
+  SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+  C.mg = std::move(M);
+}
+
+void coarse_mg_solve(CoarseSolver &C, const double *b_local, double *x_local, double tol,
+                     int maxit, cudaStream_t st) {
+  MgArgs A = C.mg->args;
+  A.b_local = b_local;
+  A.x_local = x_local;
+  A.tol2 = tol > 0 ? tol * tol : 0.0;
+  A.maxit = maxit;
+  void *args[] = {&A};
+  TraceScope ts("coarse_mgcg", 1, st);
+  SEM_CHECK_CUDA(cudaLaunchCooperativeKernel((const void *)coarse_mgcg_kernel, dim3(C.mg->grid),
+                                             dim3(kMgThreads), args, 0, st));
+}
+
+}  // namespace sem

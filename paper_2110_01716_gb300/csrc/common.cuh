@@ -187,6 +187,8 @@ void build_level(Level &L, int ex, int ey, int ez, int N, int bc, int geom, int 
                  const double *verts_host, bool want_g32, cudaStream_t st);
 void launch_ax_pair(const Level &L, const double *u, double *w, cudaStream_t st);
 void level_ensure_f32(Level &L, cudaStream_t st);
+// FP64 geometric factors of a level into `out` (computed again; for setup).
+void level_fp64_factors(const Level &L, DevBuf<double> &out, cudaStream_t st);
 
 template <typename T>
 void launch_ax(const Level &L, const T *u, T *w, cudaStream_t st);

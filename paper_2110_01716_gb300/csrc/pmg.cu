@@ -325,9 +325,14 @@ void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t s
   }
   // coarse solve: one persistent kernel at N = 1, launch-based Jacobi-PCG otherwise
   PmgLevel &Cl = *P->levp.back();
-  P->persistent_coarse = Cl.L->t.N == 1 && Cl.L->G64.p != nullptr;
+  P->persistent_coarse = Cl.L->t.N == 1 && Cl.L->geom == SEM_GEOM_STORED;
+  SEM_REQUIRE(d.coarse_mode == SEM_COARSE_JACOBI || d.coarse_mode == SEM_COARSE_MG,
+              "unknown coarse_mode %d", d.coarse_mode);
+  SEM_REQUIRE(d.coarse_mode == SEM_COARSE_JACOBI || P->persistent_coarse,
+              "SEM_COARSE_MG needs a coarsest level of order 1");
   if (P->persistent_coarse) {
     coarse_setup(P->coarse, *Cl.L, st);
+    if (d.coarse_mode == SEM_COARSE_MG) coarse_mg_setup(P->coarse, *Cl.L, st);
   } else {
     const int64_t nc = Cl.L->t.nl;
     P->cz.alloc(nc); P->cp.alloc(nc); P->cw.alloc(nc);
@@ -413,8 +418,12 @@ static void coarse_solve(sem_pmg *P, cudaStream_t st) {
   PmgLevel &Q = (*P->levp.back());
   Level &L = *Q.L;
   if (P->persistent_coarse) {
-    coarse_solve_persistent(P->coarse, L, Q.v64[0].p, Q.v64[1].p, P->desc.coarse_tol,
-                            P->desc.coarse_maxit, st);
+    if (P->coarse.mg)
+      coarse_mg_solve(P->coarse, Q.v64[0].p, Q.v64[1].p, P->desc.coarse_tol, P->desc.coarse_maxit,
+                      st);
+    else
+      coarse_solve_persistent(P->coarse, L, Q.v64[0].p, Q.v64[1].p, P->desc.coarse_tol,
+                              P->desc.coarse_maxit, st);
     return;
   }
   const Topo &t = L.t;

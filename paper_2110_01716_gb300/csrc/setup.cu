@@ -337,6 +337,18 @@ void build_level(Level &L, int ex, int ey, int ez, int N, int bc, int geom, int 
   SEM_CHECK_CUDA(cudaStreamSynchronize(st));
 }
 
+void level_fp64_factors(const Level &L, DevBuf<double> &out, cudaStream_t st) {
+  const Topo &t = L.t;
+  DevBuf<int> bad;
+  bad.alloc(1);
+  SEM_CHECK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+  out.alloc((size_t)t.E * 6 * t.Np3);
+  geometry_kernel<<<grid_for(t.nl, 256), 256, 0, st>>>(t, L.basis, L.verts.p, out.p, nullptr,
+                                                       nullptr, bad.p);
+  SEM_CHECK_CUDA(cudaGetLastError());
+  SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
 void level_ensure_f32(Level &L, cudaStream_t st) {
   const Topo &t = L.t;
   const bool need_g32 = L.geom == SEM_GEOM_STORED && !L.G32.p;

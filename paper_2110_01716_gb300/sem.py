@@ -27,6 +27,7 @@ SEM_AX_LOCAL, SEM_AX_ASSEMBLED = 0, 1
 SEM_FIELD_X, SEM_FIELD_Y, SEM_FIELD_Z, SEM_FIELD_MASS, SEM_FIELD_MULT, SEM_FIELD_MASK, \
     SEM_FIELD_DINV = range(7)
 SEM_SOLVER_PCG, SEM_SOLVER_FLEXCG = 0, 1
+SEM_COARSE_JACOBI, SEM_COARSE_MG = 0, 1
 SEM_MAX_ORDER = 11
 
 EXPORTED = ["sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_field", "sem_ax",
@@ -50,7 +51,8 @@ class sem_mesh_desc(C.Structure):
 class sem_pmg_desc(C.Structure):
     _fields_ = [("nlevels", C.c_int32), ("orders", C.c_int32 * 8), ("cheb_degree", C.c_int32),
                 ("lanczos_steps", C.c_int32), ("seed", C.c_uint64), ("smoother_dtype", C.c_int32),
-                ("coarse_tol", C.c_double), ("coarse_maxit", C.c_int32)]
+                ("coarse_tol", C.c_double), ("coarse_maxit", C.c_int32),
+                ("coarse_mode", C.c_int32)]
 
 
 class sem_solve_desc(C.Structure):
@@ -209,7 +211,8 @@ class Pmg:
     """Owning wrapper of a sem_pmg handle (keeps its mesh alive)."""
 
     def __init__(self, mesh: Mesh, orders=(7, 3, 1), cheb_degree=2, lanczos_steps=20, seed=0,
-                 smoother_dtype=SEM_F32, coarse_tol=1e-2, coarse_maxit=50, stream=None):
+                 smoother_dtype=SEM_F32, coarse_tol=1e-2, coarse_maxit=50, stream=None,
+                 coarse_mode=SEM_COARSE_JACOBI):
         desc = sem_pmg_desc()
         desc.nlevels = len(orders)
         for i, o in enumerate(orders):
@@ -220,6 +223,7 @@ class Pmg:
         desc.smoother_dtype = smoother_dtype
         desc.coarse_tol = float(coarse_tol)
         desc.coarse_maxit = int(coarse_maxit)
+        desc.coarse_mode = int(coarse_mode)
         h = C.c_void_p()
         check(lib().sem_pmg_setup(mesh.h, C.byref(desc), _stream(stream), C.byref(h)))
         self.h = h

@@ -175,3 +175,52 @@ def test_flexcg_pmg_reaches_1e8(bc, dtype):
     err = rel(x, xo)
     assert err < 1e-6, err
     assert info["iters"] <= io["iters"] + 3
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("e", [(6, 6, 6), (5, 7, 3), (12, 3, 5), (17, 16, 9)])
+def test_multigrid_coarse_mode_solves_the_n1_problem(bc, e):
+    """Single-level hierarchy at N = 1: the V-cycle is the coarse solve itself;
+    its residual, recomputed by the oracle, meets the requested tolerance."""
+    v = inputs.box_vertices(*e, 0.1, 7)
+    m = sem.Mesh(*e, 1, bc, verts=v)
+    L = oracle.Level(*e, 1, bc, v)
+    b = L.gs(inputs.random_field(L.nl, 5)) * L.mask
+    if bc == 1:
+        b -= L.dot(b, np.ones(L.nl)) / L.ng
+    P = sem.Pmg(m, orders=(1,), coarse_tol=1e-9, coarse_maxit=60, coarse_mode=sem.SEM_COARSE_MG)
+    zd = torch.empty(L.nl, device=DEV, dtype=torch.float64)
+    sem.sem_pmg_vcycle(P, torch.tensor(b, device=DEV), zd)
+    z = zd.cpu().numpy()
+    assert residual(L, b, z) <= 1.05e-9
+    # copies of each node hold the same bits (the result is a continuous field)
+    ids = L.ids
+    lo = np.full(L.ng, np.inf)
+    hi = np.full(L.ng, -np.inf)
+    np.minimum.at(lo, ids, z)
+    np.maximum.at(hi, ids, z)
+    assert np.array_equal(lo, hi)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_flexcg_with_multigrid_coarse_solve(bc):
+    e = 8
+    v = inputs.box_vertices(e, e, e, 0.1, 3)
+    m = sem.Mesh(e, e, e, 7, bc, verts=v)
+    L = oracle.Level(e, e, e, 7, bc, v)
+    b = manufactured(L)[1] if bc == 0 else fourier_rhs(L)
+    P = sem.Pmg(m, orders=(7, 3, 1), cheb_degree=3, smoother_dtype=sem.SEM_F32, coarse_tol=1e-2,
+                coarse_maxit=100, coarse_mode=sem.SEM_COARSE_MG)
+    bd = torch.tensor(b, device=DEV)
+    xd = torch.zeros_like(bd)
+    info = sem.sem_solve(m, P, bd, xd, sem.SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=100)
+    assert info["status"] == sem.SEM_OK, info
+    assert residual(L, b, xd.cpu().numpy()) <= 1.05e-8
+    assert info["iters"] <= 15
+
+
+def test_multigrid_coarse_mode_needs_order_one():
+    m = sem.Mesh(3, 3, 3, 4, 0, jitter=0.1, seed=2)
+    with pytest.raises(sem.SemError) as ei:
+        sem.Pmg(m, orders=(4, 2), coarse_mode=sem.SEM_COARSE_MG)
+    assert ei.value.status == sem.SEM_EINVAL
