@@ -44,6 +44,8 @@ METRIC = "Poisson solve time to 1e-8 (GDOF/s) & Ax GB/s vs HBM roofline; p50/p99
 E_SIDE, ORDER, MESH_SEED, RHS_SEED = 48, 7, 3, 3
 TOL = 1e-8
 CHEB_DEGREE, COARSE_TOL, COARSE_MAXIT, COARSE_MODE = 3, 1e-1, 30, 1
+SMOOTHER = "f32"
+SMOOTHER_DTYPES = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}  # sem_dtype values
 WORKLOAD = ("mixed-precision Neumann pressure solve: E=48^3=110592 jittered hexes (+-10% h, "
             "seed 3), N=7, pMG 7-3-1, Chebyshev(3)-Jacobi smoother in FP32, FP64 coarse solve "
             "(CG + lattice multigrid V(2,2), tol 1e-1, <=30 it), FP64 FlexCG to 1e-8 from x=0")
@@ -77,6 +79,8 @@ def parse_args():
     p.add_argument("--coarse-maxit", type=int, default=COARSE_MAXIT)
     p.add_argument("--coarse-tol", type=float, default=COARSE_TOL)
     p.add_argument("--cheb-degree", type=int, default=CHEB_DEGREE)
+    p.add_argument("--smoother", default=SMOOTHER, choices=["f64", "f32", "f16", "bf16"],
+                   help="arithmetic/storage of the smoothed pMG levels")
     p.add_argument("--coarse-mode", type=int, default=COARSE_MODE,
                    help="0: Jacobi-PCG, 1: multigrid-preconditioned CG on the N=1 lattice")
     return p.parse_args()
@@ -193,6 +197,8 @@ def operator_sweep(sem, torch, dev, hbm):
         kinds = ((sem.SEM_F64, torch.float64, "f64"), (sem.SEM_F32, torch.float32, "f32"))
         if gname == "stored_native":
             kinds = kinds[:1]
+        if gname == "stored":
+            kinds = kinds + ((sem.SEM_F16, torch.float32, "f16g"), (sem.SEM_BF16, torch.float32, "bf16g"))
         for dt, tdt, name in kinds:
             u = torch.rand(n, device=dev, dtype=tdt, generator=torch.Generator(dev).manual_seed(5))
             w = torch.empty_like(u)
@@ -211,7 +217,8 @@ def operator_sweep(sem, torch, dev, hbm):
             ms = statistics.median(times)
             esz = 8 if name == "f64" else 4
             stored = gname.startswith("stored")
-            bpp = 2 * esz + (6 * esz if stored else 0)
+            gsz = 2 if name in ("f16g", "bf16g") else esz
+            bpp = 2 * esz + (6 * gsz if stored else 0)
             bytes_alg = n * bpp + (mesh.ex * mesh.ey * mesh.ez * 24 * 8 if not stored else 0)
             flops = n * (12 * (N + 1) + 15)
             out[f"{name}_{gname}"] = {
@@ -304,7 +311,7 @@ def main():
     verts = inputs.box_vertices(side, side, side, 0.1, MESH_SEED)
     mesh = sem.Mesh(side, side, side, ORDER, sem.SEM_NEUMANN, sem.SEM_GEOM_STORED, verts=verts)
     pmg = sem.Pmg(mesh, orders=(7, 3, 1), cheb_degree=args.cheb_degree, lanczos_steps=20, seed=0,
-                  smoother_dtype=sem.SEM_F32, coarse_tol=args.coarse_tol,
+                  smoother_dtype=SMOOTHER_DTYPES[args.smoother], coarse_tol=args.coarse_tol,
                   coarse_maxit=args.coarse_maxit, coarse_mode=args.coarse_mode)
     b = rhs_on_device(sem, torch, mesh, dev)
     x = torch.zeros_like(b)
@@ -380,9 +387,9 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64+f32", "data": "synthetic",
+            "dtype": "f64+" + args.smoother, "data": "synthetic",
             "config": {"workload": WORKLOAD, "E": side ** 3, "N": ORDER, "n_local": nl,
-                       "cheb_degree": args.cheb_degree, "coarse_tol": args.coarse_tol,
+                       "smoother": args.smoother, "cheb_degree": args.cheb_degree, "coarse_tol": args.coarse_tol,
                        "coarse_maxit": args.coarse_maxit, "coarse_mode": args.coarse_mode,
                        "n_global": ng, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (working set ~6 GB), no flush"},

@@ -120,8 +120,15 @@ enum { SEM_AX_LOCAL = 0, SEM_AX_ASSEMBLED = 1 };
  * SEM_AX_LOCAL:     w = A_L u, element by element (no summation).
  * SEM_AX_ASSEMBLED: w = mask * gs(A_L u).
  * dtype: SEM_F64 (u, w double) or SEM_F32 (u, w float; factors rounded to
- * float once at mesh creation).  u and w are E-layout device vectors of
- * n_local elements and must not overlap. */
+ * float once at mesh creation), or SEM_F16 / SEM_BF16: u, w float and FP32
+ * arithmetic, but the six factors stored in 16 bits, G ~= scale_ef * q_p with
+ * scale_ef = float(max_p |G_ef,p|) per element e and factor f and q_p = G_p /
+ * scale_ef rounded once from FP64 (nearest, ties to even).  The 16-bit copy is
+ * built (and kept) on the first such call; this synchronises once.  u and w
+ * are E-layout device vectors of n_local elements and must not overlap; for
+ * the 32- and 16-bit kinds on stored geometry u must be 16-byte aligned
+ * (SEM_EINVAL otherwise).  The assembled FP32 forms sum the copies of a node
+ * across x-, then y-, then z-faces: every copy receives the same bits. */
 sem_status sem_ax(sem_mesh *mesh, sem_dtype dtype, const void *u, void *w, int32_t flags,
                   void *stream);
 
@@ -161,7 +168,9 @@ typedef struct {
   int32_t cheb_degree;      /* Chebyshev degree per smoothing, >= 1 */
   int32_t lanczos_steps;    /* steps of the lambda_max estimate, >= 2 */
   uint64_t seed;            /* start vector of the lambda_max estimate */
-  int32_t smoother_dtype;   /* sem_dtype of the smoothed levels: F64 or F32 */
+  int32_t smoother_dtype;   /* sem_dtype of the smoothed levels: F64, F32, or
+                               F16 / BF16 (FP32 vectors and arithmetic,
+                               factors stored as in sem_ax) */
   double coarse_tol;        /* coarsest level: FP64 Jacobi-PCG relative tol */
   int32_t coarse_maxit;     /* ... and iteration cap (tol <= 0: exactly maxit) */
   int32_t coarse_mode;      /* SEM_COARSE_JACOBI or SEM_COARSE_MG (below) */

@@ -1,0 +1,605 @@
+// ax32.cu -- FP32 stiffness operator on stored geometric factors (FP32, FP16
+// or BF16 storage), with the direct stiffness summation fused in.
+//
+// Sec. 2, footnote 1: w^e = sum_d D_d^T ( sum_e G_de D_e u^e ); Sec. 3: the
+// assembled operator is gs(A_L u) followed by the Dirichlet mask.
+//
+// Shared-memory traffic, not HBM, limits a straightforward column kernel in
+// FP32 (each FMA of the r and s contractions re-reads D and u from shared
+// memory).  Here each thread owns one (i, j) column of an element, loops over
+// k, and
+//   * keeps its rows D[i][.], D[j][.] and columns D[.][i], D[.][j] in registers;
+//   * reads the contracted u values as float4 from two shared copies of the
+//     element: natural (i fastest, for the r contraction) and transposed in
+//     (i, j) (j fastest, for the s contraction); rows are padded to an odd
+//     number of float4 so the eight rows a warp reads hit distinct banks;
+//   * reads D[k][.] and D[.][k] of the t contraction as warp-uniform float4;
+//   * keeps u and the t flux of its column in registers.
+//
+// Direct stiffness summation on the box is separable: summing the copies of
+// every shared node across x-faces, then across y-faces, then across z-faces
+// yields the full sum over all copies (a node shared by 2, 4 or 8 elements is
+// summed as a + b, (a + b) + (c + d), ...; every copy receives the same bits).
+// A CTA walks a segment of an x-line of elements in chunks of NE elements, so
+// the x-face sums of neighbouring elements happen in shared memory; the right
+// face of a chunk's last element waits in shared memory for the next chunk.
+// Faces where segments meet (seams; only when the box has too few x-lines to
+// fill the GPU) are summed by a small seam pass.  Two plane passes then sum
+// across y-faces and z-faces; face planes normal to y and z are rows of NP
+// contiguous values, so these passes move whole sectors.  Dirichlet masking is
+// done by the pass of each boundary's direction: a masked node's copies all lie
+// on that boundary plane, so later passes only add zeros.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "trace.cuh"
+
+namespace sem {
+
+template <int NP>
+struct A32 {
+  static constexpr int NP2 = NP * NP;
+  static constexpr int NP3 = NP2 * NP;
+  static constexpr int NE = (256 / NP2) < 1 ? 1 : (256 / NP2);
+  static constexpr int THREADS = NE * NP2;
+  static constexpr int C4 = (NP + 3) / 4;                            // float4 per row
+  static constexpr int RS = (C4 % 2 == 0) ? 4 * C4 + 4 : 4 * C4;     // padded row stride
+  static constexpr int PL = NP * RS;                                 // padded plane stride
+  static constexpr int ES = ((NP * PL / 4) % 2 == 0) ? NP * PL + 4 : NP * PL;  // padded element
+  // Staged variant (NP a multiple of 4): natural-order arrays keep unpadded
+  // rows (a warp reads at most four rows of one element, or of two elements
+  // 16 banks apart); the element's u and factors arrive by bulk copy.
+  static constexpr bool STAGED = NP % 4 == 0;
+  static constexpr int ESN = NP3 + (NP2 < 32 ? 16 : 0);              // natural element stride
+#ifndef SEM_AX32_MIN_CTAS
+#define SEM_AX32_MIN_CTAS 2
+#endif
+  static constexpr int MIN_CTAS = NP <= 8 ? SEM_AX32_MIN_CTAS : 1;
+};
+
+constexpr int round16(int b) { return (b + 15) & ~15; }
+
+// Shared-memory layout (bytes) of one CTA.
+template <int NP, int GK>
+struct L32 {
+  using S = A32<NP>;
+  static constexpr int GB = GK == 0 ? 4 : 2;                          // bytes per factor
+  static constexpr int U_BYTES = S::NE * S::NP3 * 4;                  // one stage of u
+  static constexpr int G_BYTES = S::NE * 6 * S::NP3 * GB;             // one stage of factors
+  static constexpr int STAGE = round16(U_BYTES) + round16(G_BYTES);
+  static constexpr int MBAR = 0;                                      // 2 x 8 bytes
+  static constexpr int STAGES = S::STAGED ? 16 : 16;
+  static constexpr int STAGES_END = S::STAGED ? STAGES + 2 * STAGE : STAGES;
+  static constexpr int DTAB = STAGES_END;                             // sD, sDT
+  static constexpr int UN = DTAB + round16(2 * NP * S::RS * 4);       // direct: padded natural u
+  static constexpr int UN_END = S::STAGED ? UN : UN + S::NE * S::ES * 4;
+  static constexpr int UT = UN_END;                                   // transposed u
+  static constexpr int WR = UT + S::NE * S::ES * 4;                   // natural r flux
+  static constexpr int WR_END = WR + S::NE * (S::STAGED ? S::ESN : S::ES) * 4;
+  static constexpr int WS = WR_END;                                   // transposed s flux
+  static constexpr int FACES = WS + S::NE * S::ES * 4;                // sFL, sFR, sCarry
+  static constexpr int BYTES = FACES + (2 * S::NE + 2) * S::NP2 * 4;
+};
+
+// Factor value from its stored bits (GK: 0 FP32, 1 FP16, 2 BF16).
+template <int GK>
+__device__ __forceinline__ float factor_value(float v) { return v; }
+template <int GK>
+__device__ __forceinline__ float factor_value(unsigned short b) {
+  if constexpr (GK == 1) return __half2float(__ushort_as_half(b));
+  else return __bfloat162float(__ushort_as_bfloat16(b));
+}
+template <int GK>
+using factor_t = typename std::conditional<GK == 0, float, unsigned short>::type;
+
+__device__ __forceinline__ float f4get(const float4 &v, int q) {
+  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
+
+// NP values of a 16-byte aligned shared row into registers.
+template <int NP>
+__device__ __forceinline__ void load_row(const float *row, float (&r)[NP]) {
+#pragma unroll
+  for (int c = 0; c < (NP + 3) / 4; ++c) {
+    const float4 v = *reinterpret_cast<const float4 *>(row + 4 * c);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (4 * c + q < NP) r[4 * c + q] = f4get(v, q);
+  }
+}
+
+// Hint: bring [p, p + bytes) into L2 (bulk prefetch; the range is shrunk to
+// whole 16-byte units inside it, so nothing outside it is touched).
+__device__ __forceinline__ void prefetch_l2(const void *p, int64_t bytes) {
+  uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t b = (a + (uintptr_t)bytes) & ~(uintptr_t)15;
+  a = (a + 15) & ~(uintptr_t)15;
+  while (a + 16 <= b) {
+    const uint32_t n = (uint32_t)((b - a) < (1u << 20) ? (b - a) : (1u << 20));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
+    a += n;
+  }
+}
+
+// ---- mbarrier and bulk-copy primitives (CTA scope)
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+// Bounded wait for the phase with the given parity; false if it never came.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// Global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+// that completes its bytes on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+constexpr int kMbarWaitLimit = 1 << 22;  // try_wait polls before a wait is declared lost
+
+struct Ax32Args {
+  Topo t;
+  const float *u;
+  float *w;
+  const void *G;       // [E][6][NP3] float or 16-bit
+  const float *scale;  // [E] per-element scale of 16-bit factors, else null
+  int32_t nseg;        // segments per x-line
+  int32_t seg_len;     // elements per segment (the last may be shorter)
+  int32_t dirichlet;
+  int *err;            // set to 1 if a bulk copy never completed
+};
+
+// First element (x index) of work unit `unit`.
+__device__ __forceinline__ int unit_ix0(const Ax32Args &a, int64_t unit) {
+  return (int)(unit % a.nseg) * a.seg_len;
+}
+
+template <int NP, int GK, bool ASSEMBLE>
+__global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
+    ax32_kernel(Ax32Args a, Basis bs) {
+  using S = A32<NP>;
+  using Lay = L32<NP, GK>;
+  using GT = factor_t<GK>;
+  constexpr int NP2 = S::NP2, NP3 = S::NP3, NE = S::NE, RS = S::RS, PL = S::PL, ES = S::ES;
+  constexpr int C4 = S::C4, N = NP - 1;
+  constexpr bool STAGED = S::STAGED;
+  extern __shared__ float4 smem4[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(smem4);
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + Lay::MBAR);
+  float *sD = reinterpret_cast<float *>(smem + Lay::DTAB);  // [NP][RS]  D[k][l]
+  float *sDT = sD + NP * RS;                                // [NP][RS]  D[l][k]
+  float *sU = reinterpret_cast<float *>(smem + Lay::UN);    // direct: padded natural u
+  float *sUT = reinterpret_cast<float *>(smem + Lay::UT);
+  float *sWR = reinterpret_cast<float *>(smem + Lay::WR);
+  float *sWS = reinterpret_cast<float *>(smem + Lay::WS);
+  float *sFL = reinterpret_cast<float *>(smem + Lay::FACES);  // [NE][NP2] left faces (i = 0)
+  float *sFR = sFL + NE * NP2;                                // [NE][NP2] right faces (i = N)
+  float *sCarry = sFR + NE * NP2;                             // [2][NP2]  deferred right face
+
+  const int le = threadIdx.x / NP2;
+  const int ij = threadIdx.x - le * NP2;
+  const int i = ij % NP, j = ij / NP;
+  for (int q = threadIdx.x; q < NP * RS; q += blockDim.x) {
+    const int r = q / RS, l = q % RS;
+    sD[q] = l < NP ? bs.D32[r * NP + l] : 0.f;
+    sDT[q] = l < NP ? bs.D32[l * NP + r] : 0.f;
+  }
+  if (STAGED && threadIdx.x == 0) {
+    mbar_init(smem_addr(&mbar[0]), 1);
+    mbar_init(smem_addr(&mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+
+  const Topo &t = a.t;
+  const int64_t units = (int64_t)t.ey * t.ez * a.nseg;
+  // natural-order views of this thread's element (rows along i)
+  constexpr int NRS = STAGED ? NP : RS, NPL = STAGED ? NP2 : PL;
+  float *uT = sUT + le * ES, *wS = sWS + le * ES;
+  float *wR = sWR + le * (STAGED ? S::ESN : ES);
+
+  // Bulk copies of a chunk's u and factors into stage `st`.
+  auto issue = [&](int64_t unit, int cx, int st) {
+    const int ix1 = min(t.ex, unit_ix0(a, unit) + a.seg_len);
+    const int n = min(NE, ix1 - cx);
+    const int64_t e0 = (unit / a.nseg) * t.ex + cx;
+    const uint32_t ub = (uint32_t)(n * NP3 * 4), gb = (uint32_t)(n * 6 * NP3 * Lay::GB);
+    unsigned char *dst = smem + Lay::STAGES + st * Lay::STAGE;
+    const uint32_t bar = smem_addr(&mbar[st]);
+    mbar_expect_tx(bar, ub + gb);
+    bulk_g2s(smem_addr(dst), a.u + e0 * NP3, ub, bar);
+    bulk_g2s(smem_addr(dst + round16(Lay::U_BYTES)),
+             static_cast<const unsigned char *>(a.G) + e0 * 6 * NP3 * Lay::GB, gb, bar);
+  };
+
+  int64_t unit = blockIdx.x;
+  int cx = unit < units ? unit_ix0(a, unit) : 0;
+  uint32_t g = 0;  // chunks done by this CTA (stage g & 1, phase parity (g >> 1) & 1)
+  if (STAGED && threadIdx.x == 0 && unit < units) issue(unit, cx, 0);
+
+  while (unit < units) {
+    const int64_t line = unit / a.nseg;
+    const int ix0 = unit_ix0(a, unit);
+    const int ix1 = min(t.ex, ix0 + a.seg_len);
+    const int cc = (cx - ix0) / NE;
+    const int nact = min(NE, ix1 - cx);
+    const bool active = le < nact;
+    const int ix = cx + le;
+    const int64_t e = line * t.ex + ix;
+    // the next chunk: in this segment, else the first of the next unit
+    int64_t nunit = unit;
+    int ncx = cx + NE;
+    if (ncx >= ix1) {
+      nunit = unit + gridDim.x;
+      ncx = nunit < units ? unit_ix0(a, nunit) : 0;
+    }
+    const float *stU = nullptr;
+    const GT *stG = nullptr;
+    if constexpr (STAGED) {
+      if (threadIdx.x == 0 && nunit < units) issue(nunit, ncx, (g + 1) & 1);
+      const bool ok = mbar_wait(smem_addr(&mbar[g & 1]), (g >> 1) & 1, kMbarWaitLimit);
+      if (__syncthreads_or(!ok)) {
+        // a copy never completed: record it, let copies in flight land, stop
+        if (threadIdx.x == 0) {
+          atomicExch(a.err, 1);
+          mbar_wait(smem_addr(&mbar[g & 1]), (g >> 1) & 1, kMbarWaitLimit);
+          if (nunit < units) mbar_wait(smem_addr(&mbar[(g + 1) & 1]), ((g + 1) >> 1) & 1,
+                                       kMbarWaitLimit);
+        }
+        __syncthreads();
+        return;
+      }
+      const unsigned char *stage = smem + Lay::STAGES + (g & 1) * Lay::STAGE;
+      stU = reinterpret_cast<const float *>(stage) + le * NP3;
+      stG = reinterpret_cast<const GT *>(stage + round16(Lay::U_BYTES)) + le * 6 * NP3;
+    } else if (threadIdx.x == 0 && nunit < units) {
+      const int64_t ne0 = (nunit / a.nseg) * t.ex + ncx;
+      const int nn = min(NE, min(t.ex, unit_ix0(a, nunit) + a.seg_len) - ncx);
+      prefetch_l2(a.u + ne0 * NP3, (int64_t)nn * NP3 * 4);
+      prefetch_l2(static_cast<const unsigned char *>(a.G) + ne0 * 6 * NP3 * Lay::GB,
+                  (int64_t)nn * 6 * NP3 * Lay::GB);
+    }
+    const float *uN = STAGED ? stU : sU + le * ES;
+
+    // ---- u: registers along k, transposed copy (and padded natural copy)
+    float ru[NP];
+    if (active) {
+      if constexpr (STAGED) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          const float v = stU[k * NP2 + ij];
+          ru[k] = v;
+          uT[k * PL + i * RS + j] = v;
+        }
+      } else {
+        const float *ue = a.u + e * NP3 + ij;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          const float v = __ldg(ue + k * NP2);
+          ru[k] = v;
+          sU[le * ES + k * PL + j * RS + i] = v;
+          uT[k * PL + i * RS + j] = v;
+        }
+      }
+    }
+    __syncthreads();
+    // ---- gradients, geometric factors, fluxes
+    float wt[NP];
+    if (active) {
+      float Dr[NP], Ds[NP];
+      load_row<NP>(sD + i * RS, Dr);
+      load_row<NP>(sD + j * RS, Ds);
+      const GT *Gg = static_cast<const GT *>(a.G) + e * 6 * NP3 + ij;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        float ur = 0.f, us = 0.f, ut = 0.f;
+        const float *pa = uN + k * NPL + j * NRS, *pb = uT + k * PL + i * RS, *pd = sD + k * RS;
+#pragma unroll
+        for (int c = 0; c < C4; ++c) {
+          const float4 va = *reinterpret_cast<const float4 *>(pa + 4 * c);
+          const float4 vb = *reinterpret_cast<const float4 *>(pb + 4 * c);
+          const float4 vd = *reinterpret_cast<const float4 *>(pd + 4 * c);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int l = 4 * c + q;
+            if (l < NP) {
+              ur = fmaf(Dr[l], f4get(va, q), ur);
+              us = fmaf(Ds[l], f4get(vb, q), us);
+              ut = fmaf(f4get(vd, q), ru[l], ut);
+            }
+          }
+        }
+        float g6[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+          if constexpr (STAGED) g6[f] = factor_value<GK>(stG[f * NP3 + k * NP2 + ij]);
+          else g6[f] = factor_value<GK>(__ldg(Gg + f * NP3 + k * NP2));
+        }
+        wR[k * NPL + j * NRS + i] = g6[0] * ur + g6[1] * us + g6[2] * ut;
+        wS[k * PL + i * RS + j] = g6[1] * ur + g6[3] * us + g6[4] * ut;
+        wt[k] = g6[2] * ur + g6[4] * us + g6[5] * ut;
+      }
+    }
+    __syncthreads();
+    // ---- divergence: w = scale * (D_r^T wr + D_s^T ws + D_t^T wt)
+    if (active) {
+      float DTr[NP], DTs[NP];
+      load_row<NP>(sDT + i * RS, DTr);
+      load_row<NP>(sDT + j * RS, DTs);
+      const float sc = GK == 0 ? 1.f : __ldg(a.scale + e);
+      float *we = a.w + e * NP3 + ij;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        float acc = 0.f;
+        const float *pa = wR + k * NPL + j * NRS, *pb = wS + k * PL + i * RS, *pd = sDT + k * RS;
+#pragma unroll
+        for (int c = 0; c < C4; ++c) {
+          const float4 va = *reinterpret_cast<const float4 *>(pa + 4 * c);
+          const float4 vb = *reinterpret_cast<const float4 *>(pb + 4 * c);
+          const float4 vd = *reinterpret_cast<const float4 *>(pd + 4 * c);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int l = 4 * c + q;
+            if (l < NP) {
+              acc = fmaf(DTr[l], f4get(va, q), acc);
+              acc = fmaf(DTs[l], f4get(vb, q), acc);
+              acc = fmaf(f4get(vd, q), wt[l], acc);
+            }
+          }
+        }
+        if (GK != 0) acc *= sc;
+        if (!ASSEMBLE || (i != 0 && i != N)) we[k * NP2] = acc;
+        else if (i == 0) sFL[le * NP2 + k * NP + j] = acc;
+        else sFR[le * NP2 + k * NP + j] = acc;
+      }
+    }
+    if constexpr (ASSEMBLE) {
+      __syncthreads();
+      // ---- x-face sums (lower-x copy + upper-x copy), masks, carries
+      if (active && i == 0) {
+        const bool from_chunk = le > 0, from_carry = le == 0 && cx > ix0;
+        const float *left = from_chunk ? sFR + (le - 1) * NP2 : sCarry + ((cc - 1) & 1) * NP2;
+        const bool zero = ix == 0 && a.dirichlet;
+        float *we = a.w + e * NP3 + j * NP;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          const float own = sFL[le * NP2 + k * NP + j];
+          if (from_chunk || from_carry) {
+            const float s = left[k * NP + j] + own;
+            we[k * NP2] = s;
+            we[k * NP2 - NP3 + N] = s;  // element e - 1, i = N
+          } else {
+            we[k * NP2] = zero ? 0.f : own;  // box boundary or seam
+          }
+        }
+      }
+      if (active && i == N && le == nact - 1) {
+        float *we = a.w + e * NP3 + j * NP + N;
+        const bool last_of_segment = ix == ix1 - 1;
+        const bool zero = ix == t.ex - 1 && a.dirichlet;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          const float own = sFR[le * NP2 + k * NP + j];
+          if (last_of_segment) we[k * NP2] = zero ? 0.f : own;  // box boundary or seam
+          else sCarry[(cc & 1) * NP2 + k * NP + j] = own;         // summed by the next chunk
+        }
+      }
+    }
+    unit = nunit;
+    cx = ncx;
+    ++g;
+  }
+}
+
+// Seams: x-faces where two segments of a line meet (lower + upper copy).
+__global__ void ax32_seam_kernel(Topo t, int nseg, int seg_len, float *__restrict__ w) {
+  const int Np = t.Np, Np2 = Np * Np;
+  const int64_t seams = (int64_t)t.ey * t.ez * (nseg - 1);
+  const int64_t total = seams * Np2;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = q / Np2;
+    const int jk = (int)(q - s * Np2);
+    const int64_t line = s / (nseg - 1);
+    const int part = (int)(s - line * (nseg - 1)) + 1;
+    const int64_t e = line * t.ex + (int64_t)part * seg_len;
+    float *hi = w + e * t.Np3 + (int64_t)jk * Np;  // i = 0 of the upper element
+    float *lo = hi - t.Np3 + (Np - 1);             // i = N of the lower element
+    const float v = *lo + *hi;
+    *lo = v;
+    *hi = v;
+  }
+}
+
+// Face planes normal to y (DIR 1) or z (DIR 2): lower copy + upper copy, and
+// the Dirichlet mask of the box boundary planes of that direction.  One thread
+// per node of each element's lower plane (plus the upper plane of the last
+// layer under Dirichlet).
+template <int DIR>
+__global__ void plane_sum_kernel(Topo t, float *__restrict__ w, int dirichlet) {
+  const int Np = t.Np, N = t.N;
+  const uint32_t Np2 = (uint32_t)Np * Np;
+  const uint64_t total = (uint64_t)t.E * Np2;
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t q32 = (uint32_t)q;  // E * Np2 < 2^32 (checked by the launcher)
+    const uint32_t r = t.div_np.div(q32);
+    const uint32_t a = q32 - r * Np;   // fastest in-plane index: i
+    const uint32_t e = t.div_np.div(r);
+    const uint32_t b = r - e * Np;     // second in-plane index: k (y planes) or j (z planes)
+    int64_t lo_off, hi_off, stride_e;
+    int layer, layers;
+    if (DIR == 1) {
+      const uint32_t ex_e = t.div_ex.div(e);
+      layer = (int)(ex_e - t.div_ey.div(ex_e) * t.ey);
+      layers = t.ey;
+      lo_off = (int64_t)b * Np2 + a;
+      hi_off = lo_off + (int64_t)N * Np;
+      stride_e = t.ex;
+    } else {
+      layer = (int)t.div_ey.div(t.div_ex.div(e));
+      layers = t.ez;
+      lo_off = (int64_t)b * Np + a;
+      hi_off = lo_off + (int64_t)N * Np2;
+      stride_e = (int64_t)t.ex * t.ey;
+    }
+    float *we = w + (int64_t)e * t.Np3;
+    if (layer > 0) {
+      float *below = we - stride_e * t.Np3 + hi_off;
+      const float v = *below + we[lo_off];
+      *below = v;
+      we[lo_off] = v;
+    } else if (dirichlet) {
+      we[lo_off] = 0.f;
+    }
+    if (dirichlet && layer == layers - 1) we[hi_off] = 0.f;
+  }
+}
+
+static int sm_count() {
+  static int n[64] = {};
+  int dev = 0;
+  SEM_CHECK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return 152;
+  if (!n[dev]) SEM_CHECK_CUDA(cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev));
+  return n[dev];
+}
+
+// Resident CTAs per SM of one kernel instantiation (queried once per device;
+// sets the dynamic shared-memory limit on the way).
+template <int NP, int GK, bool ASSEMBLE>
+static int ax32_resident() {
+  static int res[64] = {};
+  int dev = 0;
+  SEM_CHECK_CUDA(cudaGetDevice(&dev));
+  SEM_REQUIRE(dev >= 0 && dev < 64, "device index %d out of range", dev);
+  if (!res[dev]) {
+    auto kern = ax32_kernel<NP, GK, ASSEMBLE>;
+    constexpr int bytes = L32<NP, GK>::BYTES;
+    SEM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    int r = 0;
+    SEM_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, A32<NP>::THREADS, bytes));
+    SEM_REQUIRE(r >= 1, "operator kernel does not fit on an SM");
+    res[dev] = r;
+  }
+  return res[dev];
+}
+
+template <int NP, int GK>
+static void ax32_np(const Level &L, const float *u, float *w, bool assemble, cudaStream_t st) {
+  using S = A32<NP>;
+  const Topo &t = L.t;
+  Ax32Args a;
+  a.t = t;
+  a.u = u;
+  a.w = w;
+  const int s = GK == 2 ? 1 : 0;
+  a.G = GK == 0 ? (const void *)L.G32.p : (const void *)L.G16[s].p;
+  a.scale = GK == 0 ? nullptr : L.G16scale[s].p;
+  a.err = L.err.p;
+  SEM_REQUIRE(a.G != nullptr, "stored factors of this precision were not built");
+  SEM_REQUIRE(a.err != nullptr, "level has no error flag");
+  if (S::STAGED)
+    SEM_REQUIRE(reinterpret_cast<uintptr_t>(u) % 16 == 0 && reinterpret_cast<uintptr_t>(a.G) % 16 == 0,
+                "u must be 16-byte aligned");
+  a.dirichlet = t.bc == SEM_DIRICHLET;
+  const int resident = assemble ? ax32_resident<NP, GK, true>() : ax32_resident<NP, GK, false>();
+  const int64_t slots = (int64_t)sm_count() * resident;
+  // Work units are x-line segments: whole lines when there are at least two
+  // per resident CTA (no seams), otherwise lines are split.
+  const int64_t lines = (int64_t)t.ey * t.ez;
+  const int64_t target = 2 * slots;
+  int nseg = 1;
+  if (lines < target) {
+    const int64_t want = (target + lines - 1) / lines;
+    const int64_t most = (t.ex + S::NE - 1) / S::NE;  // at least one chunk per segment
+    nseg = (int)(want < most ? want : most);
+    if (nseg < 1) nseg = 1;
+  }
+  a.seg_len = (t.ex + nseg - 1) / nseg;
+  a.nseg = (t.ex + a.seg_len - 1) / a.seg_len;
+  const int64_t units = lines * a.nseg;
+  const int grid = (int)(units < slots ? units : slots);  // persistent: every CTA resident
+  constexpr int bytes = L32<NP, GK>::BYTES;
+  static const char *names[3][2] = {{"ax32_f32", "ax32_f32_local"},
+                                    {"ax32_f16g", "ax32_f16g_local"},
+                                    {"ax32_bf16g", "ax32_bf16g_local"}};
+  {
+    TraceScope ts(names[GK][assemble ? 0 : 1], t.N, st);
+    if (assemble) ax32_kernel<NP, GK, true><<<grid, S::THREADS, bytes, st>>>(a, L.basis);
+    else ax32_kernel<NP, GK, false><<<grid, S::THREADS, bytes, st>>>(a, L.basis);
+    SEM_CHECK_CUDA(cudaGetLastError());
+  }
+  if (!assemble) return;
+  SEM_REQUIRE((uint64_t)t.E * t.Np * t.Np < (1ull << 32), "mesh too large for the plane passes");
+  TraceScope ts("plane_sum", t.N, st);
+  if (a.nseg > 1) {
+    const int64_t n = lines * (a.nseg - 1) * t.Np * t.Np;
+    const int64_t b = (n + 255) / 256;
+    ax32_seam_kernel<<<(int)(b < 152 * 8 ? b : 152 * 8), 256, 0, st>>>(t, a.nseg, a.seg_len, w);
+    SEM_CHECK_CUDA(cudaGetLastError());
+  }
+  const int64_t n = t.E * t.Np * t.Np;
+  const int64_t b = (n + 255) / 256;
+  const int pg = (int)(b < 152 * 16 ? b : 152 * 16);
+  plane_sum_kernel<1><<<pg, 256, 0, st>>>(t, w, a.dirichlet);
+  SEM_CHECK_CUDA(cudaGetLastError());
+  plane_sum_kernel<2><<<pg, 256, 0, st>>>(t, w, a.dirichlet);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+template <int GK>
+static void ax32_dispatch(const Level &L, const float *u, float *w, bool assemble,
+                          cudaStream_t st) {
+  switch (L.t.Np) {
+    case 2: ax32_np<2, GK>(L, u, w, assemble, st); break;
+    case 3: ax32_np<3, GK>(L, u, w, assemble, st); break;
+    case 4: ax32_np<4, GK>(L, u, w, assemble, st); break;
+    case 5: ax32_np<5, GK>(L, u, w, assemble, st); break;
+    case 6: ax32_np<6, GK>(L, u, w, assemble, st); break;
+    case 7: ax32_np<7, GK>(L, u, w, assemble, st); break;
+    case 8: ax32_np<8, GK>(L, u, w, assemble, st); break;
+    case 9: ax32_np<9, GK>(L, u, w, assemble, st); break;
+    case 10: ax32_np<10, GK>(L, u, w, assemble, st); break;
+    case 11: ax32_np<11, GK>(L, u, w, assemble, st); break;
+    case 12: ax32_np<12, GK>(L, u, w, assemble, st); break;
+    default: fail(SEM_EINVAL, "unsupported order N=%d", L.t.N);
+  }
+}
+
+// FP32 operator on stored factors: kind SEM_F32 (float factors), SEM_F16 or
+// SEM_BF16 (16-bit factors); assemble: w = mask * gs(A_L u), else w = A_L u.
+void launch_ax32(const Level &L, int kind, const float *u, float *w, bool assemble,
+                 cudaStream_t st) {
+  SEM_REQUIRE(L.geom == SEM_GEOM_STORED, "launch_ax32 needs stored geometry");
+  if (kind == SEM_F32) ax32_dispatch<0>(L, u, w, assemble, st);
+  else if (kind == SEM_F16) ax32_dispatch<1>(L, u, w, assemble, st);
+  else if (kind == SEM_BF16) ax32_dispatch<2>(L, u, w, assemble, st);
+  else fail(SEM_EINVAL, "launch_ax32: unknown kind %d", kind);
+}
+
+}  // namespace sem

@@ -253,15 +253,22 @@ sem_status sem_ax(sem_mesh *mesh, sem_dtype dtype, const void *u, void *w, int32
         launch_gs<double>(mesh->fine, (double *)w, st);
         launch_mask<double>(mesh->fine, (double *)w, st);
       }
-    } else if (dtype == SEM_F32) {
+    } else if (dtype == SEM_F32 && mesh->fine.geom != SEM_GEOM_STORED) {
       if (!mesh->fine.dinv32.p) level_ensure_f32(mesh->fine, st);
       launch_ax<float>(mesh->fine, (const float *)u, (float *)w, st);
       if (flags == SEM_AX_ASSEMBLED) {
         launch_gs<float>(mesh->fine, (float *)w, st);
         launch_mask<float>(mesh->fine, (float *)w, st);
       }
+    } else if (dtype == SEM_F32 || dtype == SEM_F16 || dtype == SEM_BF16) {
+      if (dtype == SEM_F32) {
+        if (!mesh->fine.G32.p) level_ensure_f32(mesh->fine, st);
+      } else {
+        level_ensure_g16(mesh->fine, dtype, st);
+      }
+      launch_ax32(mesh->fine, dtype, (const float *)u, (float *)w, flags == SEM_AX_ASSEMBLED, st);
     } else {
-      fail(SEM_EINVAL, "sem_ax supports SEM_F64 and SEM_F32");
+      fail(SEM_EINVAL, "unknown dtype %d", (int)dtype);
     }
   });
 }

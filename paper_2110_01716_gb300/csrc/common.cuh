@@ -167,13 +167,16 @@ struct Level {
   DevBuf<double> G64;              // [E][6][Np3]  (rr, rs, rt, ss, st, tt)
   DevBuf<float> G32;               // [E][6][Np3]
   DevBuf<float2> G2;               // [E][6][Np3] FP64 factors split into float pairs
+  DevBuf<uint16_t> G16[2];         // [E][6][Np3] G / scale as FP16 [0] or BF16 [1] bits
+  DevBuf<float> G16scale[2];       // [E] per element: max |G| over its six factors
+  DevBuf<int> err;                 // set by kernels whose bounded waits ran out
   DevBuf<int32_t> shared_nodes;    // unique ids of nodes with more than one copy
   int64_t n_shared = 0;
   DevBuf<double> dinv64;           // mask / assembled diagonal
   DevBuf<float> dinv32;
   size_t device_bytes() const {
-    return verts.bytes() + G64.bytes() + G32.bytes() + G2.bytes() + shared_nodes.bytes() +
-           dinv64.bytes() + dinv32.bytes();
+    return verts.bytes() + G64.bytes() + G32.bytes() + G2.bytes() + G16[0].bytes() +
+           G16[1].bytes() + G16scale[0].bytes() + G16scale[1].bytes() + err.bytes() + shared_nodes.bytes() + dinv64.bytes() + dinv32.bytes();
   }
 };
 
@@ -187,6 +190,14 @@ void build_level(Level &L, int ex, int ey, int ez, int N, int bc, int geom, int 
                  const double *verts_host, bool want_g32, cudaStream_t st);
 void launch_ax_pair(const Level &L, const double *u, double *w, cudaStream_t st);
 void level_ensure_f32(Level &L, cudaStream_t st);
+// 16-bit geometric factors (kind SEM_F16 or SEM_BF16) with per-element,
+// per-factor scales, plus the FP32 Jacobi inverse.
+void level_ensure_g16(Level &L, int kind, cudaStream_t st);
+void level_ensure_dinv32(Level &L, cudaStream_t st);
+// FP32 operator on stored factors, kind SEM_F32 / SEM_F16 / SEM_BF16 (the
+// factor storage); assemble: w = mask * gs(A_L u), else w = A_L u.
+void launch_ax32(const Level &L, int kind, const float *u, float *w, bool assemble,
+                 cudaStream_t st);
 // FP64 geometric factors of a level into `out` (computed again; for setup).
 void level_fp64_factors(const Level &L, DevBuf<double> &out, cudaStream_t st);
 

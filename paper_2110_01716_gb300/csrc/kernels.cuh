@@ -34,8 +34,16 @@ template <typename A, typename B>
 void launch_convert(int64_t n, const A *a, B *b, cudaStream_t st);
 
 // Assembled operator on a level: w = mask * gs(A_L u).
+// FP32 on stored factors takes the fused operator (x-face sums in the operator
+// kernel, plane passes for y and z).
 template <typename T>
 inline void apply_assembled(const Level &L, const T *u, T *w, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (L.geom == SEM_GEOM_STORED) {
+      launch_ax32(L, SEM_F32, u, w, true, st);
+      return;
+    }
+  }
   launch_ax<T>(L, u, w, st);
   launch_gs<T>(L, w, st);
   launch_mask<T>(L, w, st);

@@ -283,8 +283,8 @@ void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t s
   SEM_REQUIRE(d.cheb_degree >= 1 && d.cheb_degree <= 16, "cheb_degree=%d outside [1,16]",
               d.cheb_degree);
   SEM_REQUIRE(d.lanczos_steps >= 2 && d.lanczos_steps <= 200, "lanczos_steps outside [2,200]");
-  SEM_REQUIRE(d.smoother_dtype == SEM_F64 || d.smoother_dtype == SEM_F32,
-              "smoother_dtype must be SEM_F64 or SEM_F32");
+  SEM_REQUIRE(d.smoother_dtype >= SEM_F64 && d.smoother_dtype <= SEM_BF16,
+              "smoother_dtype must be SEM_F64, SEM_F32, SEM_F16 or SEM_BF16");
   SEM_REQUIRE(d.coarse_maxit >= 0 && d.coarse_maxit <= 100000, "coarse_maxit out of range");
   P->mesh = mesh;
   P->desc = d;
@@ -297,7 +297,9 @@ void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t s
   for (int l = 0; l < d.nlevels; ++l) {
     PmgLevel &Q = *P->levp[l];
     const bool coarsest = (l == d.nlevels - 1);
-    Q.dtype = coarsest ? SEM_F64 : d.smoother_dtype;
+    const bool half = d.smoother_dtype == SEM_F16 || d.smoother_dtype == SEM_BF16;
+    Q.dtype = coarsest ? SEM_F64 : (half ? SEM_F32 : d.smoother_dtype);
+    Q.g16 = (!coarsest && half) ? d.smoother_dtype : 0;
     if (l == 0) {
       Q.L = &mesh->fine;
     } else {
@@ -305,10 +307,11 @@ void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t s
       // the N = 1 coarsest level keeps FP64 factors for its element matrices
       const int arith = (coarsest && d.orders[l] == 1) ? SEM_ARITH_NATIVE : F.arith;
       build_level(*Q.own, F.t.ex, F.t.ey, F.t.ez, d.orders[l], F.t.bc, SEM_GEOM_STORED, arith,
-                  F.verts_host.data(), Q.dtype == SEM_F32, st);
+                  F.verts_host.data(), Q.dtype == SEM_F32 && !Q.g16, st);
       Q.L = Q.own.get();
     }
-    if (Q.dtype == SEM_F32) level_ensure_f32(*Q.L, st);
+    if (Q.g16) level_ensure_g16(*Q.L, Q.g16, st);
+    else if (Q.dtype == SEM_F32) level_ensure_f32(*Q.L, st);
     const int64_t n = Q.L->t.nl;
     // vectors: 0 b, 1 x, 2 r, 3 d, 4 w
     for (int v = 0; v < 5; ++v) {
@@ -342,6 +345,18 @@ void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t s
 }
 
 // ------------------------------------------------------------------ V-cycle
+// Assembled operator of a smoothed level in its own precision.
+template <typename T>
+static void level_apply(const PmgLevel &Q, const T *u, T *w, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (Q.g16) {
+      launch_ax32(*Q.L, Q.g16, u, w, true, st);
+      return;
+    }
+  }
+  apply_assembled<T>(*Q.L, u, w, st);
+}
+
 template <typename T>
 static void smooth(sem_pmg *P, int l, bool x_zero, cudaStream_t st) {
   PmgLevel &Q = (*P->levp[l]);
@@ -355,7 +370,7 @@ static void smooth(sem_pmg *P, int l, bool x_zero, cudaStream_t st) {
   const double theta = 0.5 * (Q.lam_hi + Q.lam_lo), delta = 0.5 * (Q.lam_hi - Q.lam_lo);
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
-  if (!x_zero) apply_assembled<T>(L, x, w, st);
+  if (!x_zero) level_apply<T>(Q, x, w, st);
   const bool f64 = sizeof(T) == 8;
   {
   TraceScope ts(f64 ? "cheb_start_f64" : "cheb_start_f32", L.t.N, st);
@@ -364,7 +379,7 @@ static void smooth(sem_pmg *P, int l, bool x_zero, cudaStream_t st) {
   SEM_CHECK_CUDA(cudaGetLastError());
   }
   for (int it = 2; it <= P->desc.cheb_degree; ++it) {
-    apply_assembled<T>(L, d, w, st);
+    level_apply<T>(Q, d, w, st);
     double rho1 = 1.0 / (2.0 * sigma - rho);
     TraceScope ts(f64 ? "cheb_step_f64" : "cheb_step_f32", L.t.N, st);
     cheb_step_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(L.t, w, dinv, r, d, x,
@@ -469,10 +484,9 @@ static void vcycle_dispatch(sem_pmg *P, int l, cudaStream_t st) {
 template <typename T, typename Tn>
 static void vcycle_level(sem_pmg *P, int l, cudaStream_t st) {
   PmgLevel &Q = (*P->levp[l]);
-  const Level &L = *Q.L;
   smooth<T>(P, l, true, st);
   // residual w = A x (assembled); the restriction forms (b - w) / mult
-  apply_assembled<T>(L, vec_of<T>(Q, 1), vec_of<T>(Q, 4), st);
+  level_apply<T>(Q, vec_of<T>(Q, 1), vec_of<T>(Q, 4), st);
   restrict_to<T, Tn>(P, l, st);
   vcycle_dispatch<Tn>(P, l + 1, st);
   prolong_from<Tn, T>(P, l, st);

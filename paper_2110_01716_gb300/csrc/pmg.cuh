@@ -12,7 +12,8 @@ namespace sem {
 struct PmgLevel {
   Level *L = nullptr;          // level 0 is the mesh's own fine level
   std::unique_ptr<Level> own;  // coarser levels are owned here
-  int dtype = SEM_F64;         // arithmetic of the level's smoother
+  int dtype = SEM_F64;         // arithmetic of the level's smoother (F64 or F32)
+  int g16 = 0;                 // SEM_F16 / SEM_BF16: FP32 smoother on 16-bit factors
   double lam_lo = 0.0, lam_hi = 0.0;
   DevBuf<double> v64[5];       // b, x, r, d, w in FP64 ...
   DevBuf<float> v32[5];        // ... or FP32

@@ -7,6 +7,9 @@
 #include <cmath>
 #include <cstring>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "device_basis.cuh"
 
@@ -295,6 +298,8 @@ void build_level(Level &L, int ex, int ey, int ez, int N, int bc, int geom, int 
   L.verts.alloc(ev.size());
   SEM_CHECK_CUDA(cudaMemcpyAsync(L.verts.p, ev.data(), ev.size() * sizeof(double),
                                  cudaMemcpyHostToDevice, st));
+  L.err.alloc(1);
+  SEM_CHECK_CUDA(cudaMemsetAsync(L.err.p, 0, sizeof(int), st));
   DevBuf<int> bad;
   bad.alloc(1);
   SEM_CHECK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
@@ -345,6 +350,60 @@ void level_fp64_factors(const Level &L, DevBuf<double> &out, cudaStream_t st) {
   out.alloc((size_t)t.E * 6 * t.Np3);
   geometry_kernel<<<grid_for(t.nl, 256), 256, 0, st>>>(t, L.basis, L.verts.p, out.p, nullptr,
                                                        nullptr, bad.p);
+  SEM_CHECK_CUDA(cudaGetLastError());
+  SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+// One thread per element: scale = max |G| over the element's six factors and
+// points, in FP32 (1 if all are zero); stored value = G / scale rounded once
+// from FP64 to FP16 or BF16 (nearest, ties to even).
+__global__ void g16_kernel(int64_t E, int Np3, int kind, const double *__restrict__ G,
+                           uint16_t *__restrict__ G16, float *__restrict__ scale) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double *g = G + e * 6 * Np3;
+    double m = 0.0;
+    for (int p = 0; p < 6 * Np3; ++p) m = fmax(m, fabs(g[p]));
+    const float sc = m > 0.0 ? (float)m : 1.0f;
+    scale[e] = sc;
+    uint16_t *o = G16 + e * 6 * Np3;
+    for (int p = 0; p < 6 * Np3; ++p) {
+      const double v = g[p] / (double)sc;
+      o[p] = kind == SEM_F16 ? __half_as_ushort(__double2half(v))
+                             : __bfloat16_as_ushort(__double2bfloat16(v));
+    }
+  }
+}
+
+void level_ensure_dinv32(Level &L, cudaStream_t st) {
+  if (L.dinv32.p) return;
+  const Topo &t = L.t;
+  DevBuf<double> g;
+  level_fp64_factors(L, g, st);
+  L.dinv32.alloc(t.nl);
+  DevBuf<double> d;
+  d.alloc(t.nl);
+  local_diag_kernel<<<grid_for(t.nl, 256), 256, 0, st>>>(t, L.basis, g.p, L.verts.p, d.p);
+  SEM_CHECK_CUDA(cudaGetLastError());
+  launch_gs<double>(L, d.p, st);
+  invert_diag_kernel<<<grid_for(t.nl, 256), 256, 0, st>>>(t, d.p, nullptr, L.dinv32.p);
+  SEM_CHECK_CUDA(cudaGetLastError());
+  SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+void level_ensure_g16(Level &L, int kind, cudaStream_t st) {
+  SEM_REQUIRE(kind == SEM_F16 || kind == SEM_BF16, "16-bit kind must be SEM_F16 or SEM_BF16");
+  SEM_REQUIRE(L.geom == SEM_GEOM_STORED, "16-bit factors need stored geometry");
+  level_ensure_dinv32(L, st);
+  const int s = kind == SEM_F16 ? 0 : 1;
+  if (L.G16[s].p) return;
+  const Topo &t = L.t;
+  DevBuf<double> g;
+  level_fp64_factors(L, g, st);
+  L.G16[s].alloc((size_t)t.E * 6 * t.Np3);
+  L.G16scale[s].alloc((size_t)t.E);
+  g16_kernel<<<grid_for(t.E, 128), 128, 0, st>>>(t.E, t.Np3, kind, g.p, L.G16[s].p,
+                                                 L.G16scale[s].p);
   SEM_CHECK_CUDA(cudaGetLastError());
   SEM_CHECK_CUDA(cudaStreamSynchronize(st));
 }

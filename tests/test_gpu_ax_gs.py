@@ -70,18 +70,40 @@ def test_ax_fp64_matches_oracle(ex, ey, ez, N, geom, arith):
     assert rel(wd.cpu().numpy(), L.ax(u)) < TOL64
 
 
-@pytest.mark.parametrize("ex,ey,ez,N", [(3, 2, 4, 3), (5, 7, 9, 7), (2, 2, 3, 5), (2, 2, 2, 10)])
+# FP32 on stored factors runs the fused operator, whose CTAs walk x-lines of
+# elements: meshes with few lines split them into segments (seams), many
+# lines (2 x 31 x 30) take whole lines, ex < elements per chunk leaves CTA
+# slots idle; odd ex gives ragged chunks.
+FP32_CASES = [(3, 2, 4, 3), (5, 7, 9, 7), (2, 2, 3, 5), (2, 2, 2, 10), (40, 2, 2, 7), (13, 3, 2, 4),
+              (1, 3, 5, 2), (7, 1, 1, 1), (2, 31, 30, 3), (3, 31, 30, 7), (9, 2, 3, 11)]
+
+
+@pytest.mark.parametrize("ex,ey,ez,N", FP32_CASES)
 @pytest.mark.parametrize("geom", [sem.SEM_GEOM_STORED, sem.SEM_GEOM_TRILINEAR])
-def test_ax_fp32_matches_oracle_within_stated_tolerance(ex, ey, ez, N, geom):
-    m, L, _ = make(ex, ey, ez, N, geom=geom)
+@pytest.mark.parametrize("bc", [0, 1])
+def test_ax_fp32_matches_oracle_within_stated_tolerance(ex, ey, ez, N, geom, bc):
+    if geom == sem.SEM_GEOM_TRILINEAR and ey * ez > 100:
+        pytest.skip("the trilinear FP32 operator does not depend on the line split")
+    m, L, _ = make(ex, ey, ez, N, bc=bc, geom=geom)
     u = inputs.random_field(L.nl, 12)
     ud = torch.tensor(u, device=DEV, dtype=torch.float32)
     wd = torch.empty_like(ud)
     sem.sem_ax(m, sem.SEM_F32, ud, wd, sem.SEM_AX_ASSEMBLED)
     # the oracle applied to the same float-rounded input
     ref = L.ax(ud.double().cpu().numpy())
-    err = rel(wd.double().cpu().numpy(), ref)
+    w = wd.double().cpu().numpy()
+    err = rel(w, ref)
     assert err < tol32(N), err
+    # copies of every node are bit-identical and masked nodes exactly zero
+    ids = L.ids
+    lo = np.full(L.ng, np.inf)
+    hi = np.full(L.ng, -np.inf)
+    np.minimum.at(lo, ids, w)
+    np.maximum.at(hi, ids, w)
+    assert np.array_equal(lo, hi)
+    assert np.all(w[L.mask == 0] == 0)
+    sem.sem_ax(m, sem.SEM_F32, ud, wd, sem.SEM_AX_LOCAL)
+    assert rel(wd.double().cpu().numpy(), L.ax_local(ud.double().cpu().numpy())) < tol32(N)
 
 
 def test_ax_dirichlet_and_neumann_masks():
@@ -240,3 +262,115 @@ def test_ax_full_size_sampled_elements(k, geom, arith):
         Lo = oracle.Level(1, 1, 1, N, 1, lat)
         ref = Lo.ax_local(u[e * Np3:(e + 1) * Np3])
         assert rel(w[e * Np3:(e + 1) * Np3], ref) < TOL64, e
+
+
+# ---------------------------------------------------------------- 16-bit factors
+# FP16 / BF16 storage of the six factors (per element and factor scale), FP32
+# vectors and arithmetic.  Two checks: (1) against the FP64 oracle applied to
+# the same stored factors, whose rounding tests/quant16.py defines
+# independently, within the FP32 tolerance; (2) against the exact operator,
+# point by point, within the bound the storage rounding implies:
+#   |w - A u| <= |D|^T H |D| |u| + tol32 * max|A u|,  H_e = h * scale_e,
+# h = half an ulp at 1 (2^-12 FP16, 2^-9 BF16), scale_e the element's scale.
+from quant16 import quantise_factors  # noqa: E402
+
+G16_KINDS = [(sem.SEM_F16, "f16", 2.0 ** -12), (sem.SEM_BF16, "bf16", 2.0 ** -9)]
+
+
+@pytest.mark.parametrize("ex,ey,ez,N", [(3, 2, 4, 3), (5, 7, 9, 7), (2, 2, 3, 5), (2, 2, 2, 10),
+                                        (1, 1, 1, 1)])
+@pytest.mark.parametrize("kind,name,h", G16_KINDS)
+def test_ax_16bit_factors_match_oracle_on_stored_values(ex, ey, ez, N, kind, name, h):
+    m, L, _ = make(ex, ey, ez, N)
+    Np3 = (N + 1) ** 3
+    u = inputs.random_field(L.nl, 21)
+    ud = torch.tensor(u, device=DEV, dtype=torch.float32)
+    u32 = ud.double().cpu().numpy()
+    wd = torch.empty_like(ud)
+    sem.sem_ax(m, kind, ud, wd, sem.SEM_AX_LOCAL)
+    w = wd.double().cpu().numpy()
+    Gq, sc = quantise_factors(L.G, L.E, Np3, name)
+    ref = oracle.ax_local(N, L.D, Gq, u32)
+    err = rel(w, ref)
+    assert err < tol32(N), err
+    # (2) elementwise bound against the exact (unrounded) operator
+    exact = L.ax_local(u32)
+    H = np.repeat(h * sc.astype(np.float64), 6 * Np3)
+    bound = oracle.ax_local(N, np.abs(L.D), H, np.abs(u32)) + tol32(N) * np.max(np.abs(exact))
+    assert np.all(np.abs(w - exact) <= bound)
+    # assembled form: gs and mask of the local result
+    sem.sem_ax(m, kind, ud, wd, sem.SEM_AX_ASSEMBLED)
+    ref_a = L.mask * oracle.gs(L.ids, L.ng, ref)
+    assert rel(wd.double().cpu().numpy(), ref_a) < tol32(N)
+
+
+def test_ax_16bit_full_size_sampled_elements():
+    """64^3 elements of order 7 (the operator-sweep size): sampled elements
+    against the oracle on their own stored factors."""
+    e, N = 64, 7
+    v = inputs.box_vertices(e, e, e, 0.1, 9)
+    m = sem.Mesh(e, e, e, N, 0, verts=v)
+    Np3 = (N + 1) ** 3
+    nl = e ** 3 * Np3
+    ud = torch.rand(nl, device=DEV, generator=torch.Generator(DEV).manual_seed(4),
+                    dtype=torch.float32) * 2 - 1
+    wd = torch.empty_like(ud)
+    rng = np.random.Generator(np.random.PCG64(e))
+    sample = np.unique(np.concatenate([rng.integers(0, e ** 3, 12), [0, e ** 3 - 1]]))
+    for kind, name, _ in G16_KINDS:
+        sem.sem_ax(m, kind, ud, wd, sem.SEM_AX_LOCAL)
+        for el in sample:
+            Lo = oracle.Level(1, 1, 1, N, 1, _element_vertices(v, e, e, int(el)))
+            Gq, _ = quantise_factors(Lo.G, 1, Np3, name)
+            ue = ud[el * Np3:(el + 1) * Np3].double().cpu().numpy()
+            ref = oracle.ax_local(N, Lo.D, Gq, ue)
+            got = wd[el * Np3:(el + 1) * Np3].double().cpu().numpy()
+            assert rel(got, ref) < tol32(N), (name, el)
+
+
+def _sub_box(v, ex, ey, ez, c, r=1):
+    """Vertices and global element indices of the box of elements within r of
+    element c = (cx, cy, cz), clipped to the mesh; also c's index inside it."""
+    lo = [max(0, c[d] - r) for d in range(3)]
+    hi = [min((ex, ey, ez)[d] - 1, c[d] + r) for d in range(3)]
+    n = [hi[d] - lo[d] + 1 for d in range(3)]
+    V = np.asarray(v).reshape(ez + 1, ey + 1, ex + 1, 3)
+    sub = V[lo[2]:hi[2] + 2, lo[1]:hi[1] + 2, lo[0]:hi[0] + 2].reshape(-1, 3)
+    els = [(lo[0] + a) + ex * ((lo[1] + b) + ey * (lo[2] + g))
+           for g in range(n[2]) for b in range(n[1]) for a in range(n[0])]
+    centre = (c[0] - lo[0]) + n[0] * ((c[1] - lo[1]) + n[1] * (c[2] - lo[2]))
+    return n, np.ascontiguousarray(sub), np.array(els), centre
+
+
+@pytest.mark.parametrize("kind,name", [(sem.SEM_F32, None), (sem.SEM_F16, "f16"),
+                                       (sem.SEM_BF16, "bf16")])
+def test_ax_fp32_assembled_full_size_sampled(kind, name):
+    """The assembled FP32 operator at the benchmark's size (48^3 elements,
+    N = 7, Neumann) and launch configuration: every node of a sampled element
+    against the oracle's assembled operator on the box of elements around it,
+    which holds all copies of those nodes."""
+    e, N = 48, 7
+    v = inputs.box_vertices(e, e, e, 0.1, 3)
+    m = sem.Mesh(e, e, e, N, 1, verts=v)
+    Np3 = (N + 1) ** 3
+    ud = torch.rand(m.n_local, device=DEV, generator=torch.Generator(DEV).manual_seed(8),
+                    dtype=torch.float32) * 2 - 1
+    wd = torch.empty_like(ud)
+    sem.sem_ax(m, kind, ud, wd, sem.SEM_AX_ASSEMBLED)
+    rng = np.random.Generator(np.random.PCG64(48))
+    cents = [tuple(int(x) for x in rng.integers(0, e, 3)) for _ in range(6)]
+    cents += [(0, 0, 0), (e - 1, e - 1, e - 1), (0, e - 1, 17), (23, 0, e - 1)]
+    u3 = ud.view(-1, Np3)
+    w3 = wd.view(-1, Np3)
+    for c in cents:
+        n, sub, els, centre = _sub_box(v, e, e, e, c)
+        Lo = oracle.Level(*n, N, 1, sub)
+        us = u3[torch.tensor(els, device=DEV)].double().cpu().numpy().reshape(-1)
+        if name is None:
+            ref = Lo.ax(us)
+        else:
+            Gq, _ = quantise_factors(Lo.G, Lo.E, Np3, name)
+            ref = oracle.gs(Lo.ids, Lo.ng, oracle.ax_local(N, Lo.D, Gq, us))
+        ref_c = ref.reshape(-1, Np3)[centre]
+        got = w3[els[centre]].double().cpu().numpy()
+        assert rel(got, ref_c) < tol32(N), c

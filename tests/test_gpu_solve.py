@@ -153,7 +153,7 @@ def test_vcycle_fp32_close_to_fp64_oracle():
 
 
 @pytest.mark.parametrize("bc", [0, 1])
-@pytest.mark.parametrize("dtype", [sem.SEM_F64, sem.SEM_F32])
+@pytest.mark.parametrize("dtype", [sem.SEM_F64, sem.SEM_F32, sem.SEM_F16, sem.SEM_BF16])
 def test_flexcg_pmg_reaches_1e8(bc, dtype):
     e = 6
     v = inputs.box_vertices(e, e, e, 0.1, 3)
@@ -175,6 +175,24 @@ def test_flexcg_pmg_reaches_1e8(bc, dtype):
     err = rel(x, xo)
     assert err < 1e-6, err
     assert info["iters"] <= io["iters"] + 3
+
+
+@pytest.mark.parametrize("dtype,tol", [(sem.SEM_F16, 16 * 2.0 ** -11),
+                                       (sem.SEM_BF16, 16 * 2.0 ** -8)])
+def test_vcycle_16bit_factors_close_to_fp64_oracle(dtype, tol):
+    """16-bit factor storage perturbs the smoothed operators by about the
+    16-bit unit roundoff u16; the V-cycle output stays within 16 u16."""
+    e = (4, 3, 3)
+    v = inputs.box_vertices(*e, 0.1, 6)
+    m = sem.Mesh(*e, 7, 0, verts=v)
+    P = sem.Pmg(m, orders=(7, 3, 1), smoother_dtype=dtype, coarse_tol=0.0, coarse_maxit=20)
+    Po = oracle.PMG(*e, [7, 3, 1], 0, v, coarse_tol=0.0, coarse_maxit=20)
+    L = Po.levels[0]
+    _, b = manufactured(L)
+    zd = torch.empty(L.nl, device=DEV, dtype=torch.float64)
+    sem.sem_pmg_vcycle(P, torch.tensor(b, device=DEV), zd)
+    err = rel(zd.cpu().numpy(), Po.vcycle(b))
+    assert err < tol, err
 
 
 @pytest.mark.parametrize("bc", [0, 1])
