@@ -67,7 +67,12 @@ struct L32 {
   static constexpr int GB = GK == 0 ? 4 : 2;                          // bytes per factor
   static constexpr int U_BYTES = S::NE * S::NP3 * 4;                  // one stage of u
   static constexpr int G_BYTES = S::NE * 6 * S::NP3 * GB;             // one stage of factors
-  static constexpr int STAGE = round16(U_BYTES) + round16(G_BYTES);
+#ifndef SEM_AX32_STAGE_F32G
+#define SEM_AX32_STAGE_F32G 0
+#endif
+  // factors staged in shared memory too (else read from global, L2-prefetched)
+  static constexpr bool SG = S::STAGED && (GK != 0 || SEM_AX32_STAGE_F32G);
+  static constexpr int STAGE = round16(U_BYTES) + (SG ? round16(G_BYTES) : 0);
   static constexpr int MBAR = 0;                                      // 2 x 8 bytes
   static constexpr int STAGES = S::STAGED ? 16 : 16;
   static constexpr int STAGES_END = S::STAGED ? STAGES + 2 * STAGE : STAGES;
@@ -230,10 +235,13 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
     const uint32_t ub = (uint32_t)(n * NP3 * 4), gb = (uint32_t)(n * 6 * NP3 * Lay::GB);
     unsigned char *dst = smem + Lay::STAGES + st * Lay::STAGE;
     const uint32_t bar = smem_addr(&mbar[st]);
-    mbar_expect_tx(bar, ub + gb);
+    mbar_expect_tx(bar, ub + (Lay::SG ? gb : 0));
     bulk_g2s(smem_addr(dst), a.u + e0 * NP3, ub, bar);
-    bulk_g2s(smem_addr(dst + round16(Lay::U_BYTES)),
-             static_cast<const unsigned char *>(a.G) + e0 * 6 * NP3 * Lay::GB, gb, bar);
+    if (Lay::SG)
+      bulk_g2s(smem_addr(dst + round16(Lay::U_BYTES)),
+               static_cast<const unsigned char *>(a.G) + e0 * 6 * NP3 * Lay::GB, gb, bar);
+    else
+      prefetch_l2(static_cast<const unsigned char *>(a.G) + e0 * 6 * NP3 * Lay::GB, gb);
   };
 
   int64_t unit = blockIdx.x;
@@ -316,7 +324,8 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
       const GT *Gg = static_cast<const GT *>(a.G) + e * 6 * NP3 + ij;
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
-        float ur = 0.f, us = 0.f, ut = 0.f;
+        // two partial sums per contraction (even and odd l) halve the chains
+        float ur2[2] = {0.f, 0.f}, us2[2] = {0.f, 0.f}, ut2[2] = {0.f, 0.f};
         const float *pa = uN + k * NPL + j * NRS, *pb = uT + k * PL + i * RS, *pd = sD + k * RS;
 #pragma unroll
         for (int c = 0; c < C4; ++c) {
@@ -327,16 +336,17 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
           for (int q = 0; q < 4; ++q) {
             const int l = 4 * c + q;
             if (l < NP) {
-              ur = fmaf(Dr[l], f4get(va, q), ur);
-              us = fmaf(Ds[l], f4get(vb, q), us);
-              ut = fmaf(f4get(vd, q), ru[l], ut);
+              ur2[q & 1] = fmaf(Dr[l], f4get(va, q), ur2[q & 1]);
+              us2[q & 1] = fmaf(Ds[l], f4get(vb, q), us2[q & 1]);
+              ut2[q & 1] = fmaf(f4get(vd, q), ru[l], ut2[q & 1]);
             }
           }
         }
+        const float ur = ur2[0] + ur2[1], us = us2[0] + us2[1], ut = ut2[0] + ut2[1];
         float g6[6];
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
-          if constexpr (STAGED) g6[f] = factor_value<GK>(stG[f * NP3 + k * NP2 + ij]);
+          if constexpr (Lay::SG) g6[f] = factor_value<GK>(stG[f * NP3 + k * NP2 + ij]);
           else g6[f] = factor_value<GK>(__ldg(Gg + f * NP3 + k * NP2));
         }
         wR[k * NPL + j * NRS + i] = g6[0] * ur + g6[1] * us + g6[2] * ut;
@@ -354,7 +364,8 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
       float *we = a.w + e * NP3 + ij;
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
-        float acc = 0.f;
+        // one partial sum per direction (three independent chains)
+        float ar = 0.f, as = 0.f, at = 0.f;
         const float *pa = wR + k * NPL + j * NRS, *pb = wS + k * PL + i * RS, *pd = sDT + k * RS;
 #pragma unroll
         for (int c = 0; c < C4; ++c) {
@@ -365,12 +376,13 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
           for (int q = 0; q < 4; ++q) {
             const int l = 4 * c + q;
             if (l < NP) {
-              acc = fmaf(DTr[l], f4get(va, q), acc);
-              acc = fmaf(DTs[l], f4get(vb, q), acc);
-              acc = fmaf(f4get(vd, q), wt[l], acc);
+              ar = fmaf(DTr[l], f4get(va, q), ar);
+              as = fmaf(DTs[l], f4get(vb, q), as);
+              at = fmaf(f4get(vd, q), wt[l], at);
             }
           }
         }
+        float acc = (ar + as) + at;
         if (GK != 0) acc *= sc;
         if (!ASSEMBLE || (i != 0 && i != N)) we[k * NP2] = acc;
         else if (i == 0) sFL[le * NP2 + k * NP + j] = acc;
@@ -379,33 +391,33 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
     }
     if constexpr (ASSEMBLE) {
       __syncthreads();
-      // ---- x-face sums (lower-x copy + upper-x copy), masks, carries
-      if (active && i == 0) {
-        const bool from_chunk = le > 0, from_carry = le == 0 && cx > ix0;
-        const float *left = from_chunk ? sFR + (le - 1) * NP2 : sCarry + ((cc - 1) & 1) * NP2;
-        const bool zero = ix == 0 && a.dirichlet;
-        float *we = a.w + e * NP3 + j * NP;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-          const float own = sFL[le * NP2 + k * NP + j];
-          if (from_chunk || from_carry) {
-            const float s = left[k * NP + j] + own;
-            we[k * NP2] = s;
-            we[k * NP2 - NP3 + N] = s;  // element e - 1, i = N
-          } else {
-            we[k * NP2] = zero ? 0.f : own;  // box boundary or seam
-          }
+      // ---- x-face sums (lower-x copy + upper-x copy), masks, carries: one
+      // thread per node of the chunk's left faces, then of its last right face
+      for (int q = threadIdx.x; q < NE * NP2; q += blockDim.x) {
+        const int l2 = q / NP2, jk = q - l2 * NP2;  // jk = k * NP + j
+        if (l2 >= nact) continue;
+        const int ix2 = cx + l2;
+        const int jj = jk % NP, kk = jk / NP;
+        float *wl = a.w + (line * t.ex + ix2) * NP3 + kk * NP2 + jj * NP;  // i = 0
+        const float own = sFL[q];
+        if (l2 > 0 || cx > ix0) {
+          const float left = l2 > 0 ? sFR[q - NP2] : sCarry[((cc - 1) & 1) * NP2 + jk];
+          const float v = left + own;
+          wl[0] = v;
+          wl[N - NP3] = v;  // element e - 1, i = N
+        } else {
+          wl[0] = (ix2 == 0 && a.dirichlet) ? 0.f : own;  // box boundary or seam
         }
       }
-      if (active && i == N && le == nact - 1) {
-        float *we = a.w + e * NP3 + j * NP + N;
-        const bool last_of_segment = ix == ix1 - 1;
-        const bool zero = ix == t.ex - 1 && a.dirichlet;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-          const float own = sFR[le * NP2 + k * NP + j];
-          if (last_of_segment) we[k * NP2] = zero ? 0.f : own;  // box boundary or seam
-          else sCarry[(cc & 1) * NP2 + k * NP + j] = own;         // summed by the next chunk
+      for (int q = threadIdx.x; q < NP2; q += blockDim.x) {
+        const int ix2 = cx + nact - 1;
+        const float own = sFR[(nact - 1) * NP2 + q];
+        if (ix2 == ix1 - 1) {  // box boundary or seam
+          const int jj = q % NP, kk = q / NP;
+          a.w[(line * t.ex + ix2) * NP3 + kk * NP2 + jj * NP + N] =
+              (ix2 == t.ex - 1 && a.dirichlet) ? 0.f : own;
+        } else {
+          sCarry[(cc & 1) * NP2 + q] = own;  // summed by the next chunk
         }
       }
     }

@@ -138,14 +138,16 @@ def test_vcycle_fp64_matches_oracle(bc, orders, arith):
     assert rel(zd.cpu().numpy(), Po.vcycle(r)) < 1e-10
 
 
-def test_vcycle_fp32_close_to_fp64_oracle():
-    e = (4, 3, 3)
+@pytest.mark.parametrize("e,bc", [((4, 3, 3), 0), ((4, 3, 3), 1), ((2, 31, 30), 1), ((5, 2, 3), 0)])
+def test_vcycle_fp32_close_to_fp64_oracle(e, bc):
+    """FP32 smoothing (operator with the Chebyshev update fused in): boxes
+    whose x-lines are split into segments and, at 2 x 31 x 30, whole lines."""
     v = inputs.box_vertices(*e, 0.1, 6)
-    m = sem.Mesh(*e, 7, 0, verts=v)
+    m = sem.Mesh(*e, 7, bc, verts=v)
     P = sem.Pmg(m, orders=(7, 3, 1), smoother_dtype=sem.SEM_F32, coarse_tol=0.0, coarse_maxit=20)
-    Po = oracle.PMG(*e, [7, 3, 1], 0, v, coarse_tol=0.0, coarse_maxit=20)
+    Po = oracle.PMG(*e, [7, 3, 1], bc, v, coarse_tol=0.0, coarse_maxit=20)
     L = Po.levels[0]
-    _, b = manufactured(L)
+    b = manufactured(L)[1] if bc == 0 else fourier_rhs(L)
     zd = torch.empty(L.nl, device=DEV, dtype=torch.float64)
     sem.sem_pmg_vcycle(P, torch.tensor(b, device=DEV), zd)
     err = rel(zd.cpu().numpy(), Po.vcycle(b))
