@@ -3,13 +3,14 @@
 
 One step = one full pressure-type Poisson solve from a zero guess: the whole
 hot path (operator, gather-scatter, masking, Chebyshev-Jacobi smoothing in
-FP32, tensor-product transfers, FP64 coarse Jacobi-PCG, FP64 flexible CG
-with its inner products) on the mixed-precision workload
+FP32, tensor-product transfers, FP64 coarse solve, FP64 flexible CG with its
+inner products) on the mixed-precision workload
 
     box of 48^3 = 110,592 trilinear hexahedra, N = 7, vertices jittered
     +-10% of h (seed 3), Neumann, smooth random mean-free right-hand side,
-    p-multigrid 7-3-1, Chebyshev degree 2, FP32 smoother, FlexCG in FP64 to
-    a relative residual of 1e-8.
+    p-multigrid 7-3-1, Chebyshev(3)-Jacobi smoother in FP32, FP64 coarse
+    solve (CG preconditioned by a lattice multigrid V-cycle), FlexCG in FP64
+    to a relative residual of 1e-8.
 
 value = unique dofs solved per second (GDOF/s, whole job over all ranks).
 The working set (about 6 GB) is far larger than the 129 MB L2, so no L2 flush
@@ -63,6 +64,10 @@ PAIR_PEAK_TFLOPS = 152 * 128 * 2.07e9 / PAIR_INSTR_PER_FMA * 2 / 1e12
 # ncu capture (profiles/ax_f64pair_N7.md), valid while the source is unchanged.
 AX_TRAFFIC = {"source_sha256": "ab9460908abee14bcf8f1dbe80d2dc039a0c47229b82a9a9bf9600553313fc7e",
               "bytes_per_point": 62.66}
+# The same for the smoother's assembled FP32 operator, per factor storage
+# (profiles/ax32_N7.md), valid while ax32.cu is unchanged.
+AX32_TRAFFIC = {"f32": {"source_sha256": "24023321f994c1a65bfeebcf99e476be926a7355a8a716d044e9f66c85eb596e", "bytes_per_point": 31.41},
+                "f16": {"source_sha256": "24023321f994c1a65bfeebcf99e476be926a7355a8a716d044e9f66c85eb596e", "bytes_per_point": 18.80}}
 
 
 def parse_args():
@@ -79,6 +84,9 @@ def parse_args():
     p.add_argument("--coarse-maxit", type=int, default=COARSE_MAXIT)
     p.add_argument("--coarse-tol", type=float, default=COARSE_TOL)
     p.add_argument("--cheb-degree", type=int, default=CHEB_DEGREE)
+    p.add_argument("--ax-only", type=int, default=0, metavar="SIDE",
+                   help="profiling aid: build a SIDE^3 mesh of the workload's recipe, apply "
+                        "the assembled FP32 operator twice with FP32 and with FP16 factors, exit")
     p.add_argument("--smoother", default=SMOOTHER, choices=["f64", "f32", "f16", "bf16"],
                    help="arithmetic/storage of the smoothed pMG levels")
     p.add_argument("--coarse-mode", type=int, default=COARSE_MODE,
@@ -175,8 +183,8 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def ax_source_sha():
-    with open(os.path.join(ROOT, "paper_2110_01716_gb300", "csrc", "ax_pair.cu"), "rb") as f:
+def source_sha(name):
+    with open(os.path.join(ROOT, "paper_2110_01716_gb300", "csrc", name), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()
 
 
@@ -298,6 +306,20 @@ def main():
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.ax_only:
+        build.build()
+        k = args.ax_only
+        mesh = sem.Mesh(k, k, k, ORDER, sem.SEM_NEUMANN, sem.SEM_GEOM_STORED,
+                        verts=inputs.box_vertices(k, k, k, 0.1, MESH_SEED))
+        u = torch.rand(mesh.n_local, device=dev, dtype=torch.float32,
+                       generator=torch.Generator(dev).manual_seed(5)) * 2 - 1
+        w = torch.empty_like(u)
+        for kind in (sem.SEM_F32, sem.SEM_F16):
+            for _ in range(2):
+                sem.sem_ax(mesh, kind, u, w, sem.SEM_AX_ASSEMBLED)
+        torch.cuda.synchronize()
+        print(json.dumps({"ax_only": k, "n_local": mesh.n_local}))
+        return 0
     pg = None
     if world > 1:
         import torch.distributed as dist
@@ -325,7 +347,9 @@ def main():
     for _ in range(max(args.warmup, 0)):
         info = step()
     # timed region
-    sem.sem_trace_enable(True, f"ax_f64pair_N{ORDER}")
+    smoother_key = {"f32": "ax32_f32", "f16": "ax32_f16g", "bf16": "ax32_bf16g"}.get(args.smoother)
+    keys = [f"ax_f64pair_N{ORDER}"] + ([f"{smoother_key}_N{ORDER}"] if smoother_key else [])
+    sem.sem_trace_enable(True, "|".join(keys))
     sem.sem_trace_read(reset=True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -357,32 +381,54 @@ def main():
         if inf["status"] != sem.SEM_OK:
             raise SystemExit(f"solve did not converge: {inf}")
 
-    # dominant kernel: fine-level FP64 operator in FP32-pair arithmetic
-    # (FP32-pipe bound on GB300)
-    key = f"ax_f64pair_N{ORDER}"
-    ax = trace.get(key, {"launches": 0, "timed": 0, "total_ms": 0.0})
-    ax_ms = ax["total_ms"] / max(ax["timed"], 1)
     nl = mesh.n_local
+    launches = sum(v["launches"] for v in trace.values())
+
+    def timed(key):
+        ent = trace.get(key, {"launches": 0, "timed": 0, "total_ms": 0.0})
+        per = ent["total_ms"] / max(ent["timed"], 1)
+        return per, (ent["total_ms"] / total_ms if total_ms > 0 else None), ent["timed"]
+
+    # FP64 operator in FP32-pair arithmetic (FP32-pipe bound)
+    key64 = f"ax_f64pair_N{ORDER}"
+    ax_ms, ax_share, ax_n = timed(key64)
     flops_pt = 12 * (ORDER + 1) + 15
     ax_tflops = nl * flops_pt / (ax_ms / 1e3) / 1e12 if ax_ms > 0 else None
-    traffic = None
-    if AX_TRAFFIC["source_sha256"] == ax_source_sha() and AX_TRAFFIC["bytes_per_point"]:
-        traffic = AX_TRAFFIC["bytes_per_point"] * nl
-    launches = sum(v["launches"] for v in trace.values())
-    ax_share = ax["total_ms"] / total_ms if total_ms > 0 else None
-    roofline = {"bound": "alu", "achieved": ax_tflops, "peak": PAIR_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": (ax_tflops / PAIR_PEAK_TFLOPS) if ax_tflops else None,
-                "traffic": traffic, "kernel": key,
-                "per_launch_ms": ax_ms, "launches_timed": ax["timed"],
-                "share_of_step": ax_share,
-                "algorithmic": f"{flops_pt} flop/pt x {nl} local pts per launch; "
-                               f"64 B/pt x {nl} = {64 * nl / 1e9:.2f} GB",
-                "hbm_GB_s": (64 * nl / (ax_ms / 1e3) / 1e9) if ax_ms > 0 else None,
-                "hbm_frac": (64 * nl / (ax_ms / 1e3) / 1e9 / hbm) if ax_ms > 0 else None,
-                "peak_source": "derived: FP32 issue 152 SM x 128 lanes x 2.07 GHz / "
-                               f"{PAIR_INSTR_PER_FMA} instr per FP64-equivalent FMA x 2 flop "
-                               f"(native FP64 pipe: {FP64_PEAK_TFLOPS:.3f}); "
-                               f"HBM {hbm} GB/s {hbm_src}"}
+    traffic64 = None
+    if AX_TRAFFIC["source_sha256"] == source_sha("ax_pair.cu") and AX_TRAFFIC["bytes_per_point"]:
+        traffic64 = AX_TRAFFIC["bytes_per_point"] * nl
+    roof64 = {"bound": "alu", "achieved": ax_tflops, "peak": PAIR_PEAK_TFLOPS,
+              "unit": "TFLOP/s", "frac": (ax_tflops / PAIR_PEAK_TFLOPS) if ax_tflops else None,
+              "traffic": traffic64, "kernel": key64,
+              "per_launch_ms": ax_ms, "launches_timed": ax_n, "share_of_step": ax_share,
+              "algorithmic": f"{flops_pt} flop/pt x {nl} local pts per launch",
+              "peak_source": "derived: FP32 issue 152 SM x 128 lanes x 2.07 GHz / "
+                             f"{PAIR_INSTR_PER_FMA} instr per FP64-equivalent FMA x 2 flop "
+                             f"(native FP64 pipe: {FP64_PEAK_TFLOPS:.3f})"}
+    roofline = roof64
+    if smoother_key:
+        # the smoother's fused FP32 operator on stored factors (HBM bound):
+        # u and w in FP32 plus six factors per point (FP32 or 16-bit)
+        key32 = f"{smoother_key}_N{ORDER}"
+        s_ms, s_share, s_n = timed(key32)
+        gsz = 4 if args.smoother == "f32" else 2
+        bpp = 8 + 6 * gsz + (4.0 / (ORDER + 1) ** 3 if gsz == 2 else 0.0)
+        s_gbs = bpp * nl / (s_ms / 1e3) / 1e9 if s_ms > 0 else None
+        rec = AX32_TRAFFIC.get(args.smoother)
+        traffic32 = None
+        if rec and rec["source_sha256"] == source_sha("ax32.cu"):
+            traffic32 = rec["bytes_per_point"] * nl
+        roof32 = {"bound": "hbm", "achieved": s_gbs, "peak": hbm, "unit": "GB/s",
+                  "frac": (s_gbs / hbm) if s_gbs else None, "traffic": traffic32,
+                  "kernel": key32, "per_launch_ms": s_ms, "launches_timed": s_n,
+                  "share_of_step": s_share,
+                  "algorithmic": f"{bpp:.3f} B/pt x {nl} local pts = {bpp * nl / 1e9:.3f} GB per launch",
+                  "peak_source": f"HBM {hbm} GB/s {hbm_src}"}
+        # the dominant kernel (largest share of the step) is the headline roofline
+        if (s_share or 0) >= (ax_share or 0):
+            roofline = dict(roof32, other=roof64)
+        else:
+            roofline = dict(roof64, other=roof32)
 
     line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

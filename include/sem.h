@@ -229,8 +229,8 @@ sem_status sem_solve_host(sem_mesh *mesh, sem_pmg *pmg, const double *b_host, do
 /* Tracing (Sec. 4 reports timing breakdowns from CUDA events): while enabled,
  * every kernel launch of the library is counted under a class name such as
  * "ax_f64_N7" or "gs_f32_N3"; launches of classes whose name contains
- * `timed_filter` (NULL or "" = none, "*" = all) are also bracketed by CUDA events on
- * their stream.  sem_trace_read synchronises on the pending events and fills
+ * `timed_filter`, or one of its '|'-separated parts (NULL or "" = none, "*" =
+ * all), are also bracketed by CUDA events on their stream.  sem_trace_read synchronises on the pending events and fills
  * up to max_entries entries (HOST array); *n_entries receives the number of
  * classes.  reset != 0 clears the counters afterwards. */
 typedef struct {

@@ -568,7 +568,7 @@ static void ax32_np(const Level &L, const float *u, float *w, bool assemble, cud
   }
   if (!assemble) return;
   SEM_REQUIRE((uint64_t)t.E * t.Np * t.Np < (1ull << 32), "mesh too large for the plane passes");
-  TraceScope ts("plane_sum", t.N, st);
+  TraceScope ts("plane_sum", t.N, st, a.nseg > 1 ? 3 : 2);
   if (a.nseg > 1) {
     const int64_t n = lines * (a.nseg - 1) * t.Np * t.Np;
     const int64_t b = (n + 255) / 256;

@@ -351,7 +351,7 @@ void coarse_setup(CoarseSolver &C, const Level &L, cudaStream_t st) {
   C.grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
   C.part.alloc(3 * (size_t)((C.grid * 4 + 31) / 32 * 32));
   {
-    TraceScope ts("coarse_setup", 1, st);
+    TraceScope ts("coarse_setup", 1, st, 3);
     int blocks = (int)std::min<int64_t>((E * 64 + 255) / 256, 152 * 16);
     coarse_element_matrices<<<blocks, 256, 0, st>>>(E, L.basis, G, Ae.p);
     SEM_CHECK_CUDA(cudaGetLastError());

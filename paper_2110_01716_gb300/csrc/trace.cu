@@ -50,15 +50,31 @@ cudaEvent_t take_event(Tracer &T) {
 
 bool trace_on() { return tracer().on.load(std::memory_order_relaxed); }
 
-TraceScope::TraceScope(const char *name, int N, cudaStream_t st) : st_(st) {
+// "*" matches every class; otherwise the filter is a '|'-separated list of
+// substrings, any of which selects a class.
+static bool filter_matches(const std::string &filter, const char *name) {
+  if (filter.empty()) return false;
+  if (filter == "*") return true;
+  size_t start = 0;
+  while (start <= filter.size()) {
+    size_t end = filter.find('|', start);
+    if (end == std::string::npos) end = filter.size();
+    if (end > start && std::strstr(name, filter.substr(start, end - start).c_str()) != nullptr)
+      return true;
+    start = end + 1;
+  }
+  return false;
+}
+
+TraceScope::TraceScope(const char *name, int N, cudaStream_t st, int kernels) : st_(st) {
   Tracer &T = tracer();
   if (!T.on.load(std::memory_order_relaxed)) return;
   char buf[64];
   snprintf(buf, sizeof(buf), "%s_N%d", name, N);
   std::lock_guard<std::mutex> lock(T.mu);
   ClassStats &c = T.cls[buf];
-  c.launches += 1;
-  if (!T.filter.empty() && (T.filter == "*" || std::strstr(buf, T.filter.c_str()) != nullptr)) {
+  c.launches += kernels;
+  if (filter_matches(T.filter, buf)) {
     e0_ = take_event(T);
     e1_ = take_event(T);
     SEM_CHECK_CUDA(cudaEventRecord(e0_, st_));

@@ -12,7 +12,8 @@ namespace sem {
 // before the launch; it records the closing event when it goes out of scope.
 class TraceScope {
  public:
-  TraceScope(const char *name, int N, cudaStream_t st);
+  // `kernels`: how many kernels the scope launches (counted as launches)
+  TraceScope(const char *name, int N, cudaStream_t st, int kernels = 1);
   ~TraceScope();
   TraceScope(const TraceScope &) = delete;
   TraceScope &operator=(const TraceScope &) = delete;

@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(kVecThreads)
 
 void launch_remove_mean(const Topo &t, Reducer &R, double *u, double *scratch, cudaStream_t st) {
   OutPtrs<1> o{{scratch}};
-  TraceScope ts("mean", t.N, st);
+  TraceScope ts("mean", t.N, st, 2);
   sum_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, u, R.partials.p, R.counter.p, o);
   SEM_CHECK_CUDA(cudaGetLastError());
   sub_mean_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, scratch, u);
