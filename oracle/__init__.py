@@ -87,6 +87,9 @@ def lib():
     L.orc_interp3.argtypes = [C.c_int64, C.c_int, C.c_int, _dp, _dp, _dp, C.c_int]
     L.orc_flexpcg.argtypes = [C.c_void_p, C.c_int, _dp, _dp, C.c_double, C.c_int,
                               C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.orc_fgmres.argtypes = [C.c_void_p, C.c_int, _dp, _dp, C.c_double, C.c_int, C.c_int,
+                             C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                             C.c_void_p]
     _lib = L
     return L
 
@@ -320,6 +323,19 @@ class PMG:
 
     def coarse_iters(self):
         return lib().orc_pmg_coarse_iters(self.ptr)
+
+    def fgmres(self, b, x0=None, tol=1e-8, restart=30, maxit=500, precond=True):
+        """Flexible GMRES(restart); returns x and a dict with the residual
+        history (||r0||, then the least-squares residual of every step)."""
+        x = np.zeros(self.levels[0].nl) if x0 is None else np.array(x0, dtype=np.float64,
+                                                                     copy=True)
+        it, r0, r1 = C.c_int(), C.c_double(), C.c_double()
+        hist = np.zeros(maxit + 1)
+        st = lib().orc_fgmres(self.ptr, int(precond), np.ascontiguousarray(b, dtype=np.float64),
+                              x, tol, restart, maxit, C.byref(it), C.byref(r0), C.byref(r1),
+                              hist.ctypes.data_as(C.c_void_p))
+        return x, {"status": st, "iters": it.value, "res0": r0.value, "res": r1.value,
+                   "hist": hist[:it.value + 1]}
 
     def flexpcg(self, b, x0=None, tol=1e-8, maxit=500, precond=True):
         x = np.zeros(self.levels[0].nl) if x0 is None else np.array(x0, dtype=np.float64,

@@ -764,6 +764,91 @@ int orc_pmg_coarse_iters(const orc_pmg *P) { return P->coarse_iters_last; }
  * precond = 1 uses one pMG V-cycle per iteration; precond = 0 uses Jacobi
  * on the finest level (then the iterates equal those of Jacobi-PCG up to
  * rounding).  Stopping rule and return value as orc_pcg. */
+/* Flexible GMRES (Sec. 3: GMRES as the alternative outer solver to FlexCG;
+ * Sec. 5: few vectors, classical Gram-Schmidt so that the orthogonalisation
+ * needs one reduction).  Right preconditioning by the pMG V-cycle
+ * (precond = 1) or by Jacobi (precond = 0); since the V-cycle may vary from
+ * call to call, the preconditioned vectors z_j are kept and the update is
+ * x = x0 + Z y (Saad, Iterative Methods for Sparse Linear Systems, Alg. 9.6).
+ * Restart length m; the least-squares problem is reduced by Givens rotations
+ * as the Arnoldi process goes, so |g_{j+1}| is the residual norm of the
+ * current iterate.  Inner product: the unique-dof product of orc_level_dot.
+ * A cycle ends when |g_{j+1}| <= tol ||b|| or after m steps; x is then formed
+ * and its true residual recomputed, which decides convergence (restarting
+ * from it otherwise).  hist (optional, maxit + 1 entries): ||r0|| and the
+ * |g_{j+1}| of every step.  Returns 0 on convergence, 1 at maxit. */
+int orc_fgmres(orc_pmg *P, int precond, const double *b, double *x, double tol, int m, int maxit,
+               int *iters, double *res0, double *res, double *hist) {
+  orc_level *L = P->lev[0];
+  int64_t n = L->nl;
+  double *V = malloc(sizeof(double) * n * (m + 1)), *Z = malloc(sizeof(double) * n * m),
+         *w = malloc(sizeof(double) * n);
+  double *H = calloc((size_t)(m + 1) * m, sizeof(double));  /* H[i*m + j] */
+  double *cs = malloc(sizeof(double) * m), *sn = malloc(sizeof(double) * m),
+         *g = malloc(sizeof(double) * (m + 1)), *y = malloc(sizeof(double) * m);
+  double bnorm = sqrt(orc_level_dot(L, b, b));
+  orc_level_ax(L, x, w);
+  for (int64_t l = 0; l < n; ++l) V[l] = b[l] - w[l];
+  double beta = sqrt(orc_level_dot(L, V, V));
+  *res0 = beta;
+  if (hist) hist[0] = beta;
+  int k = 0, status = 1;
+  if (beta <= tol * bnorm || beta == 0.0) status = 0;
+  while (status != 0 && k < maxit) {
+    for (int64_t l = 0; l < n; ++l) V[l] /= beta;
+    for (int i = 0; i <= m; ++i) g[i] = 0.0;
+    g[0] = beta;
+    int cols = 0;
+    for (int j = 0; j < m && k < maxit; ++j) {
+      double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n, *vn = V + (size_t)(j + 1) * n;
+      if (precond) orc_pmg_vcycle(P, vj, zj);
+      else for (int64_t l = 0; l < n; ++l) zj[l] = L->dinv[l] * vj[l];
+      orc_level_ax(L, zj, w);
+      /* classical Gram-Schmidt: every coefficient from the same w */
+      for (int i = 0; i <= j; ++i) H[i * m + j] = orc_level_dot(L, w, V + (size_t)i * n);
+      for (int i = 0; i <= j; ++i)
+        for (int64_t l = 0; l < n; ++l) w[l] -= H[i * m + j] * V[(size_t)i * n + l];
+      double hn = sqrt(orc_level_dot(L, w, w));
+      H[(j + 1) * m + j] = hn;
+      for (int64_t l = 0; l < n; ++l) vn[l] = hn > 0.0 ? w[l] / hn : 0.0;
+      /* previous rotations, then a new one that zeroes H[j+1][j] */
+      for (int i = 0; i < j; ++i) {
+        double a = H[i * m + j], c = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * c;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      double a = H[j * m + j], c = H[(j + 1) * m + j];
+      double d = sqrt(a * a + c * c);
+      cs[j] = d > 0.0 ? a / d : 1.0;
+      sn[j] = d > 0.0 ? c / d : 0.0;
+      H[j * m + j] = d;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++k;
+      cols = j + 1;
+      if (hist) hist[k] = fabs(g[j + 1]);
+      if (fabs(g[j + 1]) <= tol * bnorm || hn == 0.0) break;
+    }
+    /* y = R^{-1} g by back substitution; x += Z y */
+    for (int i = cols - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int q = i + 1; q < cols; ++q) s -= H[i * m + q] * y[q];
+      y[i] = s / H[i * m + i];
+    }
+    for (int i = 0; i < cols; ++i)
+      for (int64_t l = 0; l < n; ++l) x[l] += y[i] * Z[(size_t)i * n + l];
+    orc_level_ax(L, x, w);
+    for (int64_t l = 0; l < n; ++l) V[l] = b[l] - w[l];
+    beta = sqrt(orc_level_dot(L, V, V));
+    if (beta <= tol * bnorm || beta == 0.0) status = 0;
+  }
+  *iters = k;
+  *res = beta;
+  free(V); free(Z); free(w); free(H); free(cs); free(sn); free(g); free(y);
+  return status;
+}
+
 int orc_flexpcg(orc_pmg *P, int precond, const double *b, double *x, double tol, int maxit,
                 int *iters, double *res0, double *res) {
   orc_level *L = P->lev[0];

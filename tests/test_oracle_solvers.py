@@ -225,3 +225,81 @@ def test_pmg_flexcg_iterations_flat_under_refinement(orc, bc):
         iters.append(info["iters"])
     assert iters[1] <= iters[0] + 4, iters
     assert iters[1] < 40, iters
+
+
+# ---------------------------------------------------------------- FGMRES
+def _dense_gmres_residuals(A, Minv_diag, r0, kmax):
+    """Minimal residual norms of right-preconditioned GMRES, by direct least
+    squares over an orthonormalised Krylov basis of A M (numpy QR / lstsq)."""
+    AM = A * Minv_diag[None, :]
+    cols = [r0 / np.linalg.norm(r0)]
+    out = [np.linalg.norm(r0)]
+    for k in range(1, kmax + 1):
+        Q, _ = np.linalg.qr(np.stack(cols, axis=1))
+        W = AM @ Q  # residual b - AM Q c, minimised over c
+        c, *_ = np.linalg.lstsq(W, r0, rcond=None)
+        out.append(np.linalg.norm(r0 - W @ c))
+        v = AM @ cols[-1]
+        cols.append(v / np.linalg.norm(v))
+    return np.array(out)
+
+
+def test_fgmres_with_jacobi_is_minimal_residual(orc):
+    """With a fixed (Jacobi) preconditioner FGMRES is GMRES on A D^-1: every
+    step's residual is the minimum over the Krylov space, computed here by
+    dense least squares on the unique unknowns."""
+    v = inputs.box_vertices(2, 2, 2, 0.1, 5)
+    P = orc.PMG(2, 2, 2, [3, 1], DIR, v)
+    L = P.levels[0]
+    A, rep = dense_unique(L, L.ax)
+    keep = L.mask[rep] == 1.0
+    b = L.gs(inputs.random_field(L.nl, 6)) * L.mask
+    x, info = P.fgmres(b, tol=0.0, restart=8, maxit=6, precond=False)
+    Ak = A[np.ix_(keep, keep)]
+    ref = _dense_gmres_residuals(Ak, 1.0 / np.diag(Ak), b[rep][keep], 6)
+    np.testing.assert_allclose(info["hist"], ref, rtol=1e-8)
+    # the iterate's true residual equals the last least-squares residual
+    r = b - L.ax(x)
+    assert abs(np.sqrt(L.dot(r, r)) - info["hist"][-1]) <= 1e-10 * info["hist"][0]
+
+
+def test_fgmres_terminates_within_the_dimension(orc):
+    """Without restart GMRES finds the exact solution in at most n steps
+    (n = 3 unknowns: a 2x1x1 box of order 2 under Dirichlet)."""
+    v = inputs.box_vertices(2, 1, 1, 0.1, 2)
+    P = orc.PMG(2, 1, 1, [2, 1], DIR, v)
+    L = P.levels[0]
+    A, rep = dense_unique(L, L.ax)
+    keep = L.mask[rep] == 1.0
+    assert keep.sum() == 3
+    b = L.gs(inputs.random_field(L.nl, 7)) * L.mask
+    x, info = P.fgmres(b, tol=1e-13, restart=10, maxit=10, precond=False)
+    assert info["status"] == 0 and info["iters"] <= 3
+    ref = np.zeros(L.ng)
+    ref[keep] = np.linalg.solve(A[np.ix_(keep, keep)], b[rep][keep])
+    assert np.max(np.abs(x - ref[L.ids])) < 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("bc", [DIR, NEU])
+def test_fgmres_restarted_and_pmg_preconditioned(orc, bc):
+    """pMG-preconditioned FGMRES reaches 1e-8 (residual recomputed), with and
+    without restarts, in no more iterations than FlexCG plus one; restarts
+    keep the least-squares residuals non-increasing."""
+    e = 3
+    v = inputs.box_vertices(e, e, e, 0.1, 3)
+    P = orc.PMG(e, e, e, [7, 3, 1], bc, v, cheb_degree=2, coarse_tol=1e-2, coarse_maxit=50)
+    L = P.levels[0]
+    if bc == DIR:
+        _, b = manufactured(L)
+    else:
+        b = L.gs(inputs.random_field(L.nl, 9))
+        b -= L.dot(b, np.ones(L.nl)) / L.dot(np.ones(L.nl), np.ones(L.nl))
+    xf, fi = P.flexpcg(b, tol=1e-8, maxit=100)
+    for restart in (30, 3):
+        x, info = P.fgmres(b, tol=1e-8, restart=restart, maxit=100)
+        assert info["status"] == 0
+        r = b - L.ax(x)
+        assert np.sqrt(L.dot(r, r)) <= 1.001e-8 * np.sqrt(L.dot(b, b))
+        assert np.all(np.diff(info["hist"]) <= 1e-12 * info["hist"][0])
+        if restart == 30:
+            assert info["iters"] <= fi["iters"] + 1, (info["iters"], fi["iters"])
