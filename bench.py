@@ -87,6 +87,9 @@ def parse_args():
     p.add_argument("--ax-only", type=int, default=0, metavar="SIDE",
                    help="profiling aid: build a SIDE^3 mesh of the workload's recipe, apply "
                         "the assembled FP32 operator twice with FP32 and with FP16 factors, exit")
+    p.add_argument("--solver", default="flexcg", choices=["flexcg", "fgmres"],
+                   help="outer FP64 solver (FGMRES: flexible GMRES, classical Gram-Schmidt)")
+    p.add_argument("--restart", type=int, default=20, help="FGMRES vectors per cycle")
     p.add_argument("--smoother", default=SMOOTHER, choices=["f64", "f32", "f16", "bf16"],
                    help="arithmetic/storage of the smoothed pMG levels")
     p.add_argument("--coarse-mode", type=int, default=COARSE_MODE,
@@ -339,10 +342,12 @@ def main():
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
 
+    solver = sem.SEM_SOLVER_FGMRES if args.solver == "fgmres" else sem.SEM_SOLVER_FLEXCG
+
     def step():
         x.zero_()
-        return sem.sem_solve(mesh, pmg, b, x, sem.SEM_SOLVER_FLEXCG, tol=TOL, max_iter=200,
-                             check_every=1)
+        return sem.sem_solve(mesh, pmg, b, x, solver, tol=TOL, max_iter=200, check_every=1,
+                             restart=args.restart)
 
     for _ in range(max(args.warmup, 0)):
         info = step()
@@ -435,7 +440,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+" + args.smoother, "data": "synthetic",
             "config": {"workload": WORKLOAD, "E": side ** 3, "N": ORDER, "n_local": nl,
-                       "smoother": args.smoother, "cheb_degree": args.cheb_degree, "coarse_tol": args.coarse_tol,
+                       "solver": args.solver, "smoother": args.smoother,
+                       "cheb_degree": args.cheb_degree, "coarse_tol": args.coarse_tol,
                        "coarse_maxit": args.coarse_maxit, "coarse_mode": args.coarse_mode,
                        "n_global": ng, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (working set ~6 GB), no flush"},
@@ -472,12 +478,14 @@ def main():
         xh = torch.zeros(nl, dtype=torch.float64).pin_memory()
         for _ in range(1):
             xh.zero_()
-            sem.sem_solve_host(mesh, pmg, bh, xh, sem.SEM_SOLVER_FLEXCG, tol=TOL, max_iter=200)
+            sem.sem_solve_host(mesh, pmg, bh, xh, solver, tol=TOL, max_iter=200,
+                               restart=args.restart)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             xh.zero_()
-            sem.sem_solve_host(mesh, pmg, bh, xh, sem.SEM_SOLVER_FLEXCG, tol=TOL, max_iter=200)
+            sem.sem_solve_host(mesh, pmg, bh, xh, solver, tol=TOL, max_iter=200,
+                               restart=args.restart)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
         line["e2e"] = {"value": ng / e2e_s / 1e9, "unit": "GDOF/s",

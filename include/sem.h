@@ -196,12 +196,16 @@ sem_status sem_pmg_info(const sem_pmg *pmg, int32_t level, double *lam_lo, doubl
 /* One V-cycle z = M r on the finest level (FP64 E-layout device vectors). */
 sem_status sem_pmg_vcycle(sem_pmg *pmg, const double *r, double *z, void *stream);
 
-enum { SEM_SOLVER_PCG = 0, SEM_SOLVER_FLEXCG = 1 };
+enum { SEM_SOLVER_PCG = 0, SEM_SOLVER_FLEXCG = 1, SEM_SOLVER_FGMRES = 2 };
 typedef struct {
-  int32_t solver;    /* SEM_SOLVER_PCG (Jacobi, Sec. 3) or SEM_SOLVER_FLEXCG */
+  int32_t solver;    /* SEM_SOLVER_PCG (Jacobi, Sec. 3), SEM_SOLVER_FLEXCG, or
+                        SEM_SOLVER_FGMRES (Sec. 3: flexible GMRES, classical
+                        Gram-Schmidt; pMG preconditioner, or Jacobi when pmg is
+                        NULL) */
   double tol;        /* stop when ||r|| <= tol ||b|| (unique-dof 2-norm) */
   int32_t max_iter;
-  int32_t check_every; /* read the residual norm every k iterations (>= 1) */
+  int32_t check_every; /* read the residual norm every k iterations (>= 1; CG forms) */
+  int32_t restart;   /* FGMRES: Krylov vectors per cycle, 1..32 (0: 20) */
 } sem_solve_desc;
 
 typedef struct {
@@ -215,7 +219,11 @@ typedef struct {
 /* Solve A x = b (FP64 outer iteration).  b: assembled right-hand side
  * (continuous, masked under Dirichlet; mean-free under Neumann: SEM_EINVAL if
  * |sum b / mult| > 1e-10 * ||b||_1 / mult).  x: initial guess in, solution
- * out.  pmg: NULL for Jacobi-PCG; required for SEM_SOLVER_FLEXCG.
+ * out.  pmg: NULL for Jacobi-PCG; required for SEM_SOLVER_FLEXCG; optional
+ * for SEM_SOLVER_FGMRES.  FGMRES keeps 2 restart + 1 FP64 vectors of n_local
+ * (allocated on first use, kept by the mesh); its residual test uses the
+ * least-squares residual of each step and, at the end of a cycle, the
+ * residual recomputed from x.
  * Returns SEM_OK, SEM_ENOTCONV (max_iter reached; x and info hold the last
  * iterate) or SEM_ENUMERIC (NaN/Inf).  Synchronises. */
 sem_status sem_solve(sem_mesh *mesh, sem_pmg *pmg, const double *b, double *x,

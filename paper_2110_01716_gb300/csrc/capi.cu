@@ -1,5 +1,6 @@
 // capi.cu -- the C ABI of include/sem.h: argument checks, error reporting,
 // mesh and pMG handles, and the host loops of the Krylov solvers.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -88,6 +89,144 @@ static void read_scalars(sem_mesh *M, int count, cudaStream_t st) {
   SEM_CHECK_CUDA(cudaStreamSynchronize(st));
 }
 
+// Under Neumann the right-hand side must be mean-free (Sec. 3: the pressure
+// Poisson problem with Neumann conditions is consistent only then).
+static void check_neumann_rhs(sem_mesh *M, const double *b, cudaStream_t st) {
+  const Topo &t = M->fine.t;
+  if (t.bc != SEM_NEUMANN) return;
+  launch_sum(t, M->red, b, slot(M, 6), st);
+  launch_dot(t, M->red, b, b, slot(M, 0), st);
+  read_scalars(M, 8, st);
+  double s = M->pinned[6], bb = M->pinned[0];
+  SEM_REQUIRE(std::fabs(s) <= 1e-10 * std::sqrt((double)t.ng) * std::sqrt(bb) || bb == 0.0,
+              "Neumann right-hand side is not mean-free (sum %.3e, norm %.3e)", s,
+              std::sqrt(bb));
+}
+
+// Flexible GMRES(m) (Sec. 3: the GMRES alternative to FlexCG; Sec. 5: few
+// vectors, classical Gram-Schmidt with one reduction for all coefficients of
+// a step).  Right preconditioning by one pMG V-cycle (or Jacobi without pmg);
+// the preconditioned vectors z_j are kept because the V-cycle may vary, and
+// x = x0 + Z y (Saad, Alg. 9.6).  The small least-squares problem lives on
+// the host (Givens rotations, as in the oracle); per step the device runs the
+// preconditioner, the FP64 operator, one multi-dot <w, v_i>, one fused
+// subtract-and-norm pass and a scaling, and the host reads one Hessenberg
+// column.  A cycle ends when the least-squares residual meets the tolerance
+// or after m steps; x is then updated and its residual recomputed, which
+// decides convergence (restarting from it otherwise).
+static sem_status run_fgmres(sem_mesh *M, sem_pmg *P, const double *b, double *x,
+                             const sem_solve_desc &d, sem_solve_info &info, cudaStream_t st) {
+  const Level &L = M->fine;
+  const Topo &t = L.t;
+  const int m = d.restart > 0 ? d.restart : 20;
+  SEM_REQUIRE(m >= 1 && m <= kMaxKrylov, "restart %d outside [1, %d]", m, kMaxKrylov);
+  const size_t ws = work_stride(M);
+  if (M->krylov_m < m) {
+    M->krylov.alloc((size_t)(2 * m + 2) * ws);
+    M->krylov_m = m;
+  }
+  if (!M->kred.partials.p) M->kred.init(kVecMaxBlocks, kMaxKrylov + 1);
+  if (!M->kscal.p) M->kscal.alloc(kMaxKrylov + 4);
+  if (!M->kpinned) SEM_CHECK_CUDA(cudaMallocHost(&M->kpinned, (kMaxKrylov + 4) * sizeof(double)));
+  const int cap = M->krylov_m;
+  double *V = M->krylov.p, *Z = V + (size_t)(cap + 1) * ws, *w = Z + (size_t)cap * ws;
+  double *h = M->kscal.p, *nrm2 = h + kMaxKrylov + 1;
+  cudaEvent_t e0, e1;
+  SEM_CHECK_CUDA(cudaEventCreate(&e0));
+  SEM_CHECK_CUDA(cudaEventCreate(&e1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } guard{e0, e1};
+  SEM_CHECK_CUDA(cudaEventRecord(e0, st));
+  check_neumann_rhs(M, b, st);
+  // r0 = b - A x into V_0, with <b, b> and <r0, r0>
+  apply_assembled<double>(L, x, w, st);
+  launch_cg_start(t, M->red, b, w, nullptr, V, nullptr, nullptr, slot(M, 0), slot(M, 1),
+                  slot(M, 2), st);
+  read_scalars(M, 8, st);
+  const double bb = M->pinned[0];
+  double beta = std::sqrt(M->pinned[1]);
+  info.bnorm = std::sqrt(bb);
+  info.res0 = beta;
+  const double target = d.tol * info.bnorm;
+  sem_status status = SEM_ENOTCONV;
+  if (!(beta == beta) || !(bb == bb)) status = SEM_ENUMERIC;
+  else if (beta <= target) status = SEM_OK;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  int k = 0;
+  while (status == SEM_ENOTCONV && k < d.max_iter) {
+    launch_scale(t.nl, 1.0 / beta, V, st);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int cols = 0;
+    for (int j = 0; j < m && k < d.max_iter; ++j) {
+      double *vj = V + (size_t)j * ws, *zj = Z + (size_t)j * ws, *vn = V + (size_t)(j + 1) * ws;
+      if (P) pmg_vcycle(P, vj, zj, st);
+      else launch_mul(t.nl, L.dinv64.p, vj, zj, st);
+      apply_assembled<double>(L, zj, w, st);
+      // classical Gram-Schmidt: every coefficient from the same w
+      launch_multi_dot(t, M->kred, w, V, ws, j + 1, h, st);
+      launch_orth_update(t, M->kred, w, V, ws, j + 1, h, vn, nrm2, st);
+      SEM_CHECK_CUDA(cudaMemcpyAsync(M->kpinned, h, (kMaxKrylov + 2) * sizeof(double),
+                                     cudaMemcpyDeviceToHost, st));
+      SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+      const double hn = std::sqrt(std::max(M->kpinned[kMaxKrylov + 1], 0.0));
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = M->kpinned[i];
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (!std::isfinite(hn) || !std::isfinite(M->kpinned[j])) {
+        status = SEM_ENUMERIC;
+        break;
+      }
+      for (int i = 0; i < j; ++i) {
+        const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+      const double dd = std::sqrt(a * a + c * c);
+      cs[j] = dd > 0.0 ? a / dd : 1.0;
+      sn[j] = dd > 0.0 ? c / dd : 0.0;
+      H[(size_t)j * m + j] = dd;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++k;
+      cols = j + 1;
+      if (std::fabs(g[j + 1]) <= target || hn == 0.0) break;
+      if (j + 1 < m && k < d.max_iter) launch_scale(t.nl, 1.0 / hn, vn, st);
+    }
+    if (status == SEM_ENUMERIC) break;
+    // y = R^-1 g by back substitution; x += Z y
+    for (int i = cols - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int q = i + 1; q < cols; ++q) s -= H[(size_t)i * m + q] * y[q];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    launch_combine(t.nl, Z, ws, cols, y.data(), x, st);
+    apply_assembled<double>(L, x, w, st);
+    launch_cg_start(t, M->red, b, w, nullptr, V, nullptr, nullptr, slot(M, 0), slot(M, 1),
+                    slot(M, 2), st);
+    read_scalars(M, 8, st);
+    beta = std::sqrt(M->pinned[1]);
+    if (!(beta == beta) || std::isinf(beta)) status = SEM_ENUMERIC;
+    else if (beta <= target) status = SEM_OK;
+  }
+  SEM_CHECK_CUDA(cudaEventRecord(e1, st));
+  SEM_CHECK_CUDA(cudaEventSynchronize(e1));
+  info.iters = k;
+  info.res = beta;
+  float ms = 0.f;
+  SEM_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  info.time_ms = ms;
+  info.status = status;
+  if (status == SEM_ENOTCONV)
+    set_error_message("solver reached max_iter before the tolerance");
+  else if (status == SEM_ENUMERIC)
+    set_error_message("NaN or Inf in the solver residual");
+  return status;
+}
+
 // Jacobi-PCG (Sec. 3) or flexible CG with one pMG V-cycle per iteration
 // (Sec. 3).  Scalar slots: 0 bb, 1 rr, 2/3 rho (alternating), 4 pw, 5 zw,
 // 6 sum of b, 7 unused output.
@@ -107,15 +246,7 @@ static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
     ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
   } guard{e0, e1};
   SEM_CHECK_CUDA(cudaEventRecord(e0, st));
-  if (t.bc == SEM_NEUMANN) {
-    launch_sum(t, M->red, b, slot(M, 6), st);
-    launch_dot(t, M->red, b, b, slot(M, 0), st);
-    read_scalars(M, 8, st);
-    double s = M->pinned[6], bb = M->pinned[0];
-    SEM_REQUIRE(std::fabs(s) <= 1e-10 * std::sqrt((double)t.ng) * std::sqrt(bb) || bb == 0.0,
-                "Neumann right-hand side is not mean-free (sum %.3e, norm %.3e)", s,
-                std::sqrt(bb));
-  }
+  check_neumann_rhs(M, b, st);
   apply_assembled<double>(L, x, w, st);
   launch_cg_start(t, M->red, b, w, flex ? nullptr : L.dinv64.p, r, z, p, slot(M, 0), slot(M, 1),
                   slot(M, 2), st);
@@ -216,6 +347,7 @@ sem_status sem_mesh_destroy(sem_mesh *mesh) {
   return guarded([&] {
     if (!mesh) return;
     if (mesh->pinned) cudaFreeHost(mesh->pinned);
+    if (mesh->kpinned) cudaFreeHost(mesh->kpinned);
     delete mesh;
   });
 }
@@ -228,6 +360,7 @@ sem_status sem_mesh_info(const sem_mesh *mesh, int64_t *n_local, int64_t *n_glob
     if (n_global) *n_global = mesh->fine.t.ng;
     if (dev_bytes)
       *dev_bytes = mesh->fine.device_bytes() + mesh->work.bytes() + mesh->red.partials.bytes() +
+                   mesh->krylov.bytes() + mesh->kred.partials.bytes() + mesh->kscal.bytes() +
                    mesh->scal.bytes() + mesh->host_b.bytes() + mesh->host_x.bytes();
   });
 }
@@ -328,10 +461,14 @@ sem_status sem_pmg_vcycle(sem_pmg *pmg, const double *r, double *z, void *stream
 static void check_solve_args(sem_mesh *mesh, sem_pmg *pmg, const sem_solve_desc *desc,
                              sem_solve_info *info) {
   SEM_REQUIRE(mesh && desc && info, "null argument");
-  SEM_REQUIRE(desc->solver == SEM_SOLVER_PCG || desc->solver == SEM_SOLVER_FLEXCG,
+  SEM_REQUIRE(desc->solver == SEM_SOLVER_PCG || desc->solver == SEM_SOLVER_FLEXCG ||
+                  desc->solver == SEM_SOLVER_FGMRES,
               "unknown solver %d", desc->solver);
-  SEM_REQUIRE(desc->solver == SEM_SOLVER_PCG || pmg != nullptr,
+  SEM_REQUIRE(desc->solver != SEM_SOLVER_FLEXCG || pmg != nullptr,
               "SEM_SOLVER_FLEXCG needs a pMG preconditioner");
+  SEM_REQUIRE(desc->solver != SEM_SOLVER_FGMRES ||
+                  (desc->restart >= 0 && desc->restart <= kMaxKrylov),
+              "restart %d outside [0, %d]", desc->restart, kMaxKrylov);
   SEM_REQUIRE(pmg == nullptr || pmg->mesh == mesh, "pmg was built on another mesh");
   SEM_REQUIRE(desc->tol >= 0.0 && desc->max_iter >= 0, "negative tol or max_iter");
 }
@@ -343,7 +480,9 @@ sem_status sem_solve(sem_mesh *mesh, sem_pmg *pmg, const double *b, double *x,
     check_solve_args(mesh, pmg, desc, info);
     SEM_REQUIRE(b && x && b != (const double *)x, "null or aliased b and x");
     std::memset(info, 0, sizeof(*info));
-    result = run_solve(mesh, pmg, b, x, *desc, *info, as_stream(stream));
+    result = desc->solver == SEM_SOLVER_FGMRES
+                 ? run_fgmres(mesh, pmg, b, x, *desc, *info, as_stream(stream))
+                 : run_solve(mesh, pmg, b, x, *desc, *info, as_stream(stream));
   });
   return st != SEM_OK ? st : result;
 }
@@ -365,7 +504,9 @@ sem_status sem_solve_host(sem_mesh *mesh, sem_pmg *pmg, const double *b_host, do
                                    cudaMemcpyHostToDevice, s));
     SEM_CHECK_CUDA(cudaMemcpyAsync(mesh->host_x.p, x_host, n * sizeof(double),
                                    cudaMemcpyHostToDevice, s));
-    result = run_solve(mesh, pmg, mesh->host_b.p, mesh->host_x.p, *desc, *info, s);
+    result = desc->solver == SEM_SOLVER_FGMRES
+                 ? run_fgmres(mesh, pmg, mesh->host_b.p, mesh->host_x.p, *desc, *info, s)
+                 : run_solve(mesh, pmg, mesh->host_b.p, mesh->host_x.p, *desc, *info, s);
     SEM_CHECK_CUDA(cudaMemcpyAsync(x_host, mesh->host_x.p, n * sizeof(double),
                                    cudaMemcpyDeviceToHost, s));
     SEM_CHECK_CUDA(cudaStreamSynchronize(s));

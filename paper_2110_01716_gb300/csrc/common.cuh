@@ -228,4 +228,9 @@ struct sem_mesh {
   sem::DevBuf<double> work;   // solver work vectors
   sem::DevBuf<double> host_b, host_x;  // device copies for sem_solve_host
   double *pinned = nullptr;   // host-pinned scalars
+  sem::DevBuf<double> krylov; // FGMRES: V (restart + 1) and Z (restart) vectors
+  int krylov_m = 0;
+  sem::Reducer kred;          // reductions of up to restart + 1 sums
+  sem::DevBuf<double> kscal;  // FGMRES device scalars
+  double *kpinned = nullptr;  // host-pinned copy of one Hessenberg column
 };

@@ -33,6 +33,18 @@ void launch_stop_test(const double *rr, const double *bb, double tol2, int it, i
 template <typename A, typename B>
 void launch_convert(int64_t n, const A *a, B *b, cudaStream_t st);
 
+// Flexible GMRES (krylov.cu).  Basis vectors i < c at V + i * stride.
+constexpr int kMaxKrylov = 32;  // restart length limit
+void launch_multi_dot(const Topo &t, Reducer &R, const double *w, const double *V, size_t stride,
+                      int c, double *h, cudaStream_t st);
+void launch_orth_update(const Topo &t, Reducer &R, const double *w, const double *V,
+                        size_t stride, int c, const double *h, double *v, double *nrm2,
+                        cudaStream_t st);
+void launch_scale(int64_t n, double a, double *v, cudaStream_t st);
+void launch_mul(int64_t n, const double *a, const double *b, double *out, cudaStream_t st);
+void launch_combine(int64_t n, const double *Z, size_t stride, int c, const double *y, double *x,
+                    cudaStream_t st);
+
 // Assembled operator on a level: w = mask * gs(A_L u).
 // FP32 on stored factors takes the fused operator (x-face sums in the operator
 // kernel, plane passes for y and z).

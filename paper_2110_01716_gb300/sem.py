@@ -26,7 +26,7 @@ SEM_ARITH_PAIR, SEM_ARITH_NATIVE = 0, 1
 SEM_AX_LOCAL, SEM_AX_ASSEMBLED = 0, 1
 SEM_FIELD_X, SEM_FIELD_Y, SEM_FIELD_Z, SEM_FIELD_MASS, SEM_FIELD_MULT, SEM_FIELD_MASK, \
     SEM_FIELD_DINV = range(7)
-SEM_SOLVER_PCG, SEM_SOLVER_FLEXCG = 0, 1
+SEM_SOLVER_PCG, SEM_SOLVER_FLEXCG, SEM_SOLVER_FGMRES = 0, 1, 2
 SEM_COARSE_JACOBI, SEM_COARSE_MG = 0, 1
 SEM_MAX_ORDER = 11
 
@@ -57,7 +57,7 @@ class sem_pmg_desc(C.Structure):
 
 class sem_solve_desc(C.Structure):
     _fields_ = [("solver", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("check_every", C.c_int32)]
+                ("check_every", C.c_int32), ("restart", C.c_int32)]
 
 
 class sem_trace_entry(C.Structure):
@@ -253,9 +253,9 @@ def sem_pmg_vcycle(pmg: Pmg, r, z, stream=None):
 
 
 def sem_solve(mesh: Mesh, pmg, b, x, solver=SEM_SOLVER_PCG, tol=1e-8, max_iter=1000,
-              check_every=1, stream=None, raise_on_notconv=False):
+              check_every=1, stream=None, raise_on_notconv=False, restart=0):
     """Solve in place (x: initial guess in, solution out); returns the info dict."""
-    desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every))
+    desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every), int(restart))
     info = sem_solve_info()
     st = lib().sem_solve(mesh.h, pmg.h if pmg is not None else None, _ptr(b), _ptr(x),
                          C.byref(desc), C.byref(info), _stream(stream))
@@ -267,9 +267,9 @@ def sem_solve(mesh: Mesh, pmg, b, x, solver=SEM_SOLVER_PCG, tol=1e-8, max_iter=1
 
 
 def sem_solve_host(mesh: Mesh, pmg, b_host, x_host, solver=SEM_SOLVER_PCG, tol=1e-8,
-                   max_iter=1000, check_every=1, stream=None):
+                   max_iter=1000, check_every=1, stream=None, restart=0):
     """As sem_solve with host (CPU tensor or numpy) b and x; x is updated in place."""
-    desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every))
+    desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every), int(restart))
     info = sem_solve_info()
     bp = b_host.ctypes.data if hasattr(b_host, "ctypes") else b_host.data_ptr()
     xp = x_host.ctypes.data if hasattr(x_host, "ctypes") else x_host.data_ptr()

@@ -244,3 +244,71 @@ def test_multigrid_coarse_mode_needs_order_one():
     with pytest.raises(sem.SemError) as ei:
         sem.Pmg(m, orders=(4, 2), coarse_mode=sem.SEM_COARSE_MG)
     assert ei.value.status == sem.SEM_EINVAL
+
+
+# ---------------------------------------------------------------- FGMRES
+@pytest.mark.parametrize("restart", [8, 3])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_fgmres_jacobi_matches_oracle(restart, bc):
+    """With a fixed (Jacobi) preconditioner FGMRES is a fixed map after a
+    given number of steps: the GPU iterate and residual match the oracle's,
+    with and without restarts."""
+    e, N = (3, 2, 2), 5
+    v = inputs.box_vertices(*e, 0.1, 4)
+    m = sem.Mesh(*e, N, bc, verts=v)
+    Po = oracle.PMG(*e, [N, 1], bc, v)
+    L = Po.levels[0]
+    b = manufactured(L)[1] if bc == 0 else fourier_rhs(L)
+    bd = torch.tensor(b, device=DEV)
+    xd = torch.zeros_like(bd)
+    info = sem.sem_solve(m, None, bd, xd, sem.SEM_SOLVER_FGMRES, tol=0.0, max_iter=7,
+                         restart=restart)
+    assert info["status"] == sem.SEM_ENOTCONV and info["iters"] == 7
+    xo, io = Po.fgmres(b, tol=0.0, restart=restart, maxit=7, precond=False)
+    assert rel(xd.cpu().numpy(), xo) < 1e-9
+    assert abs(info["res"] - io["res"]) <= 1e-9 * io["res0"]
+    assert abs(info["res"] - residual(L, b, xd.cpu().numpy()) * np.sqrt(L.dot(b, b))) \
+        <= 1e-9 * io["res0"]
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("dtype", [sem.SEM_F64, sem.SEM_F32])
+def test_fgmres_pmg_reaches_1e8(bc, dtype):
+    e = 6
+    v = inputs.box_vertices(e, e, e, 0.1, 3)
+    m = sem.Mesh(e, e, e, 7, bc, verts=v)
+    L = oracle.Level(e, e, e, 7, bc, v)
+    b = manufactured(L)[1] if bc == 0 else fourier_rhs(L)
+    P = sem.Pmg(m, orders=(7, 3, 1), smoother_dtype=dtype, coarse_tol=1e-2, coarse_maxit=50)
+    bd = torch.tensor(b, device=DEV)
+    xd = torch.zeros_like(bd)
+    info = sem.sem_solve(m, P, bd, xd, sem.SEM_SOLVER_FGMRES, tol=1e-8, max_iter=100, restart=20)
+    assert info["status"] == sem.SEM_OK, info
+    x = xd.cpu().numpy()
+    assert residual(L, b, x) <= 1.001e-8
+    assert abs(info["res"] / info["bnorm"] - residual(L, b, x)) <= 1e-12
+    Po = oracle.PMG(e, e, e, [7, 3, 1], bc, v, coarse_tol=1e-2, coarse_maxit=50)
+    xo, io = Po.fgmres(b, tol=1e-8, restart=20, maxit=100)
+    if bc == 1:
+        x = x - L.dot(x, np.ones(L.nl)) / L.ng
+        xo = xo - L.dot(xo, np.ones(L.nl)) / L.ng
+    assert rel(x, xo) < 1e-6
+    assert abs(info["iters"] - io["iters"]) <= 2, (info["iters"], io["iters"])
+    # restarted every 3 steps it still converges
+    xd.zero_()
+    info3 = sem.sem_solve(m, P, bd, xd, sem.SEM_SOLVER_FGMRES, tol=1e-8, max_iter=100, restart=3)
+    assert info3["status"] == sem.SEM_OK
+    assert residual(L, b, xd.cpu().numpy()) <= 1.001e-8
+
+
+def test_fgmres_argument_checks():
+    m = sem.Mesh(2, 2, 2, 3, 0)
+    bd = torch.zeros(m.n_local, device=DEV, dtype=torch.float64)
+    xd = torch.zeros_like(bd)
+    for bad in (-1, 33):
+        with pytest.raises(sem.SemError) as ex:
+            sem.sem_solve(m, None, bd, xd, sem.SEM_SOLVER_FGMRES, restart=bad)
+        assert ex.value.status == sem.SEM_EINVAL
+    # zero right-hand side: converged at once
+    info = sem.sem_solve(m, None, bd, xd, sem.SEM_SOLVER_FGMRES, tol=1e-8, restart=32)
+    assert info["status"] == sem.SEM_OK and info["iters"] == 0
