@@ -87,6 +87,14 @@ def lib():
     L.orc_interp3.argtypes = [C.c_int64, C.c_int, C.c_int, _dp, _dp, _dp, C.c_int]
     L.orc_flexpcg.argtypes = [C.c_void_p, C.c_int, _dp, _dp, C.c_double, C.c_int,
                               C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.orc_proj_create.argtypes = [C.c_void_p, C.c_int]
+    L.orc_proj_create.restype = C.c_void_p
+    L.orc_proj_destroy.argtypes = [C.c_void_p]
+    L.orc_proj_nvec.argtypes = [C.c_void_p]
+    L.orc_proj_vector.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
+    L.orc_solve_projected.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, _dp, _dp,
+                                      C.c_double, C.c_int, C.POINTER(C.c_int),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.orc_fgmres.argtypes = [C.c_void_p, C.c_int, _dp, _dp, C.c_double, C.c_int, C.c_int,
                              C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
                              C.c_void_p]
@@ -344,3 +352,34 @@ class PMG:
         st = lib().orc_flexpcg(self.ptr, int(precond), np.ascontiguousarray(b, dtype=np.float64),
                                x, tol, maxit, C.byref(it), C.byref(r0), C.byref(r1))
         return x, {"status": st, "iters": it.value, "res0": r0.value, "res": r1.value}
+
+
+class Projection:
+    """Projection onto previous solutions (orc_solve_projected) for a PMG."""
+
+    def __init__(self, pmg, Lmax):
+        self.pmg = pmg
+        self.ptr = lib().orc_proj_create(pmg.ptr, Lmax)
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            lib().orc_proj_destroy(self.ptr)
+            self.ptr = None
+
+    @property
+    def nvec(self):
+        return lib().orc_proj_nvec(self.ptr)
+
+    def vector(self, i):
+        n = self.pmg.levels[0].nl
+        p, ap = np.zeros(n), np.zeros(n)
+        lib().orc_proj_vector(self.ptr, i, p, ap)
+        return p, ap
+
+    def solve(self, b, tol=1e-8, maxit=500, solver="flexcg", restart=20):
+        x = np.zeros(self.pmg.levels[0].nl)
+        it, rp, r1 = C.c_int(), C.c_double(), C.c_double()
+        st = lib().orc_solve_projected(self.pmg.ptr, self.ptr, 1 if solver == "fgmres" else 0,
+                                       restart, np.ascontiguousarray(b, dtype=np.float64), x,
+                                       tol, maxit, C.byref(it), C.byref(rp), C.byref(r1))
+        return x, {"status": st, "iters": it.value, "res_proj": rp.value, "res": r1.value}

@@ -889,3 +889,124 @@ int orc_flexpcg(orc_pmg *P, int precond, const double *b, double *x, double tol,
   free(r); free(rold); free(z); free(p); free(w);
   return status;
 }
+
+/* ------------------------------------------------------------------ projection
+ * Projection onto previous solutions (Sec. 3, "Projection is key"): an
+ * A-orthonormal basis P = [p_1 .. p_L] of earlier solutions, with A p_i kept
+ * beside it.  For a new b the best fit in the A-norm is xbar = P P^T b
+ * (coefficients p_i^T b, one reduction); the solver then only computes the
+ * correction of A dx = b - A xbar, and x = xbar + dx.  The correction joins
+ * the basis after one classical Gram-Schmidt pass in the A-inner product,
+ * alpha_i = (A p_i)^T dx, p = dx - sum alpha_i p_i, with
+ * ||p||_A^2 = dx^T A dx - sum alpha_i^2 (the same single reduction; the
+ * paper notes dx is nearly A-orthogonal to P, so this is stable).  When L
+ * reaches Lmax the space restarts from the latest solution alone.  Inner
+ * products are the unique-dof product. */
+typedef struct orc_proj {
+  orc_level *L;
+  int Lmax, nvec;
+  double *P, *AP;  /* [Lmax][nl] */
+} orc_proj;
+
+orc_proj *orc_proj_create(orc_pmg *Pm, int Lmax) {
+  orc_proj *Q = calloc(1, sizeof(orc_proj));
+  Q->L = Pm->lev[0];
+  Q->Lmax = Lmax;
+  Q->P = calloc((size_t)Lmax * Q->L->nl, sizeof(double));
+  Q->AP = calloc((size_t)Lmax * Q->L->nl, sizeof(double));
+  return Q;
+}
+
+void orc_proj_destroy(orc_proj *Q) {
+  if (!Q) return;
+  free(Q->P); free(Q->AP); free(Q);
+}
+
+int orc_proj_nvec(const orc_proj *Q) { return Q->nvec; }
+void orc_proj_vector(const orc_proj *Q, int i, double *p, double *ap) {
+  int64_t n = Q->L->nl;
+  memcpy(p, Q->P + (size_t)i * n, sizeof(double) * n);
+  memcpy(ap, Q->AP + (size_t)i * n, sizeof(double) * n);
+}
+
+/* Add v (with Av = A v) to the basis after A-orthogonalisation; returns 1 if
+ * added, 0 if v had no component outside the span. */
+static int proj_add(orc_proj *Q, const double *v, const double *Av) {
+  orc_level *L = Q->L;
+  int64_t n = L->nl;
+  int k = Q->nvec;
+  double *alpha = malloc(sizeof(double) * (k + 1));
+  for (int i = 0; i < k; ++i) alpha[i] = orc_level_dot(L, Q->AP + (size_t)i * n, v);
+  double vav = orc_level_dot(L, v, Av);
+  double nrm2 = vav;
+  for (int i = 0; i < k; ++i) nrm2 -= alpha[i] * alpha[i];
+  int added = 0;
+  if (nrm2 > 1e-24 * vav && nrm2 > 0.0) {
+    double s = 1.0 / sqrt(nrm2);
+    double *p = Q->P + (size_t)k * n, *ap = Q->AP + (size_t)k * n;
+    for (int64_t l = 0; l < n; ++l) {
+      double a = v[l], b = Av[l];
+      for (int i = 0; i < k; ++i) {
+        a -= alpha[i] * Q->P[(size_t)i * n + l];
+        b -= alpha[i] * Q->AP[(size_t)i * n + l];
+      }
+      p[l] = a * s;
+      ap[l] = b * s;
+    }
+    Q->nvec = k + 1;
+    added = 1;
+  }
+  free(alpha);
+  return added;
+}
+
+/* Solve A x = b to tol (relative to ||b||) with projection: x is output only
+ * (the best fit is the initial guess).  solver 0: FlexCG + pMG, 1: FGMRES(m)
+ * + pMG.  Reports the iterations of the correction solve and ||b - A xbar||. */
+int orc_solve_projected(orc_pmg *Pm, orc_proj *Q, int solver, int m, const double *b, double *x,
+                        double tol, int maxit, int *iters, double *res_proj, double *res) {
+  orc_level *L = Q->L;
+  int64_t n = L->nl;
+  int k = Q->nvec;
+  double *c = malloc(sizeof(double) * (k + 1));
+  double *bp = malloc(sizeof(double) * n), *dx = calloc(n, sizeof(double)),
+         *w = malloc(sizeof(double) * n);
+  for (int i = 0; i < k; ++i) c[i] = orc_level_dot(L, Q->P + (size_t)i * n, b);
+  for (int64_t l = 0; l < n; ++l) {
+    double xb = 0.0, ab = 0.0;
+    for (int i = 0; i < k; ++i) {
+      xb += c[i] * Q->P[(size_t)i * n + l];
+      ab += c[i] * Q->AP[(size_t)i * n + l];
+    }
+    x[l] = xb;
+    bp[l] = b[l] - ab;
+  }
+  double bnorm = sqrt(orc_level_dot(L, b, b));
+  double bpn = sqrt(orc_level_dot(L, bp, bp));
+  *res_proj = bpn;
+  double tin = bpn > 0.0 ? tol * bnorm / bpn : 0.0;
+  int st = 0;
+  double r0, r1;
+  *iters = 0;
+  if (bpn > tol * bnorm) {
+    if (solver == 1) st = orc_fgmres(Pm, 1, bp, dx, tin, m, maxit, iters, &r0, &r1, NULL);
+    else st = orc_flexpcg(Pm, 1, bp, dx, tin, maxit, iters, &r0, &r1);
+  }
+  for (int64_t l = 0; l < n; ++l) x[l] += dx[l];
+  /* grow the space with the correction, or restart from the full solution */
+  if (bpn > tol * bnorm) {
+    if (Q->nvec == Q->Lmax) {
+      Q->nvec = 0;
+      orc_level_ax(L, x, w);
+      proj_add(Q, x, w);
+    } else {
+      orc_level_ax(L, dx, w);
+      proj_add(Q, dx, w);
+    }
+  }
+  orc_level_ax(L, x, w);
+  for (int64_t l = 0; l < n; ++l) w[l] = b[l] - w[l];
+  *res = sqrt(orc_level_dot(L, w, w));
+  free(c); free(bp); free(dx); free(w);
+  return st;
+}

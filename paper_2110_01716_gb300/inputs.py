@@ -87,6 +87,17 @@ def fourier_modes(seed: int, m: int = 8):
     return a, k, phi
 
 
+def fourier_sequence(seed: int, m: int = 8):
+    """A smoothly time-varying right-hand side for successive solves:
+    f_n(x) = sum_m a_m cos(2 pi k_m . x + phi_m + omega_m n), with (a, k, phi)
+    of fourier_modes(seed, m) and angular steps omega_m ~ U(0.02, 0.1) rad
+    per solve (one extra draw after the modes).  Returns (a, k, phi, omega)."""
+    a, k, phi = fourier_modes(seed, m)
+    rng = np.random.Generator(np.random.PCG64(seed + 0x5EED))
+    omega = rng.uniform(0.02, 0.1, size=m)
+    return a, k, phi, omega
+
+
 def near_cube_factors(E: int):
     """ex*ey*ez closest to E with factors differing by at most one."""
     best = None

@@ -303,3 +303,87 @@ def test_fgmres_restarted_and_pmg_preconditioned(orc, bc):
         assert np.all(np.diff(info["hist"]) <= 1e-12 * info["hist"][0])
         if restart == 30:
             assert info["iters"] <= fi["iters"] + 1, (info["iters"], fi["iters"])
+
+
+# ---------------------------------------------------------------- projection
+def _sequence_rhs(L, n, bc, seed=3):
+    a, k, phi, om = inputs.fourier_sequence(seed)
+    X = L.X
+    f = sum(a[m] * np.cos(2 * np.pi * (k[m, 0] * X[:, 0] + k[m, 1] * X[:, 1]
+                                       + k[m, 2] * X[:, 2]) + phi[m] + om[m] * n)
+            for m in range(len(a))).ravel()
+    b = L.gs(L.B * f)
+    if bc == DIR:
+        return b * L.mask
+    return b - L.dot(b, np.ones(L.nl)) / L.dot(np.ones(L.nl), np.ones(L.nl))
+
+
+def test_projection_basis_is_a_orthonormal_and_best_fit(orc):
+    """After a sequence of solves the kept basis is A-orthonormal (dense A from
+    numpy), A p_i is stored exactly, and the projected residual equals the
+    dense least-squares best fit in the A-norm."""
+    e, N = 2, 4
+    v = inputs.box_vertices(e, e, e, 0.1, 3)
+    P = orc.PMG(e, e, e, [N, 2, 1], DIR, v, coarse_tol=1e-6, coarse_maxit=100)
+    L = P.levels[0]
+    A, rep = dense_unique(L, L.ax)
+    Q = orc.Projection(P, 8)
+    for n in range(5):
+        Q.solve(_sequence_rhs(L, n, DIR), tol=1e-10)
+    k = Q.nvec
+    assert k == 5
+    Pm = np.stack([Q.vector(i)[0][rep] for i in range(k)], axis=1)
+    APm = np.stack([Q.vector(i)[1][rep] for i in range(k)], axis=1)
+    np.testing.assert_allclose(A @ Pm, APm, atol=1e-10 * np.abs(APm).max())
+    np.testing.assert_allclose(Pm.T @ A @ Pm, np.eye(k), atol=1e-9)
+    # best fit of a new right-hand side: dense normal equations in the A-norm
+    b = _sequence_rhs(L, 5, DIR)
+    c = np.linalg.solve(Pm.T @ A @ Pm, Pm.T @ b[rep])
+    rp_ref = np.linalg.norm(b[rep] - A @ Pm @ c)
+    x, info = Q.solve(b, tol=1e-10)
+    assert abs(info["res_proj"] - rp_ref) <= 1e-9 * np.linalg.norm(b[rep])
+    r = b - L.ax(x)
+    assert np.sqrt(L.dot(r, r)) <= 1.001e-10 * np.sqrt(L.dot(b, b))
+
+
+def test_projection_of_a_right_hand_side_in_the_span_is_exact(orc):
+    e, N = 2, 4
+    v = inputs.box_vertices(e, e, e, 0.1, 4)
+    P = orc.PMG(e, e, e, [N, 1], DIR, v, coarse_tol=1e-6, coarse_maxit=100)
+    L = P.levels[0]
+    Q = orc.Projection(P, 8)
+    xs = []
+    for n in range(3):
+        x, _ = Q.solve(_sequence_rhs(L, n, DIR), tol=1e-12)
+        xs.append(x)
+    target = 0.3 * xs[0] - 1.7 * xs[2]
+    b = L.ax(target)
+    x, info = Q.solve(b, tol=1e-8)
+    assert info["iters"] == 0 and info["res_proj"] <= 1e-8 * np.sqrt(L.dot(b, b))
+    assert np.max(np.abs(x - target)) <= 1e-8 * np.max(np.abs(target))
+
+
+@pytest.mark.parametrize("bc", [DIR, NEU])
+@pytest.mark.parametrize("solver", ["flexcg", "fgmres"])
+def test_projection_cuts_iterations_on_a_smooth_sequence(orc, bc, solver):
+    """Successive right-hand sides varying smoothly: every solve meets the
+    tolerance (residual recomputed), later solves need fewer iterations than
+    the first, and with Lmax = 3 the space restarts (never more than 3)."""
+    e = 3
+    v = inputs.box_vertices(e, e, e, 0.1, 3)
+    P = orc.PMG(e, e, e, [7, 3, 1], bc, v, cheb_degree=2, coarse_tol=1e-2, coarse_maxit=50)
+    L = P.levels[0]
+    for Lmax in (30, 3):
+        Q = orc.Projection(P, Lmax)
+        its = []
+        for n in range(8):
+            b = _sequence_rhs(L, n, bc)
+            x, info = Q.solve(b, tol=1e-8, solver=solver)
+            assert info["status"] == 0
+            r = b - L.ax(x)
+            assert np.sqrt(L.dot(r, r)) <= 1.001e-8 * np.sqrt(L.dot(b, b))
+            assert Q.nvec <= Lmax
+            its.append(info["iters"])
+        assert its[-1] < its[0], its
+        if Lmax == 30:
+            assert sum(its[4:]) <= sum(its[:4]) - 4, its
