@@ -113,10 +113,11 @@ def dist_setup():
     return world, rank, local
 
 
-def rhs_on_device(sem, torch, mesh, dev):
+def rhs_on_device(sem, torch, mesh, dev, step=None):
     """Neumann right-hand side b = gs(B f) minus its unique-dof mean, with f the
     seeded smooth random field of the input module, evaluated on the mesh's own
-    GLL coordinates."""
+    GLL coordinates.  With step = n: the n-th member of the smooth sequence of
+    inputs.fourier_sequence (successive solves)."""
     from paper_2110_01716_gb300 import inputs
 
     n = mesh.n_local
@@ -125,11 +126,17 @@ def rhs_on_device(sem, torch, mesh, dev):
         sem.sem_mesh_field(mesh, d, X[d])
     Bm = torch.empty(n, device=dev, dtype=torch.float64)
     sem.sem_mesh_field(mesh, sem.SEM_FIELD_MASS, Bm)
-    a, k, phi = inputs.fourier_modes(RHS_SEED)
+    if step is None:
+        a, k, phi = inputs.fourier_modes(RHS_SEED)
+        om = [0.0] * len(a)
+        step = 0
+    else:
+        a, k, phi, om = inputs.fourier_sequence(RHS_SEED)
     f = torch.zeros(n, device=dev, dtype=torch.float64)
     for m in range(len(a)):
         f += float(a[m]) * torch.cos(2 * torch.pi * (float(k[m, 0]) * X[0] + float(k[m, 1]) * X[1]
-                                                     + float(k[m, 2]) * X[2]) + float(phi[m]))
+                                                     + float(k[m, 2]) * X[2]) + float(phi[m])
+                                     + float(om[m]) * step)
     b = Bm * f
     sem.sem_gs(mesh, sem.SEM_F64, b)
     ones = torch.ones_like(b)
@@ -239,6 +246,44 @@ def operator_sweep(sem, torch, dev, hbm):
             del u, w
         mesh.close()
         torch.cuda.empty_cache()
+    return out
+
+
+def projection_sequence(sem, torch, mesh, pmg, dev, solver, restart, steps=16, Lmax=30):
+    """Successive solves on the smooth right-hand-side sequence (same mesh and
+    preconditioner): plain solves from x = 0 against projected solves with an
+    Lmax-vector space (Sec. 3).  Reports per-solve time and iterations."""
+    stream = torch.cuda.current_stream()
+    out = {"steps": steps, "Lmax": Lmax}
+    proj = sem.Projection(mesh, Lmax)
+    for mode in ("plain", "projected"):
+        ms, its = [], []
+        for n in range(steps):
+            b = rhs_on_device(sem, torch, mesh, dev, step=n)
+            x = torch.zeros_like(b)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if mode == "plain":
+                info = sem.sem_solve(mesh, pmg, b, x, solver, tol=TOL, max_iter=200,
+                                     restart=restart)
+            else:
+                info = sem.sem_solve_projected(mesh, pmg, proj, b, x, solver, tol=TOL,
+                                               max_iter=200, restart=restart)
+            e1.record(stream)
+            e1.synchronize()
+            if info["status"] != sem.SEM_OK:
+                raise SystemExit(f"projection sequence: solve {n} ({mode}) did not converge")
+            ms.append(e0.elapsed_time(e1))
+            its.append(info["iters"])
+            del b, x
+        half = steps // 2
+        out[mode] = {"iters": its, "ms": [round(v, 2) for v in ms],
+                     "mean_ms_second_half": round(sum(ms[half:]) / (steps - half), 2)}
+    proj.close()
+    out["speedup_second_half"] = round(out["plain"]["mean_ms_second_half"]
+                                       / out["projected"]["mean_ms_second_half"], 2)
+    torch.cuda.empty_cache()
     return out
 
 
@@ -491,6 +536,7 @@ def main():
         line["e2e"] = {"value": ng / e2e_s / 1e9, "unit": "GDOF/s",
                        "h2d_bytes_per_step": 2 * nl * 8, "d2h_bytes_per_step": nl * 8}
         del bh, xh
+        line["projection"] = projection_sequence(sem, torch, mesh, pmg, dev, solver, args.restart)
         pmg.close()
         mesh.close()
         del b, x

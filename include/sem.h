@@ -234,6 +234,27 @@ sem_status sem_solve(sem_mesh *mesh, sem_pmg *pmg, const double *b, double *x,
 sem_status sem_solve_host(sem_mesh *mesh, sem_pmg *pmg, const double *b_host, double *x_host,
                           const sem_solve_desc *desc, sem_solve_info *info, void *stream);
 
+/* Projection onto previous solutions (Sec. 3, "Projection is key"): the
+ * handle keeps an A-orthonormal basis P = [p_1 .. p_L] of earlier solutions
+ * and A p_i (FP64 E-layout, 2 Lmax + 3 vectors of n_local owned by the
+ * handle, allocated at creation).  sem_solve_projected computes the best fit
+ * xbar = P P^T b (one multi-dot), solves A dx = b - A xbar with the solver of
+ * desc to the tolerance tol ||b|| (relative to the original b), returns
+ * x = xbar + dx (x is output only), and adds dx to the basis after one
+ * classical Gram-Schmidt pass in the A-inner product (||p||_A from the same
+ * reduction: dx^T A dx - sum alpha_i^2).  When L reaches Lmax the basis
+ * restarts from the new solution alone.  info->res0 is ||b - A xbar||,
+ * info->iters the iterations of the correction solve.  The handle refers to
+ * the mesh, which must outlive it.  Lmax: 1..31. */
+typedef struct sem_proj sem_proj;
+sem_status sem_proj_create(sem_mesh *mesh, int32_t Lmax, void *stream, sem_proj **out);
+sem_status sem_proj_destroy(sem_proj *proj);
+/* Number of basis vectors now held (HOST output). */
+sem_status sem_proj_info(const sem_proj *proj, int32_t *nvec);
+sem_status sem_solve_projected(sem_mesh *mesh, sem_pmg *pmg, sem_proj *proj, const double *b,
+                               double *x, const sem_solve_desc *desc, sem_solve_info *info,
+                               void *stream);
+
 /* Tracing (Sec. 4 reports timing breakdowns from CUDA events): while enabled,
  * every kernel launch of the library is counted under a class name such as
  * "ax_f64_N7" or "gs_f32_N3"; launches of classes whose name contains

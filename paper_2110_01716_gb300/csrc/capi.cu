@@ -115,7 +115,8 @@ static void check_neumann_rhs(sem_mesh *M, const double *b, cudaStream_t st) {
 // or after m steps; x is then updated and its residual recomputed, which
 // decides convergence (restarting from it otherwise).
 static sem_status run_fgmres(sem_mesh *M, sem_pmg *P, const double *b, double *x,
-                             const sem_solve_desc &d, sem_solve_info &info, cudaStream_t st) {
+                             const sem_solve_desc &d, sem_solve_info &info, cudaStream_t st,
+                             bool x_zero = false, bool check_rhs = true) {
   const Level &L = M->fine;
   const Topo &t = L.t;
   const int m = d.restart > 0 ? d.restart : 20;
@@ -139,11 +140,11 @@ static sem_status run_fgmres(sem_mesh *M, sem_pmg *P, const double *b, double *x
     ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
   } guard{e0, e1};
   SEM_CHECK_CUDA(cudaEventRecord(e0, st));
-  check_neumann_rhs(M, b, st);
-  // r0 = b - A x into V_0, with <b, b> and <r0, r0>
-  apply_assembled<double>(L, x, w, st);
-  launch_cg_start(t, M->red, b, w, nullptr, V, nullptr, nullptr, slot(M, 0), slot(M, 1),
-                  slot(M, 2), st);
+  if (check_rhs) check_neumann_rhs(M, b, st);
+  // r0 = b - A x into V_0 (r0 = b when x is known to be zero), with <b, b>, <r0, r0>
+  if (!x_zero) apply_assembled<double>(L, x, w, st);
+  launch_cg_start(t, M->red, b, x_zero ? nullptr : w, nullptr, V, nullptr, nullptr, slot(M, 0),
+                  slot(M, 1), slot(M, 2), st);
   read_scalars(M, 8, st);
   const double bb = M->pinned[0];
   double beta = std::sqrt(M->pinned[1]);
@@ -231,7 +232,8 @@ static sem_status run_fgmres(sem_mesh *M, sem_pmg *P, const double *b, double *x
 // (Sec. 3).  Scalar slots: 0 bb, 1 rr, 2/3 rho (alternating), 4 pw, 5 zw,
 // 6 sum of b, 7 unused output.
 static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
-                            const sem_solve_desc &d, sem_solve_info &info, cudaStream_t st) {
+                            const sem_solve_desc &d, sem_solve_info &info, cudaStream_t st,
+                            bool x_zero = false, bool check_rhs = true) {
   const Level &L = M->fine;
   const Topo &t = L.t;
   const bool flex = d.solver == SEM_SOLVER_FLEXCG;
@@ -246,10 +248,10 @@ static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
     ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
   } guard{e0, e1};
   SEM_CHECK_CUDA(cudaEventRecord(e0, st));
-  check_neumann_rhs(M, b, st);
-  apply_assembled<double>(L, x, w, st);
-  launch_cg_start(t, M->red, b, w, flex ? nullptr : L.dinv64.p, r, z, p, slot(M, 0), slot(M, 1),
-                  slot(M, 2), st);
+  if (check_rhs) check_neumann_rhs(M, b, st);
+  if (!x_zero) apply_assembled<double>(L, x, w, st);
+  launch_cg_start(t, M->red, b, x_zero ? nullptr : w, flex ? nullptr : L.dinv64.p, r, z, p,
+                  slot(M, 0), slot(M, 1), slot(M, 2), st);
   read_scalars(M, 8, st);
   const double bb = M->pinned[0];
   double rr = M->pinned[1];
@@ -301,6 +303,88 @@ static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
     set_error_message("solver reached max_iter before the tolerance");
   else if (status == SEM_ENUMERIC)
     set_error_message("NaN or Inf in the solver residual");
+  return status;
+}
+
+// Projected solve (Sec. 3, "Projection is key"; the oracle's
+// orc_solve_projected step by step).
+static sem_status run_projected(sem_mesh *M, sem_pmg *P, sem_proj *Q, const double *b, double *x,
+                                const sem_solve_desc &d, sem_solve_info &info, cudaStream_t st) {
+  const Level &L = M->fine;
+  const Topo &t = L.t;
+  const size_t ws = work_stride(M);
+  const int64_t n = t.nl;
+  double *Pv = Q->P.p, *APv = Q->AP.p, *c = Q->coef.p;
+  if (!M->kred.partials.p) M->kred.init(kVecMaxBlocks, kMaxKrylov + 1);
+  if (!M->kpinned) SEM_CHECK_CUDA(cudaMallocHost(&M->kpinned, (kMaxKrylov + 4) * sizeof(double)));
+  auto read_coef = [&](int count) {
+    SEM_CHECK_CUDA(cudaMemcpyAsync(M->kpinned, c, count * sizeof(double), cudaMemcpyDeviceToHost,
+                                   st));
+    SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+    return std::vector<double>(M->kpinned, M->kpinned + count);
+  };
+  // the original right-hand side is checked; its projected part inherits it
+  check_neumann_rhs(M, b, st);
+  const int k = Q->nvec;
+  // best fit xbar = P P^T b into x; bp = b - AP P^T b
+  SEM_CHECK_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+  SEM_CHECK_CUDA(cudaMemcpyAsync(Q->bp.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (k > 0) {
+    launch_multi_dot(t, M->kred, b, Pv, ws, k, c, st);
+    std::vector<double> cf = read_coef(k), neg(k);
+    for (int i = 0; i < k; ++i) neg[i] = -cf[i];
+    launch_combine(n, Pv, ws, k, cf.data(), x, st);
+    launch_combine(n, APv, ws, k, neg.data(), Q->bp.p, st);
+  }
+  launch_dot(t, M->red, b, b, slot(M, 0), st);
+  launch_dot(t, M->red, Q->bp.p, Q->bp.p, slot(M, 1), st);
+  read_scalars(M, 8, st);
+  const double bnorm = std::sqrt(M->pinned[0]), bpn = std::sqrt(M->pinned[1]);
+  sem_status status = SEM_OK;
+  SEM_CHECK_CUDA(cudaMemsetAsync(Q->dx.p, 0, n * sizeof(double), st));
+  info.iters = 0;
+  info.res = bpn;
+  info.time_ms = 0.0;
+  const bool solve = bpn > d.tol * bnorm;
+  if (solve) {
+    sem_solve_desc din = d;
+    din.tol = d.tol * bnorm / bpn;
+    status = din.solver == SEM_SOLVER_FGMRES
+                 ? run_fgmres(M, P, Q->bp.p, Q->dx.p, din, info, st, true, false)
+                 : run_solve(M, P, Q->bp.p, Q->dx.p, din, info, st, true, false);
+    const double one = 1.0;
+    launch_combine(n, Q->dx.p, ws, 1, &one, x, st);
+  }
+  info.bnorm = bnorm;
+  info.res0 = bpn;
+  info.status = status;
+  if (solve && status != SEM_ENUMERIC) {
+    // grow the basis with dx (or restart it from x once it is full)
+    const double *v = Q->dx.p;
+    if (Q->nvec == Q->Lmax) {
+      Q->nvec = 0;
+      v = x;
+    }
+    const int kk = Q->nvec;
+    double *Av = APv + (size_t)kk * ws, *pk = Pv + (size_t)kk * ws;
+    apply_assembled<double>(L, v, Av, st);
+    launch_multi_dot(t, M->kred, v, APv, ws, kk + 1, c, st);
+    std::vector<double> al = read_coef(kk + 1);
+    double nrm2 = al[kk];
+    for (int i = 0; i < kk; ++i) nrm2 -= al[i] * al[i];
+    if (nrm2 > 1e-24 * al[kk] && nrm2 > 0.0) {
+      std::vector<double> neg(kk + 1);
+      for (int i = 0; i < kk; ++i) neg[i] = -al[i];
+      SEM_CHECK_CUDA(cudaMemcpyAsync(pk, v, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      launch_combine(n, Pv, ws, kk, neg.data(), pk, st);
+      launch_combine(n, APv, ws, kk, neg.data(), Av, st);
+      const double s = 1.0 / std::sqrt(nrm2);
+      launch_scale(n, s, pk, st);
+      launch_scale(n, s, Av, st);
+      Q->nvec = kk + 1;
+    }
+  }
+  SEM_CHECK_CUDA(cudaStreamSynchronize(st));
   return status;
 }
 
@@ -510,6 +594,63 @@ sem_status sem_solve_host(sem_mesh *mesh, sem_pmg *pmg, const double *b_host, do
     SEM_CHECK_CUDA(cudaMemcpyAsync(x_host, mesh->host_x.p, n * sizeof(double),
                                    cudaMemcpyDeviceToHost, s));
     SEM_CHECK_CUDA(cudaStreamSynchronize(s));
+  });
+  return st != SEM_OK ? st : result;
+}
+
+sem_status sem_proj_create(sem_mesh *mesh, int32_t Lmax, void *stream, sem_proj **out) {
+  return guarded([&] {
+    SEM_REQUIRE(mesh != nullptr && out != nullptr, "null mesh or out");
+    SEM_REQUIRE(Lmax >= 1 && Lmax <= kMaxKrylov - 1, "Lmax %d outside [1, %d]", Lmax,
+                kMaxKrylov - 1);
+    *out = nullptr;
+    std::unique_ptr<sem_proj> Q(new sem_proj());
+    Q->mesh = mesh;
+    Q->Lmax = Lmax;
+    const size_t ws = work_stride(mesh);
+    Q->P.alloc((size_t)Lmax * ws);
+    Q->AP.alloc((size_t)(Lmax + 1) * ws);
+    Q->bp.alloc(ws);
+    Q->dx.alloc(ws);
+    Q->coef.alloc(kMaxKrylov + 2);
+    SEM_CHECK_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    *out = Q.release();
+  });
+}
+
+sem_status sem_proj_destroy(sem_proj *proj) {
+  return guarded([&] { delete proj; });
+}
+
+sem_status sem_proj_info(const sem_proj *proj, int32_t *nvec) {
+  return guarded([&] {
+    SEM_REQUIRE(proj != nullptr && nvec != nullptr, "null argument");
+    *nvec = proj->nvec;
+  });
+}
+
+sem_status sem_solve_projected(sem_mesh *mesh, sem_pmg *pmg, sem_proj *proj, const double *b,
+                               double *x, const sem_solve_desc *desc, sem_solve_info *info,
+                               void *stream) {
+  sem_status result = SEM_OK;
+  sem_status st = guarded([&] {
+    check_solve_args(mesh, pmg, desc, info);
+    SEM_REQUIRE(proj != nullptr && proj->mesh == mesh, "projection handle of another mesh");
+    SEM_REQUIRE(b && x && b != (const double *)x, "null or aliased b and x");
+    std::memset(info, 0, sizeof(*info));
+    cudaStream_t s = as_stream(stream);
+    cudaEvent_t e0, e1;
+    SEM_CHECK_CUDA(cudaEventCreate(&e0));
+    SEM_CHECK_CUDA(cudaEventCreate(&e1));
+    SEM_CHECK_CUDA(cudaEventRecord(e0, s));
+    result = run_projected(mesh, pmg, proj, b, x, *desc, *info, s);
+    SEM_CHECK_CUDA(cudaEventRecord(e1, s));
+    SEM_CHECK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    info->time_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
   });
   return st != SEM_OK ? st : result;
 }

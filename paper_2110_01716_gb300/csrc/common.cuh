@@ -220,6 +220,13 @@ struct Reducer {
 }  // namespace sem
 
 // Opaque handles of the ABI.
+struct sem_proj {
+  sem_mesh *mesh = nullptr;
+  int Lmax = 0, nvec = 0;
+  sem::DevBuf<double> P, AP;  // [Lmax][stride], [Lmax + 1][stride] (last: scratch)
+  sem::DevBuf<double> bp, dx; // projected right-hand side, correction
+  sem::DevBuf<double> coef;   // device coefficients of one multi-dot
+};
 struct sem_mesh {
   sem::Level fine;
   cudaStream_t stream = nullptr;

@@ -33,7 +33,8 @@ SEM_MAX_ORDER = 11
 EXPORTED = ["sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_field", "sem_ax",
             "sem_gs", "sem_dot", "sem_pmg_setup", "sem_pmg_destroy", "sem_pmg_info",
             "sem_pmg_vcycle", "sem_solve", "sem_solve_host", "sem_trace_enable",
-            "sem_trace_read", "sem_dot_noalloc", "sem_last_error"]
+            "sem_trace_read", "sem_dot_noalloc", "sem_proj_create", "sem_proj_destroy",
+            "sem_proj_info", "sem_solve_projected", "sem_last_error"]
 
 
 class SemError(RuntimeError):
@@ -102,6 +103,11 @@ def lib():
     L.sem_solve.argtypes = [vp, vp, vp, vp, C.POINTER(sem_solve_desc), C.POINTER(sem_solve_info),
                             vp]
     L.sem_solve_host.argtypes = L.sem_solve.argtypes
+    L.sem_proj_create.argtypes = [vp, i32, vp, C.POINTER(vp)]
+    L.sem_proj_destroy.argtypes = [vp]
+    L.sem_proj_info.argtypes = [vp, C.POINTER(i32)]
+    L.sem_solve_projected.argtypes = [vp, vp, vp, vp, vp, C.POINTER(sem_solve_desc),
+                                      C.POINTER(sem_solve_info), vp]
     L.sem_trace_enable.argtypes = [i32, C.c_char_p]
     L.sem_trace_read.argtypes = [C.POINTER(sem_trace_entry), i32, C.POINTER(i32), i32]
     for name in EXPORTED:
@@ -275,6 +281,48 @@ def sem_solve_host(mesh: Mesh, pmg, b_host, x_host, solver=SEM_SOLVER_PCG, tol=1
     xp = x_host.ctypes.data if hasattr(x_host, "ctypes") else x_host.data_ptr()
     st = lib().sem_solve_host(mesh.h, pmg.h if pmg is not None else None, bp, xp, C.byref(desc),
                               C.byref(info), _stream(stream))
+    if st not in (SEM_OK, SEM_ENOTCONV):
+        raise SemError(st, last_error())
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+class Projection:
+    """sem_proj handle: projection onto previous solutions (Lmax vectors)."""
+
+    def __init__(self, mesh: "Mesh", Lmax: int, stream=None):
+        self.mesh = mesh
+        h = C.c_void_p()
+        check(lib().sem_proj_create(mesh.h, int(Lmax), _stream(stream), C.byref(h)))
+        self.h = h
+
+    @property
+    def nvec(self) -> int:
+        n = C.c_int32()
+        check(lib().sem_proj_info(self.h, C.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sem_proj_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sem_solve_projected(mesh: Mesh, pmg, proj: Projection, b, x, solver=SEM_SOLVER_FLEXCG,
+                        tol=1e-8, max_iter=1000, check_every=1, restart=0, stream=None):
+    """Projected solve: x (output) = best fit in the kept space + correction;
+    returns the info dict (res0 = residual after projection)."""
+    desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every), int(restart))
+    info = sem_solve_info()
+    st = lib().sem_solve_projected(mesh.h, pmg.h if pmg is not None else None, proj.h, _ptr(b),
+                                   _ptr(x), C.byref(desc), C.byref(info), _stream(stream))
     if st not in (SEM_OK, SEM_ENOTCONV):
         raise SemError(st, last_error())
     d = info.as_dict()

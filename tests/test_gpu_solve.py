@@ -312,3 +312,83 @@ def test_fgmres_argument_checks():
     # zero right-hand side: converged at once
     info = sem.sem_solve(m, None, bd, xd, sem.SEM_SOLVER_FGMRES, tol=1e-8, restart=32)
     assert info["status"] == sem.SEM_OK and info["iters"] == 0
+
+
+# ---------------------------------------------------------------- projection
+def sequence_rhs(L, n, bc, seed=3):
+    a, k, phi, om = inputs.fourier_sequence(seed)
+    X = L.X
+    f = sum(a[m] * np.cos(2 * np.pi * (k[m, 0] * X[:, 0] + k[m, 1] * X[:, 1]
+                                       + k[m, 2] * X[:, 2]) + phi[m] + om[m] * n)
+            for m in range(len(a))).ravel()
+    b = L.gs(L.B * f)
+    if bc == 0:
+        return b * L.mask
+    return b - L.dot(b, np.ones(L.nl)) / L.ng
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("solver", [sem.SEM_SOLVER_FLEXCG, sem.SEM_SOLVER_FGMRES])
+@pytest.mark.parametrize("Lmax", [30, 3])
+def test_projection_sequence_matches_oracle(bc, solver, Lmax):
+    """A smooth sequence of right-hand sides: every projected solve meets 1e-8
+    (residual recomputed by the oracle), the basis grows (and restarts at
+    Lmax) exactly as the oracle's, iterations follow the oracle's within one,
+    and solutions agree to 1e-6."""
+    e = 4
+    v = inputs.box_vertices(e, e, e, 0.1, 3)
+    m = sem.Mesh(e, e, e, 7, bc, verts=v)
+    P = sem.Pmg(m, orders=(7, 3, 1), smoother_dtype=sem.SEM_F64, coarse_tol=1e-2,
+                coarse_maxit=50)
+    Q = sem.Projection(m, Lmax)
+    Po = oracle.PMG(e, e, e, [7, 3, 1], bc, v, coarse_tol=1e-2, coarse_maxit=50)
+    Qo = oracle.Projection(Po, Lmax)
+    L = Po.levels[0]
+    its = []
+    ones = np.ones(L.nl)
+    for n in range(8):
+        b = sequence_rhs(L, n, bc)
+        bd = torch.tensor(b, device=DEV)
+        xd = torch.empty_like(bd)
+        info = sem.sem_solve_projected(m, P, Q, bd, xd, solver, tol=1e-8, max_iter=100,
+                                       restart=20)
+        assert info["status"] == sem.SEM_OK, info
+        x = xd.cpu().numpy()
+        assert residual(L, b, x) <= 1.001e-8
+        xo, io = Qo.solve(b, tol=1e-8, solver="fgmres" if solver == sem.SEM_SOLVER_FGMRES
+                          else "flexcg", restart=20)
+        assert Q.nvec == Qo.nvec <= Lmax
+        assert abs(info["iters"] - io["iters"]) <= 1, (n, info["iters"], io["iters"])
+        bn = np.sqrt(L.dot(b, b))
+        assert abs(info["res0"] - io["res_proj"]) <= 1e-6 * bn
+        if bc == 1:
+            x = x - L.dot(x, ones) / L.ng
+            xo = xo - L.dot(xo, ones) / L.ng
+        assert rel(x, xo) < 1e-6
+        its.append(info["iters"])
+    assert its[-1] < its[0], its
+
+
+def test_projection_reproduces_a_right_hand_side_in_its_span():
+    e = 3
+    v = inputs.box_vertices(e, e, e, 0.1, 5)
+    m = sem.Mesh(e, e, e, 5, 0, verts=v)
+    P = sem.Pmg(m, orders=(5, 2, 1), smoother_dtype=sem.SEM_F64, coarse_tol=1e-3,
+                coarse_maxit=100)
+    Q = sem.Projection(m, 8)
+    L = oracle.Level(e, e, e, 5, 0, v)
+    xs = []
+    for n in range(3):
+        bd = torch.tensor(sequence_rhs(L, n, 0), device=DEV)
+        xd = torch.empty_like(bd)
+        sem.sem_solve_projected(m, P, Q, bd, xd, sem.SEM_SOLVER_FLEXCG, tol=1e-12, max_iter=200)
+        xs.append(xd.cpu().numpy())
+    target = 0.3 * xs[0] - 1.7 * xs[2]
+    b = L.ax(target)
+    bd = torch.tensor(b, device=DEV)
+    xd = torch.empty_like(bd)
+    info = sem.sem_solve_projected(m, P, Q, bd, xd, sem.SEM_SOLVER_FLEXCG, tol=1e-8)
+    assert info["iters"] == 0 and info["res0"] <= 1e-8 * info["bnorm"]
+    assert rel(xd.cpu().numpy(), target) <= 1e-8
+    with pytest.raises(sem.SemError):
+        sem.Projection(m, 32)
