@@ -79,6 +79,8 @@ def parse_args():
     p.add_argument("--side", type=int, default=E_SIDE, help="elements per direction")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the operator sweep, e2e and CPU-baseline legs")
+    p.add_argument("--no-serve", action="store_true",
+                   help="skip the batched (config 4) and serving (config 5) legs")
     p.add_argument("--breakdown", action="store_true",
                    help="after the timed region, time every kernel class of one more solve")
     p.add_argument("--coarse-maxit", type=int, default=COARSE_MAXIT)
@@ -285,6 +287,78 @@ def projection_sequence(sem, torch, mesh, pmg, dev, solver, restart, steps=16, L
                                        / out["projected"]["mean_ms_second_half"], 2)
     torch.cuda.empty_cache()
     return out
+
+
+def batch_leg(sem, inputs, count=64, max_workers=8):
+    """64 independent problems (E log-uniform in [64, 8192] elements, N in
+    {5, 7, 9}, manufactured right-hand side, FlexCG + pMG to 1e-8): sequential
+    (one worker) with the FP64 smoother and with the FP32 smoother, and the
+    worker count the autotuner picks.  Every solve includes its setup."""
+    inst = inputs.batch_instances(4, count)
+    reqs = [sem.make_request(d["ex"], d["ey"], d["ez"], d["N"], sem.SEM_DIRICHLET, 0.1,
+                             d["seed"], tol=1e-8) for d in inst]
+
+    def run(workers, smoother):
+        S = sem.Server(workers=workers, cache_per_shape=0, smoother_dtype=smoother)
+        t0 = time.perf_counter()
+        tk = [S.submit(d["ex"], d["ey"], d["ez"], d["N"], sem.SEM_DIRICHLET, 0.1, d["seed"],
+                       tol=1e-8) for d in inst]
+        infos = [S.wait(t) for t in tk]
+        dt = time.perf_counter() - t0
+        S.close()
+        bad = [i for i, f in enumerate(infos) if f["status"] != sem.SEM_OK]
+        if bad:
+            raise SystemExit(f"batch leg: requests {bad} failed")
+        return dt, infos
+
+    t64, _ = run(1, sem.SEM_F64)
+    t32, _ = run(1, sem.SEM_F32)
+    best_w, rate = sem.server_autotune(reqs, max_workers=max_workers, cache_per_shape=0)
+    tb, infos = run(best_w, sem.SEM_F32)
+    return {"instances": count, "workload": "config 4: E log-uniform [64, 8192], N in {5,7,9}, "
+            "manufactured RHS, Dirichlet, FlexCG+pMG to 1e-8, setup included",
+            "fp64_sequential_s": round(t64, 3), "fp32_sequential_s": round(t32, 3),
+            "autotuned_workers": best_w, "autotune_rate": round(rate, 2),
+            "batched_s": round(tb, 3), "solves_per_s": round(count / tb, 2),
+            "speedup_vs_fp64_sequential": round(t64 / tb, 2),
+            "iters_mean": round(sum(f["iters"] for f in infos) / count, 2)}
+
+
+def serve_leg(sem, inputs, workers, count=200, load=0.8):
+    """Config 5: Poisson arrivals at `load` times the measured capacity (the
+    first 32 requests run back to back with the same workers), E log-uniform
+    in [512, 65536], N = 7, tolerance in {1e-6, 1e-8, 1e-10}.  Latency is
+    submit -> completion; the stream is cut to `count` requests (1000 in the
+    full recipe) to keep the bench within minutes."""
+    probe = inputs.arrival_stream(5, 32, 1.0)
+    S = sem.Server(workers=workers, cache_per_shape=0)
+    t0 = time.perf_counter()
+    tk = [S.submit(r["ex"], r["ey"], r["ez"], r["N"], sem.SEM_DIRICHLET, 0.1, r["seed"],
+                   tol=r["tol"]) for r in probe]
+    for t in tk:
+        S.wait(t)
+    capacity = len(probe) / (time.perf_counter() - t0)
+    stream = inputs.arrival_stream(5, count, load * capacity)
+    lat, tickets = [], []
+    t0 = time.perf_counter()
+    for r in stream:
+        now = time.perf_counter() - t0
+        if r["t"] > now:
+            time.sleep(r["t"] - now)
+        tickets.append(S.submit(r["ex"], r["ey"], r["ez"], r["N"], sem.SEM_DIRICHLET, 0.1,
+                                r["seed"], tol=r["tol"]))
+    infos = [S.wait(t) for t in tickets]
+    span = time.perf_counter() - t0
+    S.close()
+    lat = sorted(f["time_ms"] for f in infos)
+    if any(f["status"] != sem.SEM_OK for f in infos):
+        raise SystemExit("serve leg: a request failed")
+    return {"requests": count, "workers": workers, "capacity_solves_per_s": round(capacity, 2),
+            "offered_rate": round(load * capacity, 2), "achieved_solves_per_s": round(count / span, 2),
+            "latency_ms": {"p50": round(lat[len(lat) // 2], 2),
+                           "p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 2)},
+            "workload": "config 5 (cut to %d requests): Poisson arrivals, E log-uniform "
+                        "[512, 65536], N=7, tol in {1e-6,1e-8,1e-10}, setup included" % count}
 
 
 def oracle_sample_solve(side=12):
@@ -541,6 +615,9 @@ def main():
         mesh.close()
         del b, x
         torch.cuda.empty_cache()
+        if not args.no_serve:
+            line["batch"] = batch_leg(sem, inputs)
+            line["serve"] = serve_leg(sem, inputs, line["batch"]["autotuned_workers"])
         line["ax_sweep_64cube"] = operator_sweep(sem, torch, dev, hbm)
         if world == 1:
             dt, ng_s, it_s, threads = oracle_sample_solve(12)

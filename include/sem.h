@@ -255,6 +255,69 @@ sem_status sem_solve_projected(sem_mesh *mesh, sem_pmg *pmg, sem_proj *proj, con
                                double *x, const sem_solve_desc *desc, sem_solve_info *info,
                                void *stream);
 
+/* ---- Serving: many independent solves with continuous batching ----------
+ * The paper has no counterpart (it runs one large solve across partitions);
+ * this is a service of the library for streams of small and mid-sized
+ * problems.  A server owns `workers` host threads, each with its own CUDA
+ * stream.  A worker takes the oldest queued request whose estimated device
+ * memory fits in what the budget leaves (the oldest request runs anyway when
+ * nothing else does), takes an idle setup of the same shape from the cache or
+ * builds the mesh and pMG hierarchy (orders N, ceil(N/2), 1), solves, copies x
+ * back, and records the result; its next request starts as soon as it is done
+ * (continuous batching).  Solves of different workers overlap on the GPU.
+ * Every solve is deterministic: results do not depend on the worker count. */
+typedef struct sem_server sem_server;
+
+typedef struct {
+  int32_t workers;        /* host threads / CUDA streams, 1..64 */
+  int64_t hbm_budget;     /* device bytes the server's setups may hold (0: 80 %
+                             of the free device memory at creation) */
+  int32_t cache_per_shape;/* idle setups kept per mesh shape (0: none) */
+  int32_t cheb_degree;    /* pMG template (as sem_pmg_desc; coarse: multigrid
+                             CG for N = 1 coarsest levels) */
+  int32_t smoother_dtype;
+  double coarse_tol;
+  int32_t coarse_maxit;
+} sem_server_desc;
+
+enum { SEM_RHS_HOST = 0, SEM_RHS_MANUFACTURED = 1 };
+typedef struct {
+  int32_t ex, ey, ez, N, bc;  /* mesh: box with the built-in jittered vertices */
+  double jitter;
+  uint64_t seed;
+  int32_t rhs;          /* SEM_RHS_HOST: b below; SEM_RHS_MANUFACTURED:
+                           b = mask gs(B f), f = 3 pi^2 sin(pi x) sin(pi y)
+                           sin(pi z) (Dirichlet only), built on the device */
+  const double *b;      /* HOST, n_local values, copied at submit */
+  double *x;            /* HOST, n_local values written at completion (may be
+                           NULL); must stay valid until the request is polled */
+  sem_solve_desc solve; /* PCG, FLEXCG or FGMRES (pMG used for the latter two) */
+} sem_request;
+
+typedef struct {
+  int64_t submitted, completed, failed;
+  int64_t setups_built, setups_reused;
+  int64_t hbm_in_use;   /* estimated device bytes of running and cached setups */
+} sem_server_stats;
+
+sem_status sem_server_create(const sem_server_desc *desc, sem_server **out);
+/* Waits for every accepted request, then frees everything. */
+sem_status sem_server_destroy(sem_server *server);
+/* Queue a request; *ticket identifies it.  SEM_EINVAL for malformed requests
+ * (checked at submit), SEM_EBUSY if the queue holds 65,536 requests. */
+sem_status sem_submit(sem_server *server, const sem_request *req, uint64_t *ticket);
+/* SEM_EAGAIN while pending.  When done: fills *out (out->status is the
+ * solve's status, out->time_ms the latency from submit to completion),
+ * returns SEM_OK and forgets the ticket.  Unknown ticket: SEM_EINVAL. */
+sem_status sem_poll(sem_server *server, uint64_t ticket, sem_solve_info *out);
+sem_status sem_server_stats_read(const sem_server *server, sem_server_stats *out);
+
+/* Autotuner: runs the n sample requests (x outputs may be NULL) through
+ * servers of 1, 2, 4, ... up to max_workers workers and returns the worker
+ * count with the highest throughput (*best_rate in solves per second). */
+sem_status sem_server_autotune(const sem_server_desc *base, const sem_request *reqs, int32_t n,
+                               int32_t max_workers, int32_t *best_workers, double *best_rate);
+
 /* Tracing (Sec. 4 reports timing breakdowns from CUDA events): while enabled,
  * every kernel launch of the library is counted under a class name such as
  * "ax_f64_N7" or "gs_f32_N3"; launches of classes whose name contains

@@ -29,6 +29,10 @@
 // contiguous values, so these passes move whole sectors.  Dirichlet masking is
 // done by the pass of each boundary's direction: a masked node's copies all lie
 // on that boundary plane, so later passes only add zeros.
+#include <atomic>
+#include <cstring>
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -493,11 +497,15 @@ __global__ void plane_sum_kernel(Topo t, float *__restrict__ w, int dirichlet) {
 }
 
 static int sm_count() {
-  static int n[64] = {};
+  static std::atomic<int> n[64] = {};  // per device; host threads may race to fill it
   int dev = 0;
   SEM_CHECK_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return 152;
-  if (!n[dev]) SEM_CHECK_CUDA(cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev));
+  if (!n[dev]) {
+    int v = 0;
+    SEM_CHECK_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    n[dev] = v;
+  }
   return n[dev];
 }
 
@@ -505,7 +513,7 @@ static int sm_count() {
 // sets the dynamic shared-memory limit on the way).
 template <int NP, int GK, bool ASSEMBLE>
 static int ax32_resident() {
-  static int res[64] = {};
+  static std::atomic<int> res[64] = {};  // per device; filling it twice is harmless
   int dev = 0;
   SEM_CHECK_CUDA(cudaGetDevice(&dev));
   SEM_REQUIRE(dev >= 0 && dev < 64, "device index %d out of range", dev);

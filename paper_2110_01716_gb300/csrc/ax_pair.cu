@@ -18,6 +18,8 @@
 // hi is the value truncated to 24 significant bits, lo the next 23 bits.
 // The result is rebuilt from its float pair with integer instructions and one
 // FP64 addition.  Geometric factors are stored pre-split (float2, 8 bytes).
+#include <atomic>
+
 #include "common.cuh"
 #include "trace.cuh"
 
@@ -198,7 +200,7 @@ static void launch_pair_np(const Level &L, const double *u, double *w, cudaStrea
   const int64_t cap = 152 * 16;
   int grid = (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
   const size_t shm = sizeof(float2) * ((size_t)NP * (NP + 1) + 3 * (size_t)S::NE * S::NP3);
-  static bool attr_set[64] = {};  // the attribute is per function and device
+  static std::atomic<bool> attr_set[64] = {};  // per function and device (host threads may race)
   int dev = 0;
   SEM_CHECK_CUDA(cudaGetDevice(&dev));
   if (dev >= 64 || !attr_set[dev]) {

@@ -28,13 +28,17 @@ SEM_FIELD_X, SEM_FIELD_Y, SEM_FIELD_Z, SEM_FIELD_MASS, SEM_FIELD_MULT, SEM_FIELD
     SEM_FIELD_DINV = range(7)
 SEM_SOLVER_PCG, SEM_SOLVER_FLEXCG, SEM_SOLVER_FGMRES = 0, 1, 2
 SEM_COARSE_JACOBI, SEM_COARSE_MG = 0, 1
+SEM_RHS_HOST, SEM_RHS_MANUFACTURED = 0, 1
+SEM_EAGAIN, SEM_EBUSY = 6, 7
 SEM_MAX_ORDER = 11
 
 EXPORTED = ["sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_field", "sem_ax",
             "sem_gs", "sem_dot", "sem_pmg_setup", "sem_pmg_destroy", "sem_pmg_info",
             "sem_pmg_vcycle", "sem_solve", "sem_solve_host", "sem_trace_enable",
             "sem_trace_read", "sem_dot_noalloc", "sem_proj_create", "sem_proj_destroy",
-            "sem_proj_info", "sem_solve_projected", "sem_last_error"]
+            "sem_proj_info", "sem_solve_projected", "sem_server_create", "sem_server_destroy",
+            "sem_submit", "sem_poll", "sem_server_stats_read", "sem_server_autotune",
+            "sem_last_error"]
 
 
 class SemError(RuntimeError):
@@ -59,6 +63,25 @@ class sem_pmg_desc(C.Structure):
 class sem_solve_desc(C.Structure):
     _fields_ = [("solver", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("check_every", C.c_int32), ("restart", C.c_int32)]
+
+
+class sem_server_desc(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("hbm_budget", C.c_int64), ("cache_per_shape", C.c_int32),
+                ("cheb_degree", C.c_int32), ("smoother_dtype", C.c_int32),
+                ("coarse_tol", C.c_double), ("coarse_maxit", C.c_int32)]
+
+
+class sem_request(C.Structure):
+    _fields_ = [("ex", C.c_int32), ("ey", C.c_int32), ("ez", C.c_int32), ("N", C.c_int32),
+                ("bc", C.c_int32), ("jitter", C.c_double), ("seed", C.c_uint64),
+                ("rhs", C.c_int32), ("b", C.c_void_p), ("x", C.c_void_p),
+                ("solve", sem_solve_desc)]
+
+
+class sem_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("setups_built", C.c_int64), ("setups_reused", C.c_int64),
+                ("hbm_in_use", C.c_int64)]
 
 
 class sem_trace_entry(C.Structure):
@@ -108,6 +131,13 @@ def lib():
     L.sem_proj_info.argtypes = [vp, C.POINTER(i32)]
     L.sem_solve_projected.argtypes = [vp, vp, vp, vp, vp, C.POINTER(sem_solve_desc),
                                       C.POINTER(sem_solve_info), vp]
+    L.sem_server_create.argtypes = [C.POINTER(sem_server_desc), C.POINTER(vp)]
+    L.sem_server_destroy.argtypes = [vp]
+    L.sem_submit.argtypes = [vp, C.POINTER(sem_request), C.POINTER(C.c_uint64)]
+    L.sem_poll.argtypes = [vp, C.c_uint64, C.POINTER(sem_solve_info)]
+    L.sem_server_stats_read.argtypes = [vp, C.POINTER(sem_server_stats)]
+    L.sem_server_autotune.argtypes = [C.POINTER(sem_server_desc), C.POINTER(sem_request), i32, i32,
+                                      C.POINTER(i32), C.POINTER(d)]
     L.sem_trace_enable.argtypes = [i32, C.c_char_p]
     L.sem_trace_read.argtypes = [C.POINTER(sem_trace_entry), i32, C.POINTER(i32), i32]
     for name in EXPORTED:
@@ -328,6 +358,91 @@ def sem_solve_projected(mesh: Mesh, pmg, proj: Projection, b, x, solver=SEM_SOLV
     d = info.as_dict()
     d["status"] = st
     return d
+
+
+def make_request(ex, ey, ez, N, bc=SEM_DIRICHLET, jitter=0.1, seed=0, b=None, x=None,
+                 solver=SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=200, restart=0):
+    """A sem_request; b (host float64 array, n_local) selects SEM_RHS_HOST, else the
+    manufactured right-hand side; x (host float64 array) receives the solution."""
+    r = sem_request()
+    r.ex, r.ey, r.ez, r.N, r.bc = ex, ey, ez, N, bc
+    r.jitter, r.seed = float(jitter), int(seed)
+    r.rhs = SEM_RHS_MANUFACTURED if b is None else SEM_RHS_HOST
+    r.b = b.ctypes.data if b is not None else None
+    r.x = x.ctypes.data if x is not None else None
+    r.solve = sem_solve_desc(solver, float(tol), int(max_iter), 1, int(restart))
+    return r
+
+
+def server_desc(workers=4, hbm_budget=0, cache_per_shape=1, cheb_degree=3,
+                smoother_dtype=SEM_F32, coarse_tol=1e-1, coarse_maxit=30):
+    return sem_server_desc(int(workers), int(hbm_budget), int(cache_per_shape), int(cheb_degree),
+                           int(smoother_dtype), float(coarse_tol), int(coarse_maxit))
+
+
+class Server:
+    """Continuous-batching server of independent solves (sem_server)."""
+
+    def __init__(self, **kw):
+        self.desc = server_desc(**kw)
+        h = C.c_void_p()
+        check(lib().sem_server_create(C.byref(self.desc), C.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, *args, **kw):
+        """Arguments of make_request; returns the ticket.  Host arrays given as
+        b and x are kept alive until the request is polled."""
+        r = make_request(*args, **kw)
+        t = C.c_uint64()
+        check(lib().sem_submit(self.h, C.byref(r), C.byref(t)))
+        self._keep[t.value] = (kw.get("b"), kw.get("x"))
+        return t.value
+
+    def poll(self, ticket):
+        """The info dict when done (the ticket is then released), else None."""
+        info = sem_solve_info()
+        st = lib().sem_poll(self.h, C.c_uint64(ticket), C.byref(info))
+        if st == SEM_EAGAIN:
+            return None
+        check(st)
+        self._keep.pop(ticket, None)
+        return info.as_dict()
+
+    def wait(self, ticket, sleep=0.0005):
+        import time as _time
+
+        while True:
+            d = self.poll(ticket)
+            if d is not None:
+                return d
+            _time.sleep(sleep)
+
+    def stats(self):
+        s = sem_server_stats()
+        check(lib().sem_server_stats_read(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sem_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def server_autotune(requests, max_workers=16, **desc_kw):
+    """Fastest worker count for a sample batch: (workers, solves per second)."""
+    arr = (sem_request * len(requests))(*requests)
+    w, rate = C.c_int32(), C.c_double()
+    check(lib().sem_server_autotune(C.byref(server_desc(**desc_kw)), arr, len(requests),
+                                    int(max_workers), C.byref(w), C.byref(rate)))
+    return w.value, rate.value
 
 
 def sem_trace_enable(enable: bool, timed_filter: str = ""):
