@@ -66,8 +66,8 @@ AX_TRAFFIC = {"source_sha256": "ab9460908abee14bcf8f1dbe80d2dc039a0c47229b82a9a9
               "bytes_per_point": 62.66}
 # The same for the smoother's assembled FP32 operator, per factor storage
 # (profiles/ax32_N7.md), valid while ax32.cu is unchanged.
-AX32_TRAFFIC = {"f32": {"source_sha256": "118829ac6746fa9b16e97412595df4afd4e2d0297b24f8a8ce7458f54eca390d", "bytes_per_point": 31.41},
-                "f16": {"source_sha256": "118829ac6746fa9b16e97412595df4afd4e2d0297b24f8a8ce7458f54eca390d", "bytes_per_point": 18.80}}
+AX32_TRAFFIC = {"f32": {"source_sha256": "b145c77d79b5cbdd966aee7e10e1998242bf9d71ab90db702d378036cff7083e", "bytes_per_point": 31.41},
+                "f16": {"source_sha256": "b145c77d79b5cbdd966aee7e10e1998242bf9d71ab90db702d378036cff7083e", "bytes_per_point": 18.80}}
 
 
 def parse_args():
