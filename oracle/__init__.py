@@ -95,6 +95,14 @@ def lib():
     L.orc_solve_projected.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, _dp, _dp,
                                       C.c_double, C.c_int, C.POINTER(C.c_int),
                                       C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.orc_pmg_create2.argtypes = [C.c_int] * 4 + [_i32p, C.c_int, _dp, C.c_int, C.c_int,
+                                                  C.c_uint64, C.c_double, C.c_int, C.c_int]
+    L.orc_pmg_create2.restype = C.c_void_p
+    L.orc_asm_create.argtypes = [C.c_void_p]
+    L.orc_asm_create.restype = C.c_void_p
+    L.orc_asm_destroy.argtypes = [C.c_void_p]
+    L.orc_asm_apply.argtypes = [C.c_void_p, _dp, _dp]
+    L.orc_asm_local_matrix.argtypes = [C.c_void_p, C.c_int64, _dp]
     L.orc_fgmres.argtypes = [C.c_void_p, C.c_int, _dp, _dp, C.c_double, C.c_int, C.c_int,
                              C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
                              C.c_void_p]
@@ -305,11 +313,12 @@ class PMG:
     """p-multigrid hierarchy with Chebyshev-Jacobi smoothing (all FP64)."""
 
     def __init__(self, ex, ey, ez, orders, bc, verts, cheb_degree=2, lanczos_steps=20, seed=0,
-                 coarse_tol=1e-2, coarse_maxit=50):
+                 coarse_tol=1e-2, coarse_maxit=50, smoother="jacobi"):
         Ns = np.ascontiguousarray(orders, dtype=np.int32)
         v = np.ascontiguousarray(verts, dtype=np.float64).ravel()
-        self.ptr = lib().orc_pmg_create(ex, ey, ez, len(orders), Ns, bc, v, cheb_degree,
-                                        lanczos_steps, seed, coarse_tol, coarse_maxit)
+        self.ptr = lib().orc_pmg_create2(ex, ey, ez, len(orders), Ns, bc, v, cheb_degree,
+                                         lanczos_steps, seed, coarse_tol, coarse_maxit,
+                                         {"jacobi": 0, "asm": 1}[smoother])
         if not self.ptr:
             raise ValueError("oracle pMG creation failed")
         self.orders = list(orders)
@@ -383,3 +392,28 @@ class Projection:
                                        restart, np.ascontiguousarray(b, dtype=np.float64), x,
                                        tol, maxit, C.byref(it), C.byref(rp), C.byref(r1))
         return x, {"status": st, "iters": it.value, "res_proj": rp.value, "res": r1.value}
+
+
+class ASM:
+    """Overlapping Schwarz preconditioner of a level (orc_asm): local
+    separable problems on elements extended by one layer, solved densely."""
+
+    def __init__(self, level):
+        self.level = level
+        self.ptr = lib().orc_asm_create(level.ptr)
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            lib().orc_asm_destroy(self.ptr)
+            self.ptr = None
+
+    def apply(self, r):
+        z = np.zeros(self.level.nl)
+        lib().orc_asm_apply(self.ptr, np.ascontiguousarray(r, dtype=np.float64), z)
+        return z
+
+    def local_matrix(self, e):
+        n = self.level.N + 3
+        K = np.zeros((n ** 3, n ** 3))
+        lib().orc_asm_local_matrix(self.ptr, int(e), K)
+        return K

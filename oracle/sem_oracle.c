@@ -573,7 +573,23 @@ static double tridiag_max_eig(int m, const double *a, const double *b) {
  * the CG coefficients), with v a splitmix64 field U(-1,1) keyed by global id
  * (continuous), masked, and mean-removed under Neumann.  Returns the
  * estimate; *steps_done receives the number of steps actually taken. */
+static void jacobi_prec(void *ctx, const double *in, double *out) {
+  const orc_level *L = (const orc_level *)ctx;
+  for (int64_t l = 0; l < L->nl; ++l) out[l] = L->dinv[l] * in[l];
+}
+
+static double lanczos_max_m(orc_level *L, int m, uint64_t seed, void (*Mf)(void *, const double *, double *),
+                            void *mctx, int *steps_done);
+
 double orc_level_lanczos_max(orc_level *L, int m, uint64_t seed, int *steps_done) {
+  return lanczos_max_m(L, m, seed, jacobi_prec, L, steps_done);
+}
+
+/* The Lanczos estimate of the largest eigenvalue of M A from the
+ * coefficients of m steps of M-preconditioned CG (M = D^{-1} or the Schwarz
+ * preconditioner). */
+static double lanczos_max_m(orc_level *L, int m, uint64_t seed, void (*Mf)(void *, const double *, double *),
+                            void *mctx, int *steps_done) {
   int64_t n = L->nl;
   double *v = malloc(sizeof(double) * n), *r = malloc(sizeof(double) * n),
          *z = malloc(sizeof(double) * n), *p = malloc(sizeof(double) * n),
@@ -590,7 +606,7 @@ double orc_level_lanczos_max(orc_level *L, int m, uint64_t seed, int *steps_done
     for (int64_t l = 0; l < n; ++l) v[l] -= s / c;
   }
   for (int64_t l = 0; l < n; ++l) r[l] = v[l];
-  for (int64_t l = 0; l < n; ++l) z[l] = L->dinv[l] * r[l];
+  Mf(mctx, r, z);
   for (int64_t l = 0; l < n; ++l) p[l] = z[l];
   double rho = orc_level_dot(L, r, z), rho_start = rho;
   int k = 0;
@@ -599,7 +615,7 @@ double orc_level_lanczos_max(orc_level *L, int m, uint64_t seed, int *steps_done
     double pw = orc_level_dot(L, p, w);
     double alpha = rho / pw;
     for (int64_t l = 0; l < n; ++l) r[l] -= alpha * w[l];
-    for (int64_t l = 0; l < n; ++l) z[l] = L->dinv[l] * r[l];
+    Mf(mctx, r, z);
     double rho1 = orc_level_dot(L, r, z);
     double beta = rho1 / rho;
     alph[k] = alpha;
@@ -621,11 +637,269 @@ double orc_level_lanczos_max(orc_level *L, int m, uint64_t seed, int *steps_done
 }
 
 /* ------------------------------------------------------------------ */
+/* Overlapping Schwarz smoother with separable local problems (Sec. 3,  */
+/* Eq. 3: local Poisson problems on elements extended by one layer into */
+/* their neighbours, solved by fast diagonalisation)                     */
+/* ------------------------------------------------------------------ */
+/* Reading (the paper gives the structure, not the construction):
+ * - The extended element has n = N + 3 points per direction: the element's
+ *   own GLL points plus, on each side with a neighbour, the neighbour's
+ *   second point from the shared face.  Beyond them the local problem is
+ *   homogeneous Dirichlet.
+ * - The local operator is separable, K = Bz x By x Ax + Bz x Ay x Bx +
+ *   Az x By x Bx, with the 1D matrices of each direction taken from the 1D
+ *   SEM stiffness (2/h) sum_q w_q D_qi D_qj and mass (h/2) w_i assembled over
+ *   the neighbour, the element and the other neighbour, each with its own
+ *   mean length h along that direction (the mean of the element's four edges
+ *   in that direction), restricted to the extended points.  Without a
+ *   neighbour the extension point is decoupled (a row and column of the
+ *   identity in A and B); a Dirichlet boundary face decouples the face
+ *   points too.
+ * - Only face data enter (the paper exchanges faces, not edges or
+ *   corners): extended points outside the element in two or three
+ *   directions are not part of the local problem's data (they are zero on
+ *   input and discarded on output).
+ * - Additive combination: z = mask * sum_e R_e^T K_e^{-1} R_e r on unique
+ *   nodes.  The oracle solves each K_e densely (Cholesky, factor computed at
+ *   setup): the plain definition of what the fast diagonalisation computes. */
+typedef struct orc_asm {
+  orc_level *L;
+  int n;
+  double *h;     /* [E][3] */
+  double *chol;  /* [E][n^3][n^3] lower Cholesky factors */
+} orc_asm;
+
+static void elem_lengths(const orc_level *L, double *h) {
+  int Np = L->N + 1, Np3 = Np * Np * Np, N = L->N;
+  for (int64_t e = 0; e < L->E; ++e) {
+    const double *X = L->X + e * 3 * Np3;
+    for (int d = 0; d < 3; ++d) {
+      double s = 0.0;
+      for (int q = 0; q < 4; ++q) {
+        int c0[3] = {0, 0, 0};
+        int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+        c0[o1] = (q & 1) ? N : 0;
+        c0[o2] = (q & 2) ? N : 0;
+        int c1[3] = {c0[0], c0[1], c0[2]};
+        c1[d] = N;
+        int p0 = c0[0] + Np * (c0[1] + Np * c0[2]), p1 = c1[0] + Np * (c1[1] + Np * c1[2]);
+        double len2 = 0.0;
+        for (int m = 0; m < 3; ++m) {
+          double dx = X[m * Np3 + p1] - X[m * Np3 + p0];
+          len2 += dx * dx;
+        }
+        s += sqrt(len2);
+      }
+      h[e * 3 + d] = 0.25 * s;
+    }
+  }
+}
+
+/* element position along direction d and the element stride in d */
+static void elem_pos(const orc_level *L, int64_t e, int d, int *pos, int *cnt, int64_t *stride) {
+  int ix = (int)(e % L->ex), iy = (int)((e / L->ex) % L->ey), iz = (int)(e / ((int64_t)L->ex * L->ey));
+  if (d == 0) { *pos = ix; *cnt = L->ex; *stride = 1; }
+  else if (d == 1) { *pos = iy; *cnt = L->ey; *stride = L->ex; }
+  else { *pos = iz; *cnt = L->ez; *stride = (int64_t)L->ex * L->ey; }
+}
+
+/* 1D extended stiffness A and mass B (n x n, row-major) of element e along d */
+void orc_asm_1d(const orc_level *L, const double *h, int64_t e, int d, double *A, double *B) {
+  int N = L->N, Np = N + 1, n = N + 3;
+  double *Ar = malloc(sizeof(double) * Np * Np);
+  for (int i = 0; i < Np; ++i)
+    for (int j = 0; j < Np; ++j) {
+      double s = 0.0;
+      for (int q = 0; q < Np; ++q) s += L->w[q] * L->D[q * Np + i] * L->D[q * Np + j];
+      Ar[i * Np + j] = s;
+    }
+  for (int q = 0; q < n * n; ++q) { A[q] = 0.0; B[q] = 0.0; }
+  int pos, cnt;
+  int64_t stride;
+  elem_pos(L, e, d, &pos, &cnt, &stride);
+  double he = h[e * 3 + d];
+  for (int i = 0; i < Np; ++i) {
+    for (int j = 0; j < Np; ++j) A[(i + 1) * n + (j + 1)] += (2.0 / he) * Ar[i * Np + j];
+    B[(i + 1) * n + (i + 1)] += 0.5 * he * L->w[i];
+  }
+  if (pos > 0) {  /* left neighbour: its points N-1, N are extended points 0, 1 */
+    double hl = h[(e - stride) * 3 + d];
+    int li[2] = {N - 1, N}, ai[2] = {0, 1};
+    for (int p = 0; p < 2; ++p) {
+      for (int q = 0; q < 2; ++q) A[ai[p] * n + ai[q]] += (2.0 / hl) * Ar[li[p] * Np + li[q]];
+      B[ai[p] * n + ai[p]] += 0.5 * hl * L->w[li[p]];
+    }
+  }
+  if (pos < cnt - 1) {  /* right neighbour: its points 0, 1 are extended points N+1, N+2 */
+    double hr = h[(e + stride) * 3 + d];
+    int li[2] = {0, 1}, ai[2] = {N + 1, N + 2};
+    for (int p = 0; p < 2; ++p) {
+      for (int q = 0; q < 2; ++q) A[ai[p] * n + ai[q]] += (2.0 / hr) * Ar[li[p] * Np + li[q]];
+      B[ai[p] * n + ai[p]] += 0.5 * hr * L->w[li[p]];
+    }
+  }
+  /* decoupled points: missing extensions, and Dirichlet boundary faces */
+  int dec[4], nd = 0;
+  if (pos == 0) { dec[nd++] = 0; if (L->bc == 0) dec[nd++] = 1; }
+  if (pos == cnt - 1) { dec[nd++] = N + 2; if (L->bc == 0) dec[nd++] = N + 1; }
+  for (int t = 0; t < nd; ++t) {
+    int a = dec[t];
+    for (int q = 0; q < n; ++q) { A[a * n + q] = 0.0; A[q * n + a] = 0.0; B[a * n + q] = 0.0; B[q * n + a] = 0.0; }
+    A[a * n + a] = 1.0;
+    B[a * n + a] = 1.0;
+  }
+  free(Ar);
+}
+
+/* dense local operator K (n^3 x n^3) of element e, index a + n (b + n c) */
+void orc_asm_local_matrix(const orc_asm *M, int64_t e, double *K) {
+  int n = M->n, n3 = n * n * n;
+  double *A[3], *B[3];
+  for (int d = 0; d < 3; ++d) {
+    A[d] = malloc(sizeof(double) * n * n);
+    B[d] = malloc(sizeof(double) * n * n);
+    orc_asm_1d(M->L, M->h, e, d, A[d], B[d]);
+  }
+  for (int p = 0; p < n3; ++p) {
+    int a = p % n, b = (p / n) % n, c = p / (n * n);
+    for (int q = 0; q < n3; ++q) {
+      int a2 = q % n, b2 = (q / n) % n, c2 = q / (n * n);
+      K[(size_t)p * n3 + q] = B[2][c * n + c2] * B[1][b * n + b2] * A[0][a * n + a2] +
+                              B[2][c * n + c2] * A[1][b * n + b2] * B[0][a * n + a2] +
+                              A[2][c * n + c2] * B[1][b * n + b2] * B[0][a * n + a2];
+    }
+  }
+  for (int d = 0; d < 3; ++d) { free(A[d]); free(B[d]); }
+}
+
+orc_asm *orc_asm_create(orc_level *L) {
+  orc_asm *M = calloc(1, sizeof(orc_asm));
+  M->L = L;
+  M->n = L->N + 3;
+  int n3 = M->n * M->n * M->n;
+  M->h = malloc(sizeof(double) * L->E * 3);
+  elem_lengths(L, M->h);
+  M->chol = malloc(sizeof(double) * (size_t)L->E * n3 * n3);
+  for (int64_t e = 0; e < L->E; ++e) {
+    double *K = M->chol + (size_t)e * n3 * n3;
+    orc_asm_local_matrix(M, e, K);
+    /* Cholesky K = C C^T in the lower triangle */
+    for (int j = 0; j < n3; ++j) {
+      double s = K[(size_t)j * n3 + j];
+      for (int k = 0; k < j; ++k) s -= K[(size_t)j * n3 + k] * K[(size_t)j * n3 + k];
+      double cj = sqrt(s);
+      K[(size_t)j * n3 + j] = cj;
+      for (int i = j + 1; i < n3; ++i) {
+        double t = K[(size_t)i * n3 + j];
+        for (int k = 0; k < j; ++k) t -= K[(size_t)i * n3 + k] * K[(size_t)j * n3 + k];
+        K[(size_t)i * n3 + j] = t / cj;
+      }
+    }
+  }
+  return M;
+}
+
+void orc_asm_destroy(orc_asm *M) {
+  if (!M) return;
+  free(M->h); free(M->chol); free(M);
+}
+
+/* local index of extended point (a, b, c) of element e, or -1 if it carries
+ * no face data (outside the element in two or more directions, or beyond a
+ * side without a neighbour) */
+static int64_t ext_point(const orc_level *L, int64_t e, int a, int b, int c) {
+  int N = L->N, Np = N + 1, Np3 = Np * Np * Np;
+  int idx[3] = {a - 1, b - 1, c - 1};
+  int out = -1, nout = 0;
+  for (int d = 0; d < 3; ++d)
+    if (idx[d] < 0 || idx[d] > N) { out = d; ++nout; }
+  if (nout == 0) return e * Np3 + idx[0] + Np * (idx[1] + Np * idx[2]);
+  if (nout > 1) return -1;
+  int pos, cnt;
+  int64_t stride;
+  elem_pos(L, e, out, &pos, &cnt, &stride);
+  if (idx[out] < 0) {
+    if (pos == 0) return -1;
+    idx[out] = N - 1;
+    return (e - stride) * Np3 + idx[0] + Np * (idx[1] + Np * idx[2]);
+  }
+  if (pos == cnt - 1) return -1;
+  idx[out] = 1;
+  return (e + stride) * Np3 + idx[0] + Np * (idx[1] + Np * idx[2]);
+}
+
+/* z = mask * sum_e R_e^T K_e^{-1} R_e r (r, z continuous E-layout vectors) */
+void orc_asm_apply(const orc_asm *M, const double *r, double *z) {
+  const orc_level *L = M->L;
+  int n = M->n, n3 = n * n * n;
+  double *acc = calloc(L->ng, sizeof(double));
+  double *u = malloc(sizeof(double) * n3);
+  int64_t *loc = malloc(sizeof(int64_t) * n3);
+  for (int64_t e = 0; e < L->E; ++e) {
+    for (int p = 0; p < n3; ++p) {
+      loc[p] = ext_point(L, e, p % n, (p / n) % n, p / (n * n));
+      u[p] = loc[p] >= 0 ? r[loc[p]] : 0.0;
+    }
+    const double *C = M->chol + (size_t)e * n3 * n3;
+    for (int i = 0; i < n3; ++i) {  /* C y = u */
+      double s = u[i];
+      for (int k = 0; k < i; ++k) s -= C[(size_t)i * n3 + k] * u[k];
+      u[i] = s / C[(size_t)i * n3 + i];
+    }
+    for (int i = n3 - 1; i >= 0; --i) {  /* C^T v = y */
+      double s = u[i];
+      for (int k = i + 1; k < n3; ++k) s -= C[(size_t)k * n3 + i] * u[k];
+      u[i] = s / C[(size_t)i * n3 + i];
+    }
+    for (int p = 0; p < n3; ++p)
+      if (loc[p] >= 0) acc[L->ids[loc[p]]] += u[p];
+  }
+  for (int64_t l = 0; l < L->nl; ++l) z[l] = acc[L->ids[l]] * L->mask[l];
+  free(acc); free(u); free(loc);
+}
+
+/* Chebyshev smoothing (Saad Alg. 12.1) with a general preconditioner M in
+ * place of the Jacobi diagonal: the same recurrence on M A. */
+typedef void (*orc_prec_fn)(void *ctx, const double *in, double *out);
+void orc_cheb_m(int64_t n, orc_apply_fn A, void *actx, orc_prec_fn Mf, void *mctx,
+                const double *b, double *x, int k, double lmin, double lmax, int x_zero) {
+  double *r = malloc(sizeof(double) * n), *d = malloc(sizeof(double) * n),
+         *ad = malloc(sizeof(double) * n), *mr = malloc(sizeof(double) * n);
+  double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  double sigma = theta / delta, rho = 1.0 / sigma;
+  if (x_zero) {
+    for (int64_t l = 0; l < n; ++l) { x[l] = 0.0; r[l] = b[l]; }
+  } else {
+    A(actx, x, ad);
+    for (int64_t l = 0; l < n; ++l) r[l] = b[l] - ad[l];
+  }
+  Mf(mctx, r, mr);
+  for (int64_t l = 0; l < n; ++l) d[l] = mr[l] / theta;
+  for (int it = 1; it <= k; ++it) {
+    for (int64_t l = 0; l < n; ++l) x[l] += d[l];
+    if (it == k) break;
+    A(actx, d, ad);
+    for (int64_t l = 0; l < n; ++l) r[l] -= ad[l];
+    double rho1 = 1.0 / (2.0 * sigma - rho);
+    Mf(mctx, r, mr);
+    for (int64_t l = 0; l < n; ++l) d[l] = rho1 * rho * d[l] + (2.0 * rho1 / delta) * mr[l];
+    rho = rho1;
+  }
+  free(r); free(d); free(ad); free(mr);
+}
+
+static void asm_prec(void *ctx, const double *in, double *out) {
+  orc_asm_apply((const orc_asm *)ctx, in, out);
+}
+
+/* ------------------------------------------------------------------ */
 /* p-multigrid V-cycle (Sec. 3, pMG paragraph) and FlexCG               */
 /* ------------------------------------------------------------------ */
 
 typedef struct orc_pmg {
   int nlev, cheb_degree, coarse_maxit;
+  int smoother;          /* 0 Chebyshev-Jacobi, 1 Chebyshev-Schwarz */
+  orc_asm *asmp[8];
   double coarse_tol;
   orc_level *lev[8];
   double *J[8]; /* J[l]: (N_l+1) x (N_{l+1}+1), coarse level l+1 to fine level l */
@@ -638,6 +912,7 @@ void orc_pmg_destroy(orc_pmg *P) {
   for (int l = 0; l < P->nlev; ++l) {
     orc_level_destroy(P->lev[l]);
     free(P->J[l]); free(P->x[l]); free(P->b[l]); free(P->r[l]);
+    orc_asm_destroy(P->asmp[l]);
   }
   free(P);
 }
@@ -647,12 +922,27 @@ void orc_pmg_destroy(orc_pmg *P) {
  * geometry is rediscretised exactly at each order.  Chebyshev bounds per
  * smoothed level: lambda_hi = 1.1 * estimate (m Lanczos steps),
  * lambda_lo = lambda_hi / 10 (reading; the paper gives no bounds). */
+orc_pmg *orc_pmg_create2(int ex, int ey, int ez, int nlev, const int *Ns, int bc,
+                         const double *verts, int cheb_degree, int lanczos_steps, uint64_t seed,
+                         double coarse_tol, int coarse_maxit, int smoother);
+
 orc_pmg *orc_pmg_create(int ex, int ey, int ez, int nlev, const int *Ns, int bc,
                         const double *verts, int cheb_degree, int lanczos_steps, uint64_t seed,
                         double coarse_tol, int coarse_maxit) {
+  return orc_pmg_create2(ex, ey, ez, nlev, Ns, bc, verts, cheb_degree, lanczos_steps, seed,
+                         coarse_tol, coarse_maxit, 0);
+}
+
+/* smoother 1: Chebyshev acceleration of the overlapping Schwarz preconditioner
+ * (orc_asm) on every smoothed level, interval from the Lanczos estimate of
+ * lambda_max(M A) with the same rule. */
+orc_pmg *orc_pmg_create2(int ex, int ey, int ez, int nlev, const int *Ns, int bc,
+                         const double *verts, int cheb_degree, int lanczos_steps, uint64_t seed,
+                         double coarse_tol, int coarse_maxit, int smoother) {
   if (nlev < 1 || nlev > 8) return NULL;
   orc_pmg *P = calloc(1, sizeof(orc_pmg));
   P->nlev = nlev;
+  P->smoother = smoother;
   P->cheb_degree = cheb_degree;
   P->coarse_tol = coarse_tol;
   P->coarse_maxit = coarse_maxit;
@@ -669,7 +959,13 @@ orc_pmg *orc_pmg_create(int ex, int ey, int ez, int nlev, const int *Ns, int bc,
     P->J[l] = malloc(sizeof(double) * (F->N + 1) * (C->N + 1));
     orc_interp(F->N, F->xi, C->N, C->xi, P->J[l]);
     int steps;
-    double est = orc_level_lanczos_max(F, lanczos_steps, seed, &steps);
+    double est;
+    if (smoother == 1) {
+      P->asmp[l] = orc_asm_create(F);
+      est = lanczos_max_m(F, lanczos_steps, seed, asm_prec, P->asmp[l], &steps);
+    } else {
+      est = orc_level_lanczos_max(F, lanczos_steps, seed, &steps);
+    }
     F->lam_hi = 1.1 * est;
     F->lam_lo = F->lam_hi / 10.0;
   }
@@ -730,7 +1026,11 @@ static void vcycle(orc_pmg *P, int l) {
   }
   orc_level *C = P->lev[l + 1];
   /* pre-smoothing from zero */
-  orc_cheb(n, level_apply, L, L->dinv, b, x, P->cheb_degree, L->lam_lo, L->lam_hi, 1);
+  if (P->smoother == 1)
+    orc_cheb_m(n, level_apply, L, asm_prec, P->asmp[l], b, x, P->cheb_degree, L->lam_lo,
+               L->lam_hi, 1);
+  else
+    orc_cheb(n, level_apply, L, L->dinv, b, x, P->cheb_degree, L->lam_lo, L->lam_hi, 1);
   /* residual */
   orc_level_ax(L, x, r);
   for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
@@ -745,7 +1045,11 @@ static void vcycle(orc_pmg *P, int l) {
   orc_interp3(L->E, L->N + 1, C->N + 1, P->J[l], P->x[l + 1], r, 0);
   for (int64_t i = 0; i < n; ++i) x[i] += r[i];
   /* post-smoothing */
-  orc_cheb(n, level_apply, L, L->dinv, b, x, P->cheb_degree, L->lam_lo, L->lam_hi, 0);
+  if (P->smoother == 1)
+    orc_cheb_m(n, level_apply, L, asm_prec, P->asmp[l], b, x, P->cheb_degree, L->lam_lo,
+               L->lam_hi, 0);
+  else
+    orc_cheb(n, level_apply, L, L->dinv, b, x, P->cheb_degree, L->lam_lo, L->lam_hi, 0);
 }
 
 /* One V-cycle z = M(r) on the finest level. */
