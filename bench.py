@@ -92,6 +92,9 @@ def parse_args():
     p.add_argument("--solver", default="flexcg", choices=["flexcg", "fgmres"],
                    help="outer FP64 solver (FGMRES: flexible GMRES, classical Gram-Schmidt)")
     p.add_argument("--restart", type=int, default=20, help="FGMRES vectors per cycle")
+    p.add_argument("--schwarz", action="store_true",
+                   help="Chebyshev-accelerated overlapping Schwarz smoother (FDM local solves) "
+                        "instead of Chebyshev-Jacobi")
     p.add_argument("--smoother", default=SMOOTHER, choices=["f64", "f32", "f16", "bf16"],
                    help="arithmetic/storage of the smoothed pMG levels")
     p.add_argument("--coarse-mode", type=int, default=COARSE_MODE,
@@ -456,7 +459,8 @@ def main():
     mesh = sem.Mesh(side, side, side, ORDER, sem.SEM_NEUMANN, sem.SEM_GEOM_STORED, verts=verts)
     pmg = sem.Pmg(mesh, orders=(7, 3, 1), cheb_degree=args.cheb_degree, lanczos_steps=20, seed=0,
                   smoother_dtype=SMOOTHER_DTYPES[args.smoother], coarse_tol=args.coarse_tol,
-                  coarse_maxit=args.coarse_maxit, coarse_mode=args.coarse_mode)
+                  coarse_maxit=args.coarse_maxit, coarse_mode=args.coarse_mode,
+                  smoother=sem.SEM_SMOOTH_ASM if args.schwarz else sem.SEM_SMOOTH_JACOBI)
     b = rhs_on_device(sem, torch, mesh, dev)
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
@@ -560,6 +564,7 @@ def main():
             "dtype": "f64+" + args.smoother, "data": "synthetic",
             "config": {"workload": WORKLOAD, "E": side ** 3, "N": ORDER, "n_local": nl,
                        "solver": args.solver, "smoother": args.smoother,
+                       "smoothing": "chebyshev-schwarz" if args.schwarz else "chebyshev-jacobi",
                        "cheb_degree": args.cheb_degree, "coarse_tol": args.coarse_tol,
                        "coarse_maxit": args.coarse_maxit, "coarse_mode": args.coarse_mode,
                        "n_global": ng, "parallelism": "replicas" if world > 1 else "single",

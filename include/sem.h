@@ -174,7 +174,17 @@ typedef struct {
   double coarse_tol;        /* coarsest level: FP64 Jacobi-PCG relative tol */
   int32_t coarse_maxit;     /* ... and iteration cap (tol <= 0: exactly maxit) */
   int32_t coarse_mode;      /* SEM_COARSE_JACOBI or SEM_COARSE_MG (below) */
+  int32_t smoother;         /* SEM_SMOOTH_JACOBI or SEM_SMOOTH_ASM (below) */
 } sem_pmg_desc;
+
+/* Smoother of the smoothed levels, Chebyshev-accelerated in both cases (Sec. 3).
+ * SEM_SMOOTH_JACOBI: point Jacobi.
+ * SEM_SMOOTH_ASM: overlapping additive Schwarz (Sec. 3, Eq. 3): every element
+ * extended by one point into each face neighbour, a separable local operator
+ * (1D SEM stiffness and mass assembled over the neighbour, the element and the
+ * other neighbour at their mean lengths) inverted by fast diagonalisation,
+ * face data only, contributions summed.  Orders up to N = 9. */
+enum { SEM_SMOOTH_JACOBI = 0, SEM_SMOOTH_ASM = 1 };
 
 /* Coarsest-level solver (the coarsest order must be 1 for SEM_COARSE_MG).
  * SEM_COARSE_JACOBI: FP64 Jacobi-PCG (the default).

@@ -451,7 +451,7 @@ __global__ void ax32_seam_kernel(Topo t, int nseg, int seg_len, float *__restric
   }
 }
 
-// Face planes normal to y (DIR 1) or z (DIR 2): lower copy + upper copy, and
+// Face planes normal to x (DIR 0), y (DIR 1) or z (DIR 2): lower copy + upper copy, and
 // the Dirichlet mask of the box boundary planes of that direction.  One thread
 // per node of each element's lower plane (plus the upper plane of the last
 // layer under Dirichlet).
@@ -469,7 +469,13 @@ __global__ void plane_sum_kernel(Topo t, float *__restrict__ w, int dirichlet) {
     const uint32_t b = r - e * Np;     // second in-plane index: k (y planes) or j (z planes)
     int64_t lo_off, hi_off, stride_e;
     int layer, layers;
-    if (DIR == 1) {
+    if (DIR == 0) {  // in-plane (a, b) = (j, k); rows of the plane are Np apart
+      layer = (int)(e - t.div_ex.div(e) * t.ex);
+      layers = t.ex;
+      lo_off = (int64_t)b * Np2 + (int64_t)a * Np;
+      hi_off = lo_off + N;
+      stride_e = 1;
+    } else if (DIR == 1) {
       const uint32_t ex_e = t.div_ex.div(e);
       layer = (int)(ex_e - t.div_ey.div(ex_e) * t.ey);
       layers = t.ey;
@@ -589,6 +595,25 @@ static void ax32_np(const Level &L, const float *u, float *w, bool assemble, cud
   plane_sum_kernel<1><<<pg, 256, 0, st>>>(t, w, a.dirichlet);
   SEM_CHECK_CUDA(cudaGetLastError());
   plane_sum_kernel<2><<<pg, 256, 0, st>>>(t, w, a.dirichlet);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+// Direct stiffness summation of an FP32 E-layout vector by three plane
+// passes (x, then y, then z faces; every copy receives the same bits) and the
+// Dirichlet mask.
+void launch_planes_assemble(const Level &L, float *w, cudaStream_t st) {
+  const Topo &t = L.t;
+  SEM_REQUIRE((uint64_t)t.E * t.Np * t.Np < (1ull << 32), "mesh too large for the plane passes");
+  TraceScope ts("plane_sum3", t.N, st, 3);
+  const int64_t n = t.E * t.Np * t.Np;
+  const int64_t b = (n + 255) / 256;
+  const int pg = (int)(b < 152 * 16 ? b : 152 * 16);
+  const int dir = t.bc == SEM_DIRICHLET;
+  plane_sum_kernel<0><<<pg, 256, 0, st>>>(t, w, dir);
+  SEM_CHECK_CUDA(cudaGetLastError());
+  plane_sum_kernel<1><<<pg, 256, 0, st>>>(t, w, dir);
+  SEM_CHECK_CUDA(cudaGetLastError());
+  plane_sum_kernel<2><<<pg, 256, 0, st>>>(t, w, dir);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
 

@@ -100,6 +100,28 @@ __global__ void cheb_step4_kernel(int64_t n4, const float4 *__restrict__ w,
   }
 }
 
+// Chebyshev with a general preconditioner M (the Schwarz smoother): the
+// residual update r = b - w (b given) or r -= w, and the direction update
+// d = c1 d + c2 (M r) (c1 = 0: start), x = d (x_zero) or x += d.
+template <typename T>
+__global__ void resid_kernel(int64_t n, const T *__restrict__ b, const T *__restrict__ w,
+                             T *__restrict__ r) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x)
+    r[l] = (b ? b[l] : r[l]) - w[l];
+}
+
+template <typename T>
+__global__ void cheb_m_kernel(int64_t n, const T *__restrict__ mr, T *__restrict__ d,
+                              T *__restrict__ x, T c1, T c2, int start, int x_zero) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const T dl = start ? c2 * mr[l] : c1 * d[l] + c2 * mr[l];
+    d[l] = dl;
+    x[l] = x_zero ? dl : x[l] + dl;
+  }
+}
+
 // ------------------------------------------------------------------ transfers
 struct TransferParams {
   Topo tf;      // fine level
@@ -397,7 +419,8 @@ static double tridiag_lambda_max(const std::vector<double> &a, const std::vector
 // lambda_max(D^-1 A) from the Lanczos tridiagonal of m steps of Jacobi-PCG on
 // A y = v (alpha_j, beta_j give T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
 // T_j,j+1 = sqrt(beta_j)/alpha_j).
-static double lanczos_lambda_max(Level &L, Reducer &R, int m, uint64_t seed, cudaStream_t st) {
+static double lanczos_lambda_max(Level &L, Reducer &R, int m, uint64_t seed, cudaStream_t st,
+                                 const AsmData *asmd = nullptr) {
   const Topo &t = L.t;
   DevBuf<double> v, r, z, p, w, x, sc;
   v.alloc(t.nl); r.alloc(t.nl); z.alloc(t.nl); p.alloc(t.nl); w.alloc(t.nl); x.alloc(t.nl);
@@ -409,8 +432,18 @@ static double lanczos_lambda_max(Level &L, Reducer &R, int m, uint64_t seed, cud
   }
   if (t.bc == SEM_NEUMANN) launch_remove_mean(t, R, v.p, sc.p + 7, st);
   SEM_CHECK_CUDA(cudaMemsetAsync(x.p, 0, t.nl * sizeof(double), st));
-  // slots: 0 bb, 1 rr, 2 rho_a, 3 rho_b, 4 pw
-  launch_cg_start(t, R, v.p, nullptr, L.dinv64.p, r.p, z.p, p.p, sc.p + 0, sc.p + 1, sc.p + 2, st);
+  // slots: 0 bb, 1 rr, 2 rho_a, 3 rho_b, 4 pw.  With the Schwarz preconditioner
+  // z = M r is applied apart and rho = <r, z> taken by a dot.
+  if (asmd) {
+    launch_cg_start(t, R, v.p, nullptr, nullptr, r.p, nullptr, nullptr, sc.p + 0, sc.p + 1,
+                    sc.p + 2, st);
+    launch_asm<double>(*asmd, L, r.p, z.p, st);
+    launch_dot(t, R, r.p, z.p, sc.p + 2, st);
+    launch_convert<double, double>(t.nl, z.p, p.p, st);
+  } else {
+    launch_cg_start(t, R, v.p, nullptr, L.dinv64.p, r.p, z.p, p.p, sc.p + 0, sc.p + 1, sc.p + 2,
+                    st);
+  }
   std::vector<double> alpha, beta;
   double h[8];
   SEM_CHECK_CUDA(cudaMemcpyAsync(h, sc.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -420,8 +453,12 @@ static double lanczos_lambda_max(Level &L, Reducer &R, int m, uint64_t seed, cud
     int cur = 2 + (j & 1), nxt = 2 + ((j + 1) & 1);
     apply_assembled<double>(L, p.p, w.p, st);
     launch_dot(t, R, p.p, w.p, sc.p + 4, st);
-    launch_cg_update(t, R, sc.p + cur, sc.p + 4, p.p, w.p, L.dinv64.p, x.p, r.p, z.p, sc.p + 1,
-                     sc.p + nxt, nullptr, st);
+    launch_cg_update(t, R, sc.p + cur, sc.p + 4, p.p, w.p, asmd ? nullptr : L.dinv64.p, x.p, r.p,
+                     z.p, sc.p + 1, sc.p + nxt, nullptr, st);
+    if (asmd) {
+      launch_asm<double>(*asmd, L, r.p, z.p, st);
+      launch_dot(t, R, r.p, z.p, sc.p + nxt, st);
+    }
     SEM_CHECK_CUDA(cudaMemcpyAsync(h, sc.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
     SEM_CHECK_CUDA(cudaStreamSynchronize(st));
     double pw = h[4], rho1 = h[nxt];
@@ -463,6 +500,8 @@ void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t s
   SEM_REQUIRE(d.smoother_dtype >= SEM_F64 && d.smoother_dtype <= SEM_BF16,
               "smoother_dtype must be SEM_F64, SEM_F32, SEM_F16 or SEM_BF16");
   SEM_REQUIRE(d.coarse_maxit >= 0 && d.coarse_maxit <= 100000, "coarse_maxit out of range");
+  SEM_REQUIRE(d.smoother == SEM_SMOOTH_JACOBI || d.smoother == SEM_SMOOTH_ASM,
+              "unknown smoother %d", d.smoother);
   P->mesh = mesh;
   P->desc = d;
   const Level &F = mesh->fine;
@@ -496,7 +535,15 @@ void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t s
       else Q.v64[v].alloc(n);
     }
     if (!coarsest) {
-      double est = lanczos_lambda_max(*Q.L, P->red, d.lanczos_steps, d.seed, st);
+      if (d.smoother == SEM_SMOOTH_ASM) {
+        SEM_REQUIRE(Q.L->t.N <= 9, "the Schwarz smoother supports orders up to 9");
+        Q.asmd.reset(new AsmData());
+        asm_setup(*Q.asmd, *Q.L, Q.dtype == SEM_F32, st);
+        if (Q.dtype == SEM_F32) Q.asmd->mr32.alloc(n);
+        else Q.asmd->mr64.alloc(n);
+      }
+      double est = lanczos_lambda_max(*Q.L, P->red, d.lanczos_steps, d.seed, st,
+                                      Q.asmd.get());
       Q.lam_hi = 1.1 * est;
       Q.lam_lo = Q.lam_hi / 10.0;
       Q.J.resize((size_t)(d.orders[l] + 1) * (d.orders[l + 1] + 1));
@@ -534,10 +581,63 @@ static void level_apply(const PmgLevel &Q, const T *u, T *w, cudaStream_t st) {
   apply_assembled<T>(*Q.L, u, w, st);
 }
 
+// Chebyshev-accelerated Schwarz smoothing (Saad Alg. 12.1 with M in place
+// of the Jacobi diagonal; the interval comes from the Lanczos estimate of
+// lambda_max(M A)).
+template <typename T>
+static void smooth_asm(sem_pmg *P, int l, bool x_zero, cudaStream_t st) {
+  PmgLevel &Q = (*P->levp[l]);
+  const Level &L = *Q.L;
+  const int64_t n = L.t.nl;
+  T *b = vec_of<T>(Q, 0), *x = vec_of<T>(Q, 1), *r = vec_of<T>(Q, 2), *d = vec_of<T>(Q, 3),
+    *w = vec_of<T>(Q, 4);
+  T *mr;
+  if constexpr (sizeof(T) == 8) mr = Q.asmd->mr64.p;
+  else mr = Q.asmd->mr32.p;
+  const double theta = 0.5 * (Q.lam_hi + Q.lam_lo), delta = 0.5 * (Q.lam_hi - Q.lam_lo);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  const char *nm = sizeof(T) == 8 ? "cheb_m_f64" : "cheb_m_f32";
+  if (x_zero) {
+    launch_convert<T, T>(n, b, r, st);
+  } else {
+    level_apply<T>(Q, x, w, st);
+    TraceScope ts(nm, L.t.N, st);
+    resid_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(n, b, w, r);
+    SEM_CHECK_CUDA(cudaGetLastError());
+  }
+  launch_asm<T>(*Q.asmd, L, r, mr, st);
+  {
+    TraceScope ts(nm, L.t.N, st);
+    cheb_m_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(n, mr, d, x, (T)0, (T)(1.0 / theta), 1,
+                                                          x_zero);
+    SEM_CHECK_CUDA(cudaGetLastError());
+  }
+  for (int it = 2; it <= P->desc.cheb_degree; ++it) {
+    level_apply<T>(Q, d, w, st);
+    {
+      TraceScope ts(nm, L.t.N, st);
+      resid_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(n, nullptr, w, r);
+      SEM_CHECK_CUDA(cudaGetLastError());
+    }
+    launch_asm<T>(*Q.asmd, L, r, mr, st);
+    const double rho1 = 1.0 / (2.0 * sigma - rho);
+    TraceScope ts(nm, L.t.N, st);
+    cheb_m_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(n, mr, d, x, (T)(rho1 * rho),
+                                                          (T)(2.0 * rho1 / delta), 0, 0);
+    SEM_CHECK_CUDA(cudaGetLastError());
+    rho = rho1;
+  }
+}
+
 template <typename T>
 static void smooth(sem_pmg *P, int l, bool x_zero, cudaStream_t st) {
   PmgLevel &Q = (*P->levp[l]);
   const Level &L = *Q.L;
+  if (Q.asmd) {
+    smooth_asm<T>(P, l, x_zero, st);
+    return;
+  }
   const int64_t n = L.t.nl;
   T *b = vec_of<T>(Q, 0), *x = vec_of<T>(Q, 1), *r = vec_of<T>(Q, 2), *d = vec_of<T>(Q, 3),
     *w = vec_of<T>(Q, 4);

@@ -6,6 +6,7 @@
 
 #include "coarse.cuh"
 #include "common.cuh"
+#include "schwarz.cuh"
 
 namespace sem {
 
@@ -18,6 +19,7 @@ struct PmgLevel {
   DevBuf<double> v64[5];       // b, x, r, d, w in FP64 ...
   DevBuf<float> v32[5];        // ... or FP32
   std::vector<double> J;       // (N_l+1) x (N_{l+1}+1) interpolation to this level
+  std::unique_ptr<AsmData> asmd;  // Schwarz smoother data (SEM_SMOOTH_ASM)
 };
 
 void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t st);

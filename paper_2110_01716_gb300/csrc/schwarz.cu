@@ -1,0 +1,420 @@
+// schwarz.cu -- overlapping Schwarz preconditioner with fast-diagonalisable
+// local problems (Sec. 3, Eq. 3), the second smoother family of the pMG.
+//
+// Each element is extended by one point into each face neighbour (n = N + 3
+// points per direction) and carries a separable local operator
+//   K_e = Bz x By x Ax + Bz x Ay x Bx + Az x By x Bx,
+// whose 1D factors are the 1D SEM stiffness and mass assembled over the
+// neighbour, the element and the other neighbour (each at its mean length
+// along that direction: the mean of its four edges there), restricted to the
+// extended points; without a neighbour the extension point is decoupled, and
+// a Dirichlet boundary face is decoupled too.  With the generalised
+// eigenpairs A S = B S L, S^T B S = I of each direction,
+//   K_e^{-1} = (Sz x Sy x Sx) (I x I x Lx + I x Ly x I + Lz x I x I)^{-1} (Sz x Sy x Sx)^T.
+// The preconditioner is z = mask sum_e R_e^T K_e^{-1} R_e r with face data
+// only (extended points outside the element in two directions carry none).
+//
+// Setup: one thread per (element, direction) builds the 1D pencil and
+// diagonalises B^{-1/2} A B^{-1/2} with the cyclic Jacobi method (Golub and
+// Van Loan, Matrix Computations, Alg. 8.5.3), in FP64.
+// Apply: one CTA holds several extended elements in shared memory; one
+// thread per pencil applies the six 1D contractions (and the diagonal solve)
+// along the pencil's direction.  Own points go to z, the six face layers to a
+// side buffer; a second kernel adds each element's neighbours' layers to its
+// own points, and the copies of shared nodes are then summed.
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "schwarz.cuh"
+#include "trace.cuh"
+
+namespace sem {
+
+constexpr int kMaxExt = kMaxNp + 2;  // points per direction of an extended element
+
+// mean length of element e along d from its 8 vertices ([24] per element,
+// vertex a + 2 b + 4 c)
+__device__ double mean_length(const double *__restrict__ V, int d) {
+  double s = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    int c0[3] = {0, 0, 0};
+    const int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+    c0[o1] = q & 1;
+    c0[o2] = (q >> 1) & 1;
+    int c1[3] = {c0[0], c0[1], c0[2]};
+    c1[d] = 1;
+    const int v0 = c0[0] + 2 * c0[1] + 4 * c0[2], v1 = c1[0] + 2 * c1[1] + 4 * c1[2];
+    double l2 = 0.0;
+    for (int m = 0; m < 3; ++m) {
+      const double dx = V[3 * v1 + m] - V[3 * v0 + m];
+      l2 += dx * dx;
+    }
+    s += sqrt(l2);
+  }
+  return 0.25 * s;
+}
+
+__global__ void asm_setup_kernel(Topo t, Basis bs, const double *__restrict__ verts,
+                                 double *__restrict__ S, double *__restrict__ lam) {
+  const int N = t.N, Np = t.Np, n = N + 3;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < t.E * 3;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = q / 3;
+    const int d = (int)(q - e * 3);
+    const int ix = (int)(e % t.ex), iy = (int)((e / t.ex) % t.ey), iz = (int)(e / ((int64_t)t.ex * t.ey));
+    const int pos = d == 0 ? ix : (d == 1 ? iy : iz);
+    const int cnt = d == 0 ? t.ex : (d == 1 ? t.ey : t.ez);
+    const int64_t stride = d == 0 ? 1 : (d == 1 ? t.ex : (int64_t)t.ex * t.ey);
+    double A[kMaxExt * kMaxExt], Bd[kMaxExt], V[kMaxExt * kMaxExt];
+    for (int k = 0; k < n * n; ++k) A[k] = 0.0;
+    for (int k = 0; k < n; ++k) Bd[k] = 0.0;
+    // 1D reference stiffness sum_q w_q D_qi D_qj, scaled by 2/h; mass (h/2) w_i
+    auto add_elem = [&](double h, int i0, int i1, int a0) {
+      for (int i = i0; i <= i1; ++i) {
+        for (int j = i0; j <= i1; ++j) {
+          double s = 0.0;
+          for (int k = 0; k < Np; ++k) s += bs.w[k] * bs.D[k * Np + i] * bs.D[k * Np + j];
+          A[(a0 + i - i0) * n + (a0 + j - i0)] += (2.0 / h) * s;
+        }
+        Bd[a0 + i - i0] += 0.5 * h * bs.w[i];
+      }
+    };
+    add_elem(mean_length(verts + e * 24, d), 0, N, 1);
+    if (pos > 0) add_elem(mean_length(verts + (e - stride) * 24, d), N - 1, N, 0);
+    if (pos < cnt - 1) add_elem(mean_length(verts + (e + stride) * 24, d), 0, 1, N + 1);
+    int dec[4], nd = 0;
+    if (pos == 0) {
+      dec[nd++] = 0;
+      if (t.bc == SEM_DIRICHLET) dec[nd++] = 1;
+    }
+    if (pos == cnt - 1) {
+      dec[nd++] = N + 2;
+      if (t.bc == SEM_DIRICHLET) dec[nd++] = N + 1;
+    }
+    for (int k = 0; k < nd; ++k) {
+      const int a = dec[k];
+      for (int m = 0; m < n; ++m) A[a * n + m] = A[m * n + a] = 0.0;
+      A[a * n + a] = 1.0;
+      Bd[a] = 1.0;
+    }
+    // C = B^-1/2 A B^-1/2, then cyclic Jacobi: C = V diag V^T
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) A[i * n + j] /= sqrt(Bd[i] * Bd[j]);
+    for (int i = 0; i < n * n; ++i) V[i] = 0.0;
+    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+      double off = 0.0, tot = 0.0;
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+          tot += A[i * n + j] * A[i * n + j];
+          if (i != j) off += A[i * n + j] * A[i * n + j];
+        }
+      if (off <= 1e-30 * tot) break;
+      for (int p = 0; p < n - 1; ++p)
+        for (int r = p + 1; r < n; ++r) {
+          const double apq = A[p * n + r];
+          if (fabs(apq) < 1e-300) continue;
+          const double theta = (A[r * n + r] - A[p * n + p]) / (2.0 * apq);
+          const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
+          const double c = 1.0 / sqrt(1.0 + tt * tt), s = tt * c;
+          for (int k = 0; k < n; ++k) {  // A <- A J (columns p, r)
+            const double akp = A[k * n + p], akr = A[k * n + r];
+            A[k * n + p] = c * akp - s * akr;
+            A[k * n + r] = s * akp + c * akr;
+          }
+          for (int k = 0; k < n; ++k) {  // A <- J^T A (rows p, r)
+            const double apk = A[p * n + k], ark = A[r * n + k];
+            A[p * n + k] = c * apk - s * ark;
+            A[r * n + k] = s * apk + c * ark;
+          }
+          for (int k = 0; k < n; ++k) {  // V <- V J
+            const double vkp = V[k * n + p], vkr = V[k * n + r];
+            V[k * n + p] = c * vkp - s * vkr;
+            V[k * n + r] = s * vkp + c * vkr;
+          }
+        }
+    }
+    // S = B^-1/2 V; store S[point][mode] and the eigenvalues
+    double *So = S + (e * 3 + d) * (int64_t)n * n;
+    double *lo = lam + (e * 3 + d) * (int64_t)n;
+    for (int i = 0; i < n; ++i) {
+      lo[i] = A[i * n + i];
+      for (int m = 0; m < n; ++m) So[i * n + m] = V[i * n + m] / sqrt(Bd[i]);
+    }
+  }
+}
+
+template <typename A, typename B>
+__global__ void asm_convert_kernel(int64_t n, const A *__restrict__ a, B *__restrict__ b) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x)
+    b[l] = (B)a[l];
+}
+
+template <int NP>
+struct AsmShape {
+  static constexpr int n = NP + 2;
+  static constexpr int n2 = n * n;
+  static constexpr int NEL = (256 / n2) < 1 ? 1 : (256 / n2);  // elements per CTA
+  static constexpr int THREADS = NEL * n2;
+  static constexpr int RS = n + 1;                                // padded row stride
+  static constexpr int PS = n * RS;                               // plane stride
+  static constexpr int ES = n * PS;                               // element stride
+};
+
+// Extended element data: local index of extended point (a, b, c) of element
+// (ix, iy, iz), or -1 when it carries no face data.
+__device__ __forceinline__ int64_t ext_source(const Topo &t, int64_t e, int ix, int iy, int iz,
+                                              int a, int b, int c) {
+  const int N = t.N, Np = t.Np;
+  int idx[3] = {a - 1, b - 1, c - 1};
+  int out = -1, nout = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (idx[d] < 0 || idx[d] > N) {
+      out = d;
+      ++nout;
+    }
+  if (nout > 1) return -1;
+  int64_t ee = e;
+  if (nout == 1) {
+    const int pos = out == 0 ? ix : (out == 1 ? iy : iz);
+    const int cnt = out == 0 ? t.ex : (out == 1 ? t.ey : t.ez);
+    const int64_t stride = out == 0 ? 1 : (out == 1 ? t.ex : (int64_t)t.ex * t.ey);
+    if (idx[out] < 0) {
+      if (pos == 0) return -1;
+      idx[out] = N - 1;
+      ee = e - stride;
+    } else {
+      if (pos == cnt - 1) return -1;
+      idx[out] = 1;
+      ee = e + stride;
+    }
+  }
+  return ee * t.Np3 + idx[0] + Np * (idx[1] + Np * idx[2]);
+}
+
+// Local solves of every element: own points of K_e^{-1} R_e r into z, face
+// layers into ext[E][6][Np^2] (0: x-, 1: x+, 2: y-, 3: y+, 4: z-, 5: z+).
+template <typename T, int NP>
+__global__ void __launch_bounds__(AsmShape<NP>::THREADS)
+    asm_solve_kernel(Topo t, const T *__restrict__ S, const T *__restrict__ lam,
+                     const T *__restrict__ r, T *__restrict__ z, T *__restrict__ ext) {
+  using Sh = AsmShape<NP>;
+  constexpr int n = Sh::n, n2 = Sh::n2, NEL = Sh::NEL, RS = Sh::RS, PS = Sh::PS, ES = Sh::ES;
+  constexpr int N = NP - 1;
+  __shared__ T sU[NEL * ES];
+  __shared__ T sS[NEL][3][n * n];
+  __shared__ T sL[NEL][3][n];
+  const int le = threadIdx.x / n2, pq = threadIdx.x - le * n2;
+  const int p = pq % n, q = pq / n;
+  T *U = sU + le * ES;
+  for (int64_t e0 = (int64_t)blockIdx.x * NEL; e0 < t.E; e0 += (int64_t)gridDim.x * NEL) {
+    const int64_t e = e0 + le;
+    const bool active = e < t.E;
+    if (active) {
+      for (int k = pq; k < 3 * n * n; k += n2) sS[le][k / (n * n)][k % (n * n)] = S[e * 3 * n * n + k];
+      for (int k = pq; k < 3 * n; k += n2) sL[le][k / n][k % n] = lam[e * 3 * n + k];
+      const int ix = (int)(e % t.ex), iy = (int)((e / t.ex) % t.ey),
+                iz = (int)(e / ((int64_t)t.ex * t.ey));
+      // gather: thread (b = p, c = q) takes the pencil along a
+#pragma unroll
+      for (int a = 0; a < n; ++a) {
+        const int64_t src = ext_source(t, e, ix, iy, iz, a, p, q);
+        U[q * PS + p * RS + a] = src >= 0 ? r[src] : (T)0;
+      }
+    }
+    __syncthreads();
+    T v[n], o[n];
+    // x: (Sx^T u) along a, thread (b = p, c = q)
+    if (active) {
+#pragma unroll
+      for (int a = 0; a < n; ++a) v[a] = U[q * PS + p * RS + a];
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        T s = 0;
+#pragma unroll
+        for (int a = 0; a < n; ++a) s += sS[le][0][a * n + m] * v[a];
+        U[q * PS + p * RS + m] = s;
+      }
+    }
+    __syncthreads();
+    // y: thread (a = p, c = q)
+    if (active) {
+#pragma unroll
+      for (int b = 0; b < n; ++b) v[b] = U[q * PS + b * RS + p];
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        T s = 0;
+#pragma unroll
+        for (int b = 0; b < n; ++b) s += sS[le][1][b * n + m] * v[b];
+        U[q * PS + m * RS + p] = s;
+      }
+    }
+    __syncthreads();
+    // z, diagonal solve, z back: thread (a = p, b = q)
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < n; ++c) v[c] = U[c * PS + q * RS + p];
+      const T lxy = sL[le][0][p] + sL[le][1][q];
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        T s = 0;
+#pragma unroll
+        for (int c = 0; c < n; ++c) s += sS[le][2][c * n + m] * v[c];
+        o[m] = s / (lxy + sL[le][2][m]);
+      }
+#pragma unroll
+      for (int c = 0; c < n; ++c) {
+        T s = 0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += sS[le][2][c * n + m] * o[m];
+        U[c * PS + q * RS + p] = s;
+      }
+    }
+    __syncthreads();
+    // y back: thread (a = p, c = q)
+    if (active) {
+#pragma unroll
+      for (int m = 0; m < n; ++m) v[m] = U[q * PS + m * RS + p];
+#pragma unroll
+      for (int b = 0; b < n; ++b) {
+        T s = 0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += sS[le][1][b * n + m] * v[m];
+        U[q * PS + b * RS + p] = s;
+      }
+    }
+    __syncthreads();
+    // x back and output: thread (b = p, c = q)
+    if (active) {
+#pragma unroll
+      for (int m = 0; m < n; ++m) v[m] = U[q * PS + p * RS + m];
+      const bool bown = p >= 1 && p <= N + 1, cown = q >= 1 && q <= N + 1;
+      constexpr int NP2 = NP * NP;
+#pragma unroll
+      for (int a = 0; a < n; ++a) {
+        T s = 0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += sS[le][0][a * n + m] * v[m];
+        const bool aown = a >= 1 && a <= N + 1;
+        if (aown && bown && cown) {
+          z[e * t.Np3 + (a - 1) + NP * ((p - 1) + NP * (q - 1))] = s;
+        } else if (!aown && bown && cown) {
+          ext[(e * 6 + (a == 0 ? 0 : 1)) * NP2 + (p - 1) + NP * (q - 1)] = s;
+        } else if (aown && !bown && cown) {
+          ext[(e * 6 + (p == 0 ? 2 : 3)) * NP2 + (a - 1) + NP * (q - 1)] = s;
+        } else if (aown && bown && !cown) {
+          ext[(e * 6 + (q == 0 ? 4 : 5)) * NP2 + (a - 1) + NP * (p - 1)] = s;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// z_e(p) += the face layers of e's neighbours that cover p: a neighbour's x+
+// layer covers e's i = 1 plane, its x- layer e's i = N - 1 plane (and the
+// same in y and z).  Layers of missing neighbours are not read.
+template <typename T>
+__global__ void asm_pull_kernel(Topo t, const T *__restrict__ ext, T *__restrict__ z) {
+  const int N = t.N, Np = t.Np, Np2 = Np * Np;
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
+       l += gridDim.x * blockDim.x) {
+    const PointInfo pi = point_info(l, t);
+    const int64_t e = pi.e;
+    T s = z[l];
+    if (pi.i == 1 && pi.ix > 0) s += ext[((e - 1) * 6 + 1) * Np2 + pi.j + Np * pi.k];
+    if (pi.i == N - 1 && pi.ix < t.ex - 1) s += ext[((e + 1) * 6 + 0) * Np2 + pi.j + Np * pi.k];
+    if (pi.j == 1 && pi.iy > 0) s += ext[((e - t.ex) * 6 + 3) * Np2 + pi.i + Np * pi.k];
+    if (pi.j == N - 1 && pi.iy < t.ey - 1) s += ext[((e + t.ex) * 6 + 2) * Np2 + pi.i + Np * pi.k];
+    const int64_t exy = (int64_t)t.ex * t.ey;
+    if (pi.k == 1 && pi.iz > 0) s += ext[((e - exy) * 6 + 5) * Np2 + pi.i + Np * pi.j];
+    if (pi.k == N - 1 && pi.iz < t.ez - 1) s += ext[((e + exy) * 6 + 4) * Np2 + pi.i + Np * pi.j];
+    z[l] = s;
+  }
+}
+
+void asm_setup(AsmData &A, const Level &L, bool want_f32, cudaStream_t st) {
+  const Topo &t = L.t;
+  SEM_REQUIRE(t.N >= 1 && t.Np + 2 <= kMaxExt, "Schwarz smoother: order %d unsupported", t.N);
+  A.n = t.N + 3;
+  const int64_t ns = t.E * 3 * (int64_t)A.n * A.n, nl = t.E * 3 * (int64_t)A.n;
+  A.S64.alloc(ns);
+  A.lam64.alloc(nl);
+  {
+    TraceScope ts("asm_setup", t.N, st);
+    const int64_t g = (t.E * 3 + 127) / 128;
+    asm_setup_kernel<<<(int)(g < 152 * 16 ? g : 152 * 16), 128, 0, st>>>(t, L.basis, L.verts.p,
+                                                                        A.S64.p, A.lam64.p);
+    SEM_CHECK_CUDA(cudaGetLastError());
+  }
+  const int64_t next = t.E * 6 * (int64_t)t.Np * t.Np;
+  if (want_f32) {
+    A.S32.alloc(ns);
+    A.lam32.alloc(nl);
+    asm_convert_kernel<double, float><<<vec_grid(ns), kVecThreads, 0, st>>>(ns, A.S64.p, A.S32.p);
+    asm_convert_kernel<double, float><<<vec_grid(nl), kVecThreads, 0, st>>>(nl, A.lam64.p, A.lam32.p);
+    SEM_CHECK_CUDA(cudaGetLastError());
+    A.ext32.alloc(next);
+  }
+  A.ext64.alloc(next);
+  SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+template <typename T, int NP>
+static void asm_solve_np(const AsmData &A, const Level &L, const T *r, T *z, T *ext,
+                         cudaStream_t st) {
+  using Sh = AsmShape<NP>;
+  const int64_t g = (L.t.E + Sh::NEL - 1) / Sh::NEL;
+  const T *S, *lam;
+  if constexpr (sizeof(T) == 8) {
+    S = A.S64.p;
+    lam = A.lam64.p;
+  } else {
+    S = A.S32.p;
+    lam = A.lam32.p;
+  }
+  asm_solve_kernel<T, NP><<<(int)(g < 152 * 16 ? g : 152 * 16), Sh::THREADS, 0, st>>>(L.t, S, lam,
+                                                                                       r, z, ext);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_asm(const AsmData &A, const Level &L, const T *r, T *z, cudaStream_t st) {
+  T *ext;
+  if constexpr (sizeof(T) == 8) ext = A.ext64.p;
+  else ext = A.ext32.p;
+  SEM_REQUIRE(ext != nullptr, "Schwarz data of this precision were not built");
+  {
+    TraceScope ts(sizeof(T) == 8 ? "asm_f64" : "asm_f32", L.t.N, st, 2);
+    switch (L.t.Np) {
+      case 2: asm_solve_np<T, 2>(A, L, r, z, ext, st); break;
+      case 3: asm_solve_np<T, 3>(A, L, r, z, ext, st); break;
+      case 4: asm_solve_np<T, 4>(A, L, r, z, ext, st); break;
+      case 5: asm_solve_np<T, 5>(A, L, r, z, ext, st); break;
+      case 6: asm_solve_np<T, 6>(A, L, r, z, ext, st); break;
+      case 7: asm_solve_np<T, 7>(A, L, r, z, ext, st); break;
+      case 8: asm_solve_np<T, 8>(A, L, r, z, ext, st); break;
+      case 9: asm_solve_np<T, 9>(A, L, r, z, ext, st); break;
+      case 10: asm_solve_np<T, 10>(A, L, r, z, ext, st); break;
+      default: fail(SEM_EINVAL, "Schwarz smoother: order %d unsupported", L.t.N);
+    }
+    asm_pull_kernel<T><<<vec_grid(L.t.nl), kVecThreads, 0, st>>>(L.t, ext, z);
+    SEM_CHECK_CUDA(cudaGetLastError());
+  }
+  if constexpr (sizeof(T) == 4) {
+    launch_planes_assemble(L, z, st);
+  } else {
+    launch_gs<double>(L, z, st);
+    launch_mask<double>(L, z, st);
+  }
+}
+
+template void launch_asm<double>(const AsmData &, const Level &, const double *, double *,
+                                 cudaStream_t);
+template void launch_asm<float>(const AsmData &, const Level &, const float *, float *,
+                                cudaStream_t);
+
+}  // namespace sem

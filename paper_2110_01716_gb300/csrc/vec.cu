@@ -254,6 +254,7 @@ void launch_convert(int64_t n, const A *a, B *b, cudaStream_t st) {
 template void launch_convert<double, float>(int64_t, const double *, float *, cudaStream_t);
 template void launch_convert<float, double>(int64_t, const float *, double *, cudaStream_t);
 template void launch_convert<double, double>(int64_t, const double *, double *, cudaStream_t);
+template void launch_convert<float, float>(int64_t, const float *, float *, cudaStream_t);
 
 // Neumann: subtract the unique-dof mean, u -= (sum u/mult) / (sum 1/mult).
 __global__ void sub_mean_kernel(Topo t, const double *__restrict__ sum, double *__restrict__ u) {

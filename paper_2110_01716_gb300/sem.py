@@ -29,6 +29,7 @@ SEM_FIELD_X, SEM_FIELD_Y, SEM_FIELD_Z, SEM_FIELD_MASS, SEM_FIELD_MULT, SEM_FIELD
 SEM_SOLVER_PCG, SEM_SOLVER_FLEXCG, SEM_SOLVER_FGMRES = 0, 1, 2
 SEM_COARSE_JACOBI, SEM_COARSE_MG = 0, 1
 SEM_RHS_HOST, SEM_RHS_MANUFACTURED = 0, 1
+SEM_SMOOTH_JACOBI, SEM_SMOOTH_ASM = 0, 1
 SEM_EAGAIN, SEM_EBUSY = 6, 7
 SEM_MAX_ORDER = 11
 
@@ -57,7 +58,7 @@ class sem_pmg_desc(C.Structure):
     _fields_ = [("nlevels", C.c_int32), ("orders", C.c_int32 * 8), ("cheb_degree", C.c_int32),
                 ("lanczos_steps", C.c_int32), ("seed", C.c_uint64), ("smoother_dtype", C.c_int32),
                 ("coarse_tol", C.c_double), ("coarse_maxit", C.c_int32),
-                ("coarse_mode", C.c_int32)]
+                ("coarse_mode", C.c_int32), ("smoother", C.c_int32)]
 
 
 class sem_solve_desc(C.Structure):
@@ -248,7 +249,7 @@ class Pmg:
 
     def __init__(self, mesh: Mesh, orders=(7, 3, 1), cheb_degree=2, lanczos_steps=20, seed=0,
                  smoother_dtype=SEM_F32, coarse_tol=1e-2, coarse_maxit=50, stream=None,
-                 coarse_mode=SEM_COARSE_JACOBI):
+                 coarse_mode=SEM_COARSE_JACOBI, smoother=SEM_SMOOTH_JACOBI):
         desc = sem_pmg_desc()
         desc.nlevels = len(orders)
         for i, o in enumerate(orders):
@@ -260,6 +261,7 @@ class Pmg:
         desc.coarse_tol = float(coarse_tol)
         desc.coarse_maxit = int(coarse_maxit)
         desc.coarse_mode = int(coarse_mode)
+        desc.smoother = int(smoother)
         h = C.c_void_p()
         check(lib().sem_pmg_setup(mesh.h, C.byref(desc), _stream(stream), C.byref(h)))
         self.h = h

@@ -29,6 +29,12 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_library_has_no_unresolved_symbols(libsem):
+    """Load with immediate binding, as some loaders do: every symbol the
+    library needs (internal template instantiations included) resolves."""
+    C.CDLL(libsem.LIB_PATH, mode=os.RTLD_NOW | os.RTLD_LOCAL)
+
+
 def test_every_declared_symbol_is_exported(libsem):
     L = libsem.lib()
     missing = [n for n in declared_symbols() if not hasattr(L, n)]

@@ -392,3 +392,58 @@ def test_projection_reproduces_a_right_hand_side_in_its_span():
     assert rel(xd.cpu().numpy(), target) <= 1e-8
     with pytest.raises(sem.SemError):
         sem.Projection(m, 32)
+
+
+# ---------------------------------------------------------------- Schwarz smoother
+@pytest.mark.parametrize("bc,orders,e", [(0, (5, 2, 1), (3, 2, 2)), (1, (7, 3, 1), (2, 3, 2)),
+                                         (0, (4, 2), (2, 2, 3)), (1, (3, 1), (4, 3, 2))])
+def test_schwarz_vcycle_fp64_matches_oracle(bc, orders, e):
+    """Chebyshev-Schwarz smoothing in FP64 with a fixed coarse iteration
+    count is a fixed linear map: the GPU (fast diagonalisation) matches the
+    oracle (dense local solves) to 1e-10, and so do the Chebyshev intervals
+    (Lanczos on M A)."""
+    v = inputs.box_vertices(*e, 0.1, 7)
+    m = sem.Mesh(*e, orders[0], bc, verts=v)
+    P = sem.Pmg(m, orders=orders, smoother_dtype=sem.SEM_F64, coarse_tol=0.0, coarse_maxit=12,
+                seed=4, cheb_degree=2, smoother=sem.SEM_SMOOTH_ASM)
+    Po = oracle.PMG(*e, list(orders), bc, v, cheb_degree=2, lanczos_steps=20, seed=4,
+                    coarse_tol=0.0, coarse_maxit=12, smoother="asm")
+    for lvl in range(len(orders) - 1):
+        lo, hi = P.lam(lvl)
+        olo, ohi = Po.lam(lvl)
+        assert abs(hi - ohi) < 1e-10 * ohi and abs(lo - olo) < 1e-10 * olo
+    L = Po.levels[0]
+    r = L.gs(inputs.random_field(L.nl, 8)) * L.mask
+    if bc == 1:
+        r -= L.dot(r, np.ones(L.nl)) / L.ng
+    zd = torch.empty(L.nl, device=DEV, dtype=torch.float64)
+    sem.sem_pmg_vcycle(P, torch.tensor(r, device=DEV), zd)
+    assert rel(zd.cpu().numpy(), Po.vcycle(r)) < 1e-10
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("dtype", [sem.SEM_F64, sem.SEM_F32])
+def test_schwarz_flexcg_reaches_1e8(bc, dtype):
+    e = (3, 3, 2)
+    v = inputs.box_vertices(*e, 0.1, 3)
+    m = sem.Mesh(*e, 7, bc, verts=v)
+    L = oracle.Level(*e, 7, bc, v)
+    b = manufactured(L)[1] if bc == 0 else fourier_rhs(L)
+    its = {}
+    for sm in (sem.SEM_SMOOTH_JACOBI, sem.SEM_SMOOTH_ASM):
+        P = sem.Pmg(m, orders=(7, 3, 1), smoother_dtype=dtype, cheb_degree=3, coarse_tol=1e-2,
+                    coarse_maxit=50, smoother=sm)
+        bd = torch.tensor(b, device=DEV)
+        xd = torch.zeros_like(bd)
+        info = sem.sem_solve(m, P, bd, xd, sem.SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=100)
+        assert info["status"] == sem.SEM_OK, info
+        assert residual(L, b, xd.cpu().numpy()) <= 1.001e-8
+        its[sm] = info["iters"]
+    assert its[sem.SEM_SMOOTH_ASM] < its[sem.SEM_SMOOTH_JACOBI], its
+
+
+def test_schwarz_order_limit():
+    m = sem.Mesh(2, 2, 2, 10, 0)
+    with pytest.raises(sem.SemError) as ex:
+        sem.Pmg(m, orders=(10, 5, 1), smoother=sem.SEM_SMOOTH_ASM)
+    assert ex.value.status == sem.SEM_EINVAL
