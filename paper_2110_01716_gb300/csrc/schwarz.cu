@@ -161,51 +161,60 @@ struct AsmShape {
   static constexpr int RS = n + 1;                                // padded row stride
   static constexpr int PS = n * RS;                               // plane stride
   static constexpr int ES = n * PS;                               // element stride
+  static constexpr int SR = (n + 3) / 4 * 4;                      // S row stride (16-byte rows)
 };
 
-// Extended element data: local index of extended point (a, b, c) of element
-// (ix, iy, iz), or -1 when it carries no face data.
-__device__ __forceinline__ int64_t ext_source(const Topo &t, int64_t e, int ix, int iy, int iz,
-                                              int a, int b, int c) {
-  const int N = t.N, Np = t.Np;
-  int idx[3] = {a - 1, b - 1, c - 1};
-  int out = -1, nout = 0;
+// n values of a padded shared row (16-byte aligned) into registers
+template <typename T, int n>
+__device__ __forceinline__ void load_srow(const T *row, T (&o)[n]) {
+  if constexpr (sizeof(T) == 4) {
 #pragma unroll
-  for (int d = 0; d < 3; ++d)
-    if (idx[d] < 0 || idx[d] > N) {
-      out = d;
-      ++nout;
+    for (int c = 0; c < (n + 3) / 4; ++c) {
+      const float4 v = *reinterpret_cast<const float4 *>(row + 4 * c);
+      if (4 * c + 0 < n) o[4 * c + 0] = v.x;
+      if (4 * c + 1 < n) o[4 * c + 1] = v.y;
+      if (4 * c + 2 < n) o[4 * c + 2] = v.z;
+      if (4 * c + 3 < n) o[4 * c + 3] = v.w;
     }
-  if (nout > 1) return -1;
-  int64_t ee = e;
-  if (nout == 1) {
-    const int pos = out == 0 ? ix : (out == 1 ? iy : iz);
-    const int cnt = out == 0 ? t.ex : (out == 1 ? t.ey : t.ez);
-    const int64_t stride = out == 0 ? 1 : (out == 1 ? t.ex : (int64_t)t.ex * t.ey);
-    if (idx[out] < 0) {
-      if (pos == 0) return -1;
-      idx[out] = N - 1;
-      ee = e - stride;
-    } else {
-      if (pos == cnt - 1) return -1;
-      idx[out] = 1;
-      ee = e + stride;
+  } else {
+#pragma unroll
+    for (int c = 0; c < (n + 1) / 2; ++c) {
+      const double2 v = *reinterpret_cast<const double2 *>(row + 2 * c);
+      if (2 * c + 0 < n) o[2 * c + 0] = v.x;
+      if (2 * c + 1 < n) o[2 * c + 1] = v.y;
     }
   }
-  return ee * t.Np3 + idx[0] + Np * (idx[1] + Np * idx[2]);
+}
+
+// out[m] = sum_a M[m][a] in[a], rows of M padded to SR in shared memory
+template <typename T, int n, int SR>
+__device__ __forceinline__ void pencil_mv(const T *M, const T (&in)[n], T (&out)[n]) {
+#pragma unroll
+  for (int m = 0; m < n; ++m) {
+    T row[n];
+    load_srow<T, n>(M + m * SR, row);
+    T s = 0;
+#pragma unroll
+    for (int a = 0; a < n; ++a) s += row[a] * in[a];
+    out[m] = s;
+  }
 }
 
 // Local solves of every element: own points of K_e^{-1} R_e r into z, face
 // layers into ext[E][6][Np^2] (0: x-, 1: x+, 2: y-, 3: y+, 4: z-, 5: z+).
+// Shared memory per element: the extended data (rows padded against bank
+// conflicts) and S and S^T of the three directions with rows padded to whole
+// 16-byte vectors, so that a pencil thread reads a matrix row per vector load.
 template <typename T, int NP>
 __global__ void __launch_bounds__(AsmShape<NP>::THREADS)
     asm_solve_kernel(Topo t, const T *__restrict__ S, const T *__restrict__ lam,
                      const T *__restrict__ r, T *__restrict__ z, T *__restrict__ ext) {
   using Sh = AsmShape<NP>;
   constexpr int n = Sh::n, n2 = Sh::n2, NEL = Sh::NEL, RS = Sh::RS, PS = Sh::PS, ES = Sh::ES;
-  constexpr int N = NP - 1;
+  constexpr int SR = Sh::SR, N = NP - 1, NP2 = NP * NP;
   __shared__ T sU[NEL * ES];
-  __shared__ T sS[NEL][3][n * n];
+  __shared__ __align__(16) T sS[NEL][3][n * SR];   // S[d]: row a (point), by mode
+  __shared__ __align__(16) T sST[NEL][3][n * SR];  // S[d]^T: row m (mode), by point
   __shared__ T sL[NEL][3][n];
   const int le = threadIdx.x / n2, pq = threadIdx.x - le * n2;
   const int p = pq % n, q = pq / n;
@@ -214,14 +223,41 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS)
     const int64_t e = e0 + le;
     const bool active = e < t.E;
     if (active) {
-      for (int k = pq; k < 3 * n * n; k += n2) sS[le][k / (n * n)][k % (n * n)] = S[e * 3 * n * n + k];
+      for (int k = pq; k < 3 * n * n; k += n2) {
+        const int d = k / (n * n), a = (k / n) % n, m = k % n;
+        const T v = S[e * 3 * n * n + k];
+        sS[le][d][a * SR + m] = v;
+        sST[le][d][m * SR + a] = v;
+      }
       for (int k = pq; k < 3 * n; k += n2) sL[le][k / n][k % n] = lam[e * 3 * n + k];
       const int ix = (int)(e % t.ex), iy = (int)((e / t.ex) % t.ey),
                 iz = (int)(e / ((int64_t)t.ex * t.ey));
-      // gather: thread (b = p, c = q) takes the pencil along a
+      const int64_t exy = (int64_t)t.ex * t.ey;
+      // face neighbours (or -1): x-, x+, y-, y+, z-, z+
+      const int64_t nb[6] = {ix > 0 ? e - 1 : -1, ix < t.ex - 1 ? e + 1 : -1,
+                             iy > 0 ? e - t.ex : -1, iy < t.ey - 1 ? e + t.ex : -1,
+                             iz > 0 ? e - exy : -1, iz < t.ez - 1 ? e + exy : -1};
+      // gather: thread (b = p, c = q) takes the pencil along a; extended
+      // points outside the element in two directions carry no data
+      const int bi = p - 1, ci = q - 1;
+      const bool bown = bi >= 0 && bi <= N, cown = ci >= 0 && ci <= N;
 #pragma unroll
       for (int a = 0; a < n; ++a) {
-        const int64_t src = ext_source(t, e, ix, iy, iz, a, p, q);
+        const int ai = a - 1;
+        const bool aown = ai >= 0 && ai <= N;
+        int64_t src = -1;
+        if (aown && bown && cown) {
+          src = e * t.Np3 + ai + NP * (bi + NP * ci);
+        } else if (!aown && bown && cown) {
+          const int64_t f = nb[ai < 0 ? 0 : 1];
+          if (f >= 0) src = f * t.Np3 + (ai < 0 ? N - 1 : 1) + NP * (bi + NP * ci);
+        } else if (aown && !bown && cown) {
+          const int64_t f = nb[bi < 0 ? 2 : 3];
+          if (f >= 0) src = f * t.Np3 + ai + NP * ((bi < 0 ? N - 1 : 1) + NP * ci);
+        } else if (aown && bown && !cown) {
+          const int64_t f = nb[ci < 0 ? 4 : 5];
+          if (f >= 0) src = f * t.Np3 + ai + NP * (bi + NP * (ci < 0 ? N - 1 : 1));
+        }
         U[q * PS + p * RS + a] = src >= 0 ? r[src] : (T)0;
       }
     }
@@ -231,73 +267,51 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS)
     if (active) {
 #pragma unroll
       for (int a = 0; a < n; ++a) v[a] = U[q * PS + p * RS + a];
+      pencil_mv<T, n, SR>(sST[le][0], v, o);
 #pragma unroll
-      for (int m = 0; m < n; ++m) {
-        T s = 0;
-#pragma unroll
-        for (int a = 0; a < n; ++a) s += sS[le][0][a * n + m] * v[a];
-        U[q * PS + p * RS + m] = s;
-      }
+      for (int m = 0; m < n; ++m) U[q * PS + p * RS + m] = o[m];
     }
     __syncthreads();
     // y: thread (a = p, c = q)
     if (active) {
 #pragma unroll
       for (int b = 0; b < n; ++b) v[b] = U[q * PS + b * RS + p];
+      pencil_mv<T, n, SR>(sST[le][1], v, o);
 #pragma unroll
-      for (int m = 0; m < n; ++m) {
-        T s = 0;
-#pragma unroll
-        for (int b = 0; b < n; ++b) s += sS[le][1][b * n + m] * v[b];
-        U[q * PS + m * RS + p] = s;
-      }
+      for (int m = 0; m < n; ++m) U[q * PS + m * RS + p] = o[m];
     }
     __syncthreads();
     // z, diagonal solve, z back: thread (a = p, b = q)
     if (active) {
 #pragma unroll
       for (int c = 0; c < n; ++c) v[c] = U[c * PS + q * RS + p];
+      pencil_mv<T, n, SR>(sST[le][2], v, o);
       const T lxy = sL[le][0][p] + sL[le][1][q];
 #pragma unroll
-      for (int m = 0; m < n; ++m) {
-        T s = 0;
+      for (int m = 0; m < n; ++m) o[m] = o[m] / (lxy + sL[le][2][m]);
+      pencil_mv<T, n, SR>(sS[le][2], o, v);
 #pragma unroll
-        for (int c = 0; c < n; ++c) s += sS[le][2][c * n + m] * v[c];
-        o[m] = s / (lxy + sL[le][2][m]);
-      }
-#pragma unroll
-      for (int c = 0; c < n; ++c) {
-        T s = 0;
-#pragma unroll
-        for (int m = 0; m < n; ++m) s += sS[le][2][c * n + m] * o[m];
-        U[c * PS + q * RS + p] = s;
-      }
+      for (int c = 0; c < n; ++c) U[c * PS + q * RS + p] = v[c];
     }
     __syncthreads();
     // y back: thread (a = p, c = q)
     if (active) {
 #pragma unroll
       for (int m = 0; m < n; ++m) v[m] = U[q * PS + m * RS + p];
+      pencil_mv<T, n, SR>(sS[le][1], v, o);
 #pragma unroll
-      for (int b = 0; b < n; ++b) {
-        T s = 0;
-#pragma unroll
-        for (int m = 0; m < n; ++m) s += sS[le][1][b * n + m] * v[m];
-        U[q * PS + b * RS + p] = s;
-      }
+      for (int b = 0; b < n; ++b) U[q * PS + b * RS + p] = o[b];
     }
     __syncthreads();
     // x back and output: thread (b = p, c = q)
     if (active) {
 #pragma unroll
       for (int m = 0; m < n; ++m) v[m] = U[q * PS + p * RS + m];
+      pencil_mv<T, n, SR>(sS[le][0], v, o);
       const bool bown = p >= 1 && p <= N + 1, cown = q >= 1 && q <= N + 1;
-      constexpr int NP2 = NP * NP;
 #pragma unroll
       for (int a = 0; a < n; ++a) {
-        T s = 0;
-#pragma unroll
-        for (int m = 0; m < n; ++m) s += sS[le][0][a * n + m] * v[m];
+        const T s = o[a];
         const bool aown = a >= 1 && a <= N + 1;
         if (aown && bown && cown) {
           z[e * t.Np3 + (a - 1) + NP * ((p - 1) + NP * (q - 1))] = s;
