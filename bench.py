@@ -66,8 +66,8 @@ AX_TRAFFIC = {"source_sha256": "ab9460908abee14bcf8f1dbe80d2dc039a0c47229b82a9a9
               "bytes_per_point": 62.66}
 # The same for the smoother's assembled FP32 operator, per factor storage
 # (profiles/ax32_N7.md), valid while ax32.cu is unchanged.
-AX32_TRAFFIC = {"f32": {"source_sha256": "b145c77d79b5cbdd966aee7e10e1998242bf9d71ab90db702d378036cff7083e", "bytes_per_point": 31.41},
-                "f16": {"source_sha256": "b145c77d79b5cbdd966aee7e10e1998242bf9d71ab90db702d378036cff7083e", "bytes_per_point": 18.80}}
+AX32_TRAFFIC = {"f32": {"source_sha256": "96ad60531a1434a15ae2780ab6df1fc9c571104c512dfcfc17cc2c8dbfebbf60", "bytes_per_point": 31.40},
+                "f16": {"source_sha256": "96ad60531a1434a15ae2780ab6df1fc9c571104c512dfcfc17cc2c8dbfebbf60", "bytes_per_point": 18.82}}
 
 
 def parse_args():
