@@ -592,6 +592,7 @@ def main():
         sem.sem_trace_enable(False, "")
         tot = e0.elapsed_time(e1)
         line["breakdown"] = {"solve_ms": tot, "kernel_ms": sum(v["total_ms"] for v in bd.values()),
+                             "coarse_iters_last_vcycle": pmg.coarse_iters(),
                              "classes": {k: [v["launches"], round(v["total_ms"], 3)]
                                          for k, v in sorted(bd.items(),
                                                             key=lambda kv: -kv[1]["total_ms"])}}

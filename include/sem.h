@@ -203,6 +203,9 @@ sem_status sem_pmg_setup(sem_mesh *mesh, const sem_pmg_desc *desc, void *stream,
 sem_status sem_pmg_destroy(sem_pmg *pmg);
 /* Chebyshev interval of level l (HOST outputs). */
 sem_status sem_pmg_info(const sem_pmg *pmg, int32_t level, double *lam_lo, double *lam_hi);
+/* Iterations the coarsest-level solver took in the last V-cycle (HOST
+ * output; synchronises the stream the V-cycle ran on). */
+sem_status sem_pmg_coarse_iters(const sem_pmg *pmg, void *stream, int32_t *iters);
 /* One V-cycle z = M r on the finest level (FP64 E-layout device vectors). */
 sem_status sem_pmg_vcycle(sem_pmg *pmg, const double *r, double *z, void *stream);
 

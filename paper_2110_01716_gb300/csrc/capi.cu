@@ -525,6 +525,19 @@ sem_status sem_pmg_destroy(sem_pmg *pmg) {
   return guarded([&] { delete pmg; });
 }
 
+sem_status sem_pmg_coarse_iters(const sem_pmg *pmg, void *stream, int32_t *iters) {
+  return guarded([&] {
+    SEM_REQUIRE(pmg != nullptr && iters != nullptr, "null argument");
+    *iters = 0;
+    if (!pmg->persistent_coarse || !pmg->coarse.iters.p) return;
+    int v = 0;
+    SEM_CHECK_CUDA(cudaMemcpyAsync(&v, pmg->coarse.iters.p, sizeof(int), cudaMemcpyDeviceToHost,
+                                   as_stream(stream)));
+    SEM_CHECK_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    *iters = v;
+  });
+}
+
 sem_status sem_pmg_info(const sem_pmg *pmg, int32_t level, double *lam_lo, double *lam_hi) {
   return guarded([&] {
     SEM_REQUIRE(pmg != nullptr, "null pmg");

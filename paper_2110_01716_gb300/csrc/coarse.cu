@@ -119,19 +119,26 @@ __device__ __forceinline__ double stencil_apply(const CoarseArgs &A, int64_t g,
   if (A.bc == SEM_DIRICHLET &&
       (gx == 0 || gy == 0 || gz == 0 || gx == A.nx - 1 || gy == A.ny - 1 || gz == A.nz - 1))
     return 0.0;
-  double acc = 0.0;
+  // neighbour tests first, then one guarded load pair per neighbour, so that
+  // all the loads are in flight together
+  const bool in_x[3] = {gx > 0, true, gx < A.nx - 1};
+  const bool in_y[3] = {gy > 0, true, gy < A.ny - 1};
+  const bool in_z[3] = {gz > 0, true, gz < A.nz - 1};
+  double sv[27], vv[27];
 #pragma unroll
   for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
-        const int x = gx + dx, y = gy + dy, z = gz + dz;
-        if (x < 0 || y < 0 || z < 0 || x >= A.nx || y >= A.ny || z >= A.nz) continue;
         const int d = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-        const int64_t nb = g + dx + (int64_t)A.nx * (dy + (int64_t)A.ny * dz);
-        acc = fma(A.S[(int64_t)d * A.ng + g], v[nb], acc);
+        const bool ok = in_x[dx + 1] && in_y[dy + 1] && in_z[dz + 1];
+        sv[d] = ok ? A.S[(int64_t)d * A.ng + g] : 0.0;
+        vv[d] = ok ? v[g + dx + (int64_t)A.nx * (dy + (int64_t)A.ny * dz)] : 0.0;
       }
+  double acc = 0.0;
+#pragma unroll
+  for (int d = 0; d < 27; ++d) acc = fma(sv[d], vv[d], acc);
   return acc;
 }
 

@@ -28,6 +28,7 @@ struct MgLevelDev {
 
 struct MgArgs {
   int nlev;
+  int small_from;  // first level run by one CTA (nlev - 1: the bottom only)
   MgLevelDev L[kMgMaxLevels];
   const double *bottom_inv;
   int nbottom;

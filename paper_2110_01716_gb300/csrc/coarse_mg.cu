@@ -32,7 +32,10 @@ namespace cg = cooperative_groups;
 namespace sem {
 
 constexpr int kMgThreads = 256;
-constexpr int kMgMaxBottom = 128;
+#ifndef SEM_MG_MAX_BOTTOM
+#define SEM_MG_MAX_BOTTOM 128
+#endif
+constexpr int kMgMaxBottom = SEM_MG_MAX_BOTTOM;  // unknowns of the dense bottom level
 
 __device__ __forceinline__ void mg_coords(const MgLevelDev &L, int g, int &gx, int &gy, int &gz) {
   const uint32_t u = (uint32_t)g;
@@ -42,22 +45,31 @@ __device__ __forceinline__ void mg_coords(const MgLevelDev &L, int g, int &gx, i
   gx = (int)(rem - (uint32_t)gy * (uint32_t)L.nx);
 }
 
+// (A v)_g of the 27-point stencil.  The neighbour tests come first and every
+// load is a select on its own test, so the loads of all 27 neighbours are in
+// flight together (a load is issued only for a neighbour inside the lattice).
 __device__ __forceinline__ double mg_apply(const MgLevelDev &L, int g, const double *__restrict__ v) {
   if (!L.keep[g]) return 0.0;
   int gx, gy, gz;
   mg_coords(L, g, gx, gy, gz);
-  double acc = 0.0;
+  const bool in_x[3] = {gx > 0, true, gx < L.nx - 1};
+  const bool in_y[3] = {gy > 0, true, gy < L.ny - 1};
+  const bool in_z[3] = {gz > 0, true, gz < L.nz - 1};
+  double sv[27], vv[27];
 #pragma unroll
   for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
-        const int x = gx + dx, y = gy + dy, z = gz + dz;
-        if (x < 0 || y < 0 || z < 0 || x >= L.nx || y >= L.ny || z >= L.nz) continue;
         const int d = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-        acc = fma(L.S[(int64_t)d * L.n + g], v[g + dx + L.nx * (dy + L.ny * dz)], acc);
+        const bool ok = in_x[dx + 1] && in_y[dy + 1] && in_z[dz + 1];
+        sv[d] = ok ? L.S[(int64_t)d * L.n + g] : 0.0;
+        vv[d] = ok ? v[g + dx + L.nx * (dy + L.ny * dz)] : 0.0;
       }
+  double acc = 0.0;
+#pragma unroll
+  for (int d = 0; d < 27; ++d) acc = fma(sv[d], vv[d], acc);
   return acc;
 }
 
@@ -100,120 +112,194 @@ __device__ void mg_sum(double (&v)[NS], double *part, cg::grid_group &grid) {
   for (int s = 0; s < NS; ++s) v[s] = res[s];
 }
 
+// Barriers of the two execution modes of the V-cycle: the whole grid, or one
+// CTA (the small coarse levels, where a grid barrier would cost more than the
+// work between barriers).
+struct GridBarrier {
+  cg::grid_group *g;
+  __device__ void operator()() const { g->sync(); }
+};
+struct CtaBarrier {
+  __device__ void operator()() const { __syncthreads(); }
+};
+
+// Down the cycle at level l: pre-smoothing from zero (d = Dinv b / theta,
+// x = d, r = b; one more step), residual, restriction to level l + 1.  Every
+// phase maps node g to the same thread, so pointwise dependencies need no
+// barrier; a barrier precedes every phase that reads neighbours or another
+// level.
+template <typename Bar>
+__device__ void mg_down(const MgArgs &A, int l, const double *__restrict__ b0,
+                        double *__restrict__ x0, Bar bar, int tid, int nth) {
+  const MgLevelDev &L = A.L[l];
+  const double *b = l == 0 ? b0 : L.b;
+  double *x = l == 0 ? x0 : L.x;
+  for (int g = tid; g < L.n; g += nth) {
+    const double rg = b[g];
+    L.r[g] = rg;
+    const double d = L.dinv[g] * rg * L.inv_theta;
+    L.da[g] = d;
+    x[g] = d;
+  }
+  bar();
+  for (int g = tid; g < L.n; g += nth) {
+    const double rg = L.r[g] - mg_apply(L, g, L.da);
+    L.r[g] = rg;
+    const double d = L.c1 * L.da[g] + L.c2 * L.dinv[g] * rg;
+    L.db[g] = d;
+    x[g] += d;
+  }
+  bar();
+  for (int g = tid; g < L.n; g += nth) L.r[g] = b[g] - mg_apply(L, g, x);
+  bar();
+  const MgLevelDev &C = A.L[l + 1];
+  for (int G = tid; G < C.n; G += nth) {
+    double acc = 0.0;
+    if (C.keep[G]) {
+      int Gx, Gy, Gz;
+      mg_coords(C, G, Gx, Gy, Gz);
+      // table rows first (index -1: no fine point), then guarded loads
+      int fi[3][3];
+      double fw[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        fi[0][c] = L.ri[0][3 * Gx + c];
+        fi[1][c] = L.ri[1][3 * Gy + c];
+        fi[2][c] = L.ri[2][3 * Gz + c];
+        fw[0][c] = L.rw[0][3 * Gx + c];
+        fw[1][c] = L.rw[1][3 * Gy + c];
+        fw[2][c] = L.rw[2][3 * Gz + c];
+      }
+      double rv[27];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b2 = 0; b2 < 3; ++b2)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const bool ok = fi[2][c] >= 0 && fi[1][b2] >= 0 && fi[0][a] >= 0;
+            rv[a + 3 * (b2 + 3 * c)] = ok ? L.r[fi[0][a] + L.nx * (fi[1][b2] + L.ny * fi[2][c])] : 0.0;
+          }
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b2 = 0; b2 < 3; ++b2) {
+          const double wyz = fw[2][c] * fw[1][b2];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const bool ok = fi[2][c] >= 0 && fi[1][b2] >= 0 && fi[0][a] >= 0;
+            if (ok) acc = fma(wyz * fw[0][a], rv[a + 3 * (b2 + 3 * c)], acc);
+          }
+        }
+    }
+    C.b[G] = acc;
+  }
+  bar();
+}
+
+// The bottom: dense inverse, one row per thread.
+template <typename Bar>
+__device__ void mg_bottom(const MgArgs &A, const double *__restrict__ b0, double *__restrict__ x0,
+                          Bar bar, int tid, int nth) {
+  const MgLevelDev &B = A.L[A.nlev - 1];
+  const double *b = A.nlev == 1 ? b0 : B.b;
+  double *x = A.nlev == 1 ? x0 : B.x;
+  for (int i = tid; i < A.nbottom; i += nth) {
+    double acc = 0.0;
+    for (int j = 0; j < A.nbottom; ++j) acc = fma(A.bottom_inv[(size_t)i * A.nbottom + j], b[j], acc);
+    x[i] = acc;
+  }
+  bar();
+}
+
+// Up the cycle at level l: prolongation and correction from level l + 1,
+// post-smoothing (r = b - A x; d = Dinv r / theta; x += d; one more step).
+template <typename Bar>
+__device__ void mg_up(const MgArgs &A, int l, const double *__restrict__ b0,
+                      double *__restrict__ x0, Bar bar, int tid, int nth) {
+  const MgLevelDev &L = A.L[l];
+  const MgLevelDev &C = A.L[l + 1];
+  const double *b = l == 0 ? b0 : L.b;
+  double *x = l == 0 ? x0 : L.x;
+  for (int g = tid; g < L.n; g += nth) {
+    if (!L.keep[g]) continue;
+    int gx, gy, gz;
+    mg_coords(L, g, gx, gy, gz);
+    int ci[3][2];
+    double cw[3][2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      ci[0][c] = L.pi[0][2 * gx + c];
+      ci[1][c] = L.pi[1][2 * gy + c];
+      ci[2][c] = L.pi[2][2 * gz + c];
+      cw[0][c] = L.pw[0][2 * gx + c];
+      cw[1][c] = L.pw[1][2 * gy + c];
+      cw[2][c] = L.pw[2][2 * gz + c];
+    }
+    double xv[8];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b2 = 0; b2 < 2; ++b2)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const bool ok = ci[2][c] >= 0 && ci[1][b2] >= 0 && ci[0][a] >= 0;
+          xv[a + 2 * (b2 + 2 * c)] = ok ? C.x[ci[0][a] + C.nx * (ci[1][b2] + C.ny * ci[2][c])] : 0.0;
+        }
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b2 = 0; b2 < 2; ++b2) {
+        const double wyz = cw[2][c] * cw[1][b2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const bool ok = ci[2][c] >= 0 && ci[1][b2] >= 0 && ci[0][a] >= 0;
+          if (ok) acc = fma(wyz * cw[0][a], xv[a + 2 * (b2 + 2 * c)], acc);
+        }
+      }
+    x[g] += acc;
+  }
+  bar();
+  for (int g = tid; g < L.n; g += nth) L.r[g] = b[g] - mg_apply(L, g, x);
+  bar();
+  for (int g = tid; g < L.n; g += nth) {
+    const double d = L.dinv[g] * L.r[g] * L.inv_theta;
+    L.da[g] = d;
+    x[g] += d;
+  }
+  bar();
+  for (int g = tid; g < L.n; g += nth) {
+    const double rg = L.r[g] - mg_apply(L, g, L.da);
+    L.r[g] = rg;
+    const double d = L.c1 * L.da[g] + L.c2 * L.dinv[g] * rg;
+    x[g] += d;
+  }
+  bar();
+}
+
 // One V(2,2) cycle: level-0 right-hand side b0, result x0 (both level-0
-// vectors, b0 read only).  Every phase maps node g to the same thread, so
-// pointwise dependencies need no barrier; a barrier precedes every phase
-// that reads neighbours or another level.
+// vectors, b0 read only).  Levels from A.small_from down (and the bottom) run
+// in CTA 0 alone with CTA barriers while the other CTAs wait at one grid
+// barrier.
 __device__ void mg_vcycle(const MgArgs &A, const double *__restrict__ b0, double *__restrict__ x0,
                           cg::grid_group &grid, int tid, int nth) {
-  for (int l = 0; l < A.nlev - 1; ++l) {
-    const MgLevelDev &L = A.L[l];
-    const double *b = l == 0 ? b0 : L.b;
-    double *x = l == 0 ? x0 : L.x;
-    // pre-smoothing from zero: d = Dinv b / theta, x = d, r = b; one more step
-    for (int g = tid; g < L.n; g += nth) {
-      const double rg = b[g];
-      L.r[g] = rg;
-      const double d = L.dinv[g] * rg * L.inv_theta;
-      L.da[g] = d;
-      x[g] = d;
-    }
-    grid.sync();
-    for (int g = tid; g < L.n; g += nth) {
-      const double rg = L.r[g] - mg_apply(L, g, L.da);
-      L.r[g] = rg;
-      const double d = L.c1 * L.da[g] + L.c2 * L.dinv[g] * rg;
-      L.db[g] = d;
-      x[g] += d;
-    }
-    grid.sync();
-    // residual and restriction to the next level
-    for (int g = tid; g < L.n; g += nth) L.r[g] = b[g] - mg_apply(L, g, x);
-    grid.sync();
-    const MgLevelDev &C = A.L[l + 1];
-    for (int G = tid; G < C.n; G += nth) {
-      double acc = 0.0;
-      if (C.keep[G]) {
-        int Gx, Gy, Gz;
-        mg_coords(C, G, Gx, Gy, Gz);
-        for (int c = 0; c < 3; ++c) {
-          const int fz = L.ri[2][3 * Gz + c];
-          if (fz < 0) continue;
-          const double wz = L.rw[2][3 * Gz + c];
-          for (int b2 = 0; b2 < 3; ++b2) {
-            const int fy = L.ri[1][3 * Gy + b2];
-            if (fy < 0) continue;
-            const double wyz = wz * L.rw[1][3 * Gy + b2];
-            for (int a = 0; a < 3; ++a) {
-              const int fx = L.ri[0][3 * Gx + a];
-              if (fx < 0) continue;
-              acc = fma(wyz * L.rw[0][3 * Gx + a], L.r[fx + L.nx * (fy + L.ny * fz)], acc);
-            }
-          }
-        }
-      }
-      C.b[G] = acc;
+  const GridBarrier gb{&grid};
+  const int ls = A.small_from;  // first level handled by CTA 0 (nlev - 1: the bottom only)
+  for (int l = 0; l < ls; ++l) mg_down(A, l, b0, x0, gb, tid, nth);
+  if (ls == A.nlev - 1 && A.nbottom > (int)blockDim.x) {
+    mg_bottom(A, b0, x0, gb, tid, nth);  // a large bottom: rows across the grid
+  } else {
+    if (blockIdx.x == 0) {
+      const CtaBarrier cb;
+      const int t = threadIdx.x, n = blockDim.x;
+      for (int l = ls; l < A.nlev - 1; ++l) mg_down(A, l, b0, x0, cb, t, n);
+      mg_bottom(A, b0, x0, cb, t, n);
+      for (int l = A.nlev - 2; l >= ls; --l) mg_up(A, l, b0, x0, cb, t, n);
     }
     grid.sync();
   }
-  // bottom: dense inverse, one row per thread across the grid
-  {
-    const MgLevelDev &B = A.L[A.nlev - 1];
-    const double *b = A.nlev == 1 ? b0 : B.b;
-    double *x = A.nlev == 1 ? x0 : B.x;
-    for (int i = tid; i < A.nbottom; i += nth) {
-      double acc = 0.0;
-      for (int j = 0; j < A.nbottom; ++j) acc = fma(A.bottom_inv[(size_t)i * A.nbottom + j], b[j], acc);
-      x[i] = acc;
-    }
-    grid.sync();
-  }
-  for (int l = A.nlev - 2; l >= 0; --l) {
-    const MgLevelDev &L = A.L[l];
-    const MgLevelDev &C = A.L[l + 1];
-    const double *b = l == 0 ? b0 : L.b;
-    double *x = l == 0 ? x0 : L.x;
-    // prolongation and correction
-    for (int g = tid; g < L.n; g += nth) {
-      if (!L.keep[g]) continue;
-      int gx, gy, gz;
-      mg_coords(L, g, gx, gy, gz);
-      double acc = 0.0;
-      for (int c = 0; c < 2; ++c) {
-        const int Cz = L.pi[2][2 * gz + c];
-        if (Cz < 0) continue;
-        const double wz = L.pw[2][2 * gz + c];
-        for (int b2 = 0; b2 < 2; ++b2) {
-          const int Cy = L.pi[1][2 * gy + b2];
-          if (Cy < 0) continue;
-          const double wyz = wz * L.pw[1][2 * gy + b2];
-          for (int a = 0; a < 2; ++a) {
-            const int Cx = L.pi[0][2 * gx + a];
-            if (Cx < 0) continue;
-            acc = fma(wyz * L.pw[0][2 * gx + a], C.x[Cx + C.nx * (Cy + C.ny * Cz)], acc);
-          }
-        }
-      }
-      x[g] += acc;
-    }
-    grid.sync();
-    // post-smoothing: r = b - A x; d = Dinv r / theta; x += d; one more step
-    for (int g = tid; g < L.n; g += nth) L.r[g] = b[g] - mg_apply(L, g, x);
-    grid.sync();
-    for (int g = tid; g < L.n; g += nth) {
-      const double d = L.dinv[g] * L.r[g] * L.inv_theta;
-      L.da[g] = d;
-      x[g] += d;
-    }
-    grid.sync();
-    for (int g = tid; g < L.n; g += nth) {
-      const double rg = L.r[g] - mg_apply(L, g, L.da);
-      L.r[g] = rg;
-      const double d = L.c1 * L.da[g] + L.c2 * L.dinv[g] * rg;
-      x[g] += d;
-    }
-    grid.sync();
-  }
+  for (int l = ls - 1; l >= 0; --l) mg_up(A, l, b0, x0, gb, tid, nth);
 }
 
 __global__ void __launch_bounds__(kMgThreads) coarse_mgcg_kernel(MgArgs A) {
@@ -609,6 +695,16 @@ void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st) {
   std::copy(inv.begin(), inv.end(), hd.begin() + od);
   A.bottom_inv = M->dbuf.p + od; od += up(inv.size(), 32);
   A.nbottom = nb;
+#ifndef SEM_MG_SMALL
+#define SEM_MG_SMALL 0
+#endif
+  // levels of at most SEM_MG_SMALL unknowns run in one CTA
+  A.small_from = nlev - 1;
+  for (int l = 0; l < nlev - 1; ++l)
+    if (A.L[l].n <= SEM_MG_SMALL) {
+      A.small_from = l;
+      break;
+    }
   SEM_REQUIRE(od <= dbl && oi <= hi.size() && ok <= keeps, "multigrid buffer layout overflow");
   // guard: every device array of the hierarchy is 256-byte aligned
   auto aligned = [](const void *p) { return ((uintptr_t)p & 255u) == 0; };

@@ -35,7 +35,7 @@ SEM_MAX_ORDER = 11
 
 EXPORTED = ["sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_field", "sem_ax",
             "sem_gs", "sem_dot", "sem_pmg_setup", "sem_pmg_destroy", "sem_pmg_info",
-            "sem_pmg_vcycle", "sem_solve", "sem_solve_host", "sem_trace_enable",
+            "sem_pmg_vcycle", "sem_pmg_coarse_iters", "sem_solve", "sem_solve_host", "sem_trace_enable",
             "sem_trace_read", "sem_dot_noalloc", "sem_proj_create", "sem_proj_destroy",
             "sem_proj_info", "sem_solve_projected", "sem_server_create", "sem_server_destroy",
             "sem_submit", "sem_poll", "sem_server_stats_read", "sem_server_autotune",
@@ -124,6 +124,7 @@ def lib():
     L.sem_pmg_destroy.argtypes = [vp]
     L.sem_pmg_info.argtypes = [vp, i32, C.POINTER(d), C.POINTER(d)]
     L.sem_pmg_vcycle.argtypes = [vp, vp, vp, vp]
+    L.sem_pmg_coarse_iters.argtypes = [vp, vp, C.POINTER(i32)]
     L.sem_solve.argtypes = [vp, vp, vp, vp, C.POINTER(sem_solve_desc), C.POINTER(sem_solve_info),
                             vp]
     L.sem_solve_host.argtypes = L.sem_solve.argtypes
@@ -278,6 +279,12 @@ class Pmg:
             self.close()
         except Exception:
             pass
+
+    def coarse_iters(self, stream=None):
+        """Iterations of the coarsest-level solver in the last V-cycle."""
+        it = C.c_int32()
+        check(lib().sem_pmg_coarse_iters(self.h, _stream(stream), C.byref(it)))
+        return it.value
 
     def lam(self, level):
         lo, hi = C.c_double(), C.c_double()
