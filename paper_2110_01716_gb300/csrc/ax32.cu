@@ -455,8 +455,8 @@ __global__ void ax32_seam_kernel(Topo t, int nseg, int seg_len, float *__restric
 // the Dirichlet mask of the box boundary planes of that direction.  One thread
 // per node of each element's lower plane (plus the upper plane of the last
 // layer under Dirichlet).
-template <int DIR>
-__global__ void plane_sum_kernel(Topo t, float *__restrict__ w, int dirichlet) {
+template <int DIR, typename T = float>
+__global__ void plane_sum_kernel(Topo t, T *__restrict__ w, int dirichlet) {
   const int Np = t.Np, N = t.N;
   const uint32_t Np2 = (uint32_t)Np * Np;
   const uint64_t total = (uint64_t)t.E * Np2;
@@ -489,16 +489,16 @@ __global__ void plane_sum_kernel(Topo t, float *__restrict__ w, int dirichlet) {
       hi_off = lo_off + (int64_t)N * Np2;
       stride_e = (int64_t)t.ex * t.ey;
     }
-    float *we = w + (int64_t)e * t.Np3;
+    T *we = w + (int64_t)e * t.Np3;
     if (layer > 0) {
-      float *below = we - stride_e * t.Np3 + hi_off;
-      const float v = *below + we[lo_off];
+      T *below = we - stride_e * t.Np3 + hi_off;
+      const T v = *below + we[lo_off];
       *below = v;
       we[lo_off] = v;
     } else if (dirichlet) {
-      we[lo_off] = 0.f;
+      we[lo_off] = T(0);
     }
-    if (dirichlet && layer == layers - 1) we[hi_off] = 0.f;
+    if (dirichlet && layer == layers - 1) we[hi_off] = T(0);
   }
 }
 
@@ -601,21 +601,24 @@ static void ax32_np(const Level &L, const float *u, float *w, bool assemble, cud
 // Direct stiffness summation of an FP32 E-layout vector by three plane
 // passes (x, then y, then z faces; every copy receives the same bits) and the
 // Dirichlet mask.
-void launch_planes_assemble(const Level &L, float *w, cudaStream_t st) {
+template <typename T>
+void launch_planes_assemble(const Level &L, T *w, cudaStream_t st) {
   const Topo &t = L.t;
   SEM_REQUIRE((uint64_t)t.E * t.Np * t.Np < (1ull << 32), "mesh too large for the plane passes");
-  TraceScope ts("plane_sum3", t.N, st, 3);
+  TraceScope ts(sizeof(T) == 8 ? "plane_sum3_f64" : "plane_sum3", t.N, st, 3);
   const int64_t n = t.E * t.Np * t.Np;
   const int64_t b = (n + 255) / 256;
   const int pg = (int)(b < 152 * 16 ? b : 152 * 16);
   const int dir = t.bc == SEM_DIRICHLET;
-  plane_sum_kernel<0><<<pg, 256, 0, st>>>(t, w, dir);
+  plane_sum_kernel<0, T><<<pg, 256, 0, st>>>(t, w, dir);
   SEM_CHECK_CUDA(cudaGetLastError());
-  plane_sum_kernel<1><<<pg, 256, 0, st>>>(t, w, dir);
+  plane_sum_kernel<1, T><<<pg, 256, 0, st>>>(t, w, dir);
   SEM_CHECK_CUDA(cudaGetLastError());
-  plane_sum_kernel<2><<<pg, 256, 0, st>>>(t, w, dir);
+  plane_sum_kernel<2, T><<<pg, 256, 0, st>>>(t, w, dir);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
+template void launch_planes_assemble<float>(const Level &, float *, cudaStream_t);
+template void launch_planes_assemble<double>(const Level &, double *, cudaStream_t);
 
 template <int GK>
 static void ax32_dispatch(const Level &L, const float *u, float *w, bool assemble,

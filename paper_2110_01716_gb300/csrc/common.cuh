@@ -200,7 +200,8 @@ void launch_ax32(const Level &L, int kind, const float *u, float *w, bool assemb
                  cudaStream_t st);
 // Sum the copies of every node of an FP32 E-layout vector (x, y, z face
 // passes) and apply the Dirichlet mask.
-void launch_planes_assemble(const Level &L, float *w, cudaStream_t st);
+template <typename T>
+void launch_planes_assemble(const Level &L, T *w, cudaStream_t st);
 // FP64 geometric factors of a level into `out` (computed again; for setup).
 void level_fp64_factors(const Level &L, DevBuf<double> &out, cudaStream_t st);
 

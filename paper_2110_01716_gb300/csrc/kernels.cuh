@@ -57,8 +57,14 @@ inline void apply_assembled(const Level &L, const T *u, T *w, cudaStream_t st) {
     }
   }
   launch_ax<T>(L, u, w, st);
+#ifndef SEM_GS_NODES
+  // the copies of shared nodes summed by x, y and z face passes (whole
+  // sectors in y and z), the Dirichlet mask with them
+  launch_planes_assemble<T>(L, w, st);
+#else
   launch_gs<T>(L, w, st);
   launch_mask<T>(L, w, st);
+#endif
 }
 
 }  // namespace sem
