@@ -301,11 +301,11 @@ def batch_leg(sem, inputs, count=64, max_workers=8):
     reqs = [sem.make_request(d["ex"], d["ey"], d["ez"], d["N"], sem.SEM_DIRICHLET, 0.1,
                              d["seed"], tol=1e-8) for d in inst]
 
-    def run(workers, smoother):
+    def run(workers, smoother, graph=False):
         S = sem.Server(workers=workers, cache_per_shape=0, smoother_dtype=smoother)
         t0 = time.perf_counter()
         tk = [S.submit(d["ex"], d["ey"], d["ez"], d["N"], sem.SEM_DIRICHLET, 0.1, d["seed"],
-                       tol=1e-8) for d in inst]
+                       tol=1e-8, use_graph=graph) for d in inst]
         infos = [S.wait(t) for t in tk]
         dt = time.perf_counter() - t0
         S.close()
@@ -318,16 +318,18 @@ def batch_leg(sem, inputs, count=64, max_workers=8):
     t32, _ = run(1, sem.SEM_F32)
     best_w, rate = sem.server_autotune(reqs, max_workers=max_workers, cache_per_shape=0)
     tb, infos = run(best_w, sem.SEM_F32)
+    tg, infos_g = run(best_w, sem.SEM_F32, graph=True)
     return {"instances": count, "workload": "config 4: E log-uniform [64, 8192], N in {5,7,9}, "
             "manufactured RHS, Dirichlet, FlexCG+pMG to 1e-8, setup included",
             "fp64_sequential_s": round(t64, 3), "fp32_sequential_s": round(t32, 3),
             "autotuned_workers": best_w, "autotune_rate": round(rate, 2),
             "batched_s": round(tb, 3), "solves_per_s": round(count / tb, 2),
             "speedup_vs_fp64_sequential": round(t64 / tb, 2),
+            "batched_graph_s": round(tg, 3), "solves_per_s_graph": round(count / tg, 2),
             "iters_mean": round(sum(f["iters"] for f in infos) / count, 2)}
 
 
-def serve_leg(sem, inputs, workers, count=200, load=0.8):
+def serve_leg(sem, inputs, workers, count=200, load=0.8, graph=False):
     """Config 5: Poisson arrivals at `load` times the measured capacity (the
     first 32 requests run back to back with the same workers), E log-uniform
     in [512, 65536], N = 7, tolerance in {1e-6, 1e-8, 1e-10}.  Latency is
@@ -337,7 +339,7 @@ def serve_leg(sem, inputs, workers, count=200, load=0.8):
     S = sem.Server(workers=workers, cache_per_shape=0)
     t0 = time.perf_counter()
     tk = [S.submit(r["ex"], r["ey"], r["ez"], r["N"], sem.SEM_DIRICHLET, 0.1, r["seed"],
-                   tol=r["tol"]) for r in probe]
+                   tol=r["tol"], use_graph=graph) for r in probe]
     for t in tk:
         S.wait(t)
     capacity = len(probe) / (time.perf_counter() - t0)
@@ -349,14 +351,15 @@ def serve_leg(sem, inputs, workers, count=200, load=0.8):
         if r["t"] > now:
             time.sleep(r["t"] - now)
         tickets.append(S.submit(r["ex"], r["ey"], r["ez"], r["N"], sem.SEM_DIRICHLET, 0.1,
-                                r["seed"], tol=r["tol"]))
+                                r["seed"], tol=r["tol"], use_graph=graph))
     infos = [S.wait(t) for t in tickets]
     span = time.perf_counter() - t0
     S.close()
     lat = sorted(f["time_ms"] for f in infos)
     if any(f["status"] != sem.SEM_OK for f in infos):
         raise SystemExit("serve leg: a request failed")
-    return {"requests": count, "workers": workers, "capacity_solves_per_s": round(capacity, 2),
+    return {"requests": count, "workers": workers, "use_graph": graph,
+            "capacity_solves_per_s": round(capacity, 2),
             "offered_rate": round(load * capacity, 2), "achieved_solves_per_s": round(count / span, 2),
             "latency_ms": {"p50": round(lat[len(lat) // 2], 2),
                            "p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 2)},
@@ -616,6 +619,24 @@ def main():
         line["e2e"] = {"value": ng / e2e_s / 1e9, "unit": "GDOF/s",
                        "h2d_bytes_per_step": 2 * nl * 8, "d2h_bytes_per_step": nl * 8}
         del bh, xh
+        if solver == sem.SEM_SOLVER_FLEXCG:
+            # the same solves with iterations 2.. as one CUDA-graph launch
+            # (device-side stopping test, one host read per solve)
+            gt = []
+            for i in range(args.warmup + args.steps):
+                x.zero_()
+                ge0 = torch.cuda.Event(enable_timing=True)
+                ge1 = torch.cuda.Event(enable_timing=True)
+                ge0.record(stream)
+                ginf = sem.sem_solve(mesh, pmg, b, x, solver, tol=TOL, max_iter=200,
+                                     stream=stream, use_graph=True)
+                ge1.record(stream)
+                torch.cuda.synchronize()
+                if i >= args.warmup:
+                    gt.append(ge0.elapsed_time(ge1))
+            line["graph"] = {"ms_per_solve": statistics.mean(gt), "iters": ginf["iters"],
+                             "host_loop_ms_per_solve": ms_per_step,
+                             "value": ng / (statistics.mean(gt) / 1e3) / 1e9, "unit": "GDOF/s"}
         line["projection"] = projection_sequence(sem, torch, mesh, pmg, dev, solver, args.restart)
         pmg.close()
         mesh.close()
@@ -623,7 +644,9 @@ def main():
         torch.cuda.empty_cache()
         if not args.no_serve:
             line["batch"] = batch_leg(sem, inputs)
-            line["serve"] = serve_leg(sem, inputs, line["batch"]["autotuned_workers"])
+            bl = line["batch"]
+            line["serve"] = serve_leg(sem, inputs, bl["autotuned_workers"],
+                                      graph=bl["solves_per_s_graph"] > bl["solves_per_s"])
         line["ax_sweep_64cube"] = operator_sweep(sem, torch, dev, hbm)
         if world == 1:
             dt, ng_s, it_s, threads = oracle_sample_solve(12)

@@ -219,6 +219,14 @@ typedef struct {
   int32_t max_iter;
   int32_t check_every; /* read the residual norm every k iterations (>= 1; CG forms) */
   int32_t restart;   /* FGMRES: Krylov vectors per cycle, 1..32 (0: 20) */
+  int32_t use_graph; /* FlexCG only: 1 runs iterations 2.. as one CUDA graph
+                        launch (a device-side while loop whose stopping test
+                        runs on the GPU; the host reads the result once), 0
+                        the host-driven loop.  Results are identical; the
+                        graph saves the per-launch host cost on small
+                        problems.  check_every is ignored (the test runs
+                        every iteration).  The mesh keeps one graph, captured
+                        again when the pMG or x changes. */
 } sem_solve_desc;
 
 typedef struct {

@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI of include/sem.h: argument checks, error reporting,
 // mesh and pMG handles, and the host loops of the Krylov solvers.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -11,6 +12,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "pmg.cuh"
+#include "trace.cuh"
 
 namespace sem {
 
@@ -228,9 +230,81 @@ static sem_status run_fgmres(sem_mesh *M, sem_pmg *P, const double *b, double *x
   return status;
 }
 
+// The FlexCG loop as a CUDA graph: one while node whose body is one pass of
+// the iteration, beginning with the preconditioner of the previous
+// iteration (V-cycle, the two dots, the new direction) and ending with this
+// iteration's operator, step and stopping test (launch_graph_stop, which
+// sets the loop condition).  The body uses rho from slot 2 only: with the
+// flexible update the new rho is written by a later kernel than the one
+// that reads the old, so no alternation is needed.  The body bakes in the
+// mesh's work vectors, the pMG's buffers and x; the mesh keeps one
+// executable graph and captures again when the pMG or x changes.
+static void ensure_graph(sem_mesh *M, sem_pmg *P, double *x) {
+  if (M->graph && M->graph_pmg == P->serial && M->graph_x == x) return;
+  if (M->graph) {
+    SEM_CHECK_CUDA(cudaGraphExecDestroy(M->graph));
+    M->graph = nullptr;
+  }
+  if (!M->cstream) SEM_CHECK_CUDA(cudaStreamCreateWithFlags(&M->cstream, cudaStreamNonBlocking));
+  const Level &L = M->fine;
+  const Topo &t = L.t;
+  const size_t ws = work_stride(M);
+  double *r = M->work.p, *z = r + ws, *p = z + ws, *w = p + ws;
+  cudaStream_t cs = M->cstream;
+  cudaGraph_t g = nullptr;
+  SEM_CHECK_CUDA(cudaGraphCreate(&g, 0));
+  struct GraphGuard {
+    cudaGraph_t g;
+    ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+  } gg{g};
+  cudaGraphConditionalHandle h;
+  SEM_CHECK_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  SEM_CHECK_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  SEM_CHECK_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+  try {
+    pmg_vcycle(P, r, z, cs);
+    launch_flex_dots(t, M->red, z, r, w, slot(M, 2), slot(M, 5), cs);
+    launch_cg_direction(t.nl, slot(M, 5), slot(M, 4), -1.0, z, p, nullptr, cs);
+    apply_assembled<double>(L, p, w, cs);
+    launch_dot(t, M->red, p, w, slot(M, 4), cs);
+    launch_cg_update(t, M->red, slot(M, 2), slot(M, 4), p, w, nullptr, x, r, z, slot(M, 1),
+                     slot(M, 7), nullptr, cs);
+    launch_graph_stop(slot(M, 1), slot(M, 8), h, cs);
+  } catch (...) {
+    cudaGraph_t tmp = nullptr;
+    cudaStreamEndCapture(cs, &tmp);
+    cudaGetLastError();
+    throw;
+  }
+  cudaGraph_t out = nullptr;
+  SEM_CHECK_CUDA(cudaStreamEndCapture(cs, &out));
+  size_t nodes = 0;
+  SEM_CHECK_CUDA(cudaGraphGetNodes(body, nullptr, &nodes));
+  std::vector<cudaGraphNode_t> list(nodes);
+  if (nodes) SEM_CHECK_CUDA(cudaGraphGetNodes(body, list.data(), &nodes));
+  int kernels = 0;
+  for (cudaGraphNode_t n : list) {
+    cudaGraphNodeType ty;
+    SEM_CHECK_CUDA(cudaGraphNodeGetType(n, &ty));
+    kernels += ty == cudaGraphNodeTypeKernel;
+  }
+  SEM_CHECK_CUDA(cudaGraphInstantiate(&M->graph, g, 0));
+  M->graph_pmg = P->serial;
+  M->graph_x = x;
+  M->graph_kernels = kernels;
+}
+
 // Jacobi-PCG (Sec. 3) or flexible CG with one pMG V-cycle per iteration
 // (Sec. 3).  Scalar slots: 0 bb, 1 rr, 2/3 rho (alternating), 4 pw, 5 zw,
-// 6 sum of b, 7 unused output.
+// 6 sum of b, 7 unused output, 8-11 state of the graph loop.
 static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
                             const sem_solve_desc &d, sem_solve_info &info, cudaStream_t st,
                             bool x_zero = false, bool check_rhs = true) {
@@ -267,8 +341,25 @@ static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
     launch_convert<double, double>(t.nl, z, p, st);
     launch_dot(t, M->red, r, z, slot(M, 2), st);
   }
-  const int every = d.check_every < 1 ? 1 : d.check_every;
+  const bool graph = flex && d.use_graph != 0;
+  const int every = graph || d.check_every < 1 ? 1 : d.check_every;
   for (int it = 1; status == SEM_ENOTCONV && it <= d.max_iter; ++it) {
+    if (graph && it == 2) {
+      // iterations 2.. on the device: one graph launch, one read
+      ensure_graph(M, P, x);
+      launch_graph_arm(slot(M, 8), tol2, d.max_iter, 1, st);
+      {
+        TraceScope ts("flexcg_graph", t.N, st, 1);
+        SEM_CHECK_CUDA(cudaGraphLaunch(M->graph, st));
+      }
+      read_scalars(M, 12, st);
+      const int done = (int)M->pinned[10];
+      trace_count("flexcg_graph", t.N, (int64_t)(done - 1) * M->graph_kernels);
+      info.iters = done;
+      if (M->pinned[11] == 2.0) status = SEM_ENUMERIC;
+      else if (M->pinned[1] <= tol2) status = SEM_OK;
+      break;
+    }
     const int cur = 2 + ((it - 1) & 1), nxt = 2 + (it & 1);
     apply_assembled<double>(L, p, w, st);
     launch_dot(t, M->red, p, w, slot(M, 4), st);
@@ -282,6 +373,7 @@ static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
       if (rr <= tol2) { status = SEM_OK; break; }
     }
     if (it == d.max_iter) break;
+    if (graph) continue;  // the graph begins with this iteration's V-cycle
     if (flex) {
       pmg_vcycle(P, r, z, st);
       launch_flex_dots(t, M->red, z, r, w, slot(M, nxt), slot(M, 5), st);
@@ -432,6 +524,8 @@ sem_status sem_mesh_destroy(sem_mesh *mesh) {
     if (!mesh) return;
     if (mesh->pinned) cudaFreeHost(mesh->pinned);
     if (mesh->kpinned) cudaFreeHost(mesh->kpinned);
+    if (mesh->graph) cudaGraphExecDestroy(mesh->graph);
+    if (mesh->cstream) cudaStreamDestroy(mesh->cstream);
     delete mesh;
   });
 }
@@ -516,6 +610,8 @@ sem_status sem_pmg_setup(sem_mesh *mesh, const sem_pmg_desc *desc, void *stream,
     SEM_REQUIRE(mesh && desc && out, "null argument");
     *out = nullptr;
     std::unique_ptr<sem_pmg> P(new sem_pmg());
+    static std::atomic<uint64_t> serials{0};
+    P->serial = ++serials;
     pmg_build(P.get(), mesh, *desc, as_stream(stream));
     *out = P.release();
   });
@@ -568,6 +664,9 @@ static void check_solve_args(sem_mesh *mesh, sem_pmg *pmg, const sem_solve_desc 
               "restart %d outside [0, %d]", desc->restart, kMaxKrylov);
   SEM_REQUIRE(pmg == nullptr || pmg->mesh == mesh, "pmg was built on another mesh");
   SEM_REQUIRE(desc->tol >= 0.0 && desc->max_iter >= 0, "negative tol or max_iter");
+  SEM_REQUIRE(desc->use_graph == 0 || desc->use_graph == 1, "use_graph must be 0 or 1");
+  SEM_REQUIRE(desc->use_graph == 0 || desc->solver == SEM_SOLVER_FLEXCG,
+              "use_graph applies to SEM_SOLVER_FLEXCG only");
 }
 
 sem_status sem_solve(sem_mesh *mesh, sem_pmg *pmg, const double *b, double *x,

@@ -244,4 +244,10 @@ struct sem_mesh {
   sem::Reducer kred;          // reductions of up to restart + 1 sums
   sem::DevBuf<double> kscal;  // FGMRES device scalars
   double *kpinned = nullptr;  // host-pinned copy of one Hessenberg column
+  // FlexCG loop captured into a CUDA graph (sem_solve_desc.use_graph)
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t cstream = nullptr;  // capture stream
+  uint64_t graph_pmg = 0;          // serial of the pMG captured
+  const double *graph_x = nullptr; // solution vector captured
+  int graph_kernels = 0;           // kernels per loop pass
 };

@@ -30,6 +30,9 @@ void launch_flex_dots(const Topo &t, Reducer &R, const double *z, const double *
                       const double *w, double *zr, double *zw, cudaStream_t st);
 void launch_stop_test(const double *rr, const double *bb, double tol2, int it, int maxit,
                       int *skip, int *iters, cudaStream_t st);
+void launch_graph_stop(const double *rr, double *g, cudaGraphConditionalHandle h,
+                       cudaStream_t st);
+void launch_graph_arm(double *g, double tol2, int maxit, int done, cudaStream_t st);
 template <typename A, typename B>
 void launch_convert(int64_t n, const A *a, B *b, cudaStream_t st);
 

@@ -37,4 +37,5 @@ struct sem_pmg {
   sem::DevBuf<double> cz, cp, cw, z64;
   sem::CoarseSolver coarse;   // persistent solver when the coarsest order is 1
   bool persistent_coarse = false;
+  uint64_t serial = 0;        // distinct for every hierarchy created
 };

@@ -330,6 +330,8 @@ void check_request(const sem_request *r) {
               "unknown solver %d", s.solver);
   SEM_REQUIRE(s.tol >= 0.0 && s.max_iter >= 0, "negative tol or max_iter");
   SEM_REQUIRE(s.restart >= 0 && s.restart <= kMaxKrylov, "restart outside [0, %d]", kMaxKrylov);
+  SEM_REQUIRE(s.use_graph == 0 || (s.use_graph == 1 && s.solver == SEM_SOLVER_FLEXCG),
+              "use_graph is 0, or 1 with SEM_SOLVER_FLEXCG");
 }
 
 }  // namespace

@@ -69,6 +69,10 @@ static bool filter_matches(const std::string &filter, const char *name) {
 TraceScope::TraceScope(const char *name, int N, cudaStream_t st, int kernels) : st_(st) {
   Tracer &T = tracer();
   if (!T.on.load(std::memory_order_relaxed)) return;
+  // launches captured into a CUDA graph run later, once per replay: the
+  // graph's owner counts them
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return;
   char buf[64];
   snprintf(buf, sizeof(buf), "%s_N%d", name, N);
   std::lock_guard<std::mutex> lock(T.mu);
@@ -89,6 +93,15 @@ TraceScope::~TraceScope() {
   cudaEventRecord(e1_, st_);
   std::lock_guard<std::mutex> lock(T.mu);
   T.cls[key_].pending.emplace_back(e0_, e1_);
+}
+
+void trace_count(const char *name, int N, int64_t launches) {
+  Tracer &T = tracer();
+  if (!T.on.load(std::memory_order_relaxed)) return;
+  char buf[64];
+  snprintf(buf, sizeof(buf), "%s_N%d", name, N);
+  std::lock_guard<std::mutex> lock(T.mu);
+  T.cls[buf].launches += launches;
 }
 
 void trace_enable(bool on, const char *filter) {

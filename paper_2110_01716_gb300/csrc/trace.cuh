@@ -25,4 +25,8 @@ class TraceScope {
   std::string key_;
 };
 
+// Adds `launches` kernel launches to class "<name>_N<order>" without timing
+// (kernels that ran inside a graph launch).
+void trace_count(const char *name, int N, int64_t launches);
+
 }  // namespace sem

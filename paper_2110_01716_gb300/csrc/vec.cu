@@ -237,6 +237,41 @@ void launch_stop_test(const double *rr, const double *bb, double tol2, int it, i
   SEM_CHECK_CUDA(cudaGetLastError());
 }
 
+// Stopping test inside the device-driven FlexCG loop (a CUDA-graph while
+// node).  g: 0 squared absolute tolerance on (r, r), 1 max_iter, 2 iterations done, 3 state (0 running,
+// 1 stopped, 2 NaN/Inf residual).  Counts the iteration, stops at the
+// tolerance, at max_iter or on a non-finite residual, and sets the loop's
+// condition to "continue" only while running.
+__global__ void graph_stop_kernel(const double *__restrict__ rr, double *g,
+                                  cudaGraphConditionalHandle h) {
+  const double it = g[2] + 1.0;
+  g[2] = it;
+  const double v = *rr;
+  double state = 0.0;
+  if (!(v == v) || isinf(v)) state = 2.0;
+  else if (!(v > g[0]) || it >= g[1]) state = 1.0;
+  g[3] = state;
+  cudaGraphSetConditional(h, state == 0.0 ? 1u : 0u);
+}
+
+__global__ void graph_arm_kernel(double *g, double tol2, double maxit, double done) {
+  g[0] = tol2;
+  g[1] = maxit;
+  g[2] = done;
+  g[3] = 0.0;
+}
+
+void launch_graph_stop(const double *rr, double *g, cudaGraphConditionalHandle h,
+                       cudaStream_t st) {
+  graph_stop_kernel<<<1, 1, 0, st>>>(rr, g, h);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+void launch_graph_arm(double *g, double tol2, int maxit, int done, cudaStream_t st) {
+  graph_arm_kernel<<<1, 1, 0, st>>>(g, tol2, (double)maxit, (double)done);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
 // ------------------------------------------------------------------ conversions
 template <typename A, typename B>
 __global__ void convert_kernel(int64_t n, const A *__restrict__ a, B *__restrict__ b) {

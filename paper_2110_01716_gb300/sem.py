@@ -63,7 +63,7 @@ class sem_pmg_desc(C.Structure):
 
 class sem_solve_desc(C.Structure):
     _fields_ = [("solver", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("check_every", C.c_int32), ("restart", C.c_int32)]
+                ("check_every", C.c_int32), ("restart", C.c_int32), ("use_graph", C.c_int32)]
 
 
 class sem_server_desc(C.Structure):
@@ -298,9 +298,10 @@ def sem_pmg_vcycle(pmg: Pmg, r, z, stream=None):
 
 
 def sem_solve(mesh: Mesh, pmg, b, x, solver=SEM_SOLVER_PCG, tol=1e-8, max_iter=1000,
-              check_every=1, stream=None, raise_on_notconv=False, restart=0):
+              check_every=1, stream=None, raise_on_notconv=False, restart=0, use_graph=False):
     """Solve in place (x: initial guess in, solution out); returns the info dict."""
-    desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every), int(restart))
+    desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every), int(restart),
+                          int(bool(use_graph)))
     info = sem_solve_info()
     st = lib().sem_solve(mesh.h, pmg.h if pmg is not None else None, _ptr(b), _ptr(x),
                          C.byref(desc), C.byref(info), _stream(stream))
@@ -312,9 +313,10 @@ def sem_solve(mesh: Mesh, pmg, b, x, solver=SEM_SOLVER_PCG, tol=1e-8, max_iter=1
 
 
 def sem_solve_host(mesh: Mesh, pmg, b_host, x_host, solver=SEM_SOLVER_PCG, tol=1e-8,
-                   max_iter=1000, check_every=1, stream=None, restart=0):
+                   max_iter=1000, check_every=1, stream=None, restart=0, use_graph=False):
     """As sem_solve with host (CPU tensor or numpy) b and x; x is updated in place."""
-    desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every), int(restart))
+    desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every), int(restart),
+                          int(bool(use_graph)))
     info = sem_solve_info()
     bp = b_host.ctypes.data if hasattr(b_host, "ctypes") else b_host.data_ptr()
     xp = x_host.ctypes.data if hasattr(x_host, "ctypes") else x_host.data_ptr()
@@ -355,10 +357,12 @@ class Projection:
 
 
 def sem_solve_projected(mesh: Mesh, pmg, proj: Projection, b, x, solver=SEM_SOLVER_FLEXCG,
-                        tol=1e-8, max_iter=1000, check_every=1, restart=0, stream=None):
+                        tol=1e-8, max_iter=1000, check_every=1, restart=0, stream=None,
+                        use_graph=False):
     """Projected solve: x (output) = best fit in the kept space + correction;
     returns the info dict (res0 = residual after projection)."""
-    desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every), int(restart))
+    desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every), int(restart),
+                          int(bool(use_graph)))
     info = sem_solve_info()
     st = lib().sem_solve_projected(mesh.h, pmg.h if pmg is not None else None, proj.h, _ptr(b),
                                    _ptr(x), C.byref(desc), C.byref(info), _stream(stream))
@@ -370,7 +374,7 @@ def sem_solve_projected(mesh: Mesh, pmg, proj: Projection, b, x, solver=SEM_SOLV
 
 
 def make_request(ex, ey, ez, N, bc=SEM_DIRICHLET, jitter=0.1, seed=0, b=None, x=None,
-                 solver=SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=200, restart=0):
+                 solver=SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=200, restart=0, use_graph=False):
     """A sem_request; b (host float64 array, n_local) selects SEM_RHS_HOST, else the
     manufactured right-hand side; x (host float64 array) receives the solution."""
     r = sem_request()
@@ -379,7 +383,8 @@ def make_request(ex, ey, ez, N, bc=SEM_DIRICHLET, jitter=0.1, seed=0, b=None, x=
     r.rhs = SEM_RHS_MANUFACTURED if b is None else SEM_RHS_HOST
     r.b = b.ctypes.data if b is not None else None
     r.x = x.ctypes.data if x is not None else None
-    r.solve = sem_solve_desc(solver, float(tol), int(max_iter), 1, int(restart))
+    r.solve = sem_solve_desc(solver, float(tol), int(max_iter), 1, int(restart),
+                             int(bool(use_graph)))
     return r
 
 

@@ -149,3 +149,29 @@ def test_autotune_picks_a_worker_count():
             for ex, ey, ez, N, seed in BATCH]
     w, rate = sem.server_autotune(reqs, max_workers=4, cache_per_shape=0)
     assert w in (1, 2, 4) and rate > 0
+
+
+def test_graph_requests_equal_host_loop_requests():
+    """FlexCG requests with use_graph give the same bits as without, with
+    setups reused across requests (the graph is captured per setup)."""
+    problems = [_problem(*p) for p in BATCH]
+    xs, infos, _ = _run(3, problems)
+    S = sem.Server(workers=3)
+    xg, tickets = [], []
+    for (ex, ey, ez, N, seed), (L, us, b) in zip(BATCH, problems):
+        x = np.zeros(L.nl)
+        xg.append(x)
+        tickets.append(S.submit(ex, ey, ez, N, sem.SEM_DIRICHLET, 0.1, seed, b=b, x=x,
+                                tol=1e-8, use_graph=True))
+    ig = [S.wait(t) for t in tickets]
+    S.close()
+    for a, b_, ia, ib in zip(xs, xg, infos, ig):
+        assert ib["status"] == sem.SEM_OK and ia["iters"] == ib["iters"]
+        assert np.array_equal(a, b_)
+    with pytest.raises(sem.SemError):
+        S2 = sem.Server(workers=1)
+        try:
+            S2.submit(2, 2, 2, 3, sem.SEM_DIRICHLET, 0.1, 1, solver=sem.SEM_SOLVER_PCG,
+                      use_graph=True)
+        finally:
+            S2.close()

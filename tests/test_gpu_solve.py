@@ -447,3 +447,108 @@ def test_schwarz_order_limit():
     with pytest.raises(sem.SemError) as ex:
         sem.Pmg(m, orders=(10, 5, 1), smoother=sem.SEM_SMOOTH_ASM)
     assert ex.value.status == sem.SEM_EINVAL
+
+
+# ---------------------------------------------------------------- CUDA graph
+GRAPH_CASES = [
+    # bc, orders, coarse mode, smoother, smoother dtype
+    (0, (7, 3, 1), sem.SEM_COARSE_JACOBI, sem.SEM_SMOOTH_JACOBI, sem.SEM_F32),
+    (1, (7, 3, 1), sem.SEM_COARSE_MG, sem.SEM_SMOOTH_JACOBI, sem.SEM_F32),
+    (0, (5, 3), sem.SEM_COARSE_JACOBI, sem.SEM_SMOOTH_JACOBI, sem.SEM_F64),
+    (1, (7, 3, 1), sem.SEM_COARSE_JACOBI, sem.SEM_SMOOTH_ASM, sem.SEM_F32),
+    (0, (7, 3, 1), sem.SEM_COARSE_JACOBI, sem.SEM_SMOOTH_JACOBI, sem.SEM_F16),
+]
+
+
+def _graph_problem(bc, orders, e=(5, 4, 3), seed=4):
+    v = inputs.box_vertices(*e, 0.1, seed)
+    m = sem.Mesh(*e, orders[0], bc, verts=v)
+    L = oracle.Level(*e, orders[0], bc, v)
+    b = manufactured(L)[1] if bc == 0 else fourier_rhs(L)
+    return m, L, b
+
+
+@pytest.mark.parametrize("bc,orders,cmode,smoother,dtype", GRAPH_CASES)
+def test_graph_flexcg_matches_host_loop_bitwise(bc, orders, cmode, smoother, dtype):
+    """The device-driven loop runs the same kernels on the same data as the
+    host-driven one: same iterations, same bits, on first capture, on replay
+    and after a capture for another x."""
+    m, L, b = _graph_problem(bc, orders)
+    P = sem.Pmg(m, orders=orders, smoother_dtype=dtype, coarse_tol=1e-2, coarse_maxit=60,
+                coarse_mode=cmode, smoother=smoother)
+    bd = torch.tensor(b, device=DEV)
+    xe = torch.zeros_like(bd)
+    ie = sem.sem_solve(m, P, bd, xe, sem.SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=100)
+    assert ie["status"] == sem.SEM_OK and ie["iters"] >= 3, ie
+    for xg in (torch.zeros_like(bd), torch.zeros_like(bd), None):
+        if xg is None:
+            xg = torch.zeros_like(bd)  # a third buffer: the graph is captured again
+        ig = sem.sem_solve(m, P, bd, xg, sem.SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=100,
+                           use_graph=True)
+        assert ig["status"] == sem.SEM_OK and ig["iters"] == ie["iters"], (ig, ie)
+        assert ig["res"] == ie["res"]
+        assert torch.equal(xg, xe)
+    assert residual(L, b, xg.cpu().numpy()) <= 1.05e-8
+
+
+@pytest.mark.parametrize("max_iter", [1, 2, 3, 5])
+def test_graph_flexcg_stops_at_max_iter(max_iter):
+    m, L, b = _graph_problem(0, (7, 3, 1))
+    P = sem.Pmg(m, orders=(7, 3, 1), coarse_tol=1e-2, coarse_maxit=60)
+    bd = torch.tensor(b, device=DEV)
+    xe, xg = torch.zeros_like(bd), torch.zeros_like(bd)
+    ie = sem.sem_solve(m, P, bd, xe, sem.SEM_SOLVER_FLEXCG, tol=1e-14, max_iter=max_iter)
+    ig = sem.sem_solve(m, P, bd, xg, sem.SEM_SOLVER_FLEXCG, tol=1e-14, max_iter=max_iter,
+                       use_graph=True)
+    assert ie["status"] == ig["status"] == sem.SEM_ENOTCONV
+    assert ie["iters"] == ig["iters"] == max_iter
+    assert torch.equal(xg, xe)
+
+
+def test_graph_follows_a_new_pmg_and_nonzero_guess():
+    """A second hierarchy on the same mesh is captured afresh; a nonzero
+    initial guess goes through the same path."""
+    m, L, b = _graph_problem(0, (7, 3, 1))
+    bd = torch.tensor(b, device=DEV)
+    x0 = L.gs(inputs.random_field(L.nl, 9)) / L.gs(np.ones(L.nl)) * L.mask
+    x0 = torch.tensor(x0, device=DEV)
+    for degree in (2, 3):
+        P = sem.Pmg(m, orders=(7, 3, 1), cheb_degree=degree, coarse_tol=1e-2, coarse_maxit=60)
+        xe, xg = x0.clone(), x0.clone()
+        ie = sem.sem_solve(m, P, bd, xe, sem.SEM_SOLVER_FLEXCG, tol=1e-9, max_iter=100)
+        ig = sem.sem_solve(m, P, bd, xg, sem.SEM_SOLVER_FLEXCG, tol=1e-9, max_iter=100,
+                           use_graph=True)
+        assert ig["status"] == sem.SEM_OK and ig["iters"] == ie["iters"]
+        assert torch.equal(xg, xe)
+        P.close()
+
+
+def test_graph_host_and_projected_solves():
+    m, L, b = _graph_problem(1, (7, 3, 1))
+    P = sem.Pmg(m, orders=(7, 3, 1), coarse_tol=1e-2, coarse_maxit=60)
+    xe, xg = np.zeros(L.nl), np.zeros(L.nl)
+    ie = sem.sem_solve_host(m, P, b, xe, sem.SEM_SOLVER_FLEXCG, tol=1e-8)
+    ig = sem.sem_solve_host(m, P, b, xg, sem.SEM_SOLVER_FLEXCG, tol=1e-8, use_graph=True)
+    assert ie["iters"] == ig["iters"] and np.array_equal(xe, xg)
+    Qe, Qg = sem.Projection(m, 4), sem.Projection(m, 4)
+    for n in range(6):
+        bn = torch.tensor(sequence_rhs(L, n, 1), device=DEV)
+        ye, yg = torch.zeros_like(bn), torch.zeros_like(bn)
+        je = sem.sem_solve_projected(m, P, Qe, bn, ye, tol=1e-8)
+        jg = sem.sem_solve_projected(m, P, Qg, bn, yg, tol=1e-8, use_graph=True)
+        assert je["iters"] == jg["iters"] and je["status"] == jg["status"] == sem.SEM_OK
+        assert torch.equal(ye, yg)
+
+
+def test_graph_argument_checks():
+    m = sem.Mesh(2, 2, 2, 3, 0)
+    P = sem.Pmg(m, orders=(3, 1))
+    bd = torch.zeros(m.n_local, device=DEV, dtype=torch.float64)
+    xd = torch.zeros_like(bd)
+    for solver, pmg in ((sem.SEM_SOLVER_PCG, None), (sem.SEM_SOLVER_FGMRES, P)):
+        with pytest.raises(sem.SemError) as ex:
+            sem.sem_solve(m, pmg, bd, xd, solver, use_graph=True)
+        assert ex.value.status == sem.SEM_EINVAL
+    # zero right-hand side: converged before any graph launch
+    info = sem.sem_solve(m, P, bd, xd, sem.SEM_SOLVER_FLEXCG, use_graph=True)
+    assert info["status"] == sem.SEM_OK and info["iters"] == 0
