@@ -37,6 +37,7 @@
 #include <cuda_fp16.h>
 
 #include "common.cuh"
+#include "kernels.cuh"
 #include "trace.cuh"
 
 namespace sem {
@@ -115,19 +116,6 @@ __device__ __forceinline__ void load_row(const float *row, float (&r)[NP]) {
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       if (4 * c + q < NP) r[4 * c + q] = f4get(v, q);
-  }
-}
-
-// Hint: bring [p, p + bytes) into L2 (bulk prefetch; the range is shrunk to
-// whole 16-byte units inside it, so nothing outside it is touched).
-__device__ __forceinline__ void prefetch_l2(const void *p, int64_t bytes) {
-  uintptr_t a = reinterpret_cast<uintptr_t>(p);
-  const uintptr_t b = (a + (uintptr_t)bytes) & ~(uintptr_t)15;
-  a = (a + 15) & ~(uintptr_t)15;
-  while (a + 16 <= b) {
-    const uint32_t n = (uint32_t)((b - a) < (1u << 20) ? (b - a) : (1u << 20));
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
-    a += n;
   }
 }
 

@@ -230,13 +230,60 @@ static sem_status run_fgmres(sem_mesh *M, sem_pmg *P, const double *b, double *x
   return status;
 }
 
+// Flexible CG steps (Sec. 3).  The V-cycle reads its input from, and leaves
+// its output in, the fine level's own buffers (FP32 for an FP32 smoother):
+// cg_update writes the V-cycle input beside r, and the direction update, the
+// dots and the operator read the FP32 output directly (widened exactly), so
+// no separate conversion passes run.  With the stored-factor pair operator
+// <p, Ap> is reduced inside the operator kernel.
+// Scalar slots: 0 bb, 1 rr, 2 rho = <z,r>, 4 <p,Ap>, 5 <z,w>, 7 unused.
+static bool flex_fused(const Level &L) {
+  return L.geom == SEM_GEOM_STORED && L.arith == SEM_ARITH_PAIR;
+}
+
+// p = z (first) or p = z - (<z,w>/<p,w>) p;  w = mask gs(A p);  slot 4 = <p, w>
+static void flex_operator(sem_mesh *M, const VcycleIO &io, double *p, double *w, bool first,
+                          cudaStream_t st) {
+  const Level &L = M->fine;
+  const Topo &t = L.t;
+  if (first) {
+    if (io.out32) launch_convert<float, double>(t.nl, io.out32, p, st);
+    else launch_convert<double, double>(t.nl, io.out64, p, st);
+  } else if (io.out32) {
+    launch_cg_direction(t.nl, slot(M, 5), slot(M, 4), -1.0, io.out32, p, nullptr, st);
+  } else {
+    launch_cg_direction(t.nl, slot(M, 5), slot(M, 4), -1.0, io.out64, p, nullptr, st);
+  }
+  if (flex_fused(L)) {
+    launch_ax_pair_dot(L, p, w, slot(M, 4), M->red, st);
+    launch_planes_assemble<double>(L, w, st);
+  } else {
+    apply_assembled<double>(L, p, w, st);
+    launch_dot(t, M->red, p, w, slot(M, 4), st);
+  }
+}
+
+// x += alpha p, r -= alpha w, rr (slot 1), and the V-cycle input = r
+static void flex_update(sem_mesh *M, const VcycleIO &io, const double *p, const double *w,
+                        double *x, double *r, cudaStream_t st) {
+  launch_cg_update(M->fine.t, M->red, slot(M, 2), slot(M, 4), p, w, nullptr, x, r, nullptr,
+                   slot(M, 1), slot(M, 7), nullptr, st, io.in32, io.in64);
+}
+
+// z = V-cycle(r) (in the level's buffers); slot 2 = <z,r>, slot 5 = <z,w>
+static void flex_precondition(sem_mesh *M, sem_pmg *P, const VcycleIO &io, const double *r,
+                              const double *w, cudaStream_t st) {
+  pmg_vcycle_core(P, st);
+  if (io.out32) launch_flex_dots(M->fine.t, M->red, io.out32, r, w, slot(M, 2), slot(M, 5), st);
+  else launch_flex_dots(M->fine.t, M->red, io.out64, r, w, slot(M, 2), slot(M, 5), st);
+}
+
 // The FlexCG loop as a CUDA graph: one while node whose body is one pass of
 // the iteration, beginning with the preconditioner of the previous
-// iteration (V-cycle, the two dots, the new direction) and ending with this
-// iteration's operator, step and stopping test (launch_graph_stop, which
-// sets the loop condition).  The body uses rho from slot 2 only: with the
-// flexible update the new rho is written by a later kernel than the one
-// that reads the old, so no alternation is needed.  The body bakes in the
+// iteration (V-cycle and the two dots) and ending with this iteration's
+// direction, operator, step and stopping test (launch_graph_stop, which sets
+// the loop condition): the same kernels as the host-driven loop, in the same
+// order.  The body bakes in the
 // mesh's work vectors, the pMG's buffers and x; the mesh keeps one
 // executable graph and captures again when the pMG or x changes.
 static void ensure_graph(sem_mesh *M, sem_pmg *P, double *x) {
@@ -246,8 +293,6 @@ static void ensure_graph(sem_mesh *M, sem_pmg *P, double *x) {
     M->graph = nullptr;
   }
   if (!M->cstream) SEM_CHECK_CUDA(cudaStreamCreateWithFlags(&M->cstream, cudaStreamNonBlocking));
-  const Level &L = M->fine;
-  const Topo &t = L.t;
   const size_t ws = work_stride(M);
   double *r = M->work.p, *z = r + ws, *p = z + ws, *w = p + ws;
   cudaStream_t cs = M->cstream;
@@ -270,13 +315,10 @@ static void ensure_graph(sem_mesh *M, sem_pmg *P, double *x) {
   SEM_CHECK_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                                cudaStreamCaptureModeThreadLocal));
   try {
-    pmg_vcycle(P, r, z, cs);
-    launch_flex_dots(t, M->red, z, r, w, slot(M, 2), slot(M, 5), cs);
-    launch_cg_direction(t.nl, slot(M, 5), slot(M, 4), -1.0, z, p, nullptr, cs);
-    apply_assembled<double>(L, p, w, cs);
-    launch_dot(t, M->red, p, w, slot(M, 4), cs);
-    launch_cg_update(t, M->red, slot(M, 2), slot(M, 4), p, w, nullptr, x, r, z, slot(M, 1),
-                     slot(M, 7), nullptr, cs);
+    const VcycleIO io = pmg_io(P);
+    flex_precondition(M, P, io, r, w, cs);
+    flex_operator(M, io, p, w, false, cs);
+    flex_update(M, io, p, w, x, r, cs);
     launch_graph_stop(slot(M, 1), slot(M, 8), h, cs);
   } catch (...) {
     cudaGraph_t tmp = nullptr;
@@ -303,8 +345,8 @@ static void ensure_graph(sem_mesh *M, sem_pmg *P, double *x) {
 }
 
 // Jacobi-PCG (Sec. 3) or flexible CG with one pMG V-cycle per iteration
-// (Sec. 3).  Scalar slots: 0 bb, 1 rr, 2/3 rho (alternating), 4 pw, 5 zw,
-// 6 sum of b, 7 unused output, 8-11 state of the graph loop.
+// (Sec. 3).  Scalar slots: 0 bb, 1 rr, 2/3 rho (alternating in PCG), 4 pw,
+// 5 zw, 6 sum of b, 7 unused output, 8-11 state of the graph loop.
 static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
                             const sem_solve_desc &d, sem_solve_info &info, cudaStream_t st,
                             bool x_zero = false, bool check_rhs = true) {
@@ -336,10 +378,14 @@ static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
   const double tol2 = d.tol * d.tol * bb;
   if (!(rr == rr) || !(bb == bb)) status = SEM_ENUMERIC;
   else if (rr <= tol2) status = SEM_OK;
+  VcycleIO io;
   if (status == SEM_ENOTCONV && flex) {
-    pmg_vcycle(P, r, z, st);
-    launch_convert<double, double>(t.nl, z, p, st);
-    launch_dot(t, M->red, r, z, slot(M, 2), st);
+    io = pmg_io(P);
+    if (io.in32) launch_convert<double, float>(t.nl, r, io.in32, st);
+    else launch_convert<double, double>(t.nl, r, io.in64, st);
+    pmg_vcycle_core(P, st);
+    if (io.out32) launch_dot(t, M->red, io.out32, r, slot(M, 2), st);
+    else launch_dot(t, M->red, io.out64, r, slot(M, 2), st);
   }
   const bool graph = flex && d.use_graph != 0;
   const int every = graph || d.check_every < 1 ? 1 : d.check_every;
@@ -361,10 +407,15 @@ static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
       break;
     }
     const int cur = 2 + ((it - 1) & 1), nxt = 2 + (it & 1);
-    apply_assembled<double>(L, p, w, st);
-    launch_dot(t, M->red, p, w, slot(M, 4), st);
-    launch_cg_update(t, M->red, slot(M, cur), slot(M, 4), p, w, flex ? nullptr : L.dinv64.p, x, r,
-                     z, slot(M, 1), flex ? slot(M, 7) : slot(M, nxt), nullptr, st);
+    if (flex) {
+      flex_operator(M, io, p, w, it == 1, st);
+      flex_update(M, io, p, w, x, r, st);
+    } else {
+      apply_assembled<double>(L, p, w, st);
+      launch_dot(t, M->red, p, w, slot(M, 4), st);
+      launch_cg_update(t, M->red, slot(M, cur), slot(M, 4), p, w, L.dinv64.p, x, r, z, slot(M, 1),
+                       slot(M, nxt), nullptr, st);
+    }
     info.iters = it;
     if (it % every == 0 || it == d.max_iter) {
       read_scalars(M, 8, st);
@@ -374,13 +425,10 @@ static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
     }
     if (it == d.max_iter) break;
     if (graph) continue;  // the graph begins with this iteration's V-cycle
-    if (flex) {
-      pmg_vcycle(P, r, z, st);
-      launch_flex_dots(t, M->red, z, r, w, slot(M, nxt), slot(M, 5), st);
-      launch_cg_direction(t.nl, slot(M, 5), slot(M, 4), -1.0, z, p, nullptr, st);
-    } else {
-      launch_cg_direction(t.nl, slot(M, nxt), slot(M, cur), 1.0, z, p, nullptr, st);
-    }
+    if (flex) flex_precondition(M, P, io, r, w, st);
+    else
+      launch_cg_direction(t.nl, slot(M, nxt), slot(M, cur), 1.0, (const double *)z, p, nullptr,
+                          st);
   }
   SEM_CHECK_CUDA(cudaEventRecord(e1, st));
   read_scalars(M, 8, st);

@@ -218,6 +218,7 @@ struct Reducer {
   DevBuf<double> partials;  // [nblocks][nsums]
   DevBuf<unsigned int> counter;
   int nblocks = 0;
+  size_t capacity = 0;      // partials held (nblocks x nsums)
   void init(int blocks, int max_sums);
 };
 

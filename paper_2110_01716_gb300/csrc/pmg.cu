@@ -822,25 +822,34 @@ static void vcycle_level(sem_pmg *P, int l, cudaStream_t st) {
   smooth<T>(P, l, false, st);
 }
 
-void pmg_vcycle(sem_pmg *P, const double *r, double *z, cudaStream_t st) {
+VcycleIO pmg_io(sem_pmg *P) {
   PmgLevel &Q = (*P->levp[0]);
-  const int64_t n = Q.L->t.nl;
-  if (P->levp.size() == 1) {
-    // a single level: the coarse solver itself
-    launch_convert<double, double>(n, r, Q.v64[0].p, st);
-    coarse_solve(P, st);
-    launch_convert<double, double>(n, Q.v64[1].p, z, st);
-    return;
-  }
-  if (Q.dtype == SEM_F32) {
-    launch_convert<double, float>(n, r, Q.v32[0].p, st);
-    vcycle_dispatch<float>(P, 0, st);
-    launch_convert<float, double>(n, Q.v32[1].p, z, st);
+  VcycleIO io;
+  if (P->levp.size() > 1 && Q.dtype == SEM_F32) {
+    io.in32 = Q.v32[0].p;
+    io.out32 = Q.v32[1].p;
   } else {
-    launch_convert<double, double>(n, r, Q.v64[0].p, st);
-    vcycle_dispatch<double>(P, 0, st);
-    launch_convert<double, double>(n, Q.v64[1].p, z, st);
+    io.in64 = Q.v64[0].p;
+    io.out64 = Q.v64[1].p;
   }
+  return io;
+}
+
+void pmg_vcycle_core(sem_pmg *P, cudaStream_t st) {
+  PmgLevel &Q = (*P->levp[0]);
+  if (P->levp.size() == 1) coarse_solve(P, st);  // a single level: the coarse solver itself
+  else if (Q.dtype == SEM_F32) vcycle_dispatch<float>(P, 0, st);
+  else vcycle_dispatch<double>(P, 0, st);
+}
+
+void pmg_vcycle(sem_pmg *P, const double *r, double *z, cudaStream_t st) {
+  const int64_t n = P->levp[0]->L->t.nl;
+  const VcycleIO io = pmg_io(P);
+  if (io.in32) launch_convert<double, float>(n, r, io.in32, st);
+  else launch_convert<double, double>(n, r, io.in64, st);
+  pmg_vcycle_core(P, st);
+  if (io.out32) launch_convert<float, double>(n, io.out32, z, st);
+  else launch_convert<double, double>(n, io.out64, z, st);
 }
 
 }  // namespace sem

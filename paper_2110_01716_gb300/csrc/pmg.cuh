@@ -25,6 +25,18 @@ struct PmgLevel {
 void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t st);
 void pmg_vcycle(sem_pmg *P, const double *r, double *z, cudaStream_t st);
 
+// The fine level's V-cycle buffers in the level's arithmetic: the input
+// (residual) and the output (correction); one of each pair is set.
+struct VcycleIO {
+  float *in32 = nullptr;
+  double *in64 = nullptr;
+  const float *out32 = nullptr;
+  const double *out64 = nullptr;
+};
+VcycleIO pmg_io(sem_pmg *P);
+// One V-cycle from the input buffer to the output buffer.
+void pmg_vcycle_core(sem_pmg *P, cudaStream_t st);
+
 }  // namespace sem
 
 struct sem_pmg {

@@ -18,7 +18,8 @@ namespace sem {
 
 void Reducer::init(int blocks, int max_sums) {
   nblocks = blocks;
-  partials.alloc((size_t)blocks * max_sums);
+  capacity = (size_t)blocks * max_sums;
+  partials.alloc(capacity);
   counter.alloc(1);
   SEM_CHECK_CUDA(cudaMemset(counter.p, 0, sizeof(unsigned int)));
 }
@@ -29,25 +30,40 @@ int vec_grid(int64_t n) {
 }
 
 // ------------------------------------------------------------------ dots
-// out = sum u v / mult (optionally a second pair)
+__device__ __forceinline__ double as_f64(double v) { return v; }
+__device__ __forceinline__ double as_f64(float v) { return widen_f32(v); }
+
+// out = sum u v / mult; u in FP64 or FP32 (widened exactly)
+template <typename Tu>
 __global__ void __launch_bounds__(kVecThreads)
-    dot_kernel(Topo t, const double *__restrict__ u, const double *__restrict__ v,
+    dot_kernel(Topo t, const Tu *__restrict__ u, const double *__restrict__ v,
                double *partials, unsigned int *counter, OutPtrs<1> out) {
   double acc[1] = {0.0};
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
        l += gridDim.x * blockDim.x) {
     PointInfo q = point_info(l, t);
-    acc[0] = fma(scale_pow2_down(u[l], q.log2_mult), v[l], acc[0]);
+    acc[0] = fma(scale_pow2_down(as_f64(u[l]), q.log2_mult), v[l], acc[0]);
   }
   grid_reduce<1>(acc, partials, counter, out.p);
 }
 
-void launch_dot(const Topo &t, Reducer &R, const double *u, const double *v, double *out,
-                cudaStream_t st) {
+template <typename Tu>
+static void dot_any(const Topo &t, Reducer &R, const Tu *u, const double *v, double *out,
+                    cudaStream_t st) {
   OutPtrs<1> o{{out}};
   TraceScope ts("dot", t.N, st);
-  dot_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, u, v, R.partials.p, R.counter.p, o);
+  dot_kernel<Tu><<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, u, v, R.partials.p, R.counter.p, o);
   SEM_CHECK_CUDA(cudaGetLastError());
+}
+
+void launch_dot(const Topo &t, Reducer &R, const double *u, const double *v, double *out,
+                cudaStream_t st) {
+  dot_any(t, R, u, v, out, st);
+}
+
+void launch_dot(const Topo &t, Reducer &R, const float *u, const double *v, double *out,
+                cudaStream_t st) {
+  dot_any(t, R, u, v, out, st);
 }
 
 // ------------------------------------------------------------------ CG start
@@ -91,14 +107,16 @@ void launch_cg_start(const Topo &t, Reducer &R, const double *b, const double *w
 
 // ------------------------------------------------------------------ CG iteration
 // alpha = rho / pw;  x += alpha p;  r -= alpha w (w = A p assembled, masked);  rr = <r,r>;
-// Jacobi: z = dinv r and rz = <r,z>.  skip != null: the whole kernel is a
+// Jacobi: z = dinv r and rz = <r,z>.  rc32 / rc64: a copy of the new r (the
+// V-cycle's input, FP32 rounded to nearest or FP64).  skip != null: the whole kernel is a
 // no-op once *skip is set (device-side stop of the coarse solve).
 __global__ void __launch_bounds__(kVecThreads)
     cg_update_kernel(Topo t, const double *__restrict__ rho, const double *__restrict__ pw,
                      const double *__restrict__ p, const double *__restrict__ w,
                      const double *__restrict__ dinv, double *__restrict__ x,
                      double *__restrict__ r, double *__restrict__ z, double *partials,
-                     unsigned int *counter, OutPtrs<2> out, const int *__restrict__ skip) {
+                     unsigned int *counter, OutPtrs<2> out, const int *__restrict__ skip,
+                     float *__restrict__ rc32, double *__restrict__ rc64) {
   if (skip && *skip) return;
   const double alpha = *rho / *pw;
   double acc[2] = {0.0, 0.0};
@@ -108,6 +126,8 @@ __global__ void __launch_bounds__(kVecThreads)
     x[l] = fma(alpha, p[l], x[l]);
     double rl = fma(-alpha, w[l], r[l]);
     r[l] = rl;
+    if (rc32) rc32[l] = (float)rl;
+    if (rc64) rc64[l] = rl;
     double rs = scale_pow2_down(rl, q.log2_mult);
     acc[0] = fma(rs, rl, acc[0]);
     if (dinv) {
@@ -121,58 +141,73 @@ __global__ void __launch_bounds__(kVecThreads)
 
 void launch_cg_update(const Topo &t, Reducer &R, const double *rho, const double *pw,
                       const double *p, const double *w, const double *dinv, double *x, double *r,
-                      double *z, double *rr, double *rz, const int *skip, cudaStream_t st) {
+                      double *z, double *rr, double *rz, const int *skip, cudaStream_t st,
+                      float *rc32, double *rc64) {
   OutPtrs<2> o{{rr, rz}};
   TraceScope ts("cg_update", t.N, st);
   cg_update_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, rho, pw, p, w, dinv, x, r, z,
-                                                           R.partials.p, R.counter.p, o, skip);
+                                                           R.partials.p, R.counter.p, o, skip,
+                                                           rc32, rc64);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
 
 // p = z + beta p with beta = num / den (Fletcher-Reeves: rz_new / rz_old) or
-// beta = -num / den (flexible: -<z,w> / <p,w>).
+// beta = -num / den (flexible: -<z,w> / <p,w>); z in FP64 or FP32.
+template <typename Tz>
 __global__ void __launch_bounds__(kVecThreads)
     cg_direction_kernel(int64_t n, const double *__restrict__ num, const double *__restrict__ den,
-                        double sign, const double *__restrict__ z, double *__restrict__ p,
+                        double sign, const Tz *__restrict__ z, double *__restrict__ p,
                         const int *__restrict__ skip) {
   if (skip && *skip) return;
   const double beta = sign * *num / *den;
   for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
        l += (int64_t)gridDim.x * blockDim.x)
-    p[l] = z[l] + beta * p[l];
+    p[l] = as_f64(z[l]) + beta * p[l];
 }
 
+template <typename Tz>
 void launch_cg_direction(int64_t n, const double *num, const double *den, double sign,
-                         const double *z, double *p, const int *skip, cudaStream_t st) {
+                         const Tz *z, double *p, const int *skip, cudaStream_t st) {
   TraceScope ts("cg_direction", 0, st);
-  cg_direction_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(n, num, den, sign, z, p, skip);
+  cg_direction_kernel<Tz><<<vec_grid(n), kVecThreads, 0, st>>>(n, num, den, sign, z, p, skip);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
+template void launch_cg_direction<double>(int64_t, const double *, const double *, double,
+                                          const double *, double *, const int *, cudaStream_t);
+template void launch_cg_direction<float>(int64_t, const double *, const double *, double,
+                                         const float *, double *, const int *, cudaStream_t);
 
-// Flexible CG after the preconditioner: zr = <z, r>, zw = <z, w> (w masked).
+// Flexible CG after the preconditioner: zr = <z, r>, zw = <z, w> (w masked);
+// z in FP64, or the FP32 output of the V-cycle (widened exactly).
+template <typename Tz>
 __global__ void __launch_bounds__(kVecThreads)
-    flex_dots_kernel(Topo t, const double *__restrict__ z, const double *__restrict__ r,
+    flex_dots_kernel(Topo t, const Tz *__restrict__ z, const double *__restrict__ r,
                      const double *__restrict__ w, double *partials, unsigned int *counter,
                      OutPtrs<2> out) {
   double acc[2] = {0.0, 0.0};
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
        l += gridDim.x * blockDim.x) {
     PointInfo q = point_info(l, t);
-    const double zl = scale_pow2_down(z[l], q.log2_mult);
+    const double zl = scale_pow2_down(as_f64(z[l]), q.log2_mult);
     acc[0] = fma(zl, r[l], acc[0]);
     acc[1] = fma(zl, w[l], acc[1]);
   }
   grid_reduce<2>(acc, partials, counter, out.p);
 }
 
-void launch_flex_dots(const Topo &t, Reducer &R, const double *z, const double *r,
-                      const double *w, double *zr, double *zw, cudaStream_t st) {
+template <typename Tz>
+void launch_flex_dots(const Topo &t, Reducer &R, const Tz *z, const double *r, const double *w,
+                      double *zr, double *zw, cudaStream_t st) {
   OutPtrs<2> o{{zr, zw}};
   TraceScope ts("flex_dots", t.N, st);
-  flex_dots_kernel<<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, z, r, w, R.partials.p,
-                                                           R.counter.p, o);
+  flex_dots_kernel<Tz><<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, z, r, w, R.partials.p,
+                                                               R.counter.p, o);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
+template void launch_flex_dots<double>(const Topo &, Reducer &, const double *, const double *,
+                                       const double *, double *, double *, cudaStream_t);
+template void launch_flex_dots<float>(const Topo &, Reducer &, const float *, const double *,
+                                      const double *, double *, double *, cudaStream_t);
 
 // <p, mask gs(w)> for a continuous masked p and w = A_L p unassembled: the
 // plain sum over local points (no weights, no gather); optional skip flag.
