@@ -162,6 +162,8 @@ struct AsmShape {
   static constexpr int PS = n * RS;                               // plane stride
   static constexpr int ES = n * PS;                               // element stride
   static constexpr int SR = (n + 3) / 4 * 4;                      // S row stride (16-byte rows)
+  // resident CTAs asked of the register allocator (about 20 warps per SM)
+  static constexpr int MIN_CTAS = (20 * 32 + THREADS - 1) / THREADS;
 };
 
 // n values of a padded shared row (16-byte aligned) into registers
@@ -202,11 +204,19 @@ __device__ __forceinline__ void pencil_mv(const T *M, const T (&in)[n], T (&out)
 
 // Local solves of every element: own points of K_e^{-1} R_e r into z, face
 // layers into ext[E][6][Np^2] (0: x-, 1: x+, 2: y-, 3: y+, 4: z-, 5: z+).
-// Shared memory per element: the extended data (rows padded against bank
-// conflicts) and S and S^T of the three directions with rows padded to whole
-// 16-byte vectors, so that a pencil thread reads a matrix row per vector load.
+// The separable inverse S (Lambda)^{-1} S^T is applied direction by
+// direction, z first and last: thread (a, b) gathers its pencil along c
+// straight from HBM into registers (consecutive threads read consecutive
+// points of a row, and a thread's loads are independent), transforms it and
+// leaves it in shared memory; y and x run on shared memory (with the
+// diagonal between the forward and backward x transforms); the backward z
+// transform returns each pencil to registers and stores it straight to z and
+// ext.  Shared memory per element: the extended data (rows padded against
+// bank conflicts) and S and S^T of the three directions with rows padded to
+// whole 16-byte vectors, so that a pencil thread reads a matrix row per
+// vector load.
 template <typename T, int NP>
-__global__ void __launch_bounds__(AsmShape<NP>::THREADS)
+__global__ void __launch_bounds__(AsmShape<NP>::THREADS, AsmShape<NP>::MIN_CTAS)
     asm_solve_kernel(Topo t, const T *__restrict__ S, const T *__restrict__ lam,
                      const T *__restrict__ r, T *__restrict__ z, T *__restrict__ ext) {
   using Sh = AsmShape<NP>;
@@ -222,54 +232,52 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS)
   for (int64_t e0 = (int64_t)blockIdx.x * NEL; e0 < t.E; e0 += (int64_t)gridDim.x * NEL) {
     const int64_t e = e0 + le;
     const bool active = e < t.E;
+    T v[n], o[n];
     if (active) {
       for (int k = pq; k < 3 * n * n; k += n2) {
         const int d = k / (n * n), a = (k / n) % n, m = k % n;
-        const T v = S[e * 3 * n * n + k];
-        sS[le][d][a * SR + m] = v;
-        sST[le][d][m * SR + a] = v;
+        const T sv = S[e * 3 * n * n + k];
+        sS[le][d][a * SR + m] = sv;
+        sST[le][d][m * SR + a] = sv;
       }
       for (int k = pq; k < 3 * n; k += n2) sL[le][k / n][k % n] = lam[e * 3 * n + k];
       const int ix = (int)(e % t.ex), iy = (int)((e / t.ex) % t.ey),
                 iz = (int)(e / ((int64_t)t.ex * t.ey));
       const int64_t exy = (int64_t)t.ex * t.ey;
-      // face neighbours (or -1): x-, x+, y-, y+, z-, z+
-      const int64_t nb[6] = {ix > 0 ? e - 1 : -1, ix < t.ex - 1 ? e + 1 : -1,
-                             iy > 0 ? e - t.ex : -1, iy < t.ey - 1 ? e + t.ex : -1,
-                             iz > 0 ? e - exy : -1, iz < t.ez - 1 ? e + exy : -1};
-      // gather: thread (b = p, c = q) takes the pencil along a; extended
-      // points outside the element in two directions carry no data
-      const int bi = p - 1, ci = q - 1;
-      const bool bown = bi >= 0 && bi <= N, cown = ci >= 0 && ci <= N;
+      // face neighbours (or -1), scalars so that no local array is indexed
+      const int64_t nxm = ix > 0 ? e - 1 : -1, nxp = ix < t.ex - 1 ? e + 1 : -1;
+      const int64_t nym = iy > 0 ? e - t.ex : -1, nyp = iy < t.ey - 1 ? e + t.ex : -1;
+      const int64_t nzm = iz > 0 ? e - exy : -1, nzp = iz < t.ez - 1 ? e + exy : -1;
+      // gather the pencil (a = p, b = q) along c; extended points outside
+      // the element in two directions carry no data
+      const int ai = p - 1, bi = q - 1;
+      const bool aown = ai >= 0 && ai <= N, bown = bi >= 0 && bi <= N;
 #pragma unroll
-      for (int a = 0; a < n; ++a) {
-        const int ai = a - 1;
-        const bool aown = ai >= 0 && ai <= N;
+      for (int c = 0; c < n; ++c) {
+        const int ci = c - 1;
+        const bool cown = ci >= 0 && ci <= N;
         int64_t src = -1;
         if (aown && bown && cown) {
           src = e * t.Np3 + ai + NP * (bi + NP * ci);
         } else if (!aown && bown && cown) {
-          const int64_t f = nb[ai < 0 ? 0 : 1];
+          const int64_t f = ai < 0 ? nxm : nxp;
           if (f >= 0) src = f * t.Np3 + (ai < 0 ? N - 1 : 1) + NP * (bi + NP * ci);
         } else if (aown && !bown && cown) {
-          const int64_t f = nb[bi < 0 ? 2 : 3];
+          const int64_t f = bi < 0 ? nym : nyp;
           if (f >= 0) src = f * t.Np3 + ai + NP * ((bi < 0 ? N - 1 : 1) + NP * ci);
         } else if (aown && bown && !cown) {
-          const int64_t f = nb[ci < 0 ? 4 : 5];
+          const int64_t f = ci < 0 ? nzm : nzp;
           if (f >= 0) src = f * t.Np3 + ai + NP * (bi + NP * (ci < 0 ? N - 1 : 1));
         }
-        U[q * PS + p * RS + a] = src >= 0 ? r[src] : (T)0;
+        v[c] = src >= 0 ? r[src] : (T)0;
       }
     }
     __syncthreads();
-    T v[n], o[n];
-    // x: (Sx^T u) along a, thread (b = p, c = q)
+    // z: (Sz^T u) along c, thread (a = p, b = q)
     if (active) {
+      pencil_mv<T, n, SR>(sST[le][2], v, o);
 #pragma unroll
-      for (int a = 0; a < n; ++a) v[a] = U[q * PS + p * RS + a];
-      pencil_mv<T, n, SR>(sST[le][0], v, o);
-#pragma unroll
-      for (int m = 0; m < n; ++m) U[q * PS + p * RS + m] = o[m];
+      for (int m = 0; m < n; ++m) U[m * PS + q * RS + p] = o[m];
     }
     __syncthreads();
     // y: thread (a = p, c = q)
@@ -281,17 +289,17 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS)
       for (int m = 0; m < n; ++m) U[q * PS + m * RS + p] = o[m];
     }
     __syncthreads();
-    // z, diagonal solve, z back: thread (a = p, b = q)
+    // x, diagonal solve, x back: thread (b = p, c = q)
     if (active) {
 #pragma unroll
-      for (int c = 0; c < n; ++c) v[c] = U[c * PS + q * RS + p];
-      pencil_mv<T, n, SR>(sST[le][2], v, o);
-      const T lxy = sL[le][0][p] + sL[le][1][q];
+      for (int a = 0; a < n; ++a) v[a] = U[q * PS + p * RS + a];
+      pencil_mv<T, n, SR>(sST[le][0], v, o);
+      const T lyz = sL[le][1][p] + sL[le][2][q];
 #pragma unroll
-      for (int m = 0; m < n; ++m) o[m] = o[m] / (lxy + sL[le][2][m]);
-      pencil_mv<T, n, SR>(sS[le][2], o, v);
+      for (int m = 0; m < n; ++m) o[m] = o[m] / (sL[le][0][m] + lyz);
+      pencil_mv<T, n, SR>(sS[le][0], o, v);
 #pragma unroll
-      for (int c = 0; c < n; ++c) U[c * PS + q * RS + p] = v[c];
+      for (int a = 0; a < n; ++a) U[q * PS + p * RS + a] = v[a];
     }
     __syncthreads();
     // y back: thread (a = p, c = q)
@@ -303,24 +311,24 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS)
       for (int b = 0; b < n; ++b) U[q * PS + b * RS + p] = o[b];
     }
     __syncthreads();
-    // x back and output: thread (b = p, c = q)
+    // z back and output: thread (a = p, b = q); own points to z, the face
+    // layers to ext (rows of consecutive threads are consecutive points)
     if (active) {
 #pragma unroll
-      for (int m = 0; m < n; ++m) v[m] = U[q * PS + p * RS + m];
-      pencil_mv<T, n, SR>(sS[le][0], v, o);
-      const bool bown = p >= 1 && p <= N + 1, cown = q >= 1 && q <= N + 1;
+      for (int m = 0; m < n; ++m) v[m] = U[m * PS + q * RS + p];
+      pencil_mv<T, n, SR>(sS[le][2], v, o);
+      const bool aown = p >= 1 && p <= N + 1, bown = q >= 1 && q <= N + 1;
 #pragma unroll
-      for (int a = 0; a < n; ++a) {
-        const T s = o[a];
-        const bool aown = a >= 1 && a <= N + 1;
+      for (int c = 0; c < n; ++c) {
+        const bool cown = c >= 1 && c <= N + 1;
         if (aown && bown && cown) {
-          z[e * t.Np3 + (a - 1) + NP * ((p - 1) + NP * (q - 1))] = s;
+          z[e * t.Np3 + (p - 1) + NP * ((q - 1) + NP * (c - 1))] = o[c];
         } else if (!aown && bown && cown) {
-          ext[(e * 6 + (a == 0 ? 0 : 1)) * NP2 + (p - 1) + NP * (q - 1)] = s;
+          ext[(e * 6 + (p == 0 ? 0 : 1)) * NP2 + (q - 1) + NP * (c - 1)] = o[c];
         } else if (aown && !bown && cown) {
-          ext[(e * 6 + (p == 0 ? 2 : 3)) * NP2 + (a - 1) + NP * (q - 1)] = s;
+          ext[(e * 6 + (q == 0 ? 2 : 3)) * NP2 + (p - 1) + NP * (c - 1)] = o[c];
         } else if (aown && bown && !cown) {
-          ext[(e * 6 + (q == 0 ? 4 : 5)) * NP2 + (a - 1) + NP * (p - 1)] = s;
+          ext[(e * 6 + (c == 0 ? 4 : 5)) * NP2 + (p - 1) + NP * (q - 1)] = o[c];
         }
       }
     }
