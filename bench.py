@@ -60,14 +60,17 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # (152 SMs x 128 lanes x 2.07 GHz) / 12 x 2 flop.
 PAIR_INSTR_PER_FMA = 12
 PAIR_PEAK_TFLOPS = 152 * 128 * 2.07e9 / PAIR_INSTR_PER_FMA * 2 / 1e12
-# DRAM traffic of one fine-level FP64 operator launch per local point, from an
-# ncu capture (profiles/ax_f64pair_N7.md), valid while the source is unchanged.
-AX_TRAFFIC = {"source_sha256": "ab9460908abee14bcf8f1dbe80d2dc039a0c47229b82a9a9bf9600553313fc7e",
-              "bytes_per_point": 62.66}
+# DRAM traffic of one fine-level FP64 operator launch per local point (the
+# form with the inner product folded in, as in the solve), from an ncu capture
+# (profiles/ax_f64pair_N7.md), valid while the kernel source is unchanged.
+AX_TRAFFIC = {"source_sha256": "6b16e73cafe6141d70ec23adcdb0a12c84ac3600ad31a9b52760e2140cf8883b",
+              "bytes_per_point": 63.38}
 # The same for the smoother's assembled FP32 operator, per factor storage
 # (profiles/ax32_N7.md), valid while ax32.cu is unchanged.
-AX32_TRAFFIC = {"f32": {"source_sha256": "96ad60531a1434a15ae2780ab6df1fc9c571104c512dfcfc17cc2c8dbfebbf60", "bytes_per_point": 31.40},
-                "f16": {"source_sha256": "96ad60531a1434a15ae2780ab6df1fc9c571104c512dfcfc17cc2c8dbfebbf60", "bytes_per_point": 18.82}}
+AX32_TRAFFIC = {"f32": {"source_sha256": "a05f39842a571c47ccd5c85e39af88796248883280ea63e826d9b2a0dcc1d11e",
+                        "bytes_per_point": 31.41},
+                "f16": {"source_sha256": "a05f39842a571c47ccd5c85e39af88796248883280ea63e826d9b2a0dcc1d11e",
+                        "bytes_per_point": 18.81}}
 
 
 def parse_args():
@@ -198,9 +201,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def source_sha(name):
-    with open(os.path.join(ROOT, "paper_2110_01716_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+def source_sha(*names):
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2110_01716_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def operator_sweep(sem, torch, dev, hbm):
@@ -526,7 +532,7 @@ def main():
     flops_pt = 12 * (ORDER + 1) + 15
     ax_tflops = nl * flops_pt / (ax_ms / 1e3) / 1e12 if ax_ms > 0 else None
     traffic64 = None
-    if AX_TRAFFIC["source_sha256"] == source_sha("ax_pair.cu") and AX_TRAFFIC["bytes_per_point"]:
+    if AX_TRAFFIC["source_sha256"] == source_sha("pair.cuh") and AX_TRAFFIC["bytes_per_point"]:
         traffic64 = AX_TRAFFIC["bytes_per_point"] * nl
     roof64 = {"bound": "alu", "achieved": ax_tflops, "peak": PAIR_PEAK_TFLOPS,
               "unit": "TFLOP/s", "frac": (ax_tflops / PAIR_PEAK_TFLOPS) if ax_tflops else None,
