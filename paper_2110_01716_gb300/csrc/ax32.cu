@@ -77,11 +77,19 @@ struct L32 {
 #endif
   // factors staged in shared memory too (else read from global, L2-prefetched)
   static constexpr bool SG = S::STAGED && (GK != 0 || SEM_AX32_STAGE_F32G);
+#ifndef SEM_AX32_F32G_SINGLE
+#define SEM_AX32_F32G_SINGLE 1
+#endif
+  // FP32 factors in one stage of their own, refilled for the next chunk as
+  // soon as the gradient phase has read them (two CTAs per SM still fit)
+  static constexpr bool SGS = S::STAGED && !SG && GK == 0 && SEM_AX32_F32G_SINGLE;
   static constexpr int STAGE = round16(U_BYTES) + (SG ? round16(G_BYTES) : 0);
-  static constexpr int MBAR = 0;                                      // 2 x 8 bytes
-  static constexpr int STAGES = S::STAGED ? 16 : 16;
+  static constexpr int MBAR = 0;                                      // 3 x 8 bytes
+  static constexpr int STAGES = 32;
   static constexpr int STAGES_END = S::STAGED ? STAGES + 2 * STAGE : STAGES;
-  static constexpr int DTAB = STAGES_END;                             // sD, sDT
+  static constexpr int GSTAGE = STAGES_END;                           // single factor stage
+  static constexpr int GSTAGE_END = GSTAGE + (SGS ? round16(G_BYTES) : 0);
+  static constexpr int DTAB = GSTAGE_END;                             // sD, sDT
   static constexpr int UN = DTAB + round16(2 * NP * S::RS * 4);       // direct: padded natural u
   static constexpr int UN_END = S::STAGED ? UN : UN + S::NE * S::ES * 4;
   static constexpr int UT = UN_END;                                   // transposed u
@@ -207,6 +215,7 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
   if (STAGED && threadIdx.x == 0) {
     mbar_init(smem_addr(&mbar[0]), 1);
     mbar_init(smem_addr(&mbar[1]), 1);
+    mbar_init(smem_addr(&mbar[2]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -232,14 +241,29 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
     if (Lay::SG)
       bulk_g2s(smem_addr(dst + round16(Lay::U_BYTES)),
                static_cast<const unsigned char *>(a.G) + e0 * 6 * NP3 * Lay::GB, gb, bar);
-    else
+    else if (!Lay::SGS)
       prefetch_l2(static_cast<const unsigned char *>(a.G) + e0 * 6 * NP3 * Lay::GB, gb);
+  };
+  // Bulk copy of a chunk's FP32 factors into the single factor stage.
+  auto issue_g = [&](int64_t unit, int cx) {
+    const int ix1 = min(t.ex, unit_ix0(a, unit) + a.seg_len);
+    const int n = min(NE, ix1 - cx);
+    const int64_t e0 = (unit / a.nseg) * t.ex + cx;
+    const uint32_t gb = (uint32_t)(n * 6 * NP3 * Lay::GB);
+    const uint32_t bar = smem_addr(&mbar[2]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, gb);
+    bulk_g2s(smem_addr(smem + Lay::GSTAGE),
+             static_cast<const unsigned char *>(a.G) + e0 * 6 * NP3 * Lay::GB, gb, bar);
   };
 
   int64_t unit = blockIdx.x;
   int cx = unit < units ? unit_ix0(a, unit) : 0;
   uint32_t g = 0;  // chunks done by this CTA (stage g & 1, phase parity (g >> 1) & 1)
-  if (STAGED && threadIdx.x == 0 && unit < units) issue(unit, cx, 0);
+  if (STAGED && threadIdx.x == 0 && unit < units) {
+    issue(unit, cx, 0);
+    if constexpr (Lay::SGS) issue_g(unit, cx);
+  }
 
   while (unit < units) {
     const int64_t line = unit / a.nseg;
@@ -261,7 +285,8 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
     const GT *stG = nullptr;
     if constexpr (STAGED) {
       if (threadIdx.x == 0 && nunit < units) issue(nunit, ncx, (g + 1) & 1);
-      const bool ok = mbar_wait(smem_addr(&mbar[g & 1]), (g >> 1) & 1, kMbarWaitLimit);
+      bool ok = mbar_wait(smem_addr(&mbar[g & 1]), (g >> 1) & 1, kMbarWaitLimit);
+      if constexpr (Lay::SGS) ok = mbar_wait(smem_addr(&mbar[2]), g & 1, kMbarWaitLimit) && ok;
       if (__syncthreads_or(!ok)) {
         // a copy never completed: record it, let copies in flight land, stop
         if (threadIdx.x == 0) {
@@ -269,13 +294,15 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
           mbar_wait(smem_addr(&mbar[g & 1]), (g >> 1) & 1, kMbarWaitLimit);
           if (nunit < units) mbar_wait(smem_addr(&mbar[(g + 1) & 1]), ((g + 1) >> 1) & 1,
                                        kMbarWaitLimit);
+          if (Lay::SGS) mbar_wait(smem_addr(&mbar[2]), g & 1, kMbarWaitLimit);
         }
         __syncthreads();
         return;
       }
       const unsigned char *stage = smem + Lay::STAGES + (g & 1) * Lay::STAGE;
       stU = reinterpret_cast<const float *>(stage) + le * NP3;
-      stG = reinterpret_cast<const GT *>(stage + round16(Lay::U_BYTES)) + le * 6 * NP3;
+      if constexpr (Lay::SGS) stG = reinterpret_cast<const GT *>(smem + Lay::GSTAGE) + le * 6 * NP3;
+      else stG = reinterpret_cast<const GT *>(stage + round16(Lay::U_BYTES)) + le * 6 * NP3;
     } else if (threadIdx.x == 0 && nunit < units) {
       const int64_t ne0 = (nunit / a.nseg) * t.ex + ncx;
       const int nn = min(NE, min(t.ex, unit_ix0(a, nunit) + a.seg_len) - ncx);
@@ -338,7 +365,7 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
         float g6[6];
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
-          if constexpr (Lay::SG) g6[f] = factor_value<GK>(stG[f * NP3 + k * NP2 + ij]);
+          if constexpr (Lay::SG || Lay::SGS) g6[f] = factor_value<GK>(stG[f * NP3 + k * NP2 + ij]);
           else g6[f] = factor_value<GK>(__ldg(Gg + f * NP3 + k * NP2));
         }
         wR[k * NPL + j * NRS + i] = g6[0] * ur + g6[1] * us + g6[2] * ut;
@@ -347,6 +374,9 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
       }
     }
     __syncthreads();
+    // the factor stage is free: bring in the next chunk's factors
+    if constexpr (Lay::SGS)
+      if (threadIdx.x == 0 && nunit < units) issue_g(nunit, ncx);
     // ---- divergence: w = scale * (D_r^T wr + D_s^T ws + D_t^T wt)
     if (active) {
       float DTr[NP], DTs[NP];
