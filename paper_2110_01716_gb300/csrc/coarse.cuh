@@ -9,28 +9,31 @@ namespace sem {
 
 constexpr int kMgMaxLevels = 8;
 
-struct MgLevelDev {
+// One level of the coarse-lattice multigrid, in the arithmetic T.
+template <typename T>
+struct MgLevelT {
   int nx, ny, nz, n;
   FastDiv div_nx, div_nxy;
-  const double *S;     // [27][n] stencil (Dirichlet rows/unknowns eliminated via dinv/mask)
-  const double *dinv;  // [n] 0 on Dirichlet nodes
+  const T *S;     // [27][n] stencil (Dirichlet rows/unknowns eliminated via dinv/mask)
+  const T *dinv;  // [n] 0 on Dirichlet nodes
   const unsigned char *keep;  // [n] 1 for unknowns, 0 for Dirichlet nodes
-  double *x, *b, *r, *w, *da, *db;
-  double inv_theta, c1, c2;  // Chebyshev degree-2 coefficients
+  T *x, *b, *r, *da, *db;
+  T inv_theta, c1, c2;  // Chebyshev degree-2 coefficients
   // 1D transfer tables (this level -> next coarser): prolongation rows of the
   // fine indices (2 entries, index -1 = none), restriction rows of the coarse
   // indices (3 entries).
   const int *pi[3];
-  const double *pw[3];
+  const T *pw[3];
   const int *ri[3];
-  const double *rw[3];
+  const T *rw[3];
 };
 
 struct MgArgs {
   int nlev;
   int small_from;  // first level run by one CTA (nlev - 1: the bottom only)
-  MgLevelDev L[kMgMaxLevels];
-  const double *bottom_inv;
+  MgLevelT<double> L0;              // level 0 in FP64: the flexible CG's operator
+  MgLevelT<float> V[kMgMaxLevels];  // the V-cycle (the preconditioner) in FP32
+  const float *bottom_inv;
   int nbottom;
   int ex, ey, ez, bc;
   FastDiv div_ex, div_ey;
@@ -46,7 +49,7 @@ struct MgArgs {
 // Multigrid hierarchy of the coarse lattice (coarse_mg.cu).
 struct CoarseMg {
   MgArgs args{};
-  DevBuf<double> dbuf;
+  DevBuf<float> fbuf;
   DevBuf<int> ibuf;
   DevBuf<unsigned char> kbuf;
   DevBuf<double> part;

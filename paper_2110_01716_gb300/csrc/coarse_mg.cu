@@ -37,7 +37,8 @@ constexpr int kMgThreads = 256;
 #endif
 constexpr int kMgMaxBottom = SEM_MG_MAX_BOTTOM;  // unknowns of the dense bottom level
 
-__device__ __forceinline__ void mg_coords(const MgLevelDev &L, int g, int &gx, int &gy, int &gz) {
+template <typename T>
+__device__ __forceinline__ void mg_coords(const MgLevelT<T> &L, int g, int &gx, int &gy, int &gz) {
   const uint32_t u = (uint32_t)g;
   gz = (int)L.div_nxy.div(u);
   const uint32_t rem = u - (uint32_t)gz * (uint32_t)(L.nx * L.ny);
@@ -48,14 +49,15 @@ __device__ __forceinline__ void mg_coords(const MgLevelDev &L, int g, int &gx, i
 // (A v)_g of the 27-point stencil.  The neighbour tests come first and every
 // load is a select on its own test, so the loads of all 27 neighbours are in
 // flight together (a load is issued only for a neighbour inside the lattice).
-__device__ __forceinline__ double mg_apply(const MgLevelDev &L, int g, const double *__restrict__ v) {
-  if (!L.keep[g]) return 0.0;
+template <typename T>
+__device__ __forceinline__ T mg_apply(const MgLevelT<T> &L, int g, const T *__restrict__ v) {
+  if (!L.keep[g]) return (T)0;
   int gx, gy, gz;
   mg_coords(L, g, gx, gy, gz);
   const bool in_x[3] = {gx > 0, true, gx < L.nx - 1};
   const bool in_y[3] = {gy > 0, true, gy < L.ny - 1};
   const bool in_z[3] = {gz > 0, true, gz < L.nz - 1};
-  double sv[27], vv[27];
+  T sv[27], vv[27];
 #pragma unroll
   for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
@@ -64,10 +66,10 @@ __device__ __forceinline__ double mg_apply(const MgLevelDev &L, int g, const dou
       for (int dx = -1; dx <= 1; ++dx) {
         const int d = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
         const bool ok = in_x[dx + 1] && in_y[dy + 1] && in_z[dz + 1];
-        sv[d] = ok ? L.S[(int64_t)d * L.n + g] : 0.0;
-        vv[d] = ok ? v[g + dx + L.nx * (dy + L.ny * dz)] : 0.0;
+        sv[d] = ok ? L.S[(int64_t)d * L.n + g] : (T)0;
+        vv[d] = ok ? v[g + dx + L.nx * (dy + L.ny * dz)] : (T)0;
       }
-  double acc = 0.0;
+  T acc = 0;
 #pragma unroll
   for (int d = 0; d < 27; ++d) acc = fma(sv[d], vv[d], acc);
   return acc;
@@ -129,38 +131,37 @@ struct CtaBarrier {
 // barrier; a barrier precedes every phase that reads neighbours or another
 // level.
 template <typename Bar>
-__device__ void mg_down(const MgArgs &A, int l, const double *__restrict__ b0,
-                        double *__restrict__ x0, Bar bar, int tid, int nth) {
-  const MgLevelDev &L = A.L[l];
-  const double *b = l == 0 ? b0 : L.b;
-  double *x = l == 0 ? x0 : L.x;
+__device__ void mg_down(const MgArgs &A, int l, Bar bar, int tid, int nth) {
+  const MgLevelT<float> &L = A.V[l];
+  const float *b = L.b;
+  float *x = L.x;
   for (int g = tid; g < L.n; g += nth) {
-    const double rg = b[g];
+    const float rg = b[g];
     L.r[g] = rg;
-    const double d = L.dinv[g] * rg * L.inv_theta;
+    const float d = L.dinv[g] * rg * L.inv_theta;
     L.da[g] = d;
     x[g] = d;
   }
   bar();
   for (int g = tid; g < L.n; g += nth) {
-    const double rg = L.r[g] - mg_apply(L, g, L.da);
+    const float rg = L.r[g] - mg_apply(L, g, L.da);
     L.r[g] = rg;
-    const double d = L.c1 * L.da[g] + L.c2 * L.dinv[g] * rg;
+    const float d = L.c1 * L.da[g] + L.c2 * L.dinv[g] * rg;
     L.db[g] = d;
     x[g] += d;
   }
   bar();
   for (int g = tid; g < L.n; g += nth) L.r[g] = b[g] - mg_apply(L, g, x);
   bar();
-  const MgLevelDev &C = A.L[l + 1];
+  const MgLevelT<float> &C = A.V[l + 1];
   for (int G = tid; G < C.n; G += nth) {
-    double acc = 0.0;
+    float acc = 0.f;
     if (C.keep[G]) {
       int Gx, Gy, Gz;
       mg_coords(C, G, Gx, Gy, Gz);
       // table rows first (index -1: no fine point), then guarded loads
       int fi[3][3];
-      double fw[3][3];
+      float fw[3][3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         fi[0][c] = L.ri[0][3 * Gx + c];
@@ -170,7 +171,7 @@ __device__ void mg_down(const MgArgs &A, int l, const double *__restrict__ b0,
         fw[1][c] = L.rw[1][3 * Gy + c];
         fw[2][c] = L.rw[2][3 * Gz + c];
       }
-      double rv[27];
+      float rv[27];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -178,13 +179,13 @@ __device__ void mg_down(const MgArgs &A, int l, const double *__restrict__ b0,
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             const bool ok = fi[2][c] >= 0 && fi[1][b2] >= 0 && fi[0][a] >= 0;
-            rv[a + 3 * (b2 + 3 * c)] = ok ? L.r[fi[0][a] + L.nx * (fi[1][b2] + L.ny * fi[2][c])] : 0.0;
+            rv[a + 3 * (b2 + 3 * c)] = ok ? L.r[fi[0][a] + L.nx * (fi[1][b2] + L.ny * fi[2][c])] : 0.f;
           }
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int b2 = 0; b2 < 3; ++b2) {
-          const double wyz = fw[2][c] * fw[1][b2];
+          const float wyz = fw[2][c] * fw[1][b2];
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             const bool ok = fi[2][c] >= 0 && fi[1][b2] >= 0 && fi[0][a] >= 0;
@@ -199,15 +200,12 @@ __device__ void mg_down(const MgArgs &A, int l, const double *__restrict__ b0,
 
 // The bottom: dense inverse, one row per thread.
 template <typename Bar>
-__device__ void mg_bottom(const MgArgs &A, const double *__restrict__ b0, double *__restrict__ x0,
-                          Bar bar, int tid, int nth) {
-  const MgLevelDev &B = A.L[A.nlev - 1];
-  const double *b = A.nlev == 1 ? b0 : B.b;
-  double *x = A.nlev == 1 ? x0 : B.x;
+__device__ void mg_bottom(const MgArgs &A, Bar bar, int tid, int nth) {
+  const MgLevelT<float> &B = A.V[A.nlev - 1];
   for (int i = tid; i < A.nbottom; i += nth) {
-    double acc = 0.0;
-    for (int j = 0; j < A.nbottom; ++j) acc = fma(A.bottom_inv[(size_t)i * A.nbottom + j], b[j], acc);
-    x[i] = acc;
+    float acc = 0.f;
+    for (int j = 0; j < A.nbottom; ++j) acc = fmaf(A.bottom_inv[(size_t)i * A.nbottom + j], B.b[j], acc);
+    B.x[i] = acc;
   }
   bar();
 }
@@ -215,18 +213,17 @@ __device__ void mg_bottom(const MgArgs &A, const double *__restrict__ b0, double
 // Up the cycle at level l: prolongation and correction from level l + 1,
 // post-smoothing (r = b - A x; d = Dinv r / theta; x += d; one more step).
 template <typename Bar>
-__device__ void mg_up(const MgArgs &A, int l, const double *__restrict__ b0,
-                      double *__restrict__ x0, Bar bar, int tid, int nth) {
-  const MgLevelDev &L = A.L[l];
-  const MgLevelDev &C = A.L[l + 1];
-  const double *b = l == 0 ? b0 : L.b;
-  double *x = l == 0 ? x0 : L.x;
+__device__ void mg_up(const MgArgs &A, int l, Bar bar, int tid, int nth) {
+  const MgLevelT<float> &L = A.V[l];
+  const MgLevelT<float> &C = A.V[l + 1];
+  const float *b = L.b;
+  float *x = L.x;
   for (int g = tid; g < L.n; g += nth) {
     if (!L.keep[g]) continue;
     int gx, gy, gz;
     mg_coords(L, g, gx, gy, gz);
     int ci[3][2];
-    double cw[3][2];
+    float cw[3][2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       ci[0][c] = L.pi[0][2 * gx + c];
@@ -236,7 +233,7 @@ __device__ void mg_up(const MgArgs &A, int l, const double *__restrict__ b0,
       cw[1][c] = L.pw[1][2 * gy + c];
       cw[2][c] = L.pw[2][2 * gz + c];
     }
-    double xv[8];
+    float xv[8];
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -244,14 +241,14 @@ __device__ void mg_up(const MgArgs &A, int l, const double *__restrict__ b0,
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
           const bool ok = ci[2][c] >= 0 && ci[1][b2] >= 0 && ci[0][a] >= 0;
-          xv[a + 2 * (b2 + 2 * c)] = ok ? C.x[ci[0][a] + C.nx * (ci[1][b2] + C.ny * ci[2][c])] : 0.0;
+          xv[a + 2 * (b2 + 2 * c)] = ok ? C.x[ci[0][a] + C.nx * (ci[1][b2] + C.ny * ci[2][c])] : 0.f;
         }
-    double acc = 0.0;
+    float acc = 0.f;
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
       for (int b2 = 0; b2 < 2; ++b2) {
-        const double wyz = cw[2][c] * cw[1][b2];
+        const float wyz = cw[2][c] * cw[1][b2];
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
           const bool ok = ci[2][c] >= 0 && ci[1][b2] >= 0 && ci[0][a] >= 0;
@@ -264,49 +261,54 @@ __device__ void mg_up(const MgArgs &A, int l, const double *__restrict__ b0,
   for (int g = tid; g < L.n; g += nth) L.r[g] = b[g] - mg_apply(L, g, x);
   bar();
   for (int g = tid; g < L.n; g += nth) {
-    const double d = L.dinv[g] * L.r[g] * L.inv_theta;
+    const float d = L.dinv[g] * L.r[g] * L.inv_theta;
     L.da[g] = d;
     x[g] += d;
   }
   bar();
   for (int g = tid; g < L.n; g += nth) {
-    const double rg = L.r[g] - mg_apply(L, g, L.da);
+    const float rg = L.r[g] - mg_apply(L, g, L.da);
     L.r[g] = rg;
-    const double d = L.c1 * L.da[g] + L.c2 * L.dinv[g] * rg;
+    const float d = L.c1 * L.da[g] + L.c2 * L.dinv[g] * rg;
     x[g] += d;
   }
   bar();
 }
 
-// One V(2,2) cycle: level-0 right-hand side b0, result x0 (both level-0
-// vectors, b0 read only).  Levels from A.small_from down (and the bottom) run
-// in CTA 0 alone with CTA barriers while the other CTAs wait at one grid
-// barrier.
+// One V(2,2) cycle in FP32 (the preconditioner of the FP64 flexible CG):
+// level-0 right-hand side b0, result x0 (both FP64 level-0 vectors, b0 read
+// only; converted on the way in and out).  Levels from A.small_from down (and
+// the bottom) run in CTA 0 alone with CTA barriers while the other CTAs wait
+// at one grid barrier.
 __device__ void mg_vcycle(const MgArgs &A, const double *__restrict__ b0, double *__restrict__ x0,
                           cg::grid_group &grid, int tid, int nth) {
   const GridBarrier gb{&grid};
   const int ls = A.small_from;  // first level handled by CTA 0 (nlev - 1: the bottom only)
-  for (int l = 0; l < ls; ++l) mg_down(A, l, b0, x0, gb, tid, nth);
+  const MgLevelT<float> &V0 = A.V[0];
+  for (int g = tid; g < V0.n; g += nth) V0.b[g] = (float)b0[g];
+  if (ls == 0) grid.sync();  // CTA 0 reads every node of level 0
+  for (int l = 0; l < ls; ++l) mg_down(A, l, gb, tid, nth);
   if (ls == A.nlev - 1 && A.nbottom > (int)blockDim.x) {
-    mg_bottom(A, b0, x0, gb, tid, nth);  // a large bottom: rows across the grid
+    mg_bottom(A, gb, tid, nth);  // a large bottom: rows across the grid
   } else {
     if (blockIdx.x == 0) {
       const CtaBarrier cb;
       const int t = threadIdx.x, n = blockDim.x;
-      for (int l = ls; l < A.nlev - 1; ++l) mg_down(A, l, b0, x0, cb, t, n);
-      mg_bottom(A, b0, x0, cb, t, n);
-      for (int l = A.nlev - 2; l >= ls; --l) mg_up(A, l, b0, x0, cb, t, n);
+      for (int l = ls; l < A.nlev - 1; ++l) mg_down(A, l, cb, t, n);
+      mg_bottom(A, cb, t, n);
+      for (int l = A.nlev - 2; l >= ls; --l) mg_up(A, l, cb, t, n);
     }
     grid.sync();
   }
-  for (int l = ls - 1; l >= 0; --l) mg_up(A, l, b0, x0, gb, tid, nth);
+  for (int l = ls - 1; l >= 0; --l) mg_up(A, l, gb, tid, nth);
+  for (int g = tid; g < V0.n; g += nth) x0[g] = (double)V0.x[g];
 }
 
 __global__ void __launch_bounds__(kMgThreads) coarse_mgcg_kernel(MgArgs A) {
   cg::grid_group grid = cg::this_grid();
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
-  const MgLevelDev &L0 = A.L[0];
+  const MgLevelT<double> &L0 = A.L0;
   // right-hand side to unique layout (owner copy), x = 0
   double v1[1] = {0.0};
   for (int g = tid; g < L0.n; g += nth) {
@@ -628,91 +630,104 @@ void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st) {
   }
   // Chebyshev bounds (smoothed levels)
   for (size_t l = 0; l + 1 < H.size(); ++l) H[l].lam_hi = 1.1 * power_lambda(H[l]);
-  // Device buffers.  Every array carved out of the three buffers starts on a
-  // 256-byte boundary: the unrolled gathers read neighbouring table entries,
-  // which the compiler may merge into vector loads that need that alignment.
+  // Device buffers of the FP32 V-cycle.  Every array carved out of the three
+  // buffers starts on a 256-byte boundary: the unrolled gathers read
+  // neighbouring table entries, which the compiler may merge into vector
+  // loads that need that alignment.
   auto up = [](size_t n, size_t q) { return (n + q - 1) / q * q; };
   const int nlev = (int)H.size();
-  size_t dbl = up((size_t)nb * nb, 32), ints = 0;
+  size_t flt = up((size_t)nb * nb, 64), ints = 0;
   for (int l = 0; l < nlev; ++l) {
-    dbl += up((size_t)27 * H[l].n, 32) + up(H[l].n, 32) + (l == 0 ? 4 : 6) * up(H[l].n, 32);
+    flt += up((size_t)27 * H[l].n, 64) + 6 * up(H[l].n, 64);
     if (l + 1 < nlev)
       for (int d = 0; d < 3; ++d) {
-        dbl += up(PW[d][l].size(), 32) + up(RW[d][l].size(), 32);
+        flt += up(PW[d][l].size(), 64) + up(RW[d][l].size(), 64);
         ints += up(PI[d][l].size(), 64) + up(RI[d][l].size(), 64);
       }
   }
   size_t keeps = 0;
   for (int l = 0; l < nlev; ++l) keeps += up(H[l].n, 256);
-  M->dbuf.alloc(dbl);
+  M->fbuf.alloc(flt);
   M->ibuf.alloc(ints > 0 ? ints : 1);
   M->kbuf.alloc(keeps);
-  std::vector<double> hd(dbl, 0.0);
+  std::vector<float> hf(flt, 0.f);
   std::vector<int> hi(ints > 0 ? ints : 1, -1);
   std::vector<unsigned char> hk(keeps, 0);
-  size_t od = 0, oi = 0, ok = 0;
+  size_t of = 0, oi = 0, ok = 0;
+  auto put = [&](const std::vector<double> &v) {  // FP32 copy (rounded to nearest)
+    for (size_t q = 0; q < v.size(); ++q) hf[of + q] = (float)v[q];
+    const float *dst = M->fbuf.p + of;
+    of += up(v.size(), 64);
+    return dst;
+  };
+  auto vec = [&](int n) {
+    float *dst = M->fbuf.p + of;
+    of += up(n, 64);
+    return dst;
+  };
   MgArgs &A = M->args;
   std::memset(&A, 0, sizeof(A));
   A.nlev = nlev;
   for (int l = 0; l < nlev; ++l) {
     const HostLevel &L = H[l];
-    MgLevelDev &D = A.L[l];
+    MgLevelT<float> &D = A.V[l];
     D.nx = L.nx; D.ny = L.ny; D.nz = L.nz; D.n = L.n;
     D.div_nx = FastDiv((uint32_t)L.nx);
     D.div_nxy = FastDiv((uint32_t)(L.nx * L.ny));
-    const size_t nv = up(L.n, 32);
-    std::copy(L.S.begin(), L.S.end(), hd.begin() + od);
-    D.S = M->dbuf.p + od; od += up(L.S.size(), 32);
-    std::copy(L.dinv.begin(), L.dinv.end(), hd.begin() + od);
-    D.dinv = M->dbuf.p + od; od += nv;
+    D.S = put(L.S);
+    D.dinv = put(L.dinv);
     std::copy(L.keep.begin(), L.keep.end(), hk.begin() + ok);
     D.keep = M->kbuf.p + ok; ok += up(L.n, 256);
-    if (l > 0) { D.x = M->dbuf.p + od; od += nv; D.b = M->dbuf.p + od; od += nv; }
-    D.r = M->dbuf.p + od; od += nv;
-    D.w = M->dbuf.p + od; od += nv;
-    D.da = M->dbuf.p + od; od += nv;
-    D.db = M->dbuf.p + od; od += nv;
+    D.x = vec(L.n);
+    D.b = vec(L.n);
+    D.r = vec(L.n);
+    D.da = vec(L.n);
+    D.db = vec(L.n);
     if (l + 1 < nlev) {
       const double theta = 0.5 * (L.lam_hi + L.lam_hi / 10.0);
       const double delta = 0.5 * (L.lam_hi - L.lam_hi / 10.0);
       const double sigma = theta / delta, rho0 = 1.0 / sigma;
       const double rho1 = 1.0 / (2.0 * sigma - rho0);
-      D.inv_theta = 1.0 / theta;
-      D.c1 = rho1 * rho0;
-      D.c2 = 2.0 * rho1 / delta;
+      D.inv_theta = (float)(1.0 / theta);
+      D.c1 = (float)(rho1 * rho0);
+      D.c2 = (float)(2.0 * rho1 / delta);
       for (int d = 0; d < 3; ++d) {
         std::copy(PI[d][l].begin(), PI[d][l].end(), hi.begin() + oi);
         D.pi[d] = M->ibuf.p + oi; oi += up(PI[d][l].size(), 64);
         std::copy(RI[d][l].begin(), RI[d][l].end(), hi.begin() + oi);
         D.ri[d] = M->ibuf.p + oi; oi += up(RI[d][l].size(), 64);
-        std::copy(PW[d][l].begin(), PW[d][l].end(), hd.begin() + od);
-        D.pw[d] = M->dbuf.p + od; od += up(PW[d][l].size(), 32);
-        std::copy(RW[d][l].begin(), RW[d][l].end(), hd.begin() + od);
-        D.rw[d] = M->dbuf.p + od; od += up(RW[d][l].size(), 32);
+        D.pw[d] = put(PW[d][l]);
+        D.rw[d] = put(RW[d][l]);
       }
     }
   }
-  std::copy(inv.begin(), inv.end(), hd.begin() + od);
-  A.bottom_inv = M->dbuf.p + od; od += up(inv.size(), 32);
+  A.bottom_inv = put(inv);
   A.nbottom = nb;
+  // level 0 of the flexible CG in FP64: the coarse solver's own stencil and
+  // Jacobi inverse, the keep mask of the hierarchy
+  A.L0.nx = nx0; A.L0.ny = ny0; A.L0.nz = nz0; A.L0.n = n0;
+  A.L0.div_nx = A.V[0].div_nx;
+  A.L0.div_nxy = A.V[0].div_nxy;
+  A.L0.S = C.S.p;
+  A.L0.dinv = C.dinv.p;
+  A.L0.keep = A.V[0].keep;
 #ifndef SEM_MG_SMALL
 #define SEM_MG_SMALL 0
 #endif
   // levels of at most SEM_MG_SMALL unknowns run in one CTA
   A.small_from = nlev - 1;
   for (int l = 0; l < nlev - 1; ++l)
-    if (A.L[l].n <= SEM_MG_SMALL) {
+    if (A.V[l].n <= SEM_MG_SMALL) {
       A.small_from = l;
       break;
     }
-  SEM_REQUIRE(od <= dbl && oi <= hi.size() && ok <= keeps, "multigrid buffer layout overflow");
+  SEM_REQUIRE(of <= flt && oi <= hi.size() && ok <= keeps, "multigrid buffer layout overflow");
   // guard: every device array of the hierarchy is 256-byte aligned
   auto aligned = [](const void *p) { return ((uintptr_t)p & 255u) == 0; };
   for (int l = 0; l < nlev; ++l) {
-    const MgLevelDev &D = A.L[l];
+    const MgLevelT<float> &D = A.V[l];
     bool ok_al = aligned(D.S) && aligned(D.dinv) && aligned(D.keep) && aligned(D.r) &&
-                 aligned(D.w) && aligned(D.da) && aligned(D.db) && (l == 0 || (aligned(D.x) &&
-                                                                              aligned(D.b)));
+                 aligned(D.da) && aligned(D.db) && aligned(D.x) && aligned(D.b);
     if (l + 1 < nlev)
       for (int d = 0; d < 3; ++d)
         ok_al = ok_al && aligned(D.pi[d]) && aligned(D.pw[d]) && aligned(D.ri[d]) &&
@@ -720,13 +735,11 @@ void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st) {
     SEM_REQUIRE(ok_al, "multigrid arrays are not 256-byte aligned");
   }
   SEM_REQUIRE(aligned(A.bottom_inv), "multigrid arrays are not 256-byte aligned");
-  SEM_CHECK_CUDA(cudaMemcpyAsync(M->dbuf.p, hd.data(), hd.size() * sizeof(double),
+  SEM_CHECK_CUDA(cudaMemcpyAsync(M->fbuf.p, hf.data(), hf.size() * sizeof(float),
                                  cudaMemcpyHostToDevice, st));
   SEM_CHECK_CUDA(cudaMemcpyAsync(M->ibuf.p, hi.data(), hi.size() * sizeof(int),
                                  cudaMemcpyHostToDevice, st));
   SEM_CHECK_CUDA(cudaMemcpyAsync(M->kbuf.p, hk.data(), hk.size(), cudaMemcpyHostToDevice, st));
-  // the level-0 dinv comes from the coarse solver's unique-layout inverse
-  A.L[0].dinv = C.dinv.p;
   A.ex = Lv.t.ex; A.ey = Lv.t.ey; A.ez = Lv.t.ez; A.bc = Lv.t.bc;
   A.div_ex = FastDiv((uint32_t)Lv.t.ex);
   A.div_ey = FastDiv((uint32_t)Lv.t.ey);
