@@ -67,9 +67,9 @@ AX_TRAFFIC = {"source_sha256": "6b16e73cafe6141d70ec23adcdb0a12c84ac3600ad31a9b5
               "bytes_per_point": 63.38}
 # The same for the smoother's assembled FP32 operator, per factor storage
 # (profiles/ax32_N7.md), valid while ax32.cu is unchanged.
-AX32_TRAFFIC = {"f32": {"source_sha256": "a05f39842a571c47ccd5c85e39af88796248883280ea63e826d9b2a0dcc1d11e",
-                        "bytes_per_point": 31.41},
-                "f16": {"source_sha256": "a05f39842a571c47ccd5c85e39af88796248883280ea63e826d9b2a0dcc1d11e",
+AX32_TRAFFIC = {"f32": {"source_sha256": "8c9be90279fc9254543e00b896885499d1e83564839092296b66ebf9d1922d6e",
+                        "bytes_per_point": 31.29},
+                "f16": {"source_sha256": "8c9be90279fc9254543e00b896885499d1e83564839092296b66ebf9d1922d6e",
                         "bytes_per_point": 18.81}}
 
 
