@@ -469,18 +469,50 @@ __global__ void ax32_seam_kernel(Topo t, int nseg, int seg_len, float *__restric
   }
 }
 
+// V consecutive values as one vector access (16-byte aligned for V > 1).
+template <typename T, int V>
+struct VecOf {
+  using type = T;
+};
+template <>
+struct VecOf<float, 4> {
+  using type = float4;
+};
+template <>
+struct VecOf<double, 2> {
+  using type = double2;
+};
+template <typename T, int V>
+__device__ __forceinline__ void vload(const T *p, T (&o)[V]) {
+  using VT = typename VecOf<T, V>::type;
+  const VT v = *reinterpret_cast<const VT *>(p);
+  const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+  for (int c = 0; c < V; ++c) o[c] = pv[c];
+}
+template <typename T, int V>
+__device__ __forceinline__ void vstore(T *p, const T (&o)[V]) {
+  using VT = typename VecOf<T, V>::type;
+  VT v;
+  T *pv = reinterpret_cast<T *>(&v);
+#pragma unroll
+  for (int c = 0; c < V; ++c) pv[c] = o[c];
+  *reinterpret_cast<VT *>(p) = v;
+}
+
 // Face planes normal to x (DIR 0), y (DIR 1) or z (DIR 2): lower copy + upper copy, and
 // the Dirichlet mask of the box boundary planes of that direction.  One thread
-// per node of each element's lower plane (plus the upper plane of the last
-// layer under Dirichlet).
-template <int DIR, typename T = float>
+// per V consecutive nodes of each element's lower plane (plus the upper plane
+// of the last layer under Dirichlet); V > 1 only for y and z planes, whose rows
+// run along i, and then every access is one aligned vector.
+template <int DIR, typename T = float, int V = 1>
 __global__ void plane_sum_kernel(Topo t, T *__restrict__ w, int dirichlet) {
   const int Np = t.Np, N = t.N;
   const uint32_t Np2 = (uint32_t)Np * Np;
-  const uint64_t total = (uint64_t)t.E * Np2;
+  const uint64_t total = (uint64_t)t.E * Np2 / V;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
        q += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t q32 = (uint32_t)q;  // E * Np2 < 2^32 (checked by the launcher)
+    const uint32_t q32 = (uint32_t)(q * V);  // E * Np2 < 2^32 (checked by the launcher)
     const uint32_t r = t.div_np.div(q32);
     const uint32_t a = q32 - r * Np;   // fastest in-plane index: i
     const uint32_t e = t.div_np.div(r);
@@ -508,16 +540,38 @@ __global__ void plane_sum_kernel(Topo t, T *__restrict__ w, int dirichlet) {
       stride_e = (int64_t)t.ex * t.ey;
     }
     T *we = w + (int64_t)e * t.Np3;
+    T zero[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) zero[c] = T(0);
     if (layer > 0) {
       T *below = we - stride_e * t.Np3 + hi_off;
-      const T v = *below + we[lo_off];
-      *below = v;
-      we[lo_off] = v;
+      T lo[V], hi[V];
+      vload<T, V>(below, hi);
+      vload<T, V>(we + lo_off, lo);
+#pragma unroll
+      for (int c = 0; c < V; ++c) lo[c] = hi[c] + lo[c];
+      vstore<T, V>(below, lo);
+      vstore<T, V>(we + lo_off, lo);
     } else if (dirichlet) {
-      we[lo_off] = T(0);
+      vstore<T, V>(we + lo_off, zero);
     }
-    if (dirichlet && layer == layers - 1) we[hi_off] = T(0);
+    if (dirichlet && layer == layers - 1) vstore<T, V>(we + hi_off, zero);
   }
+}
+
+// The y or z pass with the widest vector the order and alignment allow.
+template <int DIR, typename T>
+static void launch_plane(const Topo &t, T *w, int dirichlet, cudaStream_t st) {
+  constexpr int VW = sizeof(T) == 4 ? 4 : 2;  // 16 bytes
+  const bool vec = DIR != 0 && t.Np % VW == 0 && (reinterpret_cast<uintptr_t>(w) & 15u) == 0 &&
+                   ((int64_t)t.Np3 * (int64_t)sizeof(T)) % 16 == 0;
+  const int v = vec ? VW : 1;
+  const int64_t n = t.E * t.Np * t.Np / v;
+  const int64_t b = (n + 255) / 256;
+  const int pg = (int)(b < 152 * 16 ? b : 152 * 16);
+  if (vec) plane_sum_kernel<DIR, T, VW><<<pg, 256, 0, st>>>(t, w, dirichlet);
+  else plane_sum_kernel<DIR, T, 1><<<pg, 256, 0, st>>>(t, w, dirichlet);
+  SEM_CHECK_CUDA(cudaGetLastError());
 }
 
 static int sm_count() {
@@ -607,13 +661,8 @@ static void ax32_np(const Level &L, const float *u, float *w, bool assemble, cud
     ax32_seam_kernel<<<(int)(b < 152 * 8 ? b : 152 * 8), 256, 0, st>>>(t, a.nseg, a.seg_len, w);
     SEM_CHECK_CUDA(cudaGetLastError());
   }
-  const int64_t n = t.E * t.Np * t.Np;
-  const int64_t b = (n + 255) / 256;
-  const int pg = (int)(b < 152 * 16 ? b : 152 * 16);
-  plane_sum_kernel<1><<<pg, 256, 0, st>>>(t, w, a.dirichlet);
-  SEM_CHECK_CUDA(cudaGetLastError());
-  plane_sum_kernel<2><<<pg, 256, 0, st>>>(t, w, a.dirichlet);
-  SEM_CHECK_CUDA(cudaGetLastError());
+  launch_plane<1, float>(t, w, a.dirichlet, st);
+  launch_plane<2, float>(t, w, a.dirichlet, st);
 }
 
 // Direct stiffness summation of an FP32 E-layout vector by three plane
@@ -624,16 +673,10 @@ void launch_planes_assemble(const Level &L, T *w, cudaStream_t st) {
   const Topo &t = L.t;
   SEM_REQUIRE((uint64_t)t.E * t.Np * t.Np < (1ull << 32), "mesh too large for the plane passes");
   TraceScope ts(sizeof(T) == 8 ? "plane_sum3_f64" : "plane_sum3", t.N, st, 3);
-  const int64_t n = t.E * t.Np * t.Np;
-  const int64_t b = (n + 255) / 256;
-  const int pg = (int)(b < 152 * 16 ? b : 152 * 16);
   const int dir = t.bc == SEM_DIRICHLET;
-  plane_sum_kernel<0, T><<<pg, 256, 0, st>>>(t, w, dir);
-  SEM_CHECK_CUDA(cudaGetLastError());
-  plane_sum_kernel<1, T><<<pg, 256, 0, st>>>(t, w, dir);
-  SEM_CHECK_CUDA(cudaGetLastError());
-  plane_sum_kernel<2, T><<<pg, 256, 0, st>>>(t, w, dir);
-  SEM_CHECK_CUDA(cudaGetLastError());
+  launch_plane<0, T>(t, w, dir, st);
+  launch_plane<1, T>(t, w, dir, st);
+  launch_plane<2, T>(t, w, dir, st);
 }
 template void launch_planes_assemble<float>(const Level &, float *, cudaStream_t);
 template void launch_planes_assemble<double>(const Level &, double *, cudaStream_t);
