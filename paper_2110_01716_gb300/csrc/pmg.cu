@@ -722,8 +722,8 @@ static void restrict_to(sem_pmg *P, int l, cudaStream_t st) {
     restrict_kernel<Tf, Tc><<<grid_elems(tp.tf.E), 128, shm, st>>>(tp, fb, fw, co);
   SEM_CHECK_CUDA(cudaGetLastError());
   }
-  launch_gs<Tc>(*C.L, vec_of<Tc>(C, 0), st);
-  launch_mask<Tc>(*C.L, vec_of<Tc>(C, 0), st);
+  // copies summed by the x, y and z face passes, with the Dirichlet mask
+  launch_planes_assemble<Tc>(*C.L, vec_of<Tc>(C, 0), st);
 }
 
 template <typename Tc, typename Tf>
