@@ -99,6 +99,8 @@ def parse_args():
     p.add_argument("--schwarz", action="store_true",
                    help="Chebyshev-accelerated overlapping Schwarz smoother (FDM local solves) "
                         "instead of Chebyshev-Jacobi")
+    p.add_argument("--schwarz-tc", action="store_true",
+                   help="Chebyshev-Schwarz smoothing with the local solves on the tensor cores")
     p.add_argument("--smoother", default=SMOOTHER, choices=["f64", "f32", "f16", "bf16"],
                    help="arithmetic/storage of the smoothed pMG levels")
     p.add_argument("--coarse-mode", type=int, default=COARSE_MODE,
@@ -470,7 +472,8 @@ def main():
     pmg = sem.Pmg(mesh, orders=(7, 3, 1), cheb_degree=args.cheb_degree, lanczos_steps=20, seed=0,
                   smoother_dtype=SMOOTHER_DTYPES[args.smoother], coarse_tol=args.coarse_tol,
                   coarse_maxit=args.coarse_maxit, coarse_mode=args.coarse_mode,
-                  smoother=sem.SEM_SMOOTH_ASM if args.schwarz else sem.SEM_SMOOTH_JACOBI)
+                  smoother=(sem.SEM_SMOOTH_ASM_TC if args.schwarz_tc else
+                            sem.SEM_SMOOTH_ASM if args.schwarz else sem.SEM_SMOOTH_JACOBI))
     b = rhs_on_device(sem, torch, mesh, dev)
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
@@ -574,7 +577,8 @@ def main():
             "dtype": "f64+" + args.smoother, "data": "synthetic",
             "config": {"workload": WORKLOAD, "E": side ** 3, "N": ORDER, "n_local": nl,
                        "solver": args.solver, "smoother": args.smoother,
-                       "smoothing": "chebyshev-schwarz" if args.schwarz else "chebyshev-jacobi",
+                       "smoothing": ("chebyshev-schwarz-tc" if args.schwarz_tc else
+                                     "chebyshev-schwarz" if args.schwarz else "chebyshev-jacobi"),
                        "cheb_degree": args.cheb_degree, "coarse_tol": args.coarse_tol,
                        "coarse_maxit": args.coarse_maxit, "coarse_mode": args.coarse_mode,
                        "n_global": ng, "parallelism": "replicas" if world > 1 else "single",

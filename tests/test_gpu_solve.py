@@ -442,6 +442,64 @@ def test_schwarz_flexcg_reaches_1e8(bc, dtype):
     assert its[sem.SEM_SMOOTH_ASM] < its[sem.SEM_SMOOTH_JACOBI], its
 
 
+@pytest.mark.parametrize("bc,orders,e", [(0, (5, 2, 1), (3, 2, 2)), (1, (7, 3, 1), (2, 3, 2)),
+                                         (0, (9, 4, 1), (2, 2, 2)), (1, (3, 1), (4, 3, 2))])
+def test_schwarz_tc_vcycle_close_to_fp64_oracle(bc, orders, e):
+    """Local solves on the tensor cores (TF32 head + remainder products into
+    FP32 accumulators): the V-cycle stays within FP32 accuracy of the FP64
+    oracle's (dense local solves), like the CUDA-core FP32 Schwarz V-cycle,
+    and the Chebyshev intervals are the oracle's."""
+    v = inputs.box_vertices(*e, 0.1, 7)
+    m = sem.Mesh(*e, orders[0], bc, verts=v)
+    Po = oracle.PMG(*e, list(orders), bc, v, cheb_degree=2, lanczos_steps=20, seed=4,
+                    coarse_tol=0.0, coarse_maxit=12, smoother="asm")
+    L = Po.levels[0]
+    r = L.gs(inputs.random_field(L.nl, 8)) * L.mask
+    if bc == 1:
+        r -= L.dot(r, np.ones(L.nl)) / L.ng
+    zo = Po.vcycle(r)
+    out = {}
+    for sm in (sem.SEM_SMOOTH_ASM, sem.SEM_SMOOTH_ASM_TC):
+        P = sem.Pmg(m, orders=orders, smoother_dtype=sem.SEM_F32, coarse_tol=0.0, coarse_maxit=12,
+                    seed=4, cheb_degree=2, smoother=sm)
+        for lvl in range(len(orders) - 1):
+            lo, hi = P.lam(lvl)
+            olo, ohi = Po.lam(lvl)
+            assert abs(hi - ohi) < 1e-10 * ohi and abs(lo - olo) < 1e-10 * olo
+        zd = torch.empty(L.nl, device=DEV, dtype=torch.float64)
+        sem.sem_pmg_vcycle(P, torch.tensor(r, device=DEV), zd)
+        out[sm] = zd.cpu().numpy()
+        assert rel(out[sm], zo) < 1e-4, (sm, rel(out[sm], zo))
+    assert rel(out[sem.SEM_SMOOTH_ASM_TC], out[sem.SEM_SMOOTH_ASM]) < 1e-4
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_schwarz_tc_flexcg_reaches_1e8(bc):
+    e = (3, 3, 2)
+    v = inputs.box_vertices(*e, 0.1, 3)
+    m = sem.Mesh(*e, 7, bc, verts=v)
+    L = oracle.Level(*e, 7, bc, v)
+    b = manufactured(L)[1] if bc == 0 else fourier_rhs(L)
+    its = {}
+    for sm in (sem.SEM_SMOOTH_ASM, sem.SEM_SMOOTH_ASM_TC):
+        P = sem.Pmg(m, orders=(7, 3, 1), smoother_dtype=sem.SEM_F32, cheb_degree=3,
+                    coarse_tol=1e-2, coarse_maxit=50, smoother=sm)
+        bd = torch.tensor(b, device=DEV)
+        xd = torch.zeros_like(bd)
+        info = sem.sem_solve(m, P, bd, xd, sem.SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=100)
+        assert info["status"] == sem.SEM_OK, info
+        assert residual(L, b, xd.cpu().numpy()) <= 1.001e-8
+        its[sm] = info["iters"]
+    assert abs(its[sem.SEM_SMOOTH_ASM_TC] - its[sem.SEM_SMOOTH_ASM]) <= 1, its
+
+
+def test_schwarz_tc_needs_fp32_smoothing():
+    m = sem.Mesh(2, 2, 2, 5, 0)
+    with pytest.raises(sem.SemError) as ex:
+        sem.Pmg(m, orders=(5, 2, 1), smoother_dtype=sem.SEM_F64, smoother=sem.SEM_SMOOTH_ASM_TC)
+    assert ex.value.status == sem.SEM_EINVAL
+
+
 def test_schwarz_order_limit():
     m = sem.Mesh(2, 2, 2, 10, 0)
     with pytest.raises(sem.SemError) as ex:
@@ -457,6 +515,7 @@ GRAPH_CASES = [
     (0, (5, 3), sem.SEM_COARSE_JACOBI, sem.SEM_SMOOTH_JACOBI, sem.SEM_F64),
     (1, (7, 3, 1), sem.SEM_COARSE_JACOBI, sem.SEM_SMOOTH_ASM, sem.SEM_F32),
     (0, (7, 3, 1), sem.SEM_COARSE_JACOBI, sem.SEM_SMOOTH_JACOBI, sem.SEM_F16),
+    (0, (7, 3, 1), sem.SEM_COARSE_JACOBI, sem.SEM_SMOOTH_ASM_TC, sem.SEM_F32),
 ]
 
 
