@@ -202,6 +202,9 @@ void launch_ax32(const Level &L, int kind, const float *u, float *w, bool assemb
 // passes) and apply the Dirichlet mask.
 template <typename T>
 void launch_planes_assemble(const Level &L, T *w, cudaStream_t st);
+// One FP32 face-plane pass (dir 0, 1, 2: x, y, z) with that direction's
+// Dirichlet mask (planes.cu).
+void launch_plane_pass(const Topo &t, int dir, float *w, int dirichlet, cudaStream_t st);
 // FP64 geometric factors of a level into `out` (computed again; for setup).
 void level_fp64_factors(const Level &L, DevBuf<double> &out, cudaStream_t st);
 
