@@ -263,6 +263,54 @@ def operator_sweep(sem, torch, dev, hbm):
     return out
 
 
+def size_sweep(sem, torch, dev, hbm, sides=(16, 32, 48, 64)):
+    """Config 2 across sizes: E = k^3, N = 7, stored factors, seed 2 + k.  Per
+    size and precision: the local operator, gather-scatter alone (sem_gs) and
+    the assembled operator (sem_ax with SEM_AX_ASSEMBLED: the fused path),
+    median of 10 launches after 3 warm-ups."""
+    from paper_2110_01716_gb300 import inputs
+
+    st = torch.cuda.current_stream()
+
+    def median_ms(fn):
+        for _ in range(3):
+            fn()
+        times = []
+        for _ in range(10):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return statistics.median(times)
+
+    out = {}
+    for k in sides:
+        mesh = sem.Mesh(k, k, k, ORDER, sem.SEM_DIRICHLET,
+                        verts=inputs.box_vertices(k, k, k, 0.1, 2 + k))
+        n = mesh.n_local
+        row = {"E": k ** 3, "n_local": n}
+        for dt, tdt, name, esz in ((sem.SEM_F64, torch.float64, "f64", 8),
+                                   (sem.SEM_F32, torch.float32, "f32", 4)):
+            u = torch.rand(n, device=dev, dtype=tdt, generator=torch.Generator(dev).manual_seed(5))
+            w = torch.empty_like(u)
+            ax = median_ms(lambda: sem.sem_ax(mesh, dt, u, w, sem.SEM_AX_LOCAL))
+            gs = median_ms(lambda: sem.sem_gs(mesh, dt, w))
+            asm = median_ms(lambda: sem.sem_ax(mesh, dt, u, w, sem.SEM_AX_ASSEMBLED))
+            bpp = 2 * esz + 6 * esz
+            row[name] = {"ax_local_ms": round(ax, 4), "gs_ms": round(gs, 4),
+                         "ax_assembled_ms": round(asm, 4),
+                         "ax_local_hbm_frac": round(n * bpp / ax / 1e6 / hbm, 4),
+                         "assembled_gdofs_local": round(n / asm / 1e6, 2)}
+            del u, w
+        out[str(k)] = row
+        mesh.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def projection_sequence(sem, torch, mesh, pmg, dev, solver, restart, steps=16, Lmax=30):
     """Successive solves on the smooth right-hand-side sequence (same mesh and
     preconditioner): plain solves from x = 0 against projected solves with an
@@ -659,6 +707,7 @@ def main():
             line["serve"] = serve_leg(sem, inputs, bl["autotuned_workers"],
                                       graph=bl["solves_per_s_graph"] > bl["solves_per_s"])
         line["ax_sweep_64cube"] = operator_sweep(sem, torch, dev, hbm)
+        line["ax_gs_sizes"] = size_sweep(sem, torch, dev, hbm)
         if world == 1:
             dt, ng_s, it_s, threads = oracle_sample_solve(12)
             line["cpu_baseline"] = {

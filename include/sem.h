@@ -133,8 +133,9 @@ sem_status sem_ax(sem_mesh *mesh, sem_dtype dtype, const void *u, void *w, int32
                   void *stream);
 
 /* Direct stiffness summation in place (Sec. 2: C0 continuity; Sec. 3: gs):
- * every local copy of a node receives the sum over its copies.  All copies end
- * bit-identical.  dtype SEM_F64 or SEM_F32. */
+ * every local copy of a node receives the sum over its copies, summed across
+ * x-, then y-, then z-faces (a pairwise tree; no Dirichlet mask).  All copies
+ * end bit-identical.  dtype SEM_F64 or SEM_F32. */
 sem_status sem_gs(sem_mesh *mesh, sem_dtype dtype, void *u, void *stream);
 
 /* Inner product over unique nodes of two FP64 E-layout vectors,

@@ -635,9 +635,19 @@ sem_status sem_ax(sem_mesh *mesh, sem_dtype dtype, const void *u, void *w, int32
 sem_status sem_gs(sem_mesh *mesh, sem_dtype dtype, void *u, void *stream) {
   return guarded([&] {
     SEM_REQUIRE(mesh != nullptr && u != nullptr, "null mesh or vector");
-    if (dtype == SEM_F64) launch_gs<double>(mesh->fine, (double *)u, as_stream(stream));
-    else if (dtype == SEM_F32) launch_gs<float>(mesh->fine, (float *)u, as_stream(stream));
-    else fail(SEM_EINVAL, "sem_gs supports SEM_F64 and SEM_F32");
+    SEM_REQUIRE(dtype == SEM_F64 || dtype == SEM_F32, "sem_gs supports SEM_F64 and SEM_F32");
+    const Level &L = mesh->fine;
+    cudaStream_t st = as_stream(stream);
+    // the face-plane passes (every copy gets the same bits) where the plane
+    // indices fit 32 bits, else the per-node table
+    const bool planes = (uint64_t)L.t.E * L.t.Np * L.t.Np < (1ull << 32);
+    if (dtype == SEM_F64) {
+      if (planes) launch_planes_assemble<double>(L, (double *)u, st, false);
+      else launch_gs<double>(L, (double *)u, st);
+    } else {
+      if (planes) launch_planes_assemble<float>(L, (float *)u, st, false);
+      else launch_gs<float>(L, (float *)u, st);
+    }
   });
 }
 

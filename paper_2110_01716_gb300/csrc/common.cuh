@@ -198,10 +198,10 @@ void level_ensure_dinv32(Level &L, cudaStream_t st);
 // factor storage); assemble: w = mask * gs(A_L u), else w = A_L u.
 void launch_ax32(const Level &L, int kind, const float *u, float *w, bool assemble,
                  cudaStream_t st);
-// Sum the copies of every node of an FP32 E-layout vector (x, y, z face
-// passes) and apply the Dirichlet mask.
+// Sum the copies of every node of an E-layout vector (x, y, z face passes)
+// and, with `mask`, apply the Dirichlet mask.
 template <typename T>
-void launch_planes_assemble(const Level &L, T *w, cudaStream_t st);
+void launch_planes_assemble(const Level &L, T *w, cudaStream_t st, bool mask = true);
 // One FP32 face-plane pass (dir 0, 1, 2: x, y, z) with that direction's
 // Dirichlet mask (planes.cu).
 void launch_plane_pass(const Topo &t, int dir, float *w, int dirichlet, cudaStream_t st);

@@ -128,16 +128,18 @@ void launch_plane_pass(const Topo &t, int dir, float *w, int dirichlet, cudaStre
 // passes (x, then y, then z faces; every copy receives the same bits) and the
 // Dirichlet mask.
 template <typename T>
-void launch_planes_assemble(const Level &L, T *w, cudaStream_t st) {
+void launch_planes_assemble(const Level &L, T *w, cudaStream_t st, bool mask) {
   const Topo &t = L.t;
   SEM_REQUIRE((uint64_t)t.E * t.Np * t.Np < (1ull << 32), "mesh too large for the plane passes");
-  TraceScope ts(sizeof(T) == 8 ? "plane_sum3_f64" : "plane_sum3", t.N, st, 3);
-  const int dir = t.bc == SEM_DIRICHLET;
+  TraceScope ts(mask ? (sizeof(T) == 8 ? "plane_sum3_f64" : "plane_sum3")
+                     : (sizeof(T) == 8 ? "gs_planes_f64" : "gs_planes_f32"),
+                t.N, st, 3);
+  const int dir = mask && t.bc == SEM_DIRICHLET;
   launch_plane<0, T>(t, w, dir, st);
   launch_plane<1, T>(t, w, dir, st);
   launch_plane<2, T>(t, w, dir, st);
 }
-template void launch_planes_assemble<float>(const Level &, float *, cudaStream_t);
-template void launch_planes_assemble<double>(const Level &, double *, cudaStream_t);
+template void launch_planes_assemble<float>(const Level &, float *, cudaStream_t, bool);
+template void launch_planes_assemble<double>(const Level &, double *, cudaStream_t, bool);
 
 }  // namespace sem

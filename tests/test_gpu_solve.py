@@ -611,3 +611,61 @@ def test_graph_argument_checks():
     # zero right-hand side: converged before any graph launch
     info = sem.sem_solve(m, P, bd, xd, sem.SEM_SOLVER_FLEXCG, use_graph=True)
     assert info["status"] == sem.SEM_OK and info["iters"] == 0
+
+
+# ---------------------------------------------------------------- full size
+def _sub_box(v, ex, ey, ez, c, r=1):
+    """Vertices and global element indices of the box of elements within r of
+    element c = (cx, cy, cz), clipped to the mesh; also c's index inside it."""
+    lo = [max(0, c[d] - r) for d in range(3)]
+    hi = [min((ex, ey, ez)[d] - 1, c[d] + r) for d in range(3)]
+    n = [hi[d] - lo[d] + 1 for d in range(3)]
+    V = np.asarray(v).reshape(ez + 1, ey + 1, ex + 1, 3)
+    sub = V[lo[2]:hi[2] + 2, lo[1]:hi[1] + 2, lo[0]:hi[0] + 2].reshape(-1, 3)
+    els = [(lo[0] + a) + ex * ((lo[1] + b) + ey * (lo[2] + g))
+           for g in range(n[2]) for b in range(n[1]) for a in range(n[0])]
+    centre = (c[0] - lo[0]) + n[0] * ((c[1] - lo[1]) + n[1] * (c[2] - lo[2]))
+    return n, np.ascontiguousarray(sub), np.array(els), centre
+
+
+def test_full_size_solve_residual_sampled_by_oracle():
+    """The benchmark's solve (48^3 elements, N = 7, Neumann, pMG 7-3-1 with
+    Chebyshev(3)-Jacobi in FP32, multigrid coarse solve, FlexCG to 1e-8):
+    at every node of sampled elements the oracle recomputes the residual
+    b - A x from the solution on the box of elements around them, and each
+    entry is bounded by the global tolerance (|r_i| <= ||r|| <= 1e-8 ||b||,
+    unique-point norms)."""
+    e, N = 48, 7
+    v = inputs.box_vertices(e, e, e, 0.1, 3)
+    m = sem.Mesh(e, e, e, N, 1, verts=v)
+    Np3 = (N + 1) ** 3
+    u = torch.rand(m.n_local, device=DEV, dtype=torch.float64,
+                   generator=torch.Generator(DEV).manual_seed(11)) * 2 - 1
+    b = torch.empty_like(u)
+    sem.sem_ax(m, sem.SEM_F64, u, b, sem.SEM_AX_ASSEMBLED)  # consistent: 1^T b = 0
+    P = sem.Pmg(m, orders=(7, 3, 1), cheb_degree=3, smoother_dtype=sem.SEM_F32, coarse_tol=0.2,
+                coarse_maxit=30, coarse_mode=sem.SEM_COARSE_MG)
+    x = torch.zeros_like(b)
+    info = sem.sem_solve(m, P, b, x, sem.SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=50)
+    assert info["status"] == sem.SEM_OK and info["iters"] <= 12, info
+    bnorm = float(np.sqrt(sem.sem_dot(m, b, b)))
+    # the GPU's own FP64 residual (its operator is checked against the oracle
+    # at this size elsewhere)
+    ax = torch.empty_like(x)
+    sem.sem_ax(m, sem.SEM_F64, x, ax, sem.SEM_AX_ASSEMBLED)
+    r = b - ax
+    assert np.sqrt(sem.sem_dot(m, r, r)) <= 1.001e-8 * bnorm
+    rng = np.random.Generator(np.random.PCG64(4848))
+    cents = [tuple(int(c) for c in rng.integers(0, e, 3)) for _ in range(6)]
+    cents += [(0, 0, 0), (e - 1, e - 1, e - 1), (0, e - 1, 17), (23, 0, e - 1)]
+    x3 = x.view(-1, Np3)
+    b3 = b.view(-1, Np3)
+    worst = 0.0
+    for c in cents:
+        n, sub, els, centre = _sub_box(v, e, e, e, c)
+        Lo = oracle.Level(*n, N, 1, sub)
+        xs = x3[torch.tensor(els, device=DEV)].cpu().numpy().reshape(-1)
+        axo = Lo.ax(xs).reshape(-1, Np3)[centre]
+        rc = b3[els[centre]].cpu().numpy() - axo
+        worst = max(worst, float(np.max(np.abs(rc))))
+    assert worst <= 1.001e-8 * bnorm, (worst, bnorm)
