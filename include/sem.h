@@ -235,6 +235,11 @@ typedef struct {
                         problems.  check_every is ignored (the test runs
                         every iteration).  The mesh keeps one graph, captured
                         again when the pMG or x changes. */
+  int32_t zero_guess; /* 1: start from x = 0 and ignore x's input (x is output
+                         only: sem_solve_host copies nothing to x's device
+                         copy, and no operator is applied to the guess); 0:
+                         x holds the initial guess.  The results equal those
+                         of a zero-filled x bit for bit. */
 } sem_solve_desc;
 
 typedef struct {

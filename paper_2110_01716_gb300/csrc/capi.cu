@@ -142,6 +142,10 @@ static sem_status run_fgmres(sem_mesh *M, sem_pmg *P, const double *b, double *x
     ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
   } guard{e0, e1};
   SEM_CHECK_CUDA(cudaEventRecord(e0, st));
+  if (d.zero_guess && !x_zero) {
+    SEM_CHECK_CUDA(cudaMemsetAsync(x, 0, t.nl * sizeof(double), st));
+    x_zero = true;
+  }
   if (check_rhs) check_neumann_rhs(M, b, st);
   // r0 = b - A x into V_0 (r0 = b when x is known to be zero), with <b, b>, <r0, r0>
   if (!x_zero) apply_assembled<double>(L, x, w, st);
@@ -364,6 +368,10 @@ static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
     ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
   } guard{e0, e1};
   SEM_CHECK_CUDA(cudaEventRecord(e0, st));
+  if (d.zero_guess && !x_zero) {
+    SEM_CHECK_CUDA(cudaMemsetAsync(x, 0, t.nl * sizeof(double), st));
+    x_zero = true;
+  }
   if (check_rhs) check_neumann_rhs(M, b, st);
   if (!x_zero) apply_assembled<double>(L, x, w, st);
   launch_cg_start(t, M->red, b, x_zero ? nullptr : w, flex ? nullptr : L.dinv64.p, r, z, p,
@@ -723,6 +731,7 @@ static void check_solve_args(sem_mesh *mesh, sem_pmg *pmg, const sem_solve_desc 
   SEM_REQUIRE(pmg == nullptr || pmg->mesh == mesh, "pmg was built on another mesh");
   SEM_REQUIRE(desc->tol >= 0.0 && desc->max_iter >= 0, "negative tol or max_iter");
   SEM_REQUIRE(desc->use_graph == 0 || desc->use_graph == 1, "use_graph must be 0 or 1");
+  SEM_REQUIRE(desc->zero_guess == 0 || desc->zero_guess == 1, "zero_guess must be 0 or 1");
   SEM_REQUIRE(desc->use_graph == 0 || desc->solver == SEM_SOLVER_FLEXCG,
               "use_graph applies to SEM_SOLVER_FLEXCG only");
 }
@@ -756,8 +765,9 @@ sem_status sem_solve_host(sem_mesh *mesh, sem_pmg *pmg, const double *b_host, do
     cudaStream_t s = as_stream(stream);
     SEM_CHECK_CUDA(cudaMemcpyAsync(mesh->host_b.p, b_host, n * sizeof(double),
                                    cudaMemcpyHostToDevice, s));
-    SEM_CHECK_CUDA(cudaMemcpyAsync(mesh->host_x.p, x_host, n * sizeof(double),
-                                   cudaMemcpyHostToDevice, s));
+    if (!desc->zero_guess)
+      SEM_CHECK_CUDA(cudaMemcpyAsync(mesh->host_x.p, x_host, n * sizeof(double),
+                                     cudaMemcpyHostToDevice, s));
     result = desc->solver == SEM_SOLVER_FGMRES
                  ? run_fgmres(mesh, pmg, mesh->host_b.p, mesh->host_x.p, *desc, *info, s)
                  : run_solve(mesh, pmg, mesh->host_b.p, mesh->host_x.p, *desc, *info, s);

@@ -193,9 +193,11 @@ void sem_server::serve_one(Request &q, Setup &S, cudaStream_t st) {
     SEM_CHECK_CUDA(cudaMemcpyAsync(S.b.p, q.b.data(), nl * sizeof(double),
                                    cudaMemcpyHostToDevice, st));
   }
-  SEM_CHECK_CUDA(cudaMemsetAsync(S.x.p, 0, nl * sizeof(double), st));
+  // requests start from x = 0 (their x is output only)
+  sem_solve_desc sd = q.r.solve;
+  sd.zero_guess = 1;
   sem_solve_info info{};
-  const sem_status s = sem_solve(S.mesh, S.pmg, S.b.p, S.x.p, &q.r.solve, &info, st);
+  const sem_status s = sem_solve(S.mesh, S.pmg, S.b.p, S.x.p, &sd, &info, st);
   if (s != SEM_OK && s != SEM_ENOTCONV) fail(s, "server: solve failed: %s", sem_last_error());
   if (q.r.x)
     SEM_CHECK_CUDA(cudaMemcpyAsync(q.r.x, S.x.p, nl * sizeof(double), cudaMemcpyDeviceToHost, st));

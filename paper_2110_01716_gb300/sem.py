@@ -63,7 +63,8 @@ class sem_pmg_desc(C.Structure):
 
 class sem_solve_desc(C.Structure):
     _fields_ = [("solver", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("check_every", C.c_int32), ("restart", C.c_int32), ("use_graph", C.c_int32)]
+                ("check_every", C.c_int32), ("restart", C.c_int32), ("use_graph", C.c_int32),
+                ("zero_guess", C.c_int32)]
 
 
 class sem_server_desc(C.Structure):
@@ -298,10 +299,12 @@ def sem_pmg_vcycle(pmg: Pmg, r, z, stream=None):
 
 
 def sem_solve(mesh: Mesh, pmg, b, x, solver=SEM_SOLVER_PCG, tol=1e-8, max_iter=1000,
-              check_every=1, stream=None, raise_on_notconv=False, restart=0, use_graph=False):
-    """Solve in place (x: initial guess in, solution out); returns the info dict."""
+              check_every=1, stream=None, raise_on_notconv=False, restart=0, use_graph=False,
+              zero_guess=False):
+    """Solve in place (x: initial guess in, solution out; with zero_guess the
+    guess is 0 and x is output only); returns the info dict."""
     desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every), int(restart),
-                          int(bool(use_graph)))
+                          int(bool(use_graph)), int(bool(zero_guess)))
     info = sem_solve_info()
     st = lib().sem_solve(mesh.h, pmg.h if pmg is not None else None, _ptr(b), _ptr(x),
                          C.byref(desc), C.byref(info), _stream(stream))
@@ -313,10 +316,12 @@ def sem_solve(mesh: Mesh, pmg, b, x, solver=SEM_SOLVER_PCG, tol=1e-8, max_iter=1
 
 
 def sem_solve_host(mesh: Mesh, pmg, b_host, x_host, solver=SEM_SOLVER_PCG, tol=1e-8,
-                   max_iter=1000, check_every=1, stream=None, restart=0, use_graph=False):
-    """As sem_solve with host (CPU tensor or numpy) b and x; x is updated in place."""
+                   max_iter=1000, check_every=1, stream=None, restart=0, use_graph=False,
+                   zero_guess=False):
+    """As sem_solve with host (CPU tensor or numpy) b and x; x is updated in place
+    (with zero_guess its input is not read or copied)."""
     desc = sem_solve_desc(solver, float(tol), int(max_iter), int(check_every), int(restart),
-                          int(bool(use_graph)))
+                          int(bool(use_graph)), int(bool(zero_guess)))
     info = sem_solve_info()
     bp = b_host.ctypes.data if hasattr(b_host, "ctypes") else b_host.data_ptr()
     xp = x_host.ctypes.data if hasattr(x_host, "ctypes") else x_host.data_ptr()

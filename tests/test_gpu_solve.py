@@ -669,3 +669,29 @@ def test_full_size_solve_residual_sampled_by_oracle():
         rc = b3[els[centre]].cpu().numpy() - axo
         worst = max(worst, float(np.max(np.abs(rc))))
     assert worst <= 1.001e-8 * bnorm, (worst, bnorm)
+
+
+@pytest.mark.parametrize("solver", [sem.SEM_SOLVER_PCG, sem.SEM_SOLVER_FLEXCG,
+                                    sem.SEM_SOLVER_FGMRES])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_zero_guess_equals_zero_filled_guess(solver, bc):
+    """zero_guess ignores x's input (here NaN) and gives the bits of a solve
+    from a zero-filled x, on device and host buffers."""
+    m, L, b = _graph_problem(bc, (7, 3, 1))
+    P = None if solver == sem.SEM_SOLVER_PCG else sem.Pmg(m, orders=(7, 3, 1), coarse_tol=1e-2,
+                                                         coarse_maxit=60)
+    bd = torch.tensor(b, device=DEV)
+    x0 = torch.zeros_like(bd)
+    i0 = sem.sem_solve(m, P, bd, x0, solver, tol=1e-8, max_iter=2000)
+    xn = torch.full_like(bd, float("nan"))
+    i1 = sem.sem_solve(m, P, bd, xn, solver, tol=1e-8, max_iter=2000, zero_guess=True)
+    assert i0["status"] == i1["status"] == sem.SEM_OK and i0["iters"] == i1["iters"]
+    assert torch.equal(x0, xn)
+    xh = np.full(L.nl, np.nan)
+    i2 = sem.sem_solve_host(m, P, b, xh, solver, tol=1e-8, max_iter=2000, zero_guess=True)
+    assert i2["iters"] == i0["iters"] and np.array_equal(xh, x0.cpu().numpy())
+    with pytest.raises(sem.SemError):
+        d = sem.sem_solve_desc(solver, 1e-8, 10, 1, 0, 0, 2)
+        info = sem.sem_solve_info()
+        sem.check(sem.lib().sem_solve(m.h, P.h if P else None, sem._ptr(bd), sem._ptr(x0),
+                                      sem.C.byref(d), sem.C.byref(info), None))
