@@ -59,10 +59,13 @@ __global__ void cheb_step_kernel(Topo t, const T *__restrict__ w, const T *__res
 __device__ __forceinline__ float4 f4fma(float a, float4 x, float4 y) {
   return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
 }
+// x_zero with only_d: r (= b) and x (= d) are not written; the first step
+// reads b and d in their place.
 __global__ void cheb_start4_kernel(int64_t n4, const float4 *__restrict__ b,
                                    const float4 *__restrict__ w, const float4 *__restrict__ dinv,
                                    float4 *__restrict__ r, float4 *__restrict__ d,
-                                   float4 *__restrict__ x, float inv_theta, int x_zero) {
+                                   float4 *__restrict__ x, float inv_theta, int x_zero,
+                                   int only_d) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4;
        q += (int64_t)gridDim.x * blockDim.x) {
     float4 rl = b[q];
@@ -73,8 +76,9 @@ __global__ void cheb_start4_kernel(int64_t n4, const float4 *__restrict__ b,
     const float4 di = dinv[q];
     const float4 dl = make_float4(di.x * rl.x * inv_theta, di.y * rl.y * inv_theta,
                                   di.z * rl.z * inv_theta, di.w * rl.w * inv_theta);
-    r[q] = rl;
     d[q] = dl;
+    if (only_d) continue;
+    r[q] = rl;
     if (x_zero) {
       x[q] = dl;
     } else {
@@ -84,13 +88,16 @@ __global__ void cheb_start4_kernel(int64_t n4, const float4 *__restrict__ b,
   }
 }
 
+// first: the step after a start that wrote d only (r = b, x = d there).
 __global__ void cheb_step4_kernel(int64_t n4, const float4 *__restrict__ w,
-                                  const float4 *__restrict__ dinv, float4 *__restrict__ r,
-                                  float4 *__restrict__ d, float4 *__restrict__ x, float c1,
-                                  float c2) {
+                                  const float4 *__restrict__ dinv, const float4 *__restrict__ b,
+                                  float4 *__restrict__ r, float4 *__restrict__ d,
+                                  float4 *__restrict__ x, float c1, float c2, int first) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const float4 wl = w[q], di = dinv[q], r0 = r[q], d0 = d[q], x0 = x[q];
+    const float4 wl = w[q], di = dinv[q], d0 = d[q];
+    const float4 r0 = first ? b[q] : r[q];
+    const float4 x0 = first ? d0 : x[q];
     const float4 rl = make_float4(r0.x - wl.x, r0.y - wl.y, r0.z - wl.z, r0.w - wl.w);
     const float4 dl = make_float4(c1 * d0.x + c2 * di.x * rl.x, c1 * d0.y + c2 * di.y * rl.y,
                                   c1 * d0.z + c2 * di.z * rl.z, c1 * d0.w + c2 * di.w * rl.w);
@@ -654,13 +661,15 @@ static void smooth(sem_pmg *P, int l, bool x_zero, cudaStream_t st) {
   if (!x_zero) level_apply<T>(Q, x, w, st);
   const bool f64 = sizeof(T) == 8;
   const bool v4 = !f64 && n % 4 == 0;
+  // from x = 0 with later steps: the start writes d only
+  const bool only_d = v4 && x_zero && P->desc.cheb_degree >= 2;
   {
   TraceScope ts(f64 ? "cheb_start_f64" : "cheb_start_f32", L.t.N, st);
   if constexpr (sizeof(T) == 4) {
     if (v4)
       cheb_start4_kernel<<<vec_grid(n / 4), kVecThreads, 0, st>>>(
           n / 4, (const float4 *)b, x_zero ? nullptr : (const float4 *)w, (const float4 *)dinv,
-          (float4 *)r, (float4 *)d, (float4 *)x, (float)(1.0 / theta), x_zero);
+          (float4 *)r, (float4 *)d, (float4 *)x, (float)(1.0 / theta), x_zero, (int)only_d);
   }
   if (!v4)
     cheb_start_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(L.t, b, x_zero ? nullptr : w, dinv,
@@ -674,8 +683,9 @@ static void smooth(sem_pmg *P, int l, bool x_zero, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
       if (v4)
         cheb_step4_kernel<<<vec_grid(n / 4), kVecThreads, 0, st>>>(
-            n / 4, (const float4 *)w, (const float4 *)dinv, (float4 *)r, (float4 *)d, (float4 *)x,
-            (float)(rho1 * rho), (float)(2.0 * rho1 / delta));
+            n / 4, (const float4 *)w, (const float4 *)dinv, (const float4 *)b, (float4 *)r,
+            (float4 *)d, (float4 *)x, (float)(rho1 * rho), (float)(2.0 * rho1 / delta),
+            (int)(only_d && it == 2));
     }
     if (!v4)
       cheb_step_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(L.t, w, dinv, r, d, x,
