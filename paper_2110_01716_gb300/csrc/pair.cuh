@@ -61,11 +61,8 @@ struct PairShape {
   static constexpr int NP3 = NP2 * NP;
   static constexpr int NE = (256 / NP2) < 1 ? 1 : (256 / NP2);
   static constexpr int THREADS = NE * NP2;
-#ifndef SEM_PAIR_MIN_CTAS
-#define SEM_PAIR_MIN_CTAS 2
-#endif
-  // resident CTAs asked of the register allocator (two: 16 warps, 128 registers)
-  static constexpr int MIN_CTAS = THREADS >= 128 ? SEM_PAIR_MIN_CTAS : 4;
+  // two CTAs per SM when the register budget allows (16 warps hide latency)
+  static constexpr int MIN_CTAS = THREADS >= 128 ? 2 : 4;
 };
 
 // Three phases per element, with one barrier before the last:

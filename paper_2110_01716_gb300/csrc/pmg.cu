@@ -726,6 +726,8 @@ static void restrict_to(sem_pmg *P, int l, cudaStream_t st) {
     done = true;
   };
   fast(std::integral_constant<int, 8>(), std::integral_constant<int, 4>());
+  fast(std::integral_constant<int, 8>(), std::integral_constant<int, 5>());
+  fast(std::integral_constant<int, 5>(), std::integral_constant<int, 3>());
   fast(std::integral_constant<int, 4>(), std::integral_constant<int, 2>());
   fast(std::integral_constant<int, 8>(), std::integral_constant<int, 2>());
   fast(std::integral_constant<int, 6>(), std::integral_constant<int, 4>());
@@ -760,6 +762,8 @@ static void prolong_from(sem_pmg *P, int l, cudaStream_t st) {
     done = true;
   };
   fast(std::integral_constant<int, 8>(), std::integral_constant<int, 4>());
+  fast(std::integral_constant<int, 8>(), std::integral_constant<int, 5>());
+  fast(std::integral_constant<int, 5>(), std::integral_constant<int, 3>());
   fast(std::integral_constant<int, 4>(), std::integral_constant<int, 2>());
   fast(std::integral_constant<int, 8>(), std::integral_constant<int, 2>());
   fast(std::integral_constant<int, 6>(), std::integral_constant<int, 4>());

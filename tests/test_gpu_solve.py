@@ -116,7 +116,9 @@ def test_neumann_rhs_must_be_mean_free():
                                              (1, (7, 3, 1), sem.SEM_ARITH_PAIR),
                                              (1, (7, 3, 1), sem.SEM_ARITH_NATIVE),
                                              (0, (4, 2), sem.SEM_ARITH_PAIR),
-                                             (1, (3, 1), sem.SEM_ARITH_NATIVE)])
+                                             (1, (3, 1), sem.SEM_ARITH_NATIVE),
+                                             (0, (7, 4, 2, 1), sem.SEM_ARITH_PAIR),
+                                             (1, (7, 4, 2, 1), sem.SEM_ARITH_PAIR)])
 def test_vcycle_fp64_matches_oracle(bc, orders, arith):
     e = (3, 2, 4)
     v = inputs.box_vertices(*e, 0.1, 5)
@@ -139,13 +141,15 @@ def test_vcycle_fp64_matches_oracle(bc, orders, arith):
 
 
 @pytest.mark.parametrize("e,bc", [((4, 3, 3), 0), ((4, 3, 3), 1), ((2, 31, 30), 1), ((5, 2, 3), 0)])
-def test_vcycle_fp32_close_to_fp64_oracle(e, bc):
+@pytest.mark.parametrize("orders", [(7, 3, 1), (7, 4, 2, 1)])
+def test_vcycle_fp32_close_to_fp64_oracle(e, bc, orders):
     """FP32 smoothing (operator with the Chebyshev update fused in): boxes
-    whose x-lines are split into segments and, at 2 x 31 x 30, whole lines."""
+    whose x-lines are split into segments and, at 2 x 31 x 30, whole lines;
+    the bench's schedules."""
     v = inputs.box_vertices(*e, 0.1, 6)
     m = sem.Mesh(*e, 7, bc, verts=v)
-    P = sem.Pmg(m, orders=(7, 3, 1), smoother_dtype=sem.SEM_F32, coarse_tol=0.0, coarse_maxit=20)
-    Po = oracle.PMG(*e, [7, 3, 1], bc, v, coarse_tol=0.0, coarse_maxit=20)
+    P = sem.Pmg(m, orders=orders, smoother_dtype=sem.SEM_F32, coarse_tol=0.0, coarse_maxit=20)
+    Po = oracle.PMG(*e, list(orders), bc, v, coarse_tol=0.0, coarse_maxit=20)
     L = Po.levels[0]
     b = manufactured(L)[1] if bc == 0 else fourier_rhs(L)
     zd = torch.empty(L.nl, device=DEV, dtype=torch.float64)
@@ -628,9 +632,11 @@ def _sub_box(v, ex, ey, ez, c, r=1):
     return n, np.ascontiguousarray(sub), np.array(els), centre
 
 
-def test_full_size_solve_residual_sampled_by_oracle():
-    """The benchmark's solve (48^3 elements, N = 7, Neumann, pMG 7-3-1 with
-    Chebyshev(3)-Jacobi in FP32, multigrid coarse solve, FlexCG to 1e-8):
+@pytest.mark.parametrize("orders,degree", [((7, 4, 2, 1), 3), ((7, 3, 1), 2)])
+def test_full_size_solve_residual_sampled_by_oracle(orders, degree):
+    """The benchmark's solves (48^3 elements, N = 7, Neumann, pMG 7-4-2-1 with
+    Chebyshev(3)-Jacobi and 7-3-1 with Chebyshev(2)-Jacobi in FP32,
+    multigrid coarse solve, FlexCG to 1e-8):
     at every node of sampled elements the oracle recomputes the residual
     b - A x from the solution on the box of elements around them, and each
     entry is bounded by the global tolerance (|r_i| <= ||r|| <= 1e-8 ||b||,
@@ -643,8 +649,8 @@ def test_full_size_solve_residual_sampled_by_oracle():
                    generator=torch.Generator(DEV).manual_seed(11)) * 2 - 1
     b = torch.empty_like(u)
     sem.sem_ax(m, sem.SEM_F64, u, b, sem.SEM_AX_ASSEMBLED)  # consistent: 1^T b = 0
-    P = sem.Pmg(m, orders=(7, 3, 1), cheb_degree=3, smoother_dtype=sem.SEM_F32, coarse_tol=0.2,
-                coarse_maxit=30, coarse_mode=sem.SEM_COARSE_MG)
+    P = sem.Pmg(m, orders=orders, cheb_degree=degree, smoother_dtype=sem.SEM_F32,
+                coarse_tol=0.2, coarse_maxit=30, coarse_mode=sem.SEM_COARSE_MG)
     x = torch.zeros_like(b)
     info = sem.sem_solve(m, P, b, x, sem.SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=50)
     assert info["status"] == sem.SEM_OK and info["iters"] <= 12, info
