@@ -60,7 +60,8 @@ struct A32 {
 #ifndef SEM_AX32_MIN_CTAS
 #define SEM_AX32_MIN_CTAS 2
 #endif
-  static constexpr int MIN_CTAS = NP <= 8 ? SEM_AX32_MIN_CTAS : 1;
+  // the unstaged small orders fit 64 registers (four CTAs, 32 warps per SM)
+  static constexpr int MIN_CTAS = !STAGED && NP <= 5 ? 4 : (NP <= 8 ? SEM_AX32_MIN_CTAS : 1);
 };
 
 constexpr int round16(int b) { return (b + 15) & ~15; }
