@@ -72,10 +72,10 @@ AX_TRAFFIC = {"source_sha256": "6b16e73cafe6141d70ec23adcdb0a12c84ac3600ad31a9b5
               "bytes_per_point": 63.38}
 # The same for the smoother's assembled FP32 operator, per factor storage
 # (profiles/ax32_N7.md), valid while ax32.cu is unchanged.
-AX32_TRAFFIC = {"f32": {"source_sha256": "fc963ee3bde53eff3c673b21d426d784f9e24c18d77e0b6e21739bb0286e92b8",
-                        "bytes_per_point": 31.27},
-                "f16": {"source_sha256": "fc963ee3bde53eff3c673b21d426d784f9e24c18d77e0b6e21739bb0286e92b8",
-                        "bytes_per_point": 18.79}}
+AX32_TRAFFIC = {"f32": {"source_sha256": "a1c86ef6bae402e521ec9400dc4df4087b40792cad358632c0c31adec941b4d2",
+                        "bytes_per_point": 31.29},
+                "f16": {"source_sha256": "a1c86ef6bae402e521ec9400dc4df4087b40792cad358632c0c31adec941b4d2",
+                        "bytes_per_point": 18.82}}
 
 
 def parse_args():
