@@ -123,6 +123,24 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def job_time_ms(pg, local_ms, device):
+    """Wall time of the whole job: the slowest rank's time (all-reduce MAX
+    over the process group; the local time when there is none)."""
+    if pg is None:
+        return float(local_ms)
+    import torch
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, ms_per_step):
+    """Whole-job throughput in G units per second: every rank solves its own
+    replica (weak scaling), so the job processes world x units per step."""
+    return world * units_per_rank / (ms_per_step / 1e3) / 1e9
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -592,13 +610,10 @@ def main():
     sem.sem_trace_enable(False, "")
     step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
-    if pg:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = job_time_ms(pg, total_ms, dev)
     ms_per_step = total_ms / args.steps
     ng = mesh.n_global
-    value = world * ng / (ms_per_step / 1e3) / 1e9
+    value = job_value(world, ng, ms_per_step)
     for inf in infos:
         if inf["status"] != sem.SEM_OK:
             raise SystemExit(f"solve did not converge: {inf}")
