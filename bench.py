@@ -499,6 +499,51 @@ def oracle_sample_solve(side=12):
     return dt, L.ng, info["iters"], threads
 
 
+def oracle_timings():
+    """The oracle on this host, on one core and on all of them: config 1 (the
+    8^3-element, N = 7 Dirichlet manufactured solve, Jacobi-PCG to 1e-10)
+    and config 2 at 16^3 elements (local operator, gather-scatter and the
+    assembled operator, u ~ U(-1, 1))."""
+    import numpy as np
+
+    import oracle
+    from paper_2110_01716_gb300 import inputs
+
+    oracle.build()
+    allc = os.cpu_count() or 1
+    out = {}
+    for label, nth in (("all_cores", allc), ("one_core", 1)):
+        used = oracle.set_threads(nth)
+        row = {"threads": used}
+        v = inputs.box_vertices(8, 8, 8, 0.1, 1)
+        L = oracle.Level(8, 8, 8, ORDER, 0, v)
+        X = L.X
+        us = (np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2])).ravel()
+        b = L.assembled_rhs(3 * np.pi ** 2 * us)
+        t0 = time.perf_counter()
+        _, info = L.pcg(b, tol=1e-10, maxit=2000)
+        dt = time.perf_counter() - t0
+        row["config1_pcg"] = {"s": round(dt, 3), "iters": info["iters"],
+                              "gdofs": round(L.ng / dt / 1e9, 6)}
+        k = 16
+        L2 = oracle.Level(k, k, k, ORDER, 0, inputs.box_vertices(k, k, k, 0.1, 2 + k))
+        u = np.random.default_rng(2 + k).uniform(-1, 1, L2.nl)
+        t0 = time.perf_counter()
+        w = L2.ax_local(u)
+        t1 = time.perf_counter()
+        L2.gs(w)
+        t2 = time.perf_counter()
+        L2.ax(u)
+        t3 = time.perf_counter()
+        row["config2_16cube"] = {"ax_local_s": round(t1 - t0, 4), "gs_s": round(t2 - t1, 4),
+                                 "ax_assembled_s": round(t3 - t2, 4),
+                                 "ax_local_gdofs": round(L2.nl / (t1 - t0) / 1e9, 4)}
+        out[label] = row
+        del L, L2
+    oracle.set_threads(allc)
+    return out
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -760,6 +805,7 @@ def main():
         line["ax_gs_sizes"] = size_sweep(sem, torch, dev, hbm)
         if world == 1:
             dt, ng_s, it_s, threads = oracle_sample_solve(12)
+            line["oracle_timings"] = oracle_timings()
             line["cpu_baseline"] = {
                 "value": ng_s / dt / 1e9, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
                 "sample": f"oracle FlexCG+pMG 7-3-1 solve to 1e-8 on a 12^3-element box of the "

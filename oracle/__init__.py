@@ -114,6 +114,18 @@ APPLY_FN = C.CFUNCTYPE(None, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_do
 
 
 # ---------------------------------------------------------------- 1D basis
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's parallel loops (the elements of the
+    local operator); returns the count in force (1 without OpenMP)."""
+    lib()
+    try:
+        gomp = C.CDLL("libgomp.so.1")
+    except OSError:
+        return 1
+    gomp.omp_set_num_threads(int(n))
+    return int(gomp.omp_get_max_threads())
+
+
 def gll(N: int):
     x = np.zeros(N + 1)
     w = np.zeros(N + 1)
