@@ -105,6 +105,8 @@ def parse_args():
                         "instead of Chebyshev-Jacobi")
     p.add_argument("--orders", default=ORDERS,
                    help="pMG schedule, fine to coarse (the fine order first)")
+    p.add_argument("--schwarz-tf32", action="store_true",
+                   help="Chebyshev-Schwarz smoothing with TF32 local solves on the tensor cores")
     p.add_argument("--schwarz-tc", action="store_true",
                    help="Chebyshev-Schwarz smoothing with the local solves on the tensor cores")
     p.add_argument("--smoother", default=SMOOTHER, choices=["f64", "f32", "f16", "bf16"],
@@ -617,7 +619,8 @@ def main():
     pmg = sem.Pmg(mesh, orders=orders, cheb_degree=args.cheb_degree, lanczos_steps=20, seed=0,
                   smoother_dtype=SMOOTHER_DTYPES[args.smoother], coarse_tol=args.coarse_tol,
                   coarse_maxit=args.coarse_maxit, coarse_mode=args.coarse_mode,
-                  smoother=(sem.SEM_SMOOTH_ASM_TC if args.schwarz_tc else
+                  smoother=(sem.SEM_SMOOTH_ASM_TF32 if args.schwarz_tf32 else
+                            sem.SEM_SMOOTH_ASM_TC if args.schwarz_tc else
                             sem.SEM_SMOOTH_ASM if args.schwarz else sem.SEM_SMOOTH_JACOBI))
     b = rhs_on_device(sem, torch, mesh, dev)
     x = torch.zeros_like(b)
@@ -718,7 +721,8 @@ def main():
             "dtype": "f64+" + args.smoother, "data": "synthetic",
             "config": {"workload": WORKLOAD, "E": side ** 3, "N": ORDER, "n_local": nl,
                        "solver": args.solver, "smoother": args.smoother,
-                       "smoothing": ("chebyshev-schwarz-tc" if args.schwarz_tc else
+                       "smoothing": ("chebyshev-schwarz-tf32" if args.schwarz_tf32 else
+                                     "chebyshev-schwarz-tc" if args.schwarz_tc else
                                      "chebyshev-schwarz" if args.schwarz else "chebyshev-jacobi"),
                        "orders": args.orders, "cheb_degree": args.cheb_degree,
                        "coarse_tol": args.coarse_tol,

@@ -175,8 +175,8 @@ typedef struct {
   double coarse_tol;        /* coarsest level: FP64 Jacobi-PCG relative tol */
   int32_t coarse_maxit;     /* ... and iteration cap (tol <= 0: exactly maxit) */
   int32_t coarse_mode;      /* SEM_COARSE_JACOBI or SEM_COARSE_MG (below) */
-  int32_t smoother;         /* SEM_SMOOTH_JACOBI, SEM_SMOOTH_ASM or
-                               SEM_SMOOTH_ASM_TC (below) */
+  int32_t smoother;         /* SEM_SMOOTH_JACOBI, SEM_SMOOTH_ASM,
+                               SEM_SMOOTH_ASM_TC or SEM_SMOOTH_ASM_TF32 (below) */
 } sem_pmg_desc;
 
 /* Smoother of the smoothed levels, Chebyshev-accelerated in both cases (Sec. 3).
@@ -191,8 +191,11 @@ typedef struct {
  * 128 x 16 x 16 TF32 product, FP32 accuracy from a head + remainder split of
  * both operands) for orders up to N = 8 (at N = 9 the 144 pencils exceed the
  * 128 accumulator rows and that level's local solves stay on the CUDA cores);
- * FP32 smoothing only (smoother_dtype F32, F16 or BF16, else SEM_EINVAL). */
-enum { SEM_SMOOTH_JACOBI = 0, SEM_SMOOTH_ASM = 1, SEM_SMOOTH_ASM_TC = 2 };
+ * FP32 smoothing only (smoother_dtype F32, F16 or BF16, else SEM_EINVAL).
+ * SEM_SMOOTH_ASM_TF32: as SEM_SMOOTH_ASM_TC without the remainder split: the
+ * operands of the local solves are rounded to TF32 (11 significant bits), so
+ * the smoother is that accurate; half the shared memory per element. */
+enum { SEM_SMOOTH_JACOBI = 0, SEM_SMOOTH_ASM = 1, SEM_SMOOTH_ASM_TC = 2, SEM_SMOOTH_ASM_TF32 = 3 };
 
 /* Coarsest-level solver (the coarsest order must be 1 for SEM_COARSE_MG).
  * SEM_COARSE_JACOBI: FP64 Jacobi-PCG (the default).

@@ -508,10 +508,11 @@ void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t s
               "smoother_dtype must be SEM_F64, SEM_F32, SEM_F16 or SEM_BF16");
   SEM_REQUIRE(d.coarse_maxit >= 0 && d.coarse_maxit <= 100000, "coarse_maxit out of range");
   SEM_REQUIRE(d.smoother == SEM_SMOOTH_JACOBI || d.smoother == SEM_SMOOTH_ASM ||
-                  d.smoother == SEM_SMOOTH_ASM_TC,
+                  d.smoother == SEM_SMOOTH_ASM_TC || d.smoother == SEM_SMOOTH_ASM_TF32,
               "unknown smoother %d", d.smoother);
-  SEM_REQUIRE(d.smoother != SEM_SMOOTH_ASM_TC || d.smoother_dtype != SEM_F64,
-              "SEM_SMOOTH_ASM_TC smooths in FP32 (smoother_dtype F32, F16 or BF16)");
+  SEM_REQUIRE((d.smoother != SEM_SMOOTH_ASM_TC && d.smoother != SEM_SMOOTH_ASM_TF32) ||
+                  d.smoother_dtype != SEM_F64,
+              "the tensor-core Schwarz smoothers smooth in FP32 (smoother_dtype F32, F16 or BF16)");
   P->mesh = mesh;
   P->desc = d;
   const Level &F = mesh->fine;
@@ -545,11 +546,13 @@ void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t s
       else Q.v64[v].alloc(n);
     }
     if (!coarsest) {
-      if (d.smoother == SEM_SMOOTH_ASM || d.smoother == SEM_SMOOTH_ASM_TC) {
+      if (d.smoother == SEM_SMOOTH_ASM || d.smoother == SEM_SMOOTH_ASM_TC ||
+          d.smoother == SEM_SMOOTH_ASM_TF32) {
         SEM_REQUIRE(Q.L->t.N <= 9, "the Schwarz smoother supports orders up to 9");
         Q.asmd.reset(new AsmData());
         asm_setup(*Q.asmd, *Q.L, Q.dtype == SEM_F32, st);
-        Q.asmd->tc = d.smoother == SEM_SMOOTH_ASM_TC && Q.dtype == SEM_F32;
+        if (Q.dtype == SEM_F32)
+          Q.asmd->tc = d.smoother == SEM_SMOOTH_ASM_TC ? 1 : d.smoother == SEM_SMOOTH_ASM_TF32 ? 2 : 0;
         if (Q.dtype == SEM_F32) Q.asmd->mr32.alloc(n);
         else Q.asmd->mr64.alloc(n);
       }

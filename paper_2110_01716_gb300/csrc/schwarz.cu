@@ -412,10 +412,13 @@ void launch_asm(const AsmData &A, const Level &L, const T *r, T *z, cudaStream_t
   {
     // on the tensor cores while the extended element's n^2 pencils fit the 128
     // accumulator rows (N <= 8), else on the CUDA cores
-    const bool tc = sizeof(T) == 4 && A.tc && L.t.Np <= 9;
-    TraceScope ts(sizeof(T) == 8 ? "asm_f64" : (tc ? "asm_tc" : "asm_f32"), L.t.N, st, 2);
+    const bool tc = sizeof(T) == 4 && A.tc != 0 && L.t.Np <= 9;
+    TraceScope ts(sizeof(T) == 8 ? "asm_f64"
+                  : tc           ? (A.tc == 1 ? "asm_tc" : "asm_tf32")
+                                 : "asm_f32",
+                  L.t.N, st, 2);
     if constexpr (sizeof(T) == 4)
-      if (tc) launch_asm_solve_tc(A, L, r, z, ext, st);
+      if (tc) launch_asm_solve_tc(A, L, r, z, ext, A.tc == 1, st);
     if (!tc) switch (L.t.Np) {
       case 2: asm_solve_np<T, 2>(A, L, r, z, ext, st); break;
       case 3: asm_solve_np<T, 3>(A, L, r, z, ext, st); break;

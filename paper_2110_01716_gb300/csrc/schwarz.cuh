@@ -13,7 +13,8 @@ struct AsmData {
   DevBuf<float> ext32;
   DevBuf<double> mr64;           // M r of the Chebyshev recurrence
   DevBuf<float> mr32;
-  bool tc = false;               // FP32 local solves on the tensor cores
+  int tc = 0;                     // FP32 local solves on the tensor cores: 1 with the
+                                 // head + remainder split, 2 in plain TF32
 };
 
 // Eigendecompositions of every element's 1D pencils (FP64; FP32 copies if
@@ -22,7 +23,7 @@ void asm_setup(AsmData &A, const Level &L, bool want_f32, cudaStream_t st);
 // The FP32 local solves on the tensor cores (schwarz_tc.cu): own points of
 // every extended element's solution to z, its face layers to ext.
 void launch_asm_solve_tc(const AsmData &A, const Level &L, const float *r, float *z, float *ext,
-                         cudaStream_t st);
+                         bool split, cudaStream_t st);
 // z = mask sum_e R_e^T K_e^{-1} R_e r (r continuous; z assembled).
 template <typename T>
 void launch_asm(const AsmData &A, const Level &L, const T *r, T *z, cudaStream_t st);

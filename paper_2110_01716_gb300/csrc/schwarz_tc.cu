@@ -9,7 +9,9 @@
 // matrix (K = N = 16 with zero padding): a 128 x 16 x 16 tcgen05.mma of kind
 // tf32 with FP32 accumulation in tensor memory.  FP32 accuracy comes from the
 // split of both operands into a TF32 head and a TF32 remainder
-// (a b ~= a_h b_h + a_h b_r + a_r b_h, three products into one accumulator).
+// (a b ~= a_h b_h + a_h b_r + a_r b_h, three products into one accumulator);
+// without the split (SPLIT = false) the operands are rounded to TF32 once,
+// an element needs half the shared memory and twice as many fit an SM.
 // One CTA of 128 threads owns one element at a time: thread p is row p of
 // the accumulator; it reads its row back from tensor memory (tcgen05.ld) and
 // writes it into shared memory in the layout of the next direction (the
@@ -35,13 +37,18 @@ constexpr int kTcThreads = 128;
 constexpr int kTile = 8192;                       // one 128 x 16 FP32 operand
 constexpr int kMat = 1024;                        // one 16 x 16 FP32 operand
 constexpr int kTcWaitLimit = 1 << 22;             // polls of a commit barrier
-// dynamic shared memory: A head and remainder, the six matrices (head and
-// remainder), the eigenvalues, the commit barrier and the tensor-memory slot
-constexpr int kOffA = 0;
-constexpr int kOffB = 2 * kTile;
-constexpr int kOffL = kOffB + 12 * kMat;
-constexpr int kOffBar = kOffL + 3 * 16 * 4;
-constexpr int kSmemTc = kOffBar + 16;
+// Dynamic shared memory: operand A (head, and the remainder with SPLIT), the
+// six matrices (heads, and remainders with SPLIT), the eigenvalues, the
+// commit barrier and the tensor-memory slot.
+template <bool SPLIT>
+struct TcLay {
+  static constexpr int NA = SPLIT ? 2 : 1, NB = SPLIT ? 12 : 6;
+  static constexpr int OFF_A = 0;
+  static constexpr int OFF_B = NA * kTile;
+  static constexpr int OFF_L = OFF_B + NB * kMat;
+  static constexpr int OFF_BAR = OFF_L + 3 * 16 * 4;
+  static constexpr int BYTES = OFF_BAR + 16;
+};
 
 __device__ __forceinline__ uint32_t su32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -60,12 +67,13 @@ __device__ __forceinline__ float tf32(float x) {
   return __uint_as_float(r);
 }
 
-// head and remainder of v at (row, k) of a split operand pair
+// v at (row, k): its TF32 head, and with SPLIT the TF32 remainder
+template <bool SPLIT>
 __device__ __forceinline__ void put_split(unsigned char *head, unsigned char *rem, int off,
                                           float v) {
   const float h = tf32(v);
   *reinterpret_cast<float *>(head + off) = h;
-  *reinterpret_cast<float *>(rem + off) = tf32(v - h);
+  if constexpr (SPLIT) *reinterpret_cast<float *>(rem + off) = tf32(v - h);
 }
 
 // Shared-memory matrix descriptor: start, leading (K) and stride (rows) byte
@@ -118,7 +126,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 }  // namespace
 
-template <int NP>
+template <int NP, bool SPLIT>
 __global__ void __launch_bounds__(kTcThreads)
     asm_solve_tc_kernel(Topo t, const float *__restrict__ S, const float *__restrict__ lam,
                         const float *__restrict__ r, float *__restrict__ z,
@@ -126,16 +134,17 @@ __global__ void __launch_bounds__(kTcThreads)
   constexpr int n = NP + 2, n2 = n * n, N = NP - 1, NP2 = NP * NP;
   static_assert(n2 <= 128 && n <= 16, "extended element too large for one 128 x 16 product");
   extern __shared__ __align__(1024) unsigned char smt[];
-  unsigned char *Ah = smt + kOffA, *Ar = Ah + kTile;  // operand A: head, remainder
-  unsigned char *Bh = smt + kOffB, *Br = Bh + 6 * kMat;  // 6 matrices: head, remainder
-  float *sL = reinterpret_cast<float *>(smt + kOffL);    // [3][16] eigenvalues
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smt + kOffBar);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(smt + kOffBar + 8);
+  using Lay = TcLay<SPLIT>;
+  unsigned char *Ah = smt + Lay::OFF_A, *Ar = SPLIT ? Ah + kTile : nullptr;  // A: head, rem.
+  unsigned char *Bh = smt + Lay::OFF_B, *Br = SPLIT ? Bh + 6 * kMat : nullptr;  // 6 matrices
+  float *sL = reinterpret_cast<float *>(smt + Lay::OFF_L);  // [3][16] eigenvalues
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smt + Lay::OFF_BAR);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(smt + Lay::OFF_BAR + 8);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int p = tid;  // accumulator row of this thread
 
   // zero the operands once: rows >= n^2 and K, N >= n are never written again
-  for (int q = tid; q < (2 * kTile + 12 * kMat) / 4; q += kTcThreads)
+  for (int q = tid; q < (Lay::NA * kTile + Lay::NB * kMat) / 4; q += kTcThreads)
     reinterpret_cast<float *>(smt)[q] = 0.f;
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
@@ -161,8 +170,8 @@ __global__ void __launch_bounds__(kTcThreads)
     for (int q = tid; q < 3 * n * n; q += kTcThreads) {
       const int d = q / (n * n), a = (q / n) % n, m = q % n;
       const float v = S[e * 3 * n * n + q];
-      put_split(Bh + d * kMat, Br + d * kMat, toff(m, a), v);
-      put_split(Bh + (3 + d) * kMat, Br + (3 + d) * kMat, toff(a, m), v);
+      put_split<SPLIT>(Bh + d * kMat, Br + d * kMat, toff(m, a), v);
+      put_split<SPLIT>(Bh + (3 + d) * kMat, Br + (3 + d) * kMat, toff(a, m), v);
     }
     for (int q = tid; q < 3 * n; q += kTcThreads) sL[(q / n) * 16 + q % n] = lam[e * 3 * n + q];
     // gather: row p = (c, b) is the pencil along a (x); extended points
@@ -194,7 +203,7 @@ __global__ void __launch_bounds__(kTcThreads)
           const int64_t f = ci < 0 ? nzm : nzp;
           if (f >= 0) src = f * t.Np3 + ai + NP * (bi + NP * (ci < 0 ? N - 1 : 1));
         }
-        put_split(Ah, Ar, toff(p, a), src >= 0 ? r[src] : 0.f);
+        put_split<SPLIT>(Ah, Ar, toff(p, a), src >= 0 ? r[src] : 0.f);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -206,14 +215,18 @@ __global__ void __launch_bounds__(kTcThreads)
       const int mi = step < 3 ? step : 8 - step;
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ah = su32(Ah), ar = su32(Ar);
-        const uint32_t bh = su32(Bh + mi * kMat), br = su32(Br + mi * kMat);
-        // remainder products first, the head product last (two K steps each)
-        mma_tf32(tmem, sdesc(ah), sdesc(br), 0u);
-        mma_tf32(tmem, sdesc(ah + 256), sdesc(br + 256), 1u);
-        mma_tf32(tmem, sdesc(ar), sdesc(bh), 1u);
-        mma_tf32(tmem, sdesc(ar + 256), sdesc(bh + 256), 1u);
-        mma_tf32(tmem, sdesc(ah), sdesc(bh), 1u);
+        const uint32_t ah = su32(Ah), bh = su32(Bh + mi * kMat);
+        if constexpr (SPLIT) {
+          // remainder products first, the head product last (two K steps each)
+          const uint32_t ar = su32(Ar), br = su32(Br + mi * kMat);
+          mma_tf32(tmem, sdesc(ah), sdesc(br), 0u);
+          mma_tf32(tmem, sdesc(ah + 256), sdesc(br + 256), 1u);
+          mma_tf32(tmem, sdesc(ar), sdesc(bh), 1u);
+          mma_tf32(tmem, sdesc(ar + 256), sdesc(bh + 256), 1u);
+          mma_tf32(tmem, sdesc(ah), sdesc(bh), 1u);
+        } else {
+          mma_tf32(tmem, sdesc(ah), sdesc(bh), 0u);
+        }
         mma_tf32(tmem, sdesc(ah + 256), sdesc(bh + 256), 1u);
         asm volatile(
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -237,20 +250,20 @@ __global__ void __launch_bounds__(kTcThreads)
         const int hi = p / n, lo = p % n;
         if (step == 0) {  // row (c, b), columns ma -> rows (c, ma), K = b
 #pragma unroll
-          for (int m = 0; m < n; ++m) put_split(Ah, Ar, toff(hi * n + m, lo), v[m]);
+          for (int m = 0; m < n; ++m) put_split<SPLIT>(Ah, Ar, toff(hi * n + m, lo), v[m]);
         } else if (step == 1) {  // row (c, ma), columns mb -> rows (mb, ma), K = c
 #pragma unroll
-          for (int m = 0; m < n; ++m) put_split(Ah, Ar, toff(m * n + lo, hi), v[m]);
+          for (int m = 0; m < n; ++m) put_split<SPLIT>(Ah, Ar, toff(m * n + lo, hi), v[m]);
         } else if (step == 2) {  // row (mb, ma), columns mc: divide, same rows, K = mc
           const float lxy = sL[lo] + sL[16 + hi];
 #pragma unroll
-          for (int m = 0; m < n; ++m) put_split(Ah, Ar, toff(p, m), v[m] / (sL[32 + m] + lxy));
+          for (int m = 0; m < n; ++m) put_split<SPLIT>(Ah, Ar, toff(p, m), v[m] / (sL[32 + m] + lxy));
         } else if (step == 3) {  // row (mb, ma), columns c -> rows (c, ma), K = mb
 #pragma unroll
-          for (int m = 0; m < n; ++m) put_split(Ah, Ar, toff(m * n + lo, hi), v[m]);
+          for (int m = 0; m < n; ++m) put_split<SPLIT>(Ah, Ar, toff(m * n + lo, hi), v[m]);
         } else if (step == 4) {  // row (c, ma), columns b -> rows (c, b), K = ma
 #pragma unroll
-          for (int m = 0; m < n; ++m) put_split(Ah, Ar, toff(hi * n + m, lo), v[m]);
+          for (int m = 0; m < n; ++m) put_split<SPLIT>(Ah, Ar, toff(hi * n + m, lo), v[m]);
         } else {  // row (c, b), columns a: own points to z, face layers to ext
           const int c = hi, b = lo;
           const bool bown = b >= 1 && b <= N + 1, cown = c >= 1 && c <= N + 1;
@@ -281,10 +294,11 @@ __global__ void __launch_bounds__(kTcThreads)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
-template <int NP>
+template <int NP, bool SPLIT>
 static void asm_tc_np(const AsmData &A, const Level &L, const float *r, float *z, float *ext,
                       cudaStream_t st) {
-  auto kern = asm_solve_tc_kernel<NP>;
+  auto kern = asm_solve_tc_kernel<NP, SPLIT>;
+  constexpr int kSmemTc = TcLay<SPLIT>::BYTES;
   static std::atomic<int> occ[64] = {};
   int dev = 0;
   SEM_CHECK_CUDA(cudaGetDevice(&dev));
@@ -314,20 +328,27 @@ static void asm_tc_np(const AsmData &A, const Level &L, const float *r, float *z
   SEM_CHECK_CUDA(cudaGetLastError());
 }
 
-void launch_asm_solve_tc(const AsmData &A, const Level &L, const float *r, float *z, float *ext,
-                         cudaStream_t st) {
-  SEM_REQUIRE(A.S32.p && A.lam32.p && ext && L.err.p, "Schwarz FP32 data were not built");
+template <bool SPLIT>
+static void asm_tc_any(const AsmData &A, const Level &L, const float *r, float *z, float *ext,
+                       cudaStream_t st) {
   switch (L.t.Np) {
-    case 2: asm_tc_np<2>(A, L, r, z, ext, st); break;
-    case 3: asm_tc_np<3>(A, L, r, z, ext, st); break;
-    case 4: asm_tc_np<4>(A, L, r, z, ext, st); break;
-    case 5: asm_tc_np<5>(A, L, r, z, ext, st); break;
-    case 6: asm_tc_np<6>(A, L, r, z, ext, st); break;
-    case 7: asm_tc_np<7>(A, L, r, z, ext, st); break;
-    case 8: asm_tc_np<8>(A, L, r, z, ext, st); break;
-    case 9: asm_tc_np<9>(A, L, r, z, ext, st); break;
+    case 2: asm_tc_np<2, SPLIT>(A, L, r, z, ext, st); break;
+    case 3: asm_tc_np<3, SPLIT>(A, L, r, z, ext, st); break;
+    case 4: asm_tc_np<4, SPLIT>(A, L, r, z, ext, st); break;
+    case 5: asm_tc_np<5, SPLIT>(A, L, r, z, ext, st); break;
+    case 6: asm_tc_np<6, SPLIT>(A, L, r, z, ext, st); break;
+    case 7: asm_tc_np<7, SPLIT>(A, L, r, z, ext, st); break;
+    case 8: asm_tc_np<8, SPLIT>(A, L, r, z, ext, st); break;
+    case 9: asm_tc_np<9, SPLIT>(A, L, r, z, ext, st); break;
     default: fail(SEM_EINVAL, "tensor-core Schwarz smoother: order %d unsupported", L.t.N);
   }
+}
+
+void launch_asm_solve_tc(const AsmData &A, const Level &L, const float *r, float *z, float *ext,
+                         bool split, cudaStream_t st) {
+  SEM_REQUIRE(A.S32.p && A.lam32.p && ext && L.err.p, "Schwarz FP32 data were not built");
+  if (split) asm_tc_any<true>(A, L, r, z, ext, st);
+  else asm_tc_any<false>(A, L, r, z, ext, st);
 }
 
 }  // namespace sem

@@ -29,7 +29,7 @@ SEM_FIELD_X, SEM_FIELD_Y, SEM_FIELD_Z, SEM_FIELD_MASS, SEM_FIELD_MULT, SEM_FIELD
 SEM_SOLVER_PCG, SEM_SOLVER_FLEXCG, SEM_SOLVER_FGMRES = 0, 1, 2
 SEM_COARSE_JACOBI, SEM_COARSE_MG = 0, 1
 SEM_RHS_HOST, SEM_RHS_MANUFACTURED = 0, 1
-SEM_SMOOTH_JACOBI, SEM_SMOOTH_ASM, SEM_SMOOTH_ASM_TC = 0, 1, 2
+SEM_SMOOTH_JACOBI, SEM_SMOOTH_ASM, SEM_SMOOTH_ASM_TC, SEM_SMOOTH_ASM_TF32 = 0, 1, 2, 3
 SEM_EAGAIN, SEM_EBUSY = 6, 7
 SEM_MAX_ORDER = 11
 

@@ -497,11 +497,54 @@ def test_schwarz_tc_flexcg_reaches_1e8(bc):
     assert abs(its[sem.SEM_SMOOTH_ASM_TC] - its[sem.SEM_SMOOTH_ASM]) <= 1, its
 
 
+@pytest.mark.parametrize("bc,orders,e", [(0, (5, 2, 1), (3, 2, 2)), (1, (7, 3, 1), (2, 3, 2))])
+def test_schwarz_tf32_vcycle_within_tf32_accuracy(bc, orders, e):
+    """TF32 local solves (operands rounded once to 11 significant bits, FP32
+    accumulation): the V-cycle stays within 1e-2 of the FP64 oracle's, a
+    bound a few hundred TF32 unit roundoffs (2^-11) wide."""
+    v = inputs.box_vertices(*e, 0.1, 7)
+    m = sem.Mesh(*e, orders[0], bc, verts=v)
+    Po = oracle.PMG(*e, list(orders), bc, v, cheb_degree=2, lanczos_steps=20, seed=4,
+                    coarse_tol=0.0, coarse_maxit=12, smoother="asm")
+    L = Po.levels[0]
+    r = L.gs(inputs.random_field(L.nl, 8)) * L.mask
+    if bc == 1:
+        r -= L.dot(r, np.ones(L.nl)) / L.ng
+    P = sem.Pmg(m, orders=orders, smoother_dtype=sem.SEM_F32, coarse_tol=0.0, coarse_maxit=12,
+                seed=4, cheb_degree=2, smoother=sem.SEM_SMOOTH_ASM_TF32)
+    zd = torch.empty(L.nl, device=DEV, dtype=torch.float64)
+    sem.sem_pmg_vcycle(P, torch.tensor(r, device=DEV), zd)
+    err = rel(zd.cpu().numpy(), Po.vcycle(r))
+    assert err < 1e-2, err
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_schwarz_tf32_flexcg_reaches_1e8(bc):
+    """The flexible outer CG absorbs the TF32 rounding of the smoother."""
+    e = (3, 3, 2)
+    v = inputs.box_vertices(*e, 0.1, 3)
+    m = sem.Mesh(*e, 7, bc, verts=v)
+    L = oracle.Level(*e, 7, bc, v)
+    b = manufactured(L)[1] if bc == 0 else fourier_rhs(L)
+    its = {}
+    for sm in (sem.SEM_SMOOTH_ASM, sem.SEM_SMOOTH_ASM_TF32):
+        P = sem.Pmg(m, orders=(7, 3, 1), smoother_dtype=sem.SEM_F32, cheb_degree=3,
+                    coarse_tol=1e-2, coarse_maxit=50, smoother=sm)
+        bd = torch.tensor(b, device=DEV)
+        xd = torch.zeros_like(bd)
+        info = sem.sem_solve(m, P, bd, xd, sem.SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=100)
+        assert info["status"] == sem.SEM_OK, info
+        assert residual(L, b, xd.cpu().numpy()) <= 1.001e-8
+        its[sm] = info["iters"]
+    assert its[sem.SEM_SMOOTH_ASM_TF32] <= its[sem.SEM_SMOOTH_ASM] + 2, its
+
+
 def test_schwarz_tc_needs_fp32_smoothing():
     m = sem.Mesh(2, 2, 2, 5, 0)
-    with pytest.raises(sem.SemError) as ex:
-        sem.Pmg(m, orders=(5, 2, 1), smoother_dtype=sem.SEM_F64, smoother=sem.SEM_SMOOTH_ASM_TC)
-    assert ex.value.status == sem.SEM_EINVAL
+    for sm in (sem.SEM_SMOOTH_ASM_TC, sem.SEM_SMOOTH_ASM_TF32):
+        with pytest.raises(sem.SemError) as ex:
+            sem.Pmg(m, orders=(5, 2, 1), smoother_dtype=sem.SEM_F64, smoother=sm)
+        assert ex.value.status == sem.SEM_EINVAL
 
 
 def test_schwarz_order_limit():
