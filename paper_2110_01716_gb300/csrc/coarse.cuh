@@ -1,4 +1,5 @@
-// coarse.cuh -- persistent FP64 Jacobi-PCG of the N = 1 coarsest level.
+// coarse.cuh -- the N = 1 coarsest level: persistent FP64 Jacobi-PCG, and FP64 CG
+// preconditioned by a geometric lattice multigrid V-cycle in FP32 (coarse_mg.cu).
 #pragma once
 
 #include <memory>
