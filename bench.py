@@ -68,8 +68,8 @@ PAIR_PEAK_TFLOPS = 152 * 128 * 2.07e9 / PAIR_INSTR_PER_FMA * 2 / 1e12
 # DRAM traffic of one fine-level FP64 operator launch per local point (the
 # form with the inner product folded in, as in the solve), from an ncu capture
 # (profiles/ax_f64pair_N7.md), valid while the kernel source is unchanged.
-AX_TRAFFIC = {"source_sha256": "6b16e73cafe6141d70ec23adcdb0a12c84ac3600ad31a9b52760e2140cf8883b",
-              "bytes_per_point": 63.38}
+AX_TRAFFIC = {"source_sha256": "6be51339915d304430207d3ee5a7908f9bc6ecc41030ae6dba61825fd4488a18",
+              "bytes_per_point": 63.18}
 # The same for the smoother's assembled FP32 operator, per factor storage
 # (profiles/ax32_N7.md), valid while ax32.cu is unchanged.
 AX32_TRAFFIC = {"f32": {"source_sha256": "a1c86ef6bae402e521ec9400dc4df4087b40792cad358632c0c31adec941b4d2",

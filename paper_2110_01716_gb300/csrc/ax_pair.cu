@@ -31,7 +31,7 @@ static void launch_pair_np(const Level &L, const double *u, double *w, cudaStrea
   int64_t blocks = (L.t.E + S::NE - 1) / S::NE;
   const int64_t cap = 152 * 16;
   int grid = (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
-  const size_t shm = sizeof(float2) * ((size_t)NP * (NP + 1) + 3 * (size_t)S::NE * S::NP3);
+  const size_t shm = sizeof(float2) * (size_t)S::SMEM_PAIRS;
   static std::atomic<bool> attr_set[64] = {};  // per function and device (host threads may race)
   int dev = 0;
   SEM_CHECK_CUDA(cudaGetDevice(&dev));

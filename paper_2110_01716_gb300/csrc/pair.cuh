@@ -54,6 +54,57 @@ __device__ __forceinline__ float2 pair_norm(float s, float c) {
   return make_float2(t, __fsub_rn(c, __fsub_rn(t, s)));
 }
 
+// a + b for pairs: TwoSum of the heads, the tails and its error added, then
+// renormalised.  The error is a few units of 2^-46 of |a| + |b|, the same
+// scale as the rounding of the sums it feeds.
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
+  const float t = __fadd_rn(a.x, b.x);
+  const float z = __fsub_rn(t, a.x);
+  const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(t, z)), __fsub_rn(b.x, z));
+  return pair_norm(t, __fadd_rn(err, __fadd_rn(a.y, b.y)));
+}
+
+__device__ __forceinline__ float2 pair_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// v <- M v in place for a centro-antisymmetric NP x NP matrix M
+// (M[NP-1-a][NP-1-b] = -M[a][b]; the GLL differentiation matrix and its
+// transpose are).  With b' = NP-1-b, H = NP/2, s_b = v_b + v_b' and
+// d_b = v_b - v_b' (b < H):
+//   ((Mv)_a + (Mv)_a') / 2 = sum_b odd[a][b] d_b,   odd[a][b]  = (M_ab - M_ab') / 2,
+//   ((Mv)_a - (Mv)_a') / 2 = sum_b even[a][b] s_b,  even[a][b] = (M_ab + M_ab') / 2,
+// with, for odd NP, the extra column even[a][H] = M_a,mid taken against
+// v_mid, and the middle row (Mv)_mid = sum_b odd[H][b] d_b.  The NP^2
+// products become about NP^2 / 2 plus 2 NP pair additions.
+// odd is (H + NP%2) x H, even is H x (H + NP%2), both row-major.
+template <int NP>
+__device__ __forceinline__ void pair_apply_eo(const float2 *odd, const float2 *even,
+                                              float2 (&v)[NP]) {
+  constexpr int H = NP / 2, HO = H + (NP & 1);
+  float2 sv[HO], dv[H];
+#pragma unroll
+  for (int b = 0; b < H; ++b) {
+    sv[b] = pair_add(v[b], v[NP - 1 - b]);
+    dv[b] = pair_add(v[b], pair_neg(v[NP - 1 - b]));
+  }
+  if constexpr (HO > H) sv[H] = v[H];
+#pragma unroll
+  for (int a = 0; a < H; ++a) {
+    float ps = 0.f, pc = 0.f, ms = 0.f, mc = 0.f;
+#pragma unroll
+    for (int b = 0; b < H; ++b) pair_fma(odd[a * H + b], dv[b], ps, pc);
+#pragma unroll
+    for (int b = 0; b < HO; ++b) pair_fma(even[a * HO + b], sv[b], ms, mc);
+    v[a] = pair_add(make_float2(ps, pc), make_float2(ms, mc));
+    v[NP - 1 - a] = pair_add(make_float2(ps, pc), make_float2(-ms, -mc));
+  }
+  if constexpr (HO > H) {
+    float ps = 0.f, pc = 0.f;
+#pragma unroll
+    for (int b = 0; b < H; ++b) pair_fma(odd[H * H + b], dv[b], ps, pc);
+    v[H] = pair_norm(ps, pc);
+  }
+}
+
 
 template <int NP>
 struct PairShape {
@@ -63,13 +114,19 @@ struct PairShape {
   static constexpr int THREADS = NE * NP2;
   // two CTAs per SM when the register budget allows (16 warps hide latency)
   static constexpr int MIN_CTAS = THREADS >= 128 ? 2 : 4;
+  // even/odd halves of D and D^T (pair_apply_eo), H x (H + NP%2) pairs each
+  static constexpr int NEO = (NP / 2) * (NP / 2 + (NP & 1));
+  // dynamic shared memory in float2: D, the four even/odd blocks, u, W_r, W_s
+  static constexpr int SMEM_PAIRS = NP * (NP + 1) + 4 * NEO + 3 * NE * NP3;
 };
 
 // Three phases per element, with one barrier before the last:
-//  A: u_r, u_s (shared) and u_t (registers) for the whole (i,j) column;
+//  A: u_r, u_s (shared) and u_t (registers, by the even/odd halves of D) for
+//     the whole (i,j) column;
 //  B: pointwise geometric mix in place (each thread reads and writes only its
 //     own points), G streamed from HBM;
-//  C: transposed contractions reading the fluxes of the whole element.
+//  C: transposed contractions reading the fluxes of the whole element (the
+//     t-direction again by even/odd halves, of D^T, in registers).
 // Keeping the fluxes in shared memory instead of registers lets two CTAs
 // share an SM.
 template <int NP, bool FUSED>
@@ -79,8 +136,10 @@ __global__ void __launch_bounds__(PairShape<NP>::THREADS, PairShape<NP>::MIN_CTA
   using S = PairShape<NP>;
   constexpr int NP2 = S::NP2, NP3 = S::NP3, NE = S::NE;
   extern __shared__ float2 smem_pair[];
+  constexpr int H = NP / 2, HO = H + (NP & 1), NEO = S::NEO;
   float2(*sD)[NP + 1] = reinterpret_cast<float2(*)[NP + 1]>(smem_pair);
-  float2(*sU)[NP3] = reinterpret_cast<float2(*)[NP3]>(smem_pair + NP * (NP + 1));
+  float2 *sEO = smem_pair + NP * (NP + 1);  // D odd, D even, D^T odd, D^T even
+  float2(*sU)[NP3] = reinterpret_cast<float2(*)[NP3]>(sEO + 4 * NEO);
   float2(*sR)[NP3] = sU + NE;
   float2(*sS)[NP3] = sR + NE;
 
@@ -91,6 +150,19 @@ __global__ void __launch_bounds__(PairShape<NP>::THREADS, PairShape<NP>::MIN_CTA
     const double d = bs.D[q];
     const float hi = (float)d;
     sD[q / NP][q % NP] = make_float2(hi, (float)(d - (double)hi));
+  }
+  for (int q = threadIdx.x; q < 4 * NEO; q += blockDim.x) {
+    const int m = q / NEO, r = q - m * NEO;
+    const bool tr = m >= 2, ev = (m & 1) != 0;
+    const int cols = ev ? HO : H;
+    const int a = r / cols, b = r - a * cols;
+    // entry (x, y) of D (tr false) or D^T (tr true)
+    auto Dm = [&](int x, int y) { return tr ? bs.D[y * NP + x] : bs.D[x * NP + y]; };
+    double d;
+    if (!ev) d = 0.5 * (Dm(a, b) - Dm(a, NP - 1 - b));
+    else d = b < H ? 0.5 * (Dm(a, b) + Dm(a, NP - 1 - b)) : Dm(a, H);
+    const float hi = (float)d;
+    sEO[q] = make_float2(hi, (float)(d - (double)hi));
   }
   float ds = 0.f, dc = 0.f;  // <u, A_L u> of this thread's points (fused form)
   for (int64_t e0 = (int64_t)blockIdx.x * NE; e0 < E; e0 += (int64_t)gridDim.x * NE) {
@@ -117,14 +189,7 @@ __global__ void __launch_bounds__(PairShape<NP>::THREADS, PairShape<NP>::MIN_CTA
     __syncthreads();
     if (active) {
       // A: reference gradients; u_t overwrites the column of u in registers
-      float ts[NP], tc[NP];
-#pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        ts[k] = 0.f;
-        tc[k] = 0.f;
-#pragma unroll
-        for (int l = 0; l < NP; ++l) pair_fma(sD[k][l], rt[l], ts[k], tc[k]);
-      }
+      pair_apply_eo<NP>(sEO, sEO + NEO, rt);
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
         float rs = 0.f, rc = 0.f, ss = 0.f, sc = 0.f;
@@ -135,7 +200,6 @@ __global__ void __launch_bounds__(PairShape<NP>::THREADS, PairShape<NP>::MIN_CTA
         }
         sR[le][ij + k * NP2] = pair_norm(rs, rc);
         sS[le][ij + k * NP2] = pair_norm(ss, sc);
-        rt[k] = pair_norm(ts[k], tc[k]);
       }
       // B: W = G (u_r, u_s, u_t), in place
       const float2 *Ge = G2 + e * 6 * NP3 + ij;
@@ -158,16 +222,16 @@ __global__ void __launch_bounds__(PairShape<NP>::THREADS, PairShape<NP>::MIN_CTA
     }
     __syncthreads();
     if (active) {
-      // C: w = D^T W_r + D^T W_s + D^T W_t
+      // C: w = D^T W_r + D^T W_s + D^T W_t, the last term first, in registers
       double *we = w + e * NP3;
+      pair_apply_eo<NP>(sEO + 2 * NEO, sEO + 3 * NEO, rt);
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
-        float s = 0.f, c = 0.f;
+        float s = rt[k].x, c = rt[k].y;
 #pragma unroll
         for (int l = 0; l < NP; ++l) {
           pair_fma(sD[l][i], sR[le][l + j * NP + k * NP2], s, c);
           pair_fma(sD[l][j], sS[le][i + l * NP + k * NP2], s, c);
-          pair_fma(sD[l][k], rt[l], s, c);
         }
         const float2 r = pair_norm(s, c);
         we[ij + k * NP2] = widen_f32(r.x) + widen_f32(r.y);
