@@ -58,7 +58,7 @@ WORKLOAD = ("mixed-precision Neumann pressure solve: E=48^3=110592 jittered hexe
 # Fallback peaks of the recipe, used only when MEASURED_PEAKS.json is absent.
 FALLBACK_HBM_GBS = 6800.0
 # FP64 pipe: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (the part's
-# nominal 1.25 TFLOP/s; an FMA-chain probe on this machine measured 1.195).
+# nominal 1.25 TFLOP/s; an FMA-chain probe on a GB300 measured 1.195).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # The FP64 operator runs in FP32-pair arithmetic: one FP64-equivalent FMA
 # costs 12 FP32-pipe instructions, so its ALU roof is the FP32 issue rate
