@@ -39,15 +39,16 @@ __global__ void cheb_start_kernel(Topo t, const T *__restrict__ b, const T *__re
 }
 
 // One Chebyshev step after w = A d (assembled and masked):
-// r -= w;  d = c1 d + c2 dinv r;  x += d.
+// r -= w;  d = c1 d + c2 dinv r;  x += d.  The last step of a smoothing
+// (last) does not store r: the V-cycle recomputes the residual from x.
 template <typename T>
 __global__ void cheb_step_kernel(Topo t, const T *__restrict__ w, const T *__restrict__ dinv,
                                  T *__restrict__ r, T *__restrict__ d, T *__restrict__ x, T c1,
-                                 T c2) {
+                                 T c2, int last) {
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < (uint32_t)t.nl;
        l += gridDim.x * blockDim.x) {
     T rl = r[l] - w[l];
-    r[l] = rl;
+    if (!last) r[l] = rl;
     T dl = c1 * d[l] + c2 * dinv[l] * rl;
     d[l] = dl;
     x[l] += dl;
@@ -88,11 +89,13 @@ __global__ void cheb_start4_kernel(int64_t n4, const float4 *__restrict__ b,
   }
 }
 
-// first: the step after a start that wrote d only (r = b, x = d there).
+// first: the step after a start that wrote d only (r = b, x = d there);
+// last: the smoothing's last step, whose r is not stored.
 __global__ void cheb_step4_kernel(int64_t n4, const float4 *__restrict__ w,
                                   const float4 *__restrict__ dinv, const float4 *__restrict__ b,
                                   float4 *__restrict__ r, float4 *__restrict__ d,
-                                  float4 *__restrict__ x, float c1, float c2, int first) {
+                                  float4 *__restrict__ x, float c1, float c2, int first,
+                                  int last) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4;
        q += (int64_t)gridDim.x * blockDim.x) {
     const float4 wl = w[q], di = dinv[q], d0 = d[q];
@@ -101,7 +104,7 @@ __global__ void cheb_step4_kernel(int64_t n4, const float4 *__restrict__ w,
     const float4 rl = make_float4(r0.x - wl.x, r0.y - wl.y, r0.z - wl.z, r0.w - wl.w);
     const float4 dl = make_float4(c1 * d0.x + c2 * di.x * rl.x, c1 * d0.y + c2 * di.y * rl.y,
                                   c1 * d0.z + c2 * di.z * rl.z, c1 * d0.w + c2 * di.w * rl.w);
-    r[q] = rl;
+    if (!last) r[q] = rl;
     d[q] = dl;
     x[q] = make_float4(x0.x + dl.x, x0.y + dl.y, x0.z + dl.z, x0.w + dl.w);
   }
@@ -682,17 +685,20 @@ static void smooth(sem_pmg *P, int l, bool x_zero, cudaStream_t st) {
   for (int it = 2; it <= P->desc.cheb_degree; ++it) {
     level_apply<T>(Q, d, w, st);
     double rho1 = 1.0 / (2.0 * sigma - rho);
+    // r after the last step is dead: the V-cycle forms b - A x for the
+    // restriction, and the post-smoothing starts again from b - A x
+    const int last = it == P->desc.cheb_degree;
     TraceScope ts(f64 ? "cheb_step_f64" : "cheb_step_f32", L.t.N, st);
     if constexpr (sizeof(T) == 4) {
       if (v4)
         cheb_step4_kernel<<<vec_grid(n / 4), kVecThreads, 0, st>>>(
             n / 4, (const float4 *)w, (const float4 *)dinv, (const float4 *)b, (float4 *)r,
             (float4 *)d, (float4 *)x, (float)(rho1 * rho), (float)(2.0 * rho1 / delta),
-            (int)(only_d && it == 2));
+            (int)(only_d && it == 2), last);
     }
     if (!v4)
-      cheb_step_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(L.t, w, dinv, r, d, x,
-                                                               (T)(rho1 * rho), (T)(2.0 * rho1 / delta));
+      cheb_step_kernel<T><<<vec_grid(n), kVecThreads, 0, st>>>(
+          L.t, w, dinv, r, d, x, (T)(rho1 * rho), (T)(2.0 * rho1 / delta), last);
     SEM_CHECK_CUDA(cudaGetLastError());
     rho = rho1;
   }
