@@ -81,7 +81,7 @@ AX32_TRAFFIC = {"f32": {"source_sha256": "a1c86ef6bae402e521ec9400dc4df4087b4079
 def parse_args():
     p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=15)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--side", type=int, default=E_SIDE, help="elements per direction")
