@@ -501,11 +501,24 @@ def oracle_sample_solve(side=12):
     return dt, L.ng, info["iters"], threads
 
 
+def oracle_extrapolated(sample_s, sample_iters, sample_side, side, gpu_iters, n_global):
+    """The oracle's full-size solve time, extrapolated: the sample's seconds
+    per iteration scaled by the element count (side / sample_side)^3, times
+    the GPU's iteration count.  Optimistic for the oracle, whose Jacobi-PCG
+    coarse solve needs more iterations on a larger coarse grid."""
+    per_it = sample_s / max(sample_iters, 1) * (side / sample_side) ** 3
+    solve_s = per_it * gpu_iters
+    return {"kind": "extrapolated", "per_iteration_s": per_it, "iterations": gpu_iters,
+            "solve_s": solve_s, "gdofs": n_global / solve_s / 1e9,
+            "basis": f"{sample_side}^3 sample: seconds per iteration x (E / {sample_side}^3) "
+                     "x the GPU's iterations"}
+
+
 def oracle_timings():
     """The oracle on this host, on one core and on all of them: config 1 (the
     8^3-element, N = 7 Dirichlet manufactured solve, Jacobi-PCG to 1e-10)
-    and config 2 at 16^3 elements (local operator, gather-scatter and the
-    assembled operator, u ~ U(-1, 1))."""
+    and config 2 at 16^3, 24^3 and 32^3 elements (local operator,
+    gather-scatter and the assembled operator, u ~ U(-1, 1))."""
     import numpy as np
 
     import oracle
@@ -527,21 +540,22 @@ def oracle_timings():
         dt = time.perf_counter() - t0
         row["config1_pcg"] = {"s": round(dt, 3), "iters": info["iters"],
                               "gdofs": round(L.ng / dt / 1e9, 6)}
-        k = 16
-        L2 = oracle.Level(k, k, k, ORDER, 0, inputs.box_vertices(k, k, k, 0.1, 2 + k))
-        u = np.random.default_rng(2 + k).uniform(-1, 1, L2.nl)
-        t0 = time.perf_counter()
-        w = L2.ax_local(u)
-        t1 = time.perf_counter()
-        L2.gs(w)
-        t2 = time.perf_counter()
-        L2.ax(u)
-        t3 = time.perf_counter()
-        row["config2_16cube"] = {"ax_local_s": round(t1 - t0, 4), "gs_s": round(t2 - t1, 4),
-                                 "ax_assembled_s": round(t3 - t2, 4),
-                                 "ax_local_gdofs": round(L2.nl / (t1 - t0) / 1e9, 4)}
+        del L
+        for k in (16, 24, 32):
+            L2 = oracle.Level(k, k, k, ORDER, 0, inputs.box_vertices(k, k, k, 0.1, 2 + k))
+            u = np.random.default_rng(2 + k).uniform(-1, 1, L2.nl)
+            t0 = time.perf_counter()
+            w = L2.ax_local(u)
+            t1 = time.perf_counter()
+            L2.gs(w)
+            t2 = time.perf_counter()
+            L2.ax(u)
+            t3 = time.perf_counter()
+            row[f"config2_{k}cube"] = {"ax_local_s": round(t1 - t0, 4), "gs_s": round(t2 - t1, 4),
+                                       "ax_assembled_s": round(t3 - t2, 4),
+                                       "ax_local_gdofs": round(L2.nl / (t1 - t0) / 1e9, 4)}
+            del L2, u, w
         out[label] = row
-        del L, L2
     oracle.set_threads(allc)
     return out
 
@@ -810,6 +824,8 @@ def main():
         if world == 1:
             dt, ng_s, it_s, threads = oracle_sample_solve(12)
             line["oracle_timings"] = oracle_timings()
+            line["oracle_timings"]["config3_extrapolated"] = oracle_extrapolated(
+                dt, it_s, 12, side, line["iters"][0], ng)
             line["cpu_baseline"] = {
                 "value": ng_s / dt / 1e9, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
                 "sample": f"oracle FlexCG+pMG 7-3-1 solve to 1e-8 on a 12^3-element box of the "

@@ -46,3 +46,15 @@ def test_reference_arm_prints_one_contract_line():
 def test_reference_arm_other_ranks_exit_quietly():
     out = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert out.strip() == ""
+
+
+def test_oracle_extrapolation_scales_by_elements_and_gpu_iterations():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    # 12 iterations in 1.2 s on 12^3: 0.1 s per iteration, x 64 at 48^3, x 7
+    r = bench.oracle_extrapolated(1.2, 12, 12, 48, 7, 38272753)
+    assert r["kind"] == "extrapolated" and r["iterations"] == 7
+    assert abs(r["per_iteration_s"] - 6.4) < 1e-12
+    assert abs(r["solve_s"] - 44.8) < 1e-12
+    assert abs(r["gdofs"] - 38272753 / 44.8 / 1e9) < 1e-15
