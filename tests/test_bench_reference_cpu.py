@@ -2,7 +2,8 @@
 oracle on a bounded sample of the workload and prints one JSON line with the
 same metric, unit and direction as the GPU arm, a `cpu_baseline` describing
 the run and an `e2e` entry with no host-device bytes; under several ranks only
-rank 0 runs it."""
+rank 0 runs it.  Also the full-size oracle estimate the GPU arm reports beside
+its own line."""
 
 import json
 import os
