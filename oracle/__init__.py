@@ -3,7 +3,9 @@
 TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
 benchmark's CPU-baseline leg, never by the library.  ``build()`` compiles the C
 file with gcc (no FMA contraction, so x86 and Arm give the same bits) into
-``oracle/_build``; the wrappers below only marshal numpy arrays.
+``oracle/_build``; the wrappers below only marshal numpy arrays.  With
+``SEM_ORACLE_LIB`` set, ``lib()`` loads that already built library instead
+(the planted-mistake tests load altered copies of the oracle this way).
 """
 
 from __future__ import annotations
@@ -24,26 +26,34 @@ _ip = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into a shared object (OpenMP when available)."""
-    if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
-        return _OUT
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", _SRC, "-o",
-            _OUT + ".tmp", "-lm"]
+def compile_to(src: str, out: str) -> str:
+    """Compile the C source src into the shared object out (OpenMP when
+    available), with the oracle's flags."""
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", src, "-o",
+            out + ".tmp", "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
         subprocess.run(base, check=True, capture_output=True)
-    os.replace(_OUT + ".tmp", _OUT)
-    return _OUT
+    os.replace(out + ".tmp", out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into a shared object (OpenMP when available)."""
+    if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
+        return _OUT
+    return compile_to(_SRC, _OUT)
 
 
 def lib():
     global _lib
     if _lib is not None:
         return _lib
-    L = C.CDLL(build())
+    L = C.CDLL(os.environ.get("SEM_ORACLE_LIB") or build())
+    L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+    L.orc_splitmix64.restype = C.c_uint64
     L.orc_legendre.argtypes = [C.c_int, C.c_double]
     L.orc_legendre.restype = C.c_double
     L.orc_gll.argtypes = [C.c_int, _dp, _dp]

@@ -542,6 +542,10 @@ static uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
   return z ^ (z >> 31);
 }
 
+/* Value i of stream seed, exported so that the generator can be checked
+ * against the published reference stream. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t i) { return splitmix64_at(seed, i); }
+
 /* Largest eigenvalue of the symmetric tridiagonal (a diagonal, b off-diagonal,
  * size m) by bisection on the Sturm sequence count. */
 static double tridiag_max_eig(int m, const double *a, const double *b) {

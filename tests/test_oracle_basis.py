@@ -124,6 +124,16 @@ def test_box_vertices_generator():
     assert [int(g) for g in got] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
 
 
+def test_oracle_splitmix64_reference_stream(orc):
+    """The oracle's own generator (the Lanczos start vector) against the
+    published reference stream of splitmix64 for seed 0, and the stream
+    offset: value i of seed s is value 0 of seed s + i * gamma."""
+    ref = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    assert [orc.lib().orc_splitmix64(0, i) for i in range(3)] == ref
+    gamma = 0x9E3779B97F4A7C15
+    assert orc.lib().orc_splitmix64(2 * gamma % 2**64, 0) == ref[2]
+
+
 @pytest.mark.parametrize("N", [2, 3, 5, 7])
 def test_geometry_volume_and_moments_on_jittered_cube(orc, N):
     ex, ey, ez = 3, 2, 4

@@ -200,6 +200,36 @@ def test_flexcg_with_jacobi_equals_pcg(orc):
         np.testing.assert_allclose(xf, xp, atol=1e-11 * np.abs(xp).max())
 
 
+def test_flexcg_updates_are_A_conjugate_with_a_variable_preconditioner(orc):
+    """With the flexible coefficient beta = <z', r' - r> / <z, r>, the new
+    direction is A-conjugate to the previous one whatever the preconditioner
+    did (p' = z' + beta p and A p = (r - r') / alpha give <p', A p> = 0); the
+    Fletcher-Reeves coefficient <z', r'> / <z, r> keeps that only for a fixed
+    linear preconditioner.  The pMG V-cycle with a coarse CG stopped at a loose
+    tolerance is not linear, and FlexCG's successive updates x_{k+1} - x_k
+    (parallel to the directions) must still be A-conjugate."""
+    v = inputs.box_vertices(3, 3, 3, 0.1, 6)
+    P = orc.PMG(3, 3, 3, [5, 2, 1], DIR, v, cheb_degree=2, coarse_tol=0.3, coarse_maxit=50)
+    L = P.levels[0]
+    _, b = manufactured(L)
+    # the preconditioner is not linear here
+    r1 = L.gs(L.mask * np.random.default_rng(1).uniform(-1, 1, L.nl)) * L.mask
+    r2 = b
+    lin = P.vcycle(r1) + P.vcycle(r2) - P.vcycle(r1 + r2)
+    assert np.abs(lin).max() > 1e-4 * np.abs(P.vcycle(r1 + r2)).max()
+    xs = [np.zeros(L.nl)]
+    for its in (1, 2, 3, 4):
+        x, info = P.flexpcg(b, tol=0.0, maxit=its)
+        assert info["iters"] == its
+        xs.append(x)
+    d = [xs[k + 1] - xs[k] for k in range(4)]
+    for k in range(3):
+        Ad = L.ax(d[k])
+        num = abs(L.dot(d[k + 1], Ad))
+        den = np.sqrt(L.dot(d[k + 1], L.ax(d[k + 1])) * L.dot(d[k], Ad))
+        assert num <= 1e-9 * den, (k, num / den)
+
+
 @pytest.mark.parametrize("bc", [DIR, NEU])
 def test_pmg_flexcg_iterations_flat_under_refinement(orc, bc):
     iters = []
@@ -344,6 +374,25 @@ def test_projection_basis_is_a_orthonormal_and_best_fit(orc):
     assert abs(info["res_proj"] - rp_ref) <= 1e-9 * np.linalg.norm(b[rep])
     r = b - L.ax(x)
     assert np.sqrt(L.dot(r, r)) <= 1.001e-10 * np.sqrt(L.dot(b, b))
+
+
+def test_projection_basis_stays_a_orthonormal_after_loose_solves(orc):
+    """Solved only to 1e-3, a correction keeps a visible component in the span
+    of the basis; the one-pass Gram-Schmidt must still leave the basis
+    A-orthonormal, its norm taken as dx^T A dx minus the squared coefficients
+    (dense A from numpy)."""
+    e, N = 2, 4
+    v = inputs.box_vertices(e, e, e, 0.1, 5)
+    P = orc.PMG(e, e, e, [N, 2, 1], DIR, v, coarse_tol=1e-6, coarse_maxit=100)
+    L = P.levels[0]
+    A, rep = dense_unique(L, L.ax)
+    Q = orc.Projection(P, 8)
+    for n in range(6):
+        Q.solve(_sequence_rhs(L, 3 * n, DIR), tol=1e-3)
+    k = Q.nvec
+    assert k >= 4
+    Pm = np.stack([Q.vector(i)[0][rep] for i in range(k)], axis=1)
+    np.testing.assert_allclose(Pm.T @ A @ Pm, np.eye(k), atol=1e-9)
 
 
 def test_projection_of_a_right_hand_side_in_the_span_is_exact(orc):
