@@ -82,6 +82,8 @@ def lib():
                           C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.orc_cheb.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, _dp, _dp, _dp, C.c_int,
                            C.c_double, C.c_double, C.c_int]
+    L.orc_cheb_m.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _dp,
+                             _dp, C.c_int, C.c_double, C.c_double, C.c_int]
     L.orc_level_lanczos_max.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.POINTER(C.c_int)]
     L.orc_level_lanczos_max.restype = C.c_double
     L.orc_pmg_create.argtypes = [C.c_int] * 4 + [_i32p, C.c_int, _dp, C.c_int, C.c_int,
@@ -225,6 +227,25 @@ def cheb(n, apply, dinv, b, x, k, lmin, lmax, x_zero):
     x = np.ascontiguousarray(x, dtype=np.float64).copy()
     lib().orc_cheb(n, C.cast(cb, C.c_void_p), None, np.ascontiguousarray(dinv, dtype=np.float64),
                    np.ascontiguousarray(b, dtype=np.float64), x, k, lmin, lmax, int(x_zero))
+    return x
+
+
+def cheb_m(n, apply, prec, b, x, k, lmin, lmax, x_zero):
+    """Chebyshev smoothing on M A with Python operators ``apply(in) -> out``
+    (A) and ``prec(in) -> out`` (M), the form the Schwarz smoother uses."""
+
+    def wrap(f):
+        def _cb(_ctx, pin, pout):
+            vin = np.ctypeslib.as_array(pin, shape=(n,))
+            vout = np.ctypeslib.as_array(pout, shape=(n,))
+            vout[:] = f(vin.copy())
+
+        return APPLY_FN(_cb)
+
+    ca, cm = wrap(apply), wrap(prec)
+    x = np.ascontiguousarray(x, dtype=np.float64).copy()
+    lib().orc_cheb_m(n, C.cast(ca, C.c_void_p), None, C.cast(cm, C.c_void_p), None,
+                     np.ascontiguousarray(b, dtype=np.float64), x, k, lmin, lmax, int(x_zero))
     return x
 
 

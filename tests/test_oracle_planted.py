@@ -91,6 +91,38 @@ PLANTED = [
      "B[(i + 1) * n + (i + 1)] += 0.5 / he * L->w[i];", [ASM]),
     ("Schwarz left neighbour points in the wrong order",
      "int li[2] = {N - 1, N}, ai[2] = {0, 1};", "int li[2] = {N, N - 1}, ai[2] = {0, 1};", [ASM]),
+    ("Legendre derivative recurrence from the wrong term",
+     "double d2 = d0 + (2.0 * k + 1.0) * p1;", "double d2 = d1 + (2.0 * k + 1.0) * p1;", [BASIS]),
+    ("Newton step with the wrong sign in Legendre's equation",
+     "double d2p = (2.0 * x * dp - N * (N + 1.0) * p) / (1.0 - x * x);",
+     "double d2p = (2.0 * x * dp + N * (N + 1.0) * p) / (1.0 - x * x);", [BASIS]),
+    ("Dirichlet mask misses the bottom face",
+     "int onb = gx == 0 || gy == 0 || gz == 0 ||", "int onb = gx == 0 || gy == 0 ||",
+     [BASIS, OPER, SOLV]),
+    ("Jacobi diagonal not inverted",
+     "L->dinv[l] = L->mask[l] / L->dinv[l];", "L->dinv[l] = L->mask[l] * L->dinv[l];",
+     [OPER, SOLV]),
+    ("multiplicity never summed",
+     "  orc_gs(L->nl, L->ids, L->ng, L->mult);\n", "", [BASIS, OPER, SOLV]),
+    ("prolongation with a for b in the second factor",
+     "double Jb = transpose ? J[b * nc + j] : J[j * nc + b];",
+     "double Jb = transpose ? J[b * nc + j] : J[j * nc + a];", [SOLV]),
+    ("tridiagonal bisection keeps the lowest eigenvalue",
+     "if (cnt == m) hi = mid; else lo = mid;", "if (cnt >= 1) hi = mid; else lo = mid;",
+     [SOLV, ASM]),
+    ("Schwarz extension takes the shared face point",
+     "idx[out] = N - 1;", "idx[out] = N;", [ASM]),
+    ("Schwarz local matrix with A for B in x",
+     "B[2][c * n + c2] * A[1][b * n + b2] * B[0][a * n + a2] +",
+     "B[2][c * n + c2] * A[1][b * n + b2] * A[0][a * n + a2] +", [ASM]),
+    ("Chebyshev on M A starts with delta for theta",
+     "for (int64_t l = 0; l < n; ++l) d[l] = mr[l] / theta;",
+     "for (int64_t l = 0; l < n; ++l) d[l] = mr[l] / delta;", [ASM, SOLV]),
+    ("FGMRES back substitution adds instead of subtracting",
+     "for (int q = i + 1; q < cols; ++q) s -= H[i * m + q] * y[q];",
+     "for (int q = i + 1; q < cols; ++q) s += H[i * m + q] * y[q];", [SOLV]),
+    ("projected solve forgets the best fit",
+     "    x[l] = xb;", "    x[l] = 0.0 * xb;", [SOLV]),
 ]
 
 

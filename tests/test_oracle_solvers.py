@@ -131,6 +131,36 @@ def test_chebyshev_error_polynomial_closed_form(orc, k):
     np.testing.assert_allclose(xa, xb, atol=1e-13)
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_chebyshev_on_MA_error_polynomial_closed_form(orc, k):
+    """The Chebyshev smoothing with a general preconditioner M (the form of the
+    Schwarz smoother): the error after k steps is
+    T_k((theta - M A)/delta) / T_k(theta/delta) times the initial error, for a
+    non-diagonal SPD M, evaluated through numpy's eigendecomposition of M A."""
+    n = 30
+    rng = np.random.Generator(np.random.PCG64(10 + k))
+    a = rng.uniform(0.5, 2.0, n)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    M = Q @ np.diag(rng.uniform(0.2, 1.0, n)) @ Q.T
+    lam, S = np.linalg.eig(M @ np.diag(a))
+    lam, S = lam.real, S.real
+    hi = 1.1 * lam.max()
+    lo = hi / 10
+    e0 = rng.standard_normal(n)
+    xstar = rng.standard_normal(n)
+    b = a * xstar
+    x = orc.cheb_m(n, lambda v: a * v, lambda v: M @ v, b, xstar - e0, k, lo, hi, x_zero=False)
+    theta, delta = (hi + lo) / 2, (hi - lo) / 2
+    T = np.polynomial.chebyshev.Chebyshev.basis(k)
+    factor = T((theta - lam) / delta) / T(theta / delta)
+    ref = S @ (factor * np.linalg.solve(S, e0))
+    np.testing.assert_allclose(xstar - x, ref, atol=1e-11 * np.abs(e0).max())
+    xa = orc.cheb_m(n, lambda v: a * v, lambda v: M @ v, b, np.zeros(n), k, lo, hi, x_zero=True)
+    xb = orc.cheb_m(n, lambda v: a * v, lambda v: M @ v, b, np.zeros(n), k, lo, hi,
+                    x_zero=False)
+    np.testing.assert_allclose(xa, xb, atol=1e-13 * np.abs(xb).max())
+
+
 @pytest.mark.parametrize("bc", [DIR, NEU])
 def test_lanczos_estimate_of_largest_eigenvalue(orc, bc):
     L = level(orc, 2, 2, 2, 4, bc)
