@@ -49,7 +49,8 @@ typedef enum {
   SEM_ENUMERIC = 5,  /* NaN or Inf met in a solver */
   SEM_EAGAIN = 6,    /* request still pending (sem_poll) */
   SEM_EBUSY = 7,     /* no free slot or memory for a request (sem_submit) */
-  SEM_ETIMEOUT = 8   /* a bounded wait ran out */
+  SEM_ETIMEOUT = 8   /* a bounded wait inside a kernel ran out (reported by
+                        the solves, see sem_solve) */
 } sem_status;
 
 typedef enum { SEM_F64 = 0, SEM_F32 = 1, SEM_F16 = 2, SEM_BF16 = 3 } sem_dtype;
@@ -97,6 +98,12 @@ typedef struct {
  * points), SEM_ENOMEM, SEM_ECUDA. */
 sem_status sem_mesh_create(const sem_mesh_desc *desc, void *stream, sem_mesh **out);
 sem_status sem_mesh_destroy(sem_mesh *mesh);
+
+/* Test hook: sets the fine level's wait-error flag from the host, as a
+ * kernel whose bounded wait ran out would, so that the next solve on the
+ * mesh reports SEM_ETIMEOUT (and clears it).  Nothing runs on the device.
+ * Synchronises `stream`.  Errors: SEM_EINVAL (null mesh), SEM_ECUDA. */
+sem_status sem_inject_wait_error(sem_mesh *mesh, void *stream);
 
 /* n_local = E (N+1)^3, n_global = (ex N+1)(ey N+1)(ez N+1) unique nodes,
  * dev_bytes = device memory owned by the mesh.  Any output may be NULL. */
@@ -262,7 +269,12 @@ typedef struct {
  * least-squares residual of each step and, at the end of a cycle, the
  * residual recomputed from x.
  * Returns SEM_OK, SEM_ENOTCONV (max_iter reached; x and info hold the last
- * iterate) or SEM_ENUMERIC (NaN/Inf).  Synchronises. */
+ * iterate), SEM_ENUMERIC (NaN/Inf) or SEM_ETIMEOUT: a kernel's bounded wait
+ * (a bulk copy that did not complete within its poll limit) ran out during
+ * the solve or since the last solve on this mesh, that kernel left its work
+ * undone, and x is not to be trusted.  The flags behind SEM_ETIMEOUT are
+ * read and cleared at the end of every solve (sem_solve, sem_solve_host,
+ * sem_solve_projected, served requests).  Synchronises. */
 sem_status sem_solve(sem_mesh *mesh, sem_pmg *pmg, const double *b, double *x,
                      const sem_solve_desc *desc, sem_solve_info *info, void *stream);
 

@@ -116,6 +116,39 @@ static void check_neumann_rhs(sem_mesh *M, const double *b, cudaStream_t st) {
 // column.  A cycle ends when the least-squares residual meets the tolerance
 // or after m steps; x is then updated and its residual recomputed, which
 // decides convergence (restarting from it otherwise).
+// A kernel whose bounded wait ran out (a bulk copy that never completed)
+// sets its level's flag and leaves the rest of its work undone.  After a
+// solve's last synchronisation the flags of every level it used are read and
+// cleared; a set flag makes the solve's status SEM_ETIMEOUT.
+static bool take_wait_errors(sem_mesh *M, sem_pmg *P, cudaStream_t st) {
+  std::vector<sem::Level *> levels{&M->fine};
+  if (P)
+    for (auto &q : P->levp)
+      if (q && q->L && q->L != &M->fine) levels.push_back(q->L);
+  bool any = false;
+  for (sem::Level *L : levels) {
+    if (!L->err.p) continue;
+    int v = 0;
+    SEM_CHECK_CUDA(cudaMemcpyAsync(&v, L->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (v != 0) {
+      any = true;
+      SEM_CHECK_CUDA(cudaMemsetAsync(L->err.p, 0, sizeof(int), st));
+    }
+  }
+  if (any) SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+  return any;
+}
+
+static sem_status report_wait_errors(sem_mesh *M, sem_pmg *P, cudaStream_t st,
+                                     sem_solve_info &info, sem_status status) {
+  if (!take_wait_errors(M, P, st)) return status;
+  info.status = SEM_ETIMEOUT;
+  set_error_message("a bounded wait in a kernel ran out (a bulk copy did not complete); "
+                    "the solve's results are incomplete");
+  return SEM_ETIMEOUT;
+}
+
 static sem_status run_fgmres(sem_mesh *M, sem_pmg *P, const double *b, double *x,
                              const sem_solve_desc &d, sem_solve_info &info, cudaStream_t st,
                              bool x_zero = false, bool check_rhs = true) {
@@ -231,7 +264,7 @@ static sem_status run_fgmres(sem_mesh *M, sem_pmg *P, const double *b, double *x
     set_error_message("solver reached max_iter before the tolerance");
   else if (status == SEM_ENUMERIC)
     set_error_message("NaN or Inf in the solver residual");
-  return status;
+  return report_wait_errors(M, P, st, info, status);
 }
 
 // Flexible CG steps (Sec. 3).  The V-cycle reads its input from, and leaves
@@ -451,7 +484,7 @@ static sem_status run_solve(sem_mesh *M, sem_pmg *P, const double *b, double *x,
     set_error_message("solver reached max_iter before the tolerance");
   else if (status == SEM_ENUMERIC)
     set_error_message("NaN or Inf in the solver residual");
-  return status;
+  return report_wait_errors(M, P, st, info, status);
 }
 
 // Projected solve (Sec. 3, "Projection is key"; the oracle's
@@ -506,8 +539,9 @@ static sem_status run_projected(sem_mesh *M, sem_pmg *P, sem_proj *Q, const doub
   info.bnorm = bnorm;
   info.res0 = bpn;
   info.status = status;
-  if (solve && status != SEM_ENUMERIC) {
-    // grow the basis with dx (or restart it from x once it is full)
+  if (solve && status != SEM_ENUMERIC && status != SEM_ETIMEOUT) {
+    // grow the basis with dx (or restart it from x once it is full); not
+    // with the results of a solve whose kernels left work undone
     const double *v = Q->dx.p;
     if (Q->nvec == Q->Lmax) {
       Q->nvec = 0;
@@ -583,6 +617,17 @@ sem_status sem_mesh_destroy(sem_mesh *mesh) {
     if (mesh->graph) cudaGraphExecDestroy(mesh->graph);
     if (mesh->cstream) cudaStreamDestroy(mesh->cstream);
     delete mesh;
+  });
+}
+
+sem_status sem_inject_wait_error(sem_mesh *mesh, void *stream) {
+  return guarded([&] {
+    SEM_REQUIRE(mesh != nullptr && mesh->fine.err.p != nullptr, "null mesh");
+    const int one = 1;
+    cudaStream_t st = as_stream(stream);
+    SEM_CHECK_CUDA(cudaMemcpyAsync(mesh->fine.err.p, &one, sizeof(int), cudaMemcpyHostToDevice,
+                                   st));
+    SEM_CHECK_CUDA(cudaStreamSynchronize(st));
   });
 }
 

@@ -744,3 +744,22 @@ def test_zero_guess_equals_zero_filled_guess(solver, bc):
         info = sem.sem_solve_info()
         sem.check(sem.lib().sem_solve(m.h, P.h if P else None, sem._ptr(bd), sem._ptr(x0),
                                       sem.C.byref(d), sem.C.byref(info), None))
+
+
+@pytest.mark.parametrize("solver", [sem.SEM_SOLVER_FLEXCG, sem.SEM_SOLVER_FGMRES])
+def test_wait_error_is_reported_by_the_next_solve_and_cleared(solver):
+    """A kernel whose bounded wait runs out sets its level's error flag and
+    leaves its work undone; the next solve returns SEM_ETIMEOUT and clears the
+    flag, and the solve after it runs as before.  The flag is set from the
+    host: nothing is made to fail on the device."""
+    m, L, b = _graph_problem(0, (7, 3, 1))
+    P = sem.Pmg(m, orders=(7, 3, 1), coarse_tol=1e-2, coarse_maxit=60)
+    bd = torch.tensor(b, device=DEV)
+    ok = sem.sem_solve(m, P, bd, torch.zeros_like(bd), solver, tol=1e-8, max_iter=200)
+    assert ok["status"] == sem.SEM_OK
+    sem.sem_inject_wait_error(m)
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_solve(m, P, bd, torch.zeros_like(bd), solver, tol=1e-8, max_iter=200)
+    assert ei.value.status == sem.SEM_ETIMEOUT
+    again = sem.sem_solve(m, P, bd, torch.zeros_like(bd), solver, tol=1e-8, max_iter=200)
+    assert again["status"] == sem.SEM_OK and again["iters"] == ok["iters"]
