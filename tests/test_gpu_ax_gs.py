@@ -374,3 +374,31 @@ def test_ax_fp32_assembled_full_size_sampled(kind, name):
         ref_c = ref.reshape(-1, Np3)[centre]
         got = w3[els[centre]].double().cpu().numpy()
         assert rel(got, ref_c) < tol32(N), c
+
+
+@pytest.mark.parametrize("N", [3, 7])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_operator_invariants_symmetry_null_space_and_gs(N, bc):
+    """Invariants of the assembled FP64 operator and of gs on the GPU, which
+    need no reference output: u^T A v = v^T A u in the unique-dof product for
+    continuous u, v; A 1 = 0 under Neumann; gs(u) = mult u for continuous u."""
+    m, L, _ = make(3, 2, 2, N, bc=bc)
+
+    def cont(seed):
+        return L.gs(inputs.random_field(L.nl, seed)) / L.mult * L.mask
+
+    def A(x):
+        xd = torch.tensor(x, device=DEV)
+        wd = torch.empty_like(xd)
+        sem.sem_ax(m, sem.SEM_F64, xd, wd, sem.SEM_AX_ASSEMBLED)
+        return wd.cpu().numpy()
+
+    u, v = cont(21), cont(22)
+    Au, Av = A(u), A(v)
+    uAv, vAu = np.sum(u * Av / L.mult), np.sum(v * Au / L.mult)
+    assert abs(uAv - vAu) <= 1e-11 * np.sqrt(np.sum(u * Au / L.mult) * np.sum(v * Av / L.mult))
+    if bc == 1:
+        assert np.abs(A(np.ones(L.nl))).max() <= 1e-11 * np.abs(Au).max()
+    ud = torch.tensor(u, device=DEV)
+    sem.sem_gs(m, sem.SEM_F64, ud)
+    assert np.abs(ud.cpu().numpy() - L.mult * u).max() <= 1e-14 * np.abs(L.mult * u).max()
