@@ -123,6 +123,44 @@ PLANTED = [
      "for (int q = i + 1; q < cols; ++q) s += H[i * m + q] * y[q];", [SOLV]),
     ("projected solve forgets the best fit",
      "    x[l] = xb;", "    x[l] = 0.0 * xb;", [SOLV]),
+    ("PCG initial residual with the wrong sign of A x0",
+     "  for (int64_t l = 0; l < n; ++l) r[l] = b[l] - w[l];\n  double bnorm = sqrt(orc_level_dot(L, b, b));\n"
+     "  double rnorm = sqrt(orc_level_dot(L, r, r));\n  *res0 = rnorm;\n  int k = 0, status = 1;\n"
+     "  if (rnorm <= tol * bnorm || rnorm == 0.0) status = 0;\n  if (status != 0) {\n"
+     "    for (int64_t l = 0; l < n; ++l) z[l] = (precond",
+     "  for (int64_t l = 0; l < n; ++l) r[l] = b[l] + w[l];\n  double bnorm = sqrt(orc_level_dot(L, b, b));\n"
+     "  double rnorm = sqrt(orc_level_dot(L, r, r));\n  *res0 = rnorm;\n  int k = 0, status = 1;\n"
+     "  if (rnorm <= tol * bnorm || rnorm == 0.0) status = 0;\n  if (status != 0) {\n"
+     "    for (int64_t l = 0; l < n; ++l) z[l] = (precond", [SOLV]),
+    ("Schwarz forward substitution reads the upper triangle",
+     "for (int k = 0; k < i; ++k) s -= C[(size_t)i * n3 + k] * u[k];",
+     "for (int k = 0; k < i; ++k) s -= C[(size_t)k * n3 + i] * u[k];", [ASM]),
+    ("Schwarz element length as half the sum of four edges",
+     "h[e * 3 + d] = 0.25 * s;", "h[e * 3 + d] = 0.5 * s;", [ASM]),
+    ("Schwarz right extension takes the shared face point",
+     "idx[out] = 1;", "idx[out] = 0;", [ASM]),
+    ("GLL Newton started from the mirrored guesses",
+     "double x = -cos(ORC_PI * i / N);", "double x = cos(ORC_PI * i / N);", [BASIS]),
+    ("prolongation stored transposed",
+     "ve[i + no * (j + no * k)] = s;", "ve[k + no * (j + no * i)] = s;", [SOLV]),
+    ("diagonal s-term with G_rr",
+     "s += D[l * Np + j] * D[l * Np + j] * g[3 * Np3 + i + Np * (l + Np * k)];",
+     "s += D[l * Np + j] * D[l * Np + j] * g[0 * Np3 + i + Np * (l + Np * k)];", [OPER, SOLV]),
+    ("FlexCG keeps the new residual as the old one",
+     "{ rold[l] = r[l]; r[l] -= alpha * w[l]; }", "{ r[l] -= alpha * w[l]; rold[l] = r[l]; }",
+     [SOLV]),
+    ("FGMRES first basis vector not normalised",
+     "for (int64_t l = 0; l < n; ++l) V[l] /= beta;", "(void)0;", [SOLV]),
+    ("projection coefficients against A p_i",
+     "for (int i = 0; i < k; ++i) c[i] = orc_level_dot(L, Q->P + (size_t)i * n, b);",
+     "for (int i = 0; i < k; ++i) c[i] = orc_level_dot(L, Q->AP + (size_t)i * n, b);", [SOLV]),
+    ("Lanczos off-diagonal without the square root",
+     "if (j < k - 1) tb[j] = sqrt(bet[j]) / alph[j];", "if (j < k - 1) tb[j] = bet[j] / alph[j];",
+     [SOLV, ASM]),
+    ("Dirichlet mask applied under Neumann too",
+     "(bc == 0 && onb) ? 0.0 : 1.0;", "(onb) ? 0.0 : 1.0;", [BASIS, OPER, SOLV]),
+    ("geometry interpolates x with l_b for l_c",
+     "x[m] += Xv * lr[a] * ls[b] * lt[c];", "x[m] += Xv * lr[a] * ls[b] * lt[b];", [BASIS, OPER]),
 ]
 
 

@@ -53,6 +53,24 @@ def test_pcg_matches_dense_solve_dirichlet(orc):
     assert np.sqrt(L.dot(r, r)) <= 1e-13 * np.sqrt(L.dot(b, b))
 
 
+def test_pcg_from_a_nonzero_guess_matches_dense_solve(orc):
+    """From a nonzero initial guess the solve reaches the same dense solution,
+    and its initial residual norm is ||b - A x0|| with A the dense assembled
+    matrix (unique-dof numbering)."""
+    L = level(orc, 2, 2, 2, 4, DIR)
+    A, rep = dense_unique(L, L.ax)
+    keep = L.mask[rep] == 1.0
+    b = L.gs(inputs.random_field(L.nl, 4)) * L.mask
+    x0 = L.gs(inputs.random_field(L.nl, 5)) / L.mult * L.mask
+    x, info = L.pcg(b, x0=x0, tol=1e-14, maxit=1000)
+    assert info["status"] == 0
+    ref = np.zeros(L.ng)
+    ref[keep] = np.linalg.solve(A[np.ix_(keep, keep)], b[rep][keep])
+    assert np.max(np.abs(x - ref[L.ids])) < 1e-10 * np.max(np.abs(ref))
+    r0 = b[rep] - A @ x0[rep]
+    assert abs(info["res0"] - np.linalg.norm(r0)) <= 1e-12 * np.linalg.norm(r0)
+
+
 def test_pcg_neumann_matches_least_squares(orc):
     L = level(orc, 2, 2, 2, 3, NEU)
     A, rep = dense_unique(L, L.ax)
