@@ -65,6 +65,7 @@ def test_invalid_arguments_return_einval_without_device_work(libsem):
     desc = libsem.sem_solve_desc(0, 1e-8, 10, 1)
     assert L.sem_solve(None, None, None, None, C.byref(desc), C.byref(info), None) == \
         libsem.SEM_EINVAL
+    assert L.sem_inject_wait_error(None, None) == libsem.SEM_EINVAL
     assert L.sem_mesh_destroy(None) == libsem.SEM_OK
     assert L.sem_pmg_destroy(None) == libsem.SEM_OK
 
