@@ -99,6 +99,13 @@ typedef struct {
 sem_status sem_mesh_create(const sem_mesh_desc *desc, void *stream, sem_mesh **out);
 sem_status sem_mesh_destroy(sem_mesh *mesh);
 
+/* Test hook (host-side fault injection): after > 0 makes the after-th
+ * device allocation of the library from now on fail with SEM_ENOMEM before
+ * it reaches the CUDA allocator (the call that allocates returns SEM_ENOMEM
+ * and frees what it had built); 0 disarms.  Process-wide.
+ * Errors: SEM_EINVAL (after < 0). */
+sem_status sem_inject_alloc_failure(int32_t after);
+
 /* Test hook: sets the fine level's wait-error flag from the host, as a
  * kernel whose bounded wait ran out would, so that the next solve on the
  * mesh reports SEM_ETIMEOUT (and clears it).  Nothing runs on the device.

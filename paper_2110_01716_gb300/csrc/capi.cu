@@ -620,6 +620,13 @@ sem_status sem_mesh_destroy(sem_mesh *mesh) {
   });
 }
 
+sem_status sem_inject_alloc_failure(int32_t after) {
+  return guarded([&] {
+    SEM_REQUIRE(after >= 0, "after must be >= 0 (got %d)", after);
+    g_alloc_fail_countdown.store(after);
+  });
+}
+
 sem_status sem_inject_wait_error(sem_mesh *mesh, void *stream) {
   return guarded([&] {
     SEM_REQUIRE(mesh != nullptr && mesh->fine.err.p != nullptr, "null mesh");

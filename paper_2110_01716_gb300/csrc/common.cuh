@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <string>
 #include <vector>
@@ -35,6 +36,11 @@ void set_error_message(const char *msg);
     if (!(cond)) ::sem::fail(SEM_EINVAL, __VA_ARGS__); \
   } while (0)
 
+// Host-side fault injection (sem_inject_alloc_failure): armed with k > 0,
+// the k-th device allocation through DevBuf from then on fails with
+// SEM_ENOMEM before cudaMalloc is called; 0 disarms.
+inline std::atomic<int> g_alloc_fail_countdown{0};
+
 // Device allocation owned by a library object; freed in the destructor.
 template <typename T>
 struct DevBuf {
@@ -47,6 +53,9 @@ struct DevBuf {
   void alloc(size_t count) {
     release();
     if (count == 0) return;
+    if (g_alloc_fail_countdown.load(std::memory_order_relaxed) > 0 &&
+        g_alloc_fail_countdown.fetch_sub(1) == 1)
+      ::sem::fail(SEM_ENOMEM, "injected device allocation failure");
     SEM_CHECK_CUDA(cudaMalloc(&p, count * sizeof(T)));
     n = count;
   }

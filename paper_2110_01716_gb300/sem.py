@@ -39,7 +39,7 @@ EXPORTED = ["sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_fi
             "sem_trace_read", "sem_dot_noalloc", "sem_proj_create", "sem_proj_destroy",
             "sem_proj_info", "sem_solve_projected", "sem_server_create", "sem_server_destroy",
             "sem_submit", "sem_poll", "sem_server_stats_read", "sem_server_autotune",
-            "sem_inject_wait_error", "sem_last_error"]
+            "sem_inject_wait_error", "sem_inject_alloc_failure", "sem_last_error"]
 
 
 class SemError(RuntimeError):
@@ -118,6 +118,7 @@ def lib():
     L.sem_mesh_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_size_t)]
     L.sem_mesh_field.argtypes = [vp, i32, vp, vp]
     L.sem_inject_wait_error.argtypes = [vp, vp]
+    L.sem_inject_alloc_failure.argtypes = [i32]
     L.sem_ax.argtypes = [vp, i32, vp, vp, i32, vp]
     L.sem_gs.argtypes = [vp, i32, vp, vp]
     L.sem_dot.argtypes = [vp, vp, vp, C.POINTER(d), vp]
@@ -228,6 +229,12 @@ def sem_inject_wait_error(mesh: Mesh, stream=None):
     """Test hook: set the fine level's wait-error flag from the host, so that
     the next solve on the mesh reports SEM_ETIMEOUT."""
     check(lib().sem_inject_wait_error(mesh.h, _stream(stream)))
+
+
+def sem_inject_alloc_failure(after: int):
+    """Test hook: make the after-th device allocation of the library from now
+    on fail with SEM_ENOMEM (0 disarms)."""
+    check(lib().sem_inject_alloc_failure(int(after)))
 
 
 def sem_ax(mesh: Mesh, dtype: int, u, w, flags=SEM_AX_ASSEMBLED, stream=None):

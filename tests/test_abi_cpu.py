@@ -77,3 +77,21 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(sem, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         sem.lib()
+
+
+def test_injected_allocation_failure_returns_enomem_without_device_work(libsem):
+    """Host-side fault injection: the armed allocation fails with SEM_ENOMEM
+    before reaching the CUDA allocator (no GPU is needed to see it) and the
+    call returns no handle."""
+    L = libsem.lib()
+    assert L.sem_inject_alloc_failure(-1) == libsem.SEM_EINVAL
+    desc = libsem.sem_mesh_desc(ex=2, ey=2, ez=2, N=3, jitter=0.1, seed=1, bc=0, geom=0,
+                                verts=None)
+    h = C.c_void_p()
+    try:
+        assert L.sem_inject_alloc_failure(1) == libsem.SEM_OK
+        assert L.sem_mesh_create(C.byref(desc), None, C.byref(h)) == libsem.SEM_ENOMEM
+        assert "injected" in libsem.last_error()
+        assert not h.value
+    finally:
+        assert L.sem_inject_alloc_failure(0) == libsem.SEM_OK
