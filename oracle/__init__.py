@@ -85,6 +85,7 @@ def lib():
     L.orc_cheb_m.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _dp,
                              _dp, C.c_int, C.c_double, C.c_double, C.c_int]
     L.orc_level_lanczos_max.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.POINTER(C.c_int)]
+    L.orc_lanczos_start.argtypes = [C.c_void_p, C.c_uint64, _dp]
     L.orc_level_lanczos_max.restype = C.c_double
     L.orc_pmg_create.argtypes = [C.c_int] * 4 + [_i32p, C.c_int, _dp, C.c_int, C.c_int,
                                                  C.c_uint64, C.c_double, C.c_int]
@@ -341,6 +342,11 @@ class Level:
         st = lib().orc_pcg(self.ptr, np.ascontiguousarray(b, dtype=np.float64), x, tol, maxit,
                            int(precond), C.byref(it), C.byref(r0), C.byref(r1))
         return x, {"status": st, "iters": it.value, "res0": r0.value, "res": r1.value}
+
+    def lanczos_start(self, seed=0):
+        v = np.zeros(self.nl)
+        lib().orc_lanczos_start(self.ptr, seed, v)
+        return v
 
     def lanczos_max(self, m=20, seed=0):
         steps = C.c_int()

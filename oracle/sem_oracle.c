@@ -585,6 +585,23 @@ static void jacobi_prec(void *ctx, const double *in, double *out) {
 static double lanczos_max_m(orc_level *L, int m, uint64_t seed, void (*Mf)(void *, const double *, double *),
                             void *mctx, int *steps_done);
 
+/* The Lanczos start vector: value 2 u - 1 at every local copy of global node
+ * g, with u the 53-bit fraction of splitmix64 value g of stream seed
+ * (continuous), masked, and under Neumann minus its unique-dof mean. */
+void orc_lanczos_start(const orc_level *L, uint64_t seed, double *v) {
+  int64_t n = L->nl;
+  for (int64_t l = 0; l < n; ++l) {
+    uint64_t bits = splitmix64_at(seed, (uint64_t)L->ids[l]);
+    double u01 = (double)(bits >> 11) * (1.0 / 9007199254740992.0);
+    v[l] = (2.0 * u01 - 1.0) * L->mask[l];
+  }
+  if (L->bc == 1) {
+    double s = 0.0, c = 0.0;
+    for (int64_t l = 0; l < n; ++l) { s += v[l] * L->inv_mult[l]; c += L->inv_mult[l]; }
+    for (int64_t l = 0; l < n; ++l) v[l] -= s / c;
+  }
+}
+
 double orc_level_lanczos_max(orc_level *L, int m, uint64_t seed, int *steps_done) {
   return lanczos_max_m(L, m, seed, jacobi_prec, L, steps_done);
 }
@@ -599,16 +616,7 @@ static double lanczos_max_m(orc_level *L, int m, uint64_t seed, void (*Mf)(void 
          *z = malloc(sizeof(double) * n), *p = malloc(sizeof(double) * n),
          *w = malloc(sizeof(double) * n);
   double *alph = malloc(sizeof(double) * (m + 1)), *bet = malloc(sizeof(double) * (m + 1));
-  for (int64_t l = 0; l < n; ++l) {
-    uint64_t bits = splitmix64_at(seed, (uint64_t)L->ids[l]);
-    double u01 = (double)(bits >> 11) * (1.0 / 9007199254740992.0);
-    v[l] = (2.0 * u01 - 1.0) * L->mask[l];
-  }
-  if (L->bc == 1) {
-    double s = 0.0, c = 0.0;
-    for (int64_t l = 0; l < n; ++l) { s += v[l] * L->inv_mult[l]; c += L->inv_mult[l]; }
-    for (int64_t l = 0; l < n; ++l) v[l] -= s / c;
-  }
+  orc_lanczos_start(L, seed, v);
   for (int64_t l = 0; l < n; ++l) r[l] = v[l];
   Mf(mctx, r, z);
   for (int64_t l = 0; l < n; ++l) p[l] = z[l];

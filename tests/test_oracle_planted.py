@@ -107,6 +107,8 @@ PLANTED = [
     ("prolongation with a for b in the second factor",
      "double Jb = transpose ? J[b * nc + j] : J[j * nc + b];",
      "double Jb = transpose ? J[b * nc + j] : J[j * nc + a];", [SOLV]),
+    ("Lanczos start vector keeps its mean under Neumann",
+     "for (int64_t l = 0; l < n; ++l) v[l] -= s / c;", "(void)s;", [SOLV, ASM]),
     ("tridiagonal bisection keeps the lowest eigenvalue",
      "if (cnt == m) hi = mid; else lo = mid;", "if (cnt >= 1) hi = mid; else lo = mid;",
      [SOLV, ASM]),

@@ -180,6 +180,22 @@ def test_chebyshev_on_MA_error_polynomial_closed_form(orc, k):
 
 
 @pytest.mark.parametrize("bc", [DIR, NEU])
+def test_lanczos_start_vector_from_the_published_generator(orc, bc):
+    """The start vector of the Lanczos estimate: 2u - 1 at every copy of global
+    node g, u the 53-bit fraction of splitmix64 value g (computed here by the
+    input module's generator, pinned to the published stream), masked, and
+    under Neumann minus its unique-dof mean."""
+    L = level(orc, 3, 2, 2, 4, bc)
+    seed = 12345
+    v = L.lanczos_start(seed)
+    ref = (2.0 * inputs.splitmix64_unit(seed, L.ids.astype(np.uint64)) - 1.0) * L.mask
+    if bc == NEU:
+        ref = ref - np.sum(ref / L.mult) / np.sum(1.0 / L.mult)
+        assert abs(np.sum(v / L.mult)) <= 1e-12 * np.sum(np.abs(v) / L.mult)
+    np.testing.assert_allclose(v, ref, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("bc", [DIR, NEU])
 def test_lanczos_estimate_of_largest_eigenvalue(orc, bc):
     L = level(orc, 2, 2, 2, 4, bc)
     A, rep = dense_unique(L, L.ax)
