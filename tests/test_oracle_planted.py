@@ -6,7 +6,8 @@ missing weight), compiles it with the oracle's own flags and runs the pin
 tests that cover that function against it (``SEM_ORACLE_LIB``).  The pins
 must fail.  The unaltered copy, built and loaded the same way, must pass, so
 the failures come from the planted mistakes and not from the harness.  The
-copies are built and run in parallel, each test process on one thread.
+copies are built and run in parallel, each test process on one thread, and
+the pins marked slow (larger meshes of the same checks) are left out.
 """
 
 import os
@@ -175,7 +176,8 @@ def _build_and_run(src_text, out_dir, files):
         f.write(src_text)
     so = oracle.compile_to(src, os.path.join(out_dir, "libsemoracle.so"))
     env = dict(os.environ, SEM_ORACLE_LIB=so, OMP_NUM_THREADS="1")
-    p = subprocess.run([sys.executable, "-m", "pytest", *files, "-x", "-q", "-m", "not gpu",
+    p = subprocess.run([sys.executable, "-m", "pytest", *files, "-x", "-q", "-m",
+                        "not gpu and not slow",
                         "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True,
                        text=True, timeout=900)
     return p.returncode, p.stdout[-2000:] + p.stderr[-2000:]

@@ -294,10 +294,14 @@ def test_flexcg_updates_are_A_conjugate_with_a_variable_preconditioner(orc):
         assert num <= 1e-9 * den, (k, num / den)
 
 
+@pytest.mark.slow
 @pytest.mark.parametrize("bc", [DIR, NEU])
 def test_pmg_flexcg_iterations_flat_under_refinement(orc, bc):
+    """pMG-preconditioned FlexCG at N = 7 from E = 2^3 to 16^3 (4096
+    elements, 2.1 M local points): every solve meets 1e-8, recomputed, and
+    from 4^3 on the iteration count stays within two of itself."""
     iters = []
-    for e in (2, 4):
+    for e in (2, 4, 8, 16):
         v = inputs.box_vertices(e, e, e, 0.1, 3)
         P = orc.PMG(e, e, e, [7, 3, 1], bc, v, cheb_degree=2, coarse_tol=1e-2,
                     coarse_maxit=50)
@@ -318,7 +322,8 @@ def test_pmg_flexcg_iterations_flat_under_refinement(orc, bc):
         assert np.sqrt(L.dot(r, r)) <= 1.01e-8 * np.sqrt(L.dot(b, b))
         iters.append(info["iters"])
     assert iters[1] <= iters[0] + 4, iters
-    assert iters[1] < 40, iters
+    assert max(iters[1:]) - min(iters[1:]) <= 2, iters
+    assert max(iters) < 20, iters
 
 
 # ---------------------------------------------------------------- FGMRES
