@@ -105,17 +105,6 @@ static void check_neumann_rhs(sem_mesh *M, const double *b, cudaStream_t st) {
               std::sqrt(bb));
 }
 
-// Flexible GMRES(m) (Sec. 3: the GMRES alternative to FlexCG; Sec. 5: few
-// vectors, classical Gram-Schmidt with one reduction for all coefficients of
-// a step).  Right preconditioning by one pMG V-cycle (or Jacobi without pmg);
-// the preconditioned vectors z_j are kept because the V-cycle may vary, and
-// x = x0 + Z y (Saad, Alg. 9.6).  The small least-squares problem lives on
-// the host (Givens rotations, as in the oracle); per step the device runs the
-// preconditioner, the FP64 operator, one multi-dot <w, v_i>, one fused
-// subtract-and-norm pass and a scaling, and the host reads one Hessenberg
-// column.  A cycle ends when the least-squares residual meets the tolerance
-// or after m steps; x is then updated and its residual recomputed, which
-// decides convergence (restarting from it otherwise).
 // A kernel whose bounded wait ran out (a bulk copy that never completed)
 // sets its level's flag and leaves the rest of its work undone.  After a
 // solve's last synchronisation the flags of every level it used are read and
@@ -149,6 +138,17 @@ static sem_status report_wait_errors(sem_mesh *M, sem_pmg *P, cudaStream_t st,
   return SEM_ETIMEOUT;
 }
 
+// Flexible GMRES(m) (Sec. 3: the GMRES alternative to FlexCG; Sec. 5: few
+// vectors, classical Gram-Schmidt with one reduction for all coefficients of
+// a step).  Right preconditioning by one pMG V-cycle (or Jacobi without pmg);
+// the preconditioned vectors z_j are kept because the V-cycle may vary, and
+// x = x0 + Z y (Saad, Alg. 9.6).  The small least-squares problem lives on
+// the host (Givens rotations, as in the oracle); per step the device runs the
+// preconditioner, the FP64 operator, one multi-dot <w, v_i>, one fused
+// subtract-and-norm pass and a scaling, and the host reads one Hessenberg
+// column.  A cycle ends when the least-squares residual meets the tolerance
+// or after m steps; x is then updated and its residual recomputed, which
+// decides convergence (restarting from it otherwise).
 static sem_status run_fgmres(sem_mesh *M, sem_pmg *P, const double *b, double *x,
                              const sem_solve_desc &d, sem_solve_info &info, cudaStream_t st,
                              bool x_zero = false, bool check_rhs = true) {
