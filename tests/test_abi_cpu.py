@@ -57,6 +57,12 @@ def test_invalid_arguments_return_einval_without_device_work(libsem):
         assert st == libsem.SEM_EINVAL, (bad, st)
         assert libsem.last_error()
         assert not h.value
+    # maximum sizes: more than 2^31 elements, more than 2^31 - 1 local points
+    for ex, N, msg in ((1300, 3, "too many elements"), (120, 11, "too large")):
+        desc = libsem.sem_mesh_desc(ex=ex, ey=ex, ez=ex, N=N, jitter=0.1, seed=1, bc=0, geom=0,
+                                    verts=None)
+        assert L.sem_mesh_create(C.byref(desc), None, C.byref(h)) == libsem.SEM_EINVAL
+        assert msg in libsem.last_error() and not h.value
     # null handles are rejected
     assert L.sem_ax(None, 0, None, None, 0, None) == libsem.SEM_EINVAL
     assert L.sem_gs(None, 0, None, None) == libsem.SEM_EINVAL
