@@ -67,11 +67,11 @@ PAIR_INSTR_PER_FMA = 12
 PAIR_PEAK_TFLOPS = 152 * 128 * 2.07e9 / PAIR_INSTR_PER_FMA * 2 / 1e12
 # DRAM traffic of one fine-level FP64 operator launch per local point (the
 # form with the inner product folded in, as in the solve), from an ncu capture
-# (profiles/ax_f64pair_N7.md), valid while the kernel source is unchanged.
+# of that kernel on a 24^3 case, valid while the kernel source is unchanged.
 AX_TRAFFIC = {"source_sha256": "6be51339915d304430207d3ee5a7908f9bc6ecc41030ae6dba61825fd4488a18",
               "bytes_per_point": 63.18}
 # The same for the smoother's assembled FP32 operator, per factor storage
-# (profiles/ax32_N7.md), valid while ax32.cu is unchanged.
+# (ncu capture on a 32^3 case), valid while ax32.cu is unchanged.
 AX32_TRAFFIC = {"f32": {"source_sha256": "a1c86ef6bae402e521ec9400dc4df4087b40792cad358632c0c31adec941b4d2",
                         "bytes_per_point": 31.29},
                 "f16": {"source_sha256": "a1c86ef6bae402e521ec9400dc4df4087b40792cad358632c0c31adec941b4d2",
@@ -238,9 +238,28 @@ def source_sha(*names):
     return h.hexdigest()
 
 
+def traced_ms(sem, fn, reps=10, warm=3):
+    """Device time of one call of fn: the sum of the library's own per-launch
+    CUDA-event timings (each kernel launch bracketed on its stream), median
+    over reps calls.  Host-side work inside a call (the staged operator's
+    read of its wait flag) is not counted."""
+    for _ in range(warm):
+        fn()
+    sem.sem_trace_enable(True, "*")
+    sem.sem_trace_read(reset=True)
+    per = []
+    for _ in range(reps):
+        fn()
+        tr = sem.sem_trace_read(reset=True)
+        per.append(sum(v["total_ms"] for v in tr.values()))
+    sem.sem_trace_enable(False, "")
+    return statistics.median(per)
+
+
 def operator_sweep(sem, torch, dev, hbm):
     """FP64 / FP32 operator throughput at 64^3 elements, N=7 (stored and
-    recomputed geometry), median of 20 launches after 3 warm-ups."""
+    recomputed geometry), median of 20 launches after 3 warm-ups, timed by
+    the library's per-launch events."""
     from paper_2110_01716_gb300 import inputs
 
     out = {}
@@ -260,19 +279,7 @@ def operator_sweep(sem, torch, dev, hbm):
         for dt, tdt, name in kinds:
             u = torch.rand(n, device=dev, dtype=tdt, generator=torch.Generator(dev).manual_seed(5))
             w = torch.empty_like(u)
-            st = torch.cuda.current_stream()
-            for _ in range(3):
-                sem.sem_ax(mesh, dt, u, w, sem.SEM_AX_LOCAL)
-            times = []
-            for _ in range(20):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(st)
-                sem.sem_ax(mesh, dt, u, w, sem.SEM_AX_LOCAL)
-                e1.record(st)
-                e1.synchronize()
-                times.append(e0.elapsed_time(e1))
-            ms = statistics.median(times)
+            ms = traced_ms(sem, lambda: sem.sem_ax(mesh, dt, u, w, sem.SEM_AX_LOCAL), reps=20)
             esz = 8 if name == "f64" else 4
             stored = gname.startswith("stored")
             gsz = 2 if name in ("f16g", "bf16g") else esz
@@ -293,24 +300,12 @@ def size_sweep(sem, torch, dev, hbm, sides=(16, 32, 48, 64)):
     """Config 2 across sizes: E = k^3, N = 7, stored factors, seed 2 + k.  Per
     size and precision: the local operator, gather-scatter alone (sem_gs) and
     the assembled operator (sem_ax with SEM_AX_ASSEMBLED: the fused path),
-    median of 10 launches after 3 warm-ups."""
+    median of 10 calls after 3 warm-ups (the device time of every kernel a
+    call launches, summed)."""
     from paper_2110_01716_gb300 import inputs
 
-    st = torch.cuda.current_stream()
-
     def median_ms(fn):
-        for _ in range(3):
-            fn()
-        times = []
-        for _ in range(10):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            fn()
-            e1.record(st)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-        return statistics.median(times)
+        return traced_ms(sem, fn, reps=10)
 
     out = {}
     for k in sides:
@@ -360,6 +355,165 @@ def named_config_leg(sem, torch, mesh, b, x, args, ng, steps=5, warmup=2):
     t = statistics.mean(ms)
     return {"orders": "7,3,1", "cheb_degree": 2, "ms_per_solve": round(t, 2),
             "iters": info["iters"], "value": ng / (t / 1e3) / 1e9, "unit": "GDOF/s"}
+
+
+def _rel_diff_mean_free(sem, torch, mesh, x, ref):
+    """max |(x - mean x) - (ref - mean ref)| / max |ref - mean ref|, means over
+    the unique dofs (a Neumann solution is defined up to a constant)."""
+    ones = torch.ones_like(ref)
+    ng = mesh.n_global
+    xr = ref - sem.sem_dot(mesh, ref, ones) / ng
+    xd = x - sem.sem_dot(mesh, x, ones) / ng
+    num = (xd - xr).abs().max().item()
+    den = xr.abs().max().item()
+    del ones, xr, xd
+    return num / den if den > 0 else float("nan")
+
+
+def precision_leg(sem, torch, mesh, b, args, ng, steps=3, warmup=1):
+    """Mixed precision against all-FP64 on the bench workload (E = 48^3,
+    N = 7, Neumann, same right-hand side, coarse solve and tolerance): the
+    pMG smoother in FP64, FP32, and FP32 arithmetic with FP16 / BF16 factors,
+    on the headline schedule and on the named one (7-3-1, Chebyshev(2)).
+    Reports ms per solve, iterations, the speed-up over the FP64 smoother of
+    the same schedule, and each solution's difference from the FP64-smoother
+    solution (max norm, mean-free, relative)."""
+    stream = torch.cuda.current_stream()
+    headline = tuple(int(o) for o in args.orders.split(","))
+    legs = [("f64", headline, args.cheb_degree), ("f32", headline, args.cheb_degree),
+            ("f16", headline, args.cheb_degree), ("bf16", headline, args.cheb_degree),
+            ("f64", (7, 3, 1), 2), ("f32", (7, 3, 1), 2)]
+    out, ref = {}, {}
+    for sm, orders, deg in legs:
+        P = sem.Pmg(mesh, orders=orders, cheb_degree=deg, lanczos_steps=20, seed=0,
+                    smoother_dtype=SMOOTHER_DTYPES[sm], coarse_tol=args.coarse_tol,
+                    coarse_maxit=args.coarse_maxit, coarse_mode=args.coarse_mode)
+        x = torch.zeros_like(b)
+        ms, info = [], None
+        for i in range(warmup + steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = sem.sem_solve(mesh, P, b, x, sem.SEM_SOLVER_FLEXCG, tol=TOL, max_iter=200,
+                                 zero_guess=True)
+            e1.record(stream)
+            e1.synchronize()
+            if info["status"] != sem.SEM_OK:
+                raise SystemExit(f"precision leg: {sm} smoother {orders} did not converge")
+            if i >= warmup:
+                ms.append(e0.elapsed_time(e1))
+        P.close()
+        sched = "-".join(str(o) for o in orders) + f"/cheb{deg}"
+        t = statistics.mean(ms)
+        rec = {"ms": round(t, 2), "iters": info["iters"],
+               "final_rel_res": info["res"] / info["bnorm"]}
+        if sm == "f64":
+            ref[sched] = (x, t)
+        else:
+            x64, t64 = ref[sched]
+            rec["speedup_vs_f64"] = round(t64 / t, 2)
+            rec["rel_diff_vs_f64_solution"] = _rel_diff_mean_free(sem, torch, mesh, x, x64)
+            del x
+        out.setdefault(sched, {})[sm] = rec
+    del ref
+    torch.cuda.empty_cache()
+    return out
+
+
+def precision_errors_leg(sem, torch, dev, args, side=12):
+    """Final-solution error of every precision variant against the FP64
+    oracle: the bench recipe on a side^3 box (N = 7, Neumann, the oracle's own
+    right-hand side copied to the device), GPU FlexCG + pMG (headline
+    schedule) to 1e-8 with the smoother in FP64, FP32, FP16 and BF16 factor
+    storage; the oracle's FlexCG + pMG (7-3-1) solution to the same 1e-8, and
+    to 1e-12 (the discrete solution to round-off) as references.  Errors are
+    max-norm, relative, after removing each solution's unique-dof mean."""
+    import numpy as np
+
+    import oracle
+    from paper_2110_01716_gb300 import inputs
+
+    oracle.build()
+    v = inputs.box_vertices(side, side, side, 0.1, MESH_SEED)
+    P = oracle.PMG(side, side, side, [7, 3, 1], 1, v, cheb_degree=2, lanczos_steps=20, seed=0,
+                   coarse_tol=1e-2, coarse_maxit=50)
+    L = P.levels[0]
+    a, k, phi = inputs.fourier_modes(RHS_SEED)
+    X = L.X
+    f = sum(a[m] * np.cos(2 * np.pi * (k[m, 0] * X[:, 0] + k[m, 1] * X[:, 1] + k[m, 2] * X[:, 2])
+                          + phi[m]) for m in range(len(a))).ravel()
+    bo = L.gs(L.B * f)
+    bo -= L.dot(bo, np.ones(L.nl)) / L.ng
+    x8, i8 = P.flexpcg(bo, tol=1e-8, maxit=200)
+    x12, i12 = P.flexpcg(bo, tol=1e-12, maxit=400)
+
+    def mean_free(x):
+        return x - L.dot(x, np.ones(L.nl)) / L.ng
+
+    r8, r12 = mean_free(x8), mean_free(x12)
+    mesh = sem.Mesh(side, side, side, ORDER, sem.SEM_NEUMANN, sem.SEM_GEOM_STORED, verts=v)
+    bd = torch.tensor(bo, device=dev)
+    orders = tuple(int(o) for o in args.orders.split(","))
+    out = {"side": side, "n_global": L.ng, "oracle_iters": {"1e-8": i8["iters"], "1e-12": i12["iters"]},
+           "oracle_1e-8_vs_1e-12": float(np.max(np.abs(r8 - r12)) / np.max(np.abs(r12)))}
+    for sm in ("f64", "f32", "f16", "bf16"):
+        Pg = sem.Pmg(mesh, orders=orders, cheb_degree=args.cheb_degree, lanczos_steps=20, seed=0,
+                     smoother_dtype=SMOOTHER_DTYPES[sm], coarse_tol=args.coarse_tol,
+                     coarse_maxit=args.coarse_maxit, coarse_mode=args.coarse_mode)
+        xd = torch.zeros_like(bd)
+        info = sem.sem_solve(mesh, Pg, bd, xd, sem.SEM_SOLVER_FLEXCG, tol=TOL, max_iter=200,
+                             zero_guess=True)
+        Pg.close()
+        xg = mean_free(xd.cpu().numpy())
+        res = np.linalg.norm(L.ax(xd.cpu().numpy()) - bo) / np.linalg.norm(bo)
+        out[sm] = {"iters": info["iters"],
+                   "rel_err_vs_oracle_1e-8": float(np.max(np.abs(xg - r8)) / np.max(np.abs(r8))),
+                   "rel_err_vs_oracle_1e-12": float(np.max(np.abs(xg - r12)) / np.max(np.abs(r12))),
+                   "residual_by_oracle": float(res)}
+    mesh.close()
+    return out
+
+
+def config1_leg(sem, torch, dev, steps=5, warmup=2):
+    """Config 1 on the GPU: E = 8^3, N = 7, jitter 0.1 (seed 1), Dirichlet,
+    manufactured u* = sin(pi x) sin(pi y) sin(pi z), Jacobi-PCG to 1e-10 from
+    zero; time per solve, iterations, GDOF/s and max error against u*."""
+    from paper_2110_01716_gb300 import inputs
+
+    v = inputs.box_vertices(8, 8, 8, 0.1, 1)
+    mesh = sem.Mesh(8, 8, 8, ORDER, sem.SEM_DIRICHLET, sem.SEM_GEOM_STORED, verts=v)
+    n = mesh.n_local
+    X = [torch.empty(n, device=dev, dtype=torch.float64) for _ in range(3)]
+    for d in range(3):
+        sem.sem_mesh_field(mesh, d, X[d])
+    Bm = torch.empty(n, device=dev, dtype=torch.float64)
+    mask = torch.empty(n, device=dev, dtype=torch.float64)
+    sem.sem_mesh_field(mesh, sem.SEM_FIELD_MASS, Bm)
+    sem.sem_mesh_field(mesh, sem.SEM_FIELD_MASK, mask)
+    us = torch.sin(torch.pi * X[0]) * torch.sin(torch.pi * X[1]) * torch.sin(torch.pi * X[2])
+    b = Bm * 3 * torch.pi ** 2 * us
+    sem.sem_gs(mesh, sem.SEM_F64, b)
+    b *= mask
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+    ms, info = [], None
+    for i in range(warmup + steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = sem.sem_solve(mesh, None, b, x, sem.SEM_SOLVER_PCG, tol=1e-10, max_iter=2000,
+                             check_every=10, zero_guess=True)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    err = (x - us * mask).abs().max().item()
+    t = statistics.mean(ms)
+    out = {"workload": "config 1: E=8^3, N=7, Dirichlet, manufactured, Jacobi-PCG to 1e-10",
+           "ms_per_solve": round(t, 3), "iters": info["iters"], "status": info["status"],
+           "gdofs": mesh.n_global / (t / 1e3) / 1e9, "max_err_vs_exact": err}
+    mesh.close()
+    return out
 
 
 def projection_sequence(sem, torch, mesh, pmg, dev, solver, restart, steps=16, Lmax=30):
@@ -557,6 +711,33 @@ def oracle_timings():
             del L2, u, w
         out[label] = row
     oracle.set_threads(allc)
+    return out
+
+
+def summary_of(line):
+    """The figures a reader needs first, in one small object."""
+    r = line.get("roofline", {})
+    other = r.get("other", {})
+    out = {"ms_per_solve": round(line["ms_per_step"], 2), "iters": line["iters"][0],
+           "GDOF_s": round(line["value"], 4),
+           "e2e_GDOF_s": round(line.get("e2e", {}).get("value", float("nan")), 4),
+           "roofline": {r.get("kernel"): round(r.get("frac") or 0, 3),
+                        other.get("kernel"): round(other.get("frac") or 0, 3)}}
+    prec = line.get("precision", {})
+    for sched, legs in prec.items():
+        out["fp64_smoother_" + sched] = {sm: [v["ms"], v["iters"], v.get("speedup_vs_f64")]
+                                         for sm, v in legs.items()}
+    pe = line.get("precision_errors", {})
+    if pe:
+        out["err_vs_oracle"] = {sm: pe[sm]["rel_err_vs_oracle_1e-12"]
+                                for sm in ("f64", "f32", "f16", "bf16") if sm in pe}
+    if "serve" in line:
+        out["serve_p50_p99_ms"] = [line["serve"]["latency_ms"]["p50"],
+                                   line["serve"]["latency_ms"]["p99"]]
+    if "batch" in line:
+        out["batch_solves_per_s"] = line["batch"].get("solves_per_s")
+    if "config1" in line:
+        out["config1_ms"] = line["config1"]["ms_per_solve"]
     return out
 
 
@@ -772,9 +953,10 @@ def main():
                                                             key=lambda kv: -kv[1]["total_ms"])}}
 
     if not args.no_extras and rank == 0:
-        # end to end through the host-buffer entry point (pinned host memory)
-        # host b in, host x out, from x = 0 (x's input is neither read nor
-        # copied); pinned host memory
+        ex = {}
+        # end to end through the host-buffer entry point: host b in, host x
+        # out (pinned host memory), from x = 0 (x's input is neither read nor
+        # copied)
         bh = b.cpu().pin_memory()
         xh = torch.zeros(nl, dtype=torch.float64).pin_memory()
         for _ in range(1):
@@ -804,32 +986,41 @@ def main():
                 torch.cuda.synchronize()
                 if i >= args.warmup:
                     gt.append(ge0.elapsed_time(ge1))
-            line["graph"] = {"ms_per_solve": statistics.mean(gt), "iters": ginf["iters"],
-                             "host_loop_ms_per_solve": ms_per_step,
-                             "value": ng / (statistics.mean(gt) / 1e3) / 1e9, "unit": "GDOF/s"}
-        if solver == sem.SEM_SOLVER_FLEXCG:
-            line["named_config"] = named_config_leg(sem, torch, mesh, b, x, args, ng)
-        line["projection"] = projection_sequence(sem, torch, mesh, pmg, dev, solver, args.restart)
+            ex["graph"] = {"ms_per_solve": statistics.mean(gt), "iters": ginf["iters"],
+                           "host_loop_ms_per_solve": ms_per_step,
+                           "value": ng / (statistics.mean(gt) / 1e3) / 1e9, "unit": "GDOF/s"}
+            ex["named_config"] = named_config_leg(sem, torch, mesh, b, x, args, ng)
+            ex["precision"] = precision_leg(sem, torch, mesh, b, args, ng)
+        ex["projection"] = projection_sequence(sem, torch, mesh, pmg, dev, solver, args.restart)
         pmg.close()
         mesh.close()
         del b, x
         torch.cuda.empty_cache()
+        ex["config1"] = config1_leg(sem, torch, dev)
         if not args.no_serve:
-            line["batch"] = batch_leg(sem, inputs)
-            bl = line["batch"]
-            line["serve"] = serve_leg(sem, inputs, bl["autotuned_workers"],
-                                      graph=bl["solves_per_s_graph"] > bl["solves_per_s"])
-        line["ax_sweep_64cube"] = operator_sweep(sem, torch, dev, hbm)
-        line["ax_gs_sizes"] = size_sweep(sem, torch, dev, hbm)
+            ex["batch"] = batch_leg(sem, inputs)
+            bl = ex["batch"]
+            ex["serve"] = serve_leg(sem, inputs, bl["autotuned_workers"],
+                                    graph=bl["solves_per_s_graph"] > bl["solves_per_s"])
+        ex["ax_sweep_64cube"] = operator_sweep(sem, torch, dev, hbm)
+        ex["ax_gs_sizes"] = size_sweep(sem, torch, dev, hbm)
         if world == 1:
+            ex["precision_errors"] = precision_errors_leg(sem, torch, dev, args)
             dt, ng_s, it_s, threads = oracle_sample_solve(12)
-            line["oracle_timings"] = oracle_timings()
-            line["oracle_timings"]["config3_extrapolated"] = oracle_extrapolated(
+            ex["oracle_timings"] = oracle_timings()
+            ex["oracle_timings"]["config3_extrapolated"] = oracle_extrapolated(
                 dt, it_s, 12, side, line["iters"][0], ng)
             line["cpu_baseline"] = {
                 "value": ng_s / dt / 1e9, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
-                "sample": f"oracle FlexCG+pMG 7-3-1 solve to 1e-8 on a 12^3-element box of the "
+                "sample": f"oracle FlexCG+pMG 7-3-1 solve to 1e-8 on a {12}^3-element box of the "
                           f"same recipe ({ng_s} unique dofs, {it_s} iterations, {dt:.1f} s)"}
+        # long sweeps first and the legs that matter last, so that a reader of
+        # the end of the line sees them; a compact summary closes the line
+        for key in ("ax_sweep_64cube", "ax_gs_sizes", "oracle_timings", "projection", "config1",
+                    "batch", "serve", "graph", "named_config", "precision_errors", "precision"):
+            if key in ex:
+                line[key] = ex.pop(key)
+        line["summary"] = summary_of(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

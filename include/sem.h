@@ -50,7 +50,8 @@ typedef enum {
   SEM_EAGAIN = 6,    /* request still pending (sem_poll) */
   SEM_EBUSY = 7,     /* no free slot or memory for a request (sem_submit) */
   SEM_ETIMEOUT = 8   /* a bounded wait inside a kernel ran out (reported by
-                        the solves, see sem_solve) */
+                        the solves, sem_pmg_vcycle and the staged kinds of
+                        sem_ax; see sem_solve) */
 } sem_status;
 
 typedef enum { SEM_F64 = 0, SEM_F32 = 1, SEM_F16 = 2, SEM_BF16 = 3 } sem_dtype;
@@ -107,8 +108,9 @@ sem_status sem_mesh_destroy(sem_mesh *mesh);
 sem_status sem_inject_alloc_failure(int32_t after);
 
 /* Test hook: sets the fine level's wait-error flag from the host, as a
- * kernel whose bounded wait ran out would, so that the next solve on the
- * mesh reports SEM_ETIMEOUT (and clears it).  Nothing runs on the device.
+ * kernel whose bounded wait ran out would, so that the next call that reads
+ * the flags (a solve, sem_pmg_vcycle, a staged kind of sem_ax) reports
+ * SEM_ETIMEOUT and clears it.  Nothing runs on the device.
  * Synchronises `stream`.  Errors: SEM_EINVAL (null mesh), SEM_ECUDA. */
 sem_status sem_inject_wait_error(sem_mesh *mesh, void *stream);
 
@@ -142,7 +144,11 @@ enum { SEM_AX_LOCAL = 0, SEM_AX_ASSEMBLED = 1 };
  * are E-layout device vectors of n_local elements and must not overlap; for
  * the 32- and 16-bit kinds on stored geometry u must be 16-byte aligned
  * (SEM_EINVAL otherwise).  The assembled FP32 forms sum the copies of a node
- * across x-, then y-, then z-faces: every copy receives the same bits. */
+ * across x-, then y-, then z-faces: every copy receives the same bits.
+ * The 32- and 16-bit kinds on stored geometry stage their inputs by bulk
+ * copies with bounded waits: those calls synchronise `stream`, read the
+ * mesh's wait flag and return SEM_ETIMEOUT (w incomplete) if a wait ran out
+ * (the flag is cleared). */
 sem_status sem_ax(sem_mesh *mesh, sem_dtype dtype, const void *u, void *w, int32_t flags,
                   void *stream);
 
@@ -231,7 +237,10 @@ sem_status sem_pmg_info(const sem_pmg *pmg, int32_t level, double *lam_lo, doubl
 /* Iterations the coarsest-level solver took in the last V-cycle (HOST
  * output; synchronises the stream the V-cycle ran on). */
 sem_status sem_pmg_coarse_iters(const sem_pmg *pmg, void *stream, int32_t *iters);
-/* One V-cycle z = M r on the finest level (FP64 E-layout device vectors). */
+/* One V-cycle z = M r on the finest level (FP64 E-layout device vectors).
+ * Synchronises `stream` to read the levels' wait flags: SEM_ETIMEOUT (z
+ * incomplete; flags cleared) if a bounded wait in a smoother kernel ran
+ * out. */
 sem_status sem_pmg_vcycle(sem_pmg *pmg, const double *r, double *z, void *stream);
 
 enum { SEM_SOLVER_PCG = 0, SEM_SOLVER_FLEXCG = 1, SEM_SOLVER_FGMRES = 2 };

@@ -686,6 +686,10 @@ sem_status sem_ax(sem_mesh *mesh, sem_dtype dtype, const void *u, void *w, int32
         level_ensure_g16(mesh->fine, dtype, st);
       }
       launch_ax32(mesh->fine, dtype, (const float *)u, (float *)w, flags == SEM_AX_ASSEMBLED, st);
+      // the staged kernel leaves its work undone if a bounded wait ran out
+      if (take_wait_errors(mesh, nullptr, st))
+        fail(SEM_ETIMEOUT, "a bounded wait in the operator kernel ran out (a bulk copy did not "
+                           "complete); w is incomplete");
     } else {
       fail(SEM_EINVAL, "unknown dtype %d", (int)dtype);
     }
@@ -765,7 +769,12 @@ sem_status sem_pmg_vcycle(sem_pmg *pmg, const double *r, double *z, void *stream
   return guarded([&] {
     SEM_REQUIRE(pmg && r && z, "null argument");
     SEM_REQUIRE(r != z, "r and z must not alias");
-    pmg_vcycle(pmg, r, z, as_stream(stream));
+    cudaStream_t st = as_stream(stream);
+    pmg_vcycle(pmg, r, z, st);
+    // staged smoother kernels leave their work undone if a bounded wait ran out
+    if (take_wait_errors(pmg->mesh, pmg, st))
+      fail(SEM_ETIMEOUT, "a bounded wait in a smoother kernel ran out (a bulk copy did not "
+                         "complete); z is incomplete");
   });
 }
 

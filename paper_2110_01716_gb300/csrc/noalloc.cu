@@ -9,6 +9,7 @@
 // array below, which every GPU that loads the library holds until the process
 // exits.  The caller passes the inputs and the device location of the result.
 #include <mutex>
+#include <new>
 
 #include "common.cuh"
 
@@ -112,5 +113,12 @@ extern "C" sem_status sem_dot_noalloc(const sem_mesh *mesh, const double *u, con
     return SEM_OK;
   } catch (const sem::Failure &f) {
     return f.status;
+  } catch (const std::bad_alloc &) {
+    sem::set_error_message("host allocation failed");
+    return SEM_ENOMEM;
+  } catch (...) {
+    // e.g. std::system_error from the lock: no exception crosses the C ABI
+    sem::set_error_message("unexpected internal error");
+    return SEM_ECUDA;
   }
 }

@@ -256,6 +256,12 @@ def sem_dot(mesh: Mesh, u, v, stream=None) -> float:
 def sem_dot_noalloc(mesh: Mesh, u, v, result, stream=None):
     """Unique-node inner product into ``result`` (a one-element device tensor)
     for callers that cannot have the library allocate; see include/sem.h."""
+    for name, t in (("u", u), ("v", v)):
+        if str(t.dtype) != "torch.float64" or not t.is_cuda or t.numel() < mesh.n_local:
+            raise ValueError(f"{name} must be a float64 CUDA tensor of at least n_local "
+                             f"= {mesh.n_local} values")
+    if str(result.dtype) != "torch.float64" or not result.is_cuda or result.numel() < 1:
+        raise ValueError("result must be a float64 CUDA tensor with at least one element")
     check(lib().sem_dot_noalloc(mesh.h, _ptr(u), _ptr(v), _ptr(result), _stream(stream)))
     return result
 

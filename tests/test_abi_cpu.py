@@ -72,6 +72,8 @@ def test_invalid_arguments_return_einval_without_device_work(libsem):
     assert L.sem_solve(None, None, None, None, C.byref(desc), C.byref(info), None) == \
         libsem.SEM_EINVAL
     assert L.sem_inject_wait_error(None, None) == libsem.SEM_EINVAL
+    assert L.sem_dot_noalloc(None, None, None, None, None) == libsem.SEM_EINVAL
+    assert "null argument" in libsem.last_error()
     assert L.sem_mesh_destroy(None) == libsem.SEM_OK
     assert L.sem_pmg_destroy(None) == libsem.SEM_OK
 

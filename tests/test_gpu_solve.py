@@ -763,3 +763,31 @@ def test_wait_error_is_reported_by_the_next_solve_and_cleared(solver):
     assert ei.value.status == sem.SEM_ETIMEOUT
     again = sem.sem_solve(m, P, bd, torch.zeros_like(bd), solver, tol=1e-8, max_iter=200)
     assert again["status"] == sem.SEM_OK and again["iters"] == ok["iters"]
+
+
+def test_wait_error_is_reported_by_vcycle_and_staged_operator():
+    """sem_pmg_vcycle and the staged FP32 operator read the wait flags too: a
+    flag set from the host turns the next such call into SEM_ETIMEOUT (and is
+    cleared), so a later solve on the mesh is not blamed for it."""
+    m, L, b = _graph_problem(0, (7, 3, 1))
+    P = sem.Pmg(m, orders=(7, 3, 1), coarse_tol=1e-2, coarse_maxit=60)
+    bd = torch.tensor(b, device=DEV)
+    z = torch.empty_like(bd)
+    sem.sem_pmg_vcycle(P, bd, z)
+    z_ok = z.clone()
+    sem.sem_inject_wait_error(m)
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_pmg_vcycle(P, bd, z)
+    assert ei.value.status == sem.SEM_ETIMEOUT
+    sem.sem_pmg_vcycle(P, bd, z)
+    assert torch.equal(z, z_ok)
+    u = torch.tensor(inputs.random_field(L.nl, 3), device=DEV, dtype=torch.float32)
+    w = torch.empty_like(u)
+    sem.sem_inject_wait_error(m)
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_ax(m, sem.SEM_F32, u, w, sem.SEM_AX_ASSEMBLED)
+    assert ei.value.status == sem.SEM_ETIMEOUT
+    sem.sem_ax(m, sem.SEM_F32, u, w, sem.SEM_AX_ASSEMBLED)
+    ok = sem.sem_solve(m, P, bd, torch.zeros_like(bd), sem.SEM_SOLVER_FLEXCG, tol=1e-8,
+                       max_iter=200)
+    assert ok["status"] == sem.SEM_OK
