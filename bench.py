@@ -554,50 +554,139 @@ def projection_sequence(sem, torch, mesh, pmg, dev, solver, restart, steps=16, L
     return out
 
 
-def batch_leg(sem, inputs, count=64, max_workers=8):
-    """64 independent problems (E log-uniform in [64, 8192] elements, N in
-    {5, 7, 9}, manufactured right-hand side, FlexCG + pMG to 1e-8): sequential
-    (one worker) with the FP64 smoother and with the FP32 smoother, and the
-    worker count the autotuner picks.  Every solve includes its setup."""
+def batch_orders(N):
+    o = [N]
+    if 1 < N // 2 < N:
+        o.append(N // 2)
+    if N > 1:
+        o.append(1)
+    return tuple(o)
+
+
+def batch_leg(sem, torch, inputs, dev, count=64, reps=5):
+    """Config 4: 64 independent problems (E log-uniform in [64, 8192] on
+    near-cubic boxes, N in {5, 7, 9}, manufactured right-hand side, Dirichlet,
+    FlexCG + pMG (N, N/2, 1) to 1e-8), solved (a) one after another with
+    sem_solve, FP64 smoother and FP32 smoother, and (b) all at once by one
+    launch of the batch's CUDA graph (sem_batch, FP32 smoother), its work split
+    picked by the batch autotuner.  Setup is excluded from all three (it is
+    reported apart); times are CUDA events around the solves."""
+    import numpy as np
+
     inst = inputs.batch_instances(4, count)
-    reqs = [sem.make_request(d["ex"], d["ey"], d["ez"], d["N"], sem.SEM_DIRICHLET, 0.1,
-                             d["seed"], tol=1e-8) for d in inst]
+    stream = torch.cuda.current_stream()
+    meshes, bs = [], []
+    for d in inst:
+        m = sem.Mesh(d["ex"], d["ey"], d["ez"], d["N"], sem.SEM_DIRICHLET, jitter=0.1,
+                     seed=d["seed"])
+        n = m.n_local
+        X = [torch.empty(n, device=dev, dtype=torch.float64) for _ in range(4)]
+        for k in range(3):
+            sem.sem_mesh_field(m, k, X[k])
+        sem.sem_mesh_field(m, sem.SEM_FIELD_MASS, X[3])
+        b = X[3] * 3 * torch.pi ** 2 * torch.sin(torch.pi * X[0]) * torch.sin(torch.pi * X[1]) \
+            * torch.sin(torch.pi * X[2])
+        sem.sem_gs(m, sem.SEM_F64, b)
+        mask = torch.empty_like(b)
+        sem.sem_mesh_field(m, sem.SEM_FIELD_MASK, mask)
+        b *= mask
+        meshes.append(m)
+        bs.append(b)
+        del X, mask
 
-    def run(workers, smoother, graph=False):
-        S = sem.Server(workers=workers, cache_per_shape=0, smoother_dtype=smoother)
-        t0 = time.perf_counter()
-        tk = [S.submit(d["ex"], d["ey"], d["ez"], d["N"], sem.SEM_DIRICHLET, 0.1, d["seed"],
-                       tol=1e-8, use_graph=graph) for d in inst]
-        infos = [S.wait(t) for t in tk]
-        dt = time.perf_counter() - t0
-        S.close()
-        bad = [i for i, f in enumerate(infos) if f["status"] != sem.SEM_OK]
-        if bad:
-            raise SystemExit(f"batch leg: requests {bad} failed")
-        return dt, infos
+    def sequential(smoother):
+        pmgs = [sem.Pmg(m, orders=batch_orders(d["N"]), cheb_degree=3, smoother_dtype=smoother,
+                        coarse_tol=0.2, coarse_maxit=30, coarse_mode=sem.SEM_COARSE_MG)
+                for m, d in zip(meshes, inst)]
+        xs = [torch.zeros_like(b) for b in bs]
 
-    t64, _ = run(1, sem.SEM_F64)
-    t32, _ = run(1, sem.SEM_F32)
-    best_w, rate = sem.server_autotune(reqs, max_workers=max_workers, cache_per_shape=0)
-    tb, infos = run(best_w, sem.SEM_F32)
-    tg, infos_g = run(best_w, sem.SEM_F32, graph=True)
-    return {"instances": count, "workload": "config 4: E log-uniform [64, 8192], N in {5,7,9}, "
-            "manufactured RHS, Dirichlet, FlexCG+pMG to 1e-8, setup included",
-            "fp64_sequential_s": round(t64, 3), "fp32_sequential_s": round(t32, 3),
-            "autotuned_workers": best_w, "autotune_rate": round(rate, 2),
-            "batched_s": round(tb, 3), "solves_per_s": round(count / tb, 2),
+        def run():
+            its = []
+            for m, P, b, x in zip(meshes, pmgs, bs, xs):
+                f = sem.sem_solve(m, P, b, x, sem.SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=200,
+                                  zero_guess=True)
+                if f["status"] != sem.SEM_OK:
+                    raise SystemExit("batch leg: a sequential solve failed")
+                its.append(f["iters"])
+            return its
+
+        run()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = run()
+        e1.record(stream)
+        e1.synchronize()
+        for P in pmgs:
+            P.close()
+        return e0.elapsed_time(e1) / 1e3, its
+
+    t64, _ = sequential(sem.SEM_F64)
+    t32, its32 = sequential(sem.SEM_F32)
+    hb = [b.cpu().numpy() for b in bs]
+    xs = [np.zeros_like(b) for b in hb]
+    reqs = [sem.make_request(d["ex"], d["ey"], d["ez"], d["N"], sem.SEM_DIRICHLET, 0.1, d["seed"],
+                             b=b, x=x, tol=1e-8) for d, b, x in zip(inst, hb, xs)]
+    for m in meshes:
+        m.close()
+    del meshes, bs
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    B = sem.Batch(reqs, smoother_dtype=sem.SEM_F32, cheb_degree=3, coarse_tol=0.2,
+                  coarse_maxit=30, coarse_ctas=1, keep=hb + xs)
+    setup_s = time.perf_counter() - t0
+    infos = B.solve()
+    default_ms = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = B.solve()
+        e1.record(stream)
+        e1.synchronize()
+        default_ms.append(e0.elapsed_time(e1))
+    chosen, tuned_ms = B.autotune(candidates=(2.0, 1.0, 0.5, 0.25, 0.125, 0.0625), reps=3)
+    ms = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = B.solve()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    info = B.info()
+    B.close()
+    if any(f["status"] != sem.SEM_OK for f in infos):
+        raise SystemExit("batch leg: a batched solve failed")
+    tb = statistics.median(ms) / 1e3
+    return {"instances": count,
+            "workload": "config 4: E log-uniform [64, 8192], N in {5,7,9}, manufactured RHS, "
+                        "Dirichlet, FlexCG+pMG (N, N/2, 1) to 1e-8, setup excluded",
+            "fp64_sequential_s": round(t64, 4), "fp32_sequential_s": round(t32, 4),
+            "batched_s": round(tb, 4), "batched_default_split_s": round(
+                statistics.median(default_ms) / 1e3, 4),
+            "solves_per_s": round(count / tb, 1),
             "speedup_vs_fp64_sequential": round(t64 / tb, 2),
-            "batched_graph_s": round(tg, 3), "solves_per_s_graph": round(count / tg, 2),
-            "iters_mean": round(sum(f["iters"] for f in infos) / count, 2)}
+            "speedup_vs_fp32_sequential": round(t32 / tb, 2),
+            "autotuned_ax_fill_by_order": {str(k): v for k, v in sorted(chosen.items())},
+            "graph_nodes": info["graph_nodes"], "setup_s": round(setup_s, 2),
+            "arena_GB": round(info["dev_bytes"] / 1e9, 2),
+            "iters_mean": round(sum(f["iters"] for f in infos) / count, 2),
+            "same_iters_as_sequential_fp32": [f["iters"] for f in infos] == its32}
 
 
-def serve_leg(sem, inputs, workers, count=200, load=0.8, graph=False):
+def serve_leg(sem, inputs, workers=None, count=200, load=0.8, graph=False):
     """Config 5: Poisson arrivals at `load` times the measured capacity (the
     first 32 requests run back to back with the same workers), E log-uniform
     in [512, 65536], N = 7, tolerance in {1e-6, 1e-8, 1e-10}.  Latency is
     submit -> completion; the stream is cut to `count` requests (1000 in the
     full recipe) to keep the bench within minutes."""
     probe = inputs.arrival_stream(5, 32, 1.0)
+    if workers is None:
+        sample = [sem.make_request(r["ex"], r["ey"], r["ez"], r["N"], sem.SEM_DIRICHLET, 0.1,
+                                   r["seed"], tol=r["tol"]) for r in probe[:16]]
+        workers, _ = sem.server_autotune(sample, max_workers=8, cache_per_shape=0)
     S = sem.Server(workers=workers, cache_per_shape=0)
     t0 = time.perf_counter()
     tk = [S.submit(r["ex"], r["ey"], r["ez"], r["N"], sem.SEM_DIRICHLET, 0.1, r["seed"],
@@ -998,10 +1087,8 @@ def main():
         torch.cuda.empty_cache()
         ex["config1"] = config1_leg(sem, torch, dev)
         if not args.no_serve:
-            ex["batch"] = batch_leg(sem, inputs)
-            bl = ex["batch"]
-            ex["serve"] = serve_leg(sem, inputs, bl["autotuned_workers"],
-                                    graph=bl["solves_per_s_graph"] > bl["solves_per_s"])
+            ex["batch"] = batch_leg(sem, torch, inputs, dev)
+            ex["serve"] = serve_leg(sem, inputs)
         ex["ax_sweep_64cube"] = operator_sweep(sem, torch, dev, hbm)
         ex["ax_gs_sizes"] = size_sweep(sem, torch, dev, hbm)
         if world == 1:

@@ -197,6 +197,13 @@ typedef struct {
   int32_t coarse_mode;      /* SEM_COARSE_JACOBI or SEM_COARSE_MG (below) */
   int32_t smoother;         /* SEM_SMOOTH_JACOBI, SEM_SMOOTH_ASM,
                                SEM_SMOOTH_ASM_TC or SEM_SMOOTH_ASM_TF32 (below) */
+  int32_t coarse_ctas;      /* CTAs of the persistent N = 1 coarse kernel: 0 =
+                               one per SM (capped by the lattice size), k > 0 =
+                               at most k.  Small caps let the coarse solves of
+                               many problems run side by side (sem_batch);
+                               the CTA count fixes the order of the coarse
+                               solver's reductions, so results are identical
+                               only between equal caps. */
 } sem_pmg_desc;
 
 /* Smoother of the smoothed levels, Chebyshev-accelerated in both cases (Sec. 3).
@@ -237,6 +244,13 @@ sem_status sem_pmg_info(const sem_pmg *pmg, int32_t level, double *lam_lo, doubl
 /* Iterations the coarsest-level solver took in the last V-cycle (HOST
  * output; synchronises the stream the V-cycle ran on). */
 sem_status sem_pmg_coarse_iters(const sem_pmg *pmg, void *stream, int32_t *iters);
+/* The solve of the coarsest level alone, as a V-cycle runs it (Sec. 4: the
+ * coarse-grid solve): b is a right-hand side of that level (FP64 E-layout
+ * device vector of E (N_c+1)^3 values, assembled; masked under Dirichlet),
+ * x receives the solution after the coarse solver's tolerance or iteration
+ * cap (sem_pmg_desc coarse_tol, coarse_maxit, coarse_mode).  Does not
+ * synchronise. */
+sem_status sem_pmg_coarse_solve(sem_pmg *pmg, const double *b, double *x, void *stream);
 /* One V-cycle z = M r on the finest level (FP64 E-layout device vectors).
  * Synchronises `stream` to read the levels' wait flags: SEM_ETIMEOUT (z
  * incomplete; flags cleared) if a bounded wait in a smoother kernel ran
@@ -382,6 +396,69 @@ sem_status sem_server_stats_read(const sem_server *server, sem_server_stats *out
  * count with the highest throughput (*best_rate in solves per second). */
 sem_status sem_server_autotune(const sem_server_desc *base, const sem_request *reqs, int32_t n,
                                int32_t max_workers, int32_t *best_workers, double *best_rate);
+
+/* ---- Batched solves: many independent problems in one graph launch -----
+ * The paper has no counterpart (it runs one large solve across partitions);
+ * this is a service of the library for many small and mid-sized problems,
+ * whose kernels, each alone, would leave most of the GPU idle.
+ * sem_batch_create builds every problem's mesh, pMG hierarchy (orders N,
+ * N/2 when it lies strictly between 1 and N, and 1; coarse solve:
+ * multigrid-preconditioned CG in one cooperative kernel of coarse_ctas CTAs),
+ * right-hand side and work vectors in one device arena (a few cudaMalloc
+ * calls for the whole batch, no allocation per problem), runs one warm-up
+ * solve per distinct order, and captures one CUDA graph that holds every
+ * problem's whole FlexCG solve from x = 0 as an independent branch: the
+ * V-cycles, operators, inner products and stopping tests run on the device
+ * (a conditional node per problem for its iterations), concurrently across
+ * problems.  sem_batch_solve launches that graph once, copies each x to the
+ * request's host x (when not NULL) and returns every problem's
+ * sem_solve_info.  Each x equals, bit for bit, sem_solve (FlexCG, zero
+ * guess) on a mesh built from the request and a pMG built from
+ * sem_batch_pmg_desc(batch, i), whatever the other problems and ax_fill
+ * are.  Requests: SEM_SOLVER_FLEXCG only, 2 <= N <= SEM_MAX_ORDER, SEM_RHS_HOST
+ * (b copied at creation; mean-free under Neumann) or SEM_RHS_MANUFACTURED;
+ * their x pointers must stay valid while the batch solves. */
+typedef struct sem_batch sem_batch;
+typedef struct {
+  int32_t cheb_degree;      /* pMG template (as sem_pmg_desc) */
+  int32_t smoother_dtype;
+  double coarse_tol;
+  int32_t coarse_maxit;
+  int32_t coarse_ctas;      /* CTAs of each coarse solve (0: 1) */
+  float ax_fill[SEM_MAX_ORDER + 1];
+                            /* per level order: work units (x-line segments)
+                               of the FP32 operator per resident CTA slot of
+                               the GPU; 0 = 2 (the single-problem default);
+                               below 1 a problem's operator also takes only
+                               that share of the slots.  Moves work between
+                               CTAs only: results do not change. */
+  int64_t arena_chunk;      /* bytes per device arena chunk (0: 1 GiB) */
+} sem_batch_desc;
+/* Errors: SEM_EINVAL (descriptions), SEM_ENOMEM, SEM_ECUDA.  Synchronises. */
+sem_status sem_batch_create(const sem_batch_desc *desc, const sem_request *reqs, int32_t n,
+                            void *stream, sem_batch **out);
+/* infos: HOST array of n entries (may be NULL).  Returns SEM_OK when every
+ * problem converged, else the first problem's failing status (SEM_ENOTCONV,
+ * SEM_ENUMERIC, SEM_ETIMEOUT); infos hold each problem's.  Synchronises. */
+sem_status sem_batch_solve(sem_batch *batch, sem_solve_info *infos, void *stream);
+/* Device bytes of the arena, nodes of the graph's top level, host time of
+ * the setup in ms (any output may be NULL). */
+sem_status sem_batch_info(const sem_batch *batch, size_t *dev_bytes, int32_t *graph_nodes,
+                          double *setup_ms);
+/* The pMG description of problem i (to reproduce its solve with sem_solve). */
+sem_status sem_batch_pmg_desc(const sem_batch *batch, int32_t i, sem_pmg_desc *out);
+/* Device address of problem i's solution (owned by the batch). */
+sem_status sem_batch_x(const sem_batch *batch, int32_t i, const double **x_dev);
+sem_status sem_batch_destroy(sem_batch *batch);
+/* Autotuner of the batch's work split: for every fine order present, the
+ * graph of that order's problems alone is captured with each candidate
+ * ax_fill (for the levels of that order) and timed (median of reps
+ * launches, CUDA events); the fastest is kept.  The batch's graph is then
+ * captured again with the chosen values, written to chosen[0..SEM_MAX_ORDER]
+ * (HOST), and *best_ms is the median time of one launch of the whole batch.
+ * Synchronises. */
+sem_status sem_batch_autotune(sem_batch *batch, const float *candidates, int32_t ncand,
+                              int32_t reps, void *stream, float *chosen, double *best_ms);
 
 /* Tracing (Sec. 4 reports timing breakdowns from CUDA events): while enabled,
  * every kernel launch of the library is counted under a class name such as

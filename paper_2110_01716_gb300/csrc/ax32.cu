@@ -29,6 +29,8 @@
 // contiguous values, so these passes move whole sectors.  Dirichlet masking is
 // done by the pass of each boundary's direction: a masked node's copies all lie
 // on that boundary plane, so later passes only add zeros.
+#include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstring>
 #include <type_traits>
@@ -526,7 +528,9 @@ static void ax32_np(const Level &L, const float *u, float *w, bool assemble, cud
   // Work units are x-line segments: whole lines when there are at least two
   // per resident CTA (no seams), otherwise lines are split.
   const int64_t lines = (int64_t)t.ey * t.ez;
-  const int64_t target = 2 * slots;
+  const double fill = L.ax32_fill > 0.f ? (double)L.ax32_fill : 2.0;
+  const int64_t target = std::max<int64_t>(1, (int64_t)std::ceil(fill * (double)slots));
+  const int64_t cap = std::min<int64_t>(slots, target);
   int nseg = 1;
   if (lines < target) {
     const int64_t want = (target + lines - 1) / lines;
@@ -537,7 +541,7 @@ static void ax32_np(const Level &L, const float *u, float *w, bool assemble, cud
   a.seg_len = (t.ex + nseg - 1) / nseg;
   a.nseg = (t.ex + a.seg_len - 1) / a.seg_len;
   const int64_t units = lines * a.nseg;
-  const int grid = (int)(units < slots ? units : slots);  // persistent: every CTA resident
+  const int grid = (int)(units < cap ? units : cap);  // persistent: every CTA resident
   constexpr int bytes = L32<NP, GK>::BYTES;
   static const char *names[3][2] = {{"ax32_f32", "ax32_f32_local"},
                                     {"ax32_f16g", "ax32_f16g_local"},

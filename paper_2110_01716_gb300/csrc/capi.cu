@@ -381,6 +381,155 @@ static void ensure_graph(sem_mesh *M, sem_pmg *P, double *x) {
   M->graph_kernels = kernels;
 }
 
+// Nodes of `g` that no other node of `g` depends on (the end of what a
+// capture appended, when the capture was one sequence).
+static std::vector<cudaGraphNode_t> graph_sinks(cudaGraph_t g) {
+  size_t n = 0;
+  SEM_CHECK_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n), sinks;
+  if (n) SEM_CHECK_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+  for (cudaGraphNode_t v : nodes) {
+    size_t m = 0;
+    SEM_CHECK_CUDA(cudaGraphNodeGetDependentNodes(v, nullptr, nullptr, &m));
+    if (m == 0) sinks.push_back(v);
+  }
+  return sinks;
+}
+
+// Capture into `g` one sequence run on stream cs, after the nodes `deps` of
+// `g`; returns the nodes it added that nothing depends on.
+template <typename F>
+static std::vector<cudaGraphNode_t> capture_into(cudaGraph_t g, cudaStream_t cs,
+                                                 const std::vector<cudaGraphNode_t> &deps,
+                                                 F &&work) {
+  size_t n0 = 0;
+  SEM_CHECK_CUDA(cudaGraphGetNodes(g, nullptr, &n0));
+  std::vector<cudaGraphNode_t> old(n0);
+  if (n0) SEM_CHECK_CUDA(cudaGraphGetNodes(g, old.data(), &n0));
+  SEM_CHECK_CUDA(cudaStreamBeginCaptureToGraph(cs, g, deps.empty() ? nullptr : deps.data(),
+                                               nullptr, deps.size(),
+                                               cudaStreamCaptureModeThreadLocal));
+  try {
+    work();
+  } catch (...) {
+    cudaGraph_t tmp = nullptr;
+    cudaStreamEndCapture(cs, &tmp);
+    cudaGetLastError();
+    throw;
+  }
+  cudaGraph_t out = nullptr;
+  SEM_CHECK_CUDA(cudaStreamEndCapture(cs, &out));
+  std::vector<cudaGraphNode_t> sinks;
+  for (cudaGraphNode_t v : graph_sinks(g))
+    if (std::find(old.begin(), old.end(), v) == old.end()) sinks.push_back(v);
+  return sinks;
+}
+
+// A conditional node of type ty in g after deps; returns its body graph and,
+// in *node, the node.
+static cudaGraph_t add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
+                                   cudaGraphConditionalHandle h, cudaGraphConditionalNodeType ty,
+                                   cudaGraphNode_t *node) {
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = ty;
+  np.conditional.size = 1;
+  SEM_CHECK_CUDA(cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr,
+                                  deps.size(), &np));
+  return np.conditional.phGraph_out[0];
+}
+
+// A whole FlexCG solve from x = 0 (Sec. 3), run by the device, appended to
+// graph `g` as a branch of its own (no dependencies on the graph's other
+// nodes): the kernels of run_solve with use_graph and zero_guess, in the same
+// order, the host's stopping tests replaced by device ones (the arm kernel
+// after the start, the stop kernel after every iteration).  The branch is
+//   memset x, start (r = b, <b,b>, <r,r>), arm -> IF(iterations due) {
+//     V-cycle of r, <z,r>, iteration 1, stop -> WHILE(not done) {
+//       V-cycle, dots, direction, operator, update, stop } }
+// so its results equal those of sem_solve bit for bit.  The state is left in
+// the mesh's scalar slots: 0 <b,b>, 1 <r,r>, 8 tol^2 <b,b>, 9 max_iter,
+// 10 iterations, 11 stopping state (1 done, 2 NaN/Inf), 12 initial <r,r>
+// (flexcg_graph_result reads them).  Returns the branch's last node.  The
+// work vectors are allocated before the capture begins.
+cudaGraphNode_t capture_flexcg(sem_mesh *M, sem_pmg *P, const double *b, double *x, double tol,
+                               int maxit, cudaGraph_t g, cudaStream_t cs) {
+  const Level &L = M->fine;
+  const Topo &t = L.t;
+  ensure_work(M);
+  const size_t ws = work_stride(M);
+  double *r = M->work.p, *z = r + ws, *p = z + ws, *w = p + ws;
+  cudaGraphConditionalHandle hif, hwhile;
+  SEM_CHECK_CUDA(cudaGraphConditionalHandleCreate(&hif, g, 0, cudaGraphCondAssignDefault));
+  std::vector<cudaGraphNode_t> head = capture_into(g, cs, {}, [&] {
+    SEM_CHECK_CUDA(cudaMemsetAsync(x, 0, t.nl * sizeof(double), cs));
+    launch_cg_start(t, M->red, b, nullptr, nullptr, r, z, p, slot(M, 0), slot(M, 1), slot(M, 2),
+                    cs);
+    launch_graph_arm_full(slot(M, 0), slot(M, 1), slot(M, 8), tol, maxit, hif, cs);
+  });
+  cudaGraphNode_t if_node, while_node;
+  cudaGraph_t body_if = add_conditional(g, head, hif, cudaGraphCondTypeIf, &if_node);
+  SEM_CHECK_CUDA(
+      cudaGraphConditionalHandleCreate(&hwhile, body_if, 0, cudaGraphCondAssignDefault));
+  const VcycleIO io = pmg_io(P);
+  std::vector<cudaGraphNode_t> first = capture_into(body_if, cs, {}, [&] {
+    if (io.in32) launch_convert<double, float>(t.nl, r, io.in32, cs);
+    else launch_convert<double, double>(t.nl, r, io.in64, cs);
+    pmg_vcycle_core(P, cs);
+    if (io.out32) launch_dot(t, M->red, io.out32, r, slot(M, 2), cs);
+    else launch_dot(t, M->red, io.out64, r, slot(M, 2), cs);
+    flex_operator(M, io, p, w, true, cs);
+    flex_update(M, io, p, w, x, r, cs);
+    launch_graph_stop(slot(M, 1), slot(M, 8), hwhile, cs);
+  });
+  cudaGraph_t body_while =
+      add_conditional(body_if, first, hwhile, cudaGraphCondTypeWhile, &while_node);
+  capture_into(body_while, cs, {}, [&] {
+    flex_precondition(M, P, io, r, w, cs);
+    flex_operator(M, io, p, w, false, cs);
+    flex_update(M, io, p, w, x, r, cs);
+    launch_graph_stop(slot(M, 1), slot(M, 8), hwhile, cs);
+  });
+  return if_node;
+}
+
+// Append to g, after `after`, a copy of the mesh's scalar slots 0..12 into
+// dst (device) and return the copy's node.
+cudaGraphNode_t capture_slots_copy(sem_mesh *M, double *dst, cudaGraph_t g, cudaGraphNode_t after,
+                                   cudaStream_t cs) {
+  std::vector<cudaGraphNode_t> tail = capture_into(g, cs, {after}, [&] {
+    SEM_CHECK_CUDA(cudaMemcpyAsync(dst, slot(M, 0), 13 * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, cs));
+  });
+  SEM_REQUIRE(tail.size() == 1, "slot copy capture");
+  return tail[0];
+}
+
+// The Neumann right-hand-side check of the solves (check_neumann_rhs).
+void mesh_check_rhs(sem_mesh *M, const double *b, cudaStream_t st) { check_neumann_rhs(M, b, st); }
+
+// Read and clear the wait flags of a mesh and its pMG (take_wait_errors).
+bool mesh_take_wait_errors(sem_mesh *M, sem_pmg *P, cudaStream_t st) {
+  return take_wait_errors(M, P, st);
+}
+
+// The stopping state of a solve captured by capture_flexcg, from its scalar
+// slots s[0..12] (read by the caller): fills info and returns the status the
+// host loop of run_solve would have returned.
+sem_status flexcg_graph_result(const double *s, sem_solve_info &info) {
+  const double bb = s[0], rr = s[1], tol2 = s[8];
+  info.bnorm = std::sqrt(bb);
+  info.res0 = std::sqrt(s[12]);
+  info.res = std::sqrt(rr);
+  info.iters = (int32_t)s[10];
+  sem_status st;
+  if (s[11] == 2.0) st = SEM_ENUMERIC;
+  else st = rr <= tol2 ? SEM_OK : SEM_ENOTCONV;
+  info.status = st;
+  return st;
+}
+
 // Jacobi-PCG (Sec. 3) or flexible CG with one pMG V-cycle per iteration
 // (Sec. 3).  Scalar slots: 0 bb, 1 rr, 2/3 rho (alternating in PCG), 4 pw,
 // 5 zw, 6 sum of b, 7 unused output, 8-11 state of the graph loop.
@@ -753,6 +902,14 @@ sem_status sem_pmg_coarse_iters(const sem_pmg *pmg, void *stream, int32_t *iters
                                    as_stream(stream)));
     SEM_CHECK_CUDA(cudaStreamSynchronize(as_stream(stream)));
     *iters = v;
+  });
+}
+
+sem_status sem_pmg_coarse_solve(sem_pmg *pmg, const double *b, double *x, void *stream) {
+  return guarded([&] {
+    SEM_REQUIRE(pmg && b && x, "null argument");
+    SEM_REQUIRE(b != x, "b and x must not alias");
+    pmg_coarse_solve(pmg, b, x, as_stream(stream));
   });
 }
 

@@ -327,7 +327,7 @@ static CoarseArgs base_args(const CoarseSolver &C, const Level &L) {
   return A;
 }
 
-void coarse_setup(CoarseSolver &C, const Level &L, cudaStream_t st) {
+void coarse_setup(CoarseSolver &C, const Level &L, cudaStream_t st, int max_ctas) {
   SEM_REQUIRE(L.t.N == 1, "the persistent coarse solver needs N = 1");
   DevBuf<double> Gtmp;
   const double *G = L.G64.p;
@@ -356,6 +356,7 @@ void coarse_setup(CoarseSolver &C, const Level &L, cudaStream_t st) {
   const int64_t want = (ng + kCoarseThreads - 1) / kCoarseThreads;
   per_sm = std::min(per_sm, SEM_COARSE_CTAS_PER_SM);
   C.grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
+  if (max_ctas > 0 && C.grid > max_ctas) C.grid = max_ctas;
   C.part.alloc(3 * (size_t)((C.grid * 4 + 31) / 32 * 32));
   {
     TraceScope ts("coarse_setup", 1, st, 3);

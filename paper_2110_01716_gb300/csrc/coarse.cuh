@@ -68,10 +68,11 @@ struct CoarseSolver {
   std::unique_ptr<CoarseMg> mg;  // multigrid-preconditioned mode
 };
 
-void coarse_setup(CoarseSolver &C, const Level &L, cudaStream_t st);
+// max_ctas > 0 caps the persistent kernel's grid (sem_pmg_desc.coarse_ctas).
+void coarse_setup(CoarseSolver &C, const Level &L, cudaStream_t st, int max_ctas = 0);
 void coarse_solve_persistent(CoarseSolver &C, const Level &L, const double *b_local,
                              double *x_local, double tol, int maxit, cudaStream_t st);
-void coarse_mg_setup(CoarseSolver &C, const Level &L, cudaStream_t st);
+void coarse_mg_setup(CoarseSolver &C, const Level &L, cudaStream_t st, int max_ctas = 0);
 void coarse_mg_solve(CoarseSolver &C, const double *b_local, double *x_local, double tol,
                      int maxit, cudaStream_t st);
 

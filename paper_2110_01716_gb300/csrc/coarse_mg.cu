@@ -479,7 +479,7 @@ double power_lambda(const HostLevel &L) {
 
 }  // namespace
 
-void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st) {
+void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st, int max_ctas) {
   const int nx0 = Lv.t.ex + 1, ny0 = Lv.t.ey + 1, nz0 = Lv.t.ez + 1;
   const int n0 = nx0 * ny0 * nz0;
   std::unique_ptr<CoarseMg> M(new CoarseMg());
@@ -757,6 +757,7 @@ void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st) {
 #endif
   M->grid = std::max(1, std::min(sms * std::min(per_sm, SEM_MG_CTAS_PER_SM),
                                  (n0 + kMgThreads - 1) / kMgThreads));
+  if (max_ctas > 0 && M->grid > max_ctas) M->grid = max_ctas;
   const size_t ps = up((size_t)M->grid * 4, 32);
   M->part.alloc(4 * ps);
   A.partM = M->part.p;

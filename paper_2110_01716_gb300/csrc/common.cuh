@@ -41,11 +41,64 @@ void set_error_message(const char *msg);
 // SEM_ENOMEM before cudaMalloc is called; 0 disarms.
 inline std::atomic<int> g_alloc_fail_countdown{0};
 
-// Device allocation owned by a library object; freed in the destructor.
+// Device memory arena.  While a thread has one installed (ArenaScope), every
+// DevBuf allocation made on that thread is carved from it: 256-byte aligned
+// bump allocation from chunks of at least `chunk` bytes, so that building many
+// small problems costs a few cudaMalloc calls instead of hundreds (each of
+// which synchronises the device).  Buffers carved from an arena release
+// nothing; the arena frees its chunks when it is destroyed, after every
+// object built in it.
+struct DevArena {
+  size_t chunk = (size_t)1 << 30;
+  std::vector<void *> chunks;
+  char *cur = nullptr;
+  size_t cap = 0, used = 0;
+  size_t carved = 0;    // bytes handed out (alignment included)
+  size_t reserved = 0;  // bytes of all chunks
+  DevArena() = default;
+  DevArena(const DevArena &) = delete;
+  DevArena &operator=(const DevArena &) = delete;
+  ~DevArena() {
+    for (void *c : chunks) cudaFree(c);
+  }
+  void *take(size_t bytes) {
+    const size_t a = (used + 255) & ~(size_t)255;
+    if (!cur || a + bytes > cap) {
+      const size_t sz = bytes > chunk ? bytes : chunk;
+      if (g_alloc_fail_countdown.load(std::memory_order_relaxed) > 0 &&
+          g_alloc_fail_countdown.fetch_sub(1) == 1)
+        ::sem::fail(SEM_ENOMEM, "injected device allocation failure");
+      void *c = nullptr;
+      SEM_CHECK_CUDA(cudaMalloc(&c, sz));
+      chunks.push_back(c);
+      cur = static_cast<char *>(c);
+      cap = sz;
+      reserved += sz;
+      carved += bytes;
+      used = bytes;
+      return cur;
+    }
+    carved += (a - used) + bytes;
+    used = a + bytes;
+    return cur + a;
+  }
+};
+inline thread_local DevArena *t_arena = nullptr;
+struct ArenaScope {
+  DevArena *prev;
+  explicit ArenaScope(DevArena *a) : prev(t_arena) { t_arena = a; }
+  ~ArenaScope() { t_arena = prev; }
+  ArenaScope(const ArenaScope &) = delete;
+  ArenaScope &operator=(const ArenaScope &) = delete;
+};
+
+// Device allocation owned by a library object; freed in the destructor
+// (unless it was carved from an arena, which frees it).
 template <typename T>
 struct DevBuf {
   T *p = nullptr;
   size_t n = 0;
+  bool pooled = false;
   DevBuf() = default;
   DevBuf(const DevBuf &) = delete;
   DevBuf &operator=(const DevBuf &) = delete;
@@ -53,6 +106,12 @@ struct DevBuf {
   void alloc(size_t count) {
     release();
     if (count == 0) return;
+    if (t_arena) {
+      p = static_cast<T *>(t_arena->take(count * sizeof(T)));
+      pooled = true;
+      n = count;
+      return;
+    }
     if (g_alloc_fail_countdown.load(std::memory_order_relaxed) > 0 &&
         g_alloc_fail_countdown.fetch_sub(1) == 1)
       ::sem::fail(SEM_ENOMEM, "injected device allocation failure");
@@ -60,9 +119,10 @@ struct DevBuf {
     n = count;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p && !pooled) cudaFree(p);
     p = nullptr;
     n = 0;
+    pooled = false;
   }
   size_t bytes() const { return n * sizeof(T); }
 };
@@ -179,6 +239,11 @@ struct Level {
   DevBuf<uint16_t> G16[2];         // [E][6][Np3] G / scale as FP16 [0] or BF16 [1] bits
   DevBuf<float> G16scale[2];       // [E] per element: max |G| over its six factors
   DevBuf<int> err;                 // set by kernels whose bounded waits ran out
+  // Work units (x-line segments) the FP32 operator aims for per resident CTA
+  // slot of the GPU; below 1 the operator also uses only that share of the
+  // slots (batched solves share the GPU).  The x-face sums are the same bits
+  // for any value: this only moves work between CTAs.
+  float ax32_fill = 2.0f;
   DevBuf<int32_t> shared_nodes;    // unique ids of nodes with more than one copy
   int64_t n_shared = 0;
   DevBuf<double> dinv64;           // mask / assembled diagonal

@@ -75,8 +75,14 @@ void launch_ax_pair_dot(const Level &L, const double *u, double *w, double *pw, 
 void launch_graph_stop(const double *rr, double *g, cudaGraphConditionalHandle h,
                        cudaStream_t st);
 void launch_graph_arm(double *g, double tol2, int maxit, int done, cudaStream_t st);
+void launch_graph_arm_full(const double *bb, const double *rr, double *g, double tol, int maxit,
+                           cudaGraphConditionalHandle h, cudaStream_t st);
 template <typename A, typename B>
 void launch_convert(int64_t n, const A *a, B *b, cudaStream_t st);
+
+// b = mask gs(B f), f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) on the level's
+// points (tmp: 4 n_local doubles of scratch) -- serve.cu.
+void build_manufactured_rhs(const Level &L, double *b, double *tmp, cudaStream_t st);
 
 // Flexible GMRES (krylov.cu).  Basis vectors i < c at V + i * stride.
 constexpr int kMaxKrylov = 32;  // restart length limit

@@ -48,6 +48,16 @@ __device__ __forceinline__ void pair_fma(float2 a, float2 b, float &s, float &c)
   c = __fadd_rn(c, __fadd_rn(err, e));
 }
 
+// (s, c) = a * b for pair values a, b: the first term of a sum, where the
+// TwoSum of pair_fma against a zero accumulator would be exact (s = p).
+__device__ __forceinline__ void pair_mul_first(float2 a, float2 b, float &s, float &c) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  c = __fmaf_rn(a.y, b.x, e);
+  s = p;
+}
+
 // Renormalise (s, c) into a pair (Fast2Sum; |c| is far below |s| here).
 __device__ __forceinline__ float2 pair_norm(float s, float c) {
   const float t = __fadd_rn(s, c);
@@ -89,22 +99,65 @@ __device__ __forceinline__ void pair_apply_eo(const float2 *odd, const float2 *e
   if constexpr (HO > H) sv[H] = v[H];
 #pragma unroll
   for (int a = 0; a < H; ++a) {
-    float ps = 0.f, pc = 0.f, ms = 0.f, mc = 0.f;
+    float ps, pc, ms, mc;
+    pair_mul_first(odd[a * H], dv[0], ps, pc);
 #pragma unroll
-    for (int b = 0; b < H; ++b) pair_fma(odd[a * H + b], dv[b], ps, pc);
+    for (int b = 1; b < H; ++b) pair_fma(odd[a * H + b], dv[b], ps, pc);
+    pair_mul_first(even[a * HO], sv[0], ms, mc);
 #pragma unroll
-    for (int b = 0; b < HO; ++b) pair_fma(even[a * HO + b], sv[b], ms, mc);
+    for (int b = 1; b < HO; ++b) pair_fma(even[a * HO + b], sv[b], ms, mc);
     v[a] = pair_add(make_float2(ps, pc), make_float2(ms, mc));
     v[NP - 1 - a] = pair_add(make_float2(ps, pc), make_float2(-ms, -mc));
   }
   if constexpr (HO > H) {
-    float ps = 0.f, pc = 0.f;
+    float ps, pc;
+    pair_mul_first(odd[H * H], dv[0], ps, pc);
 #pragma unroll
-    for (int b = 0; b < H; ++b) pair_fma(odd[H * H + b], dv[b], ps, pc);
+    for (int b = 1; b < H; ++b) pair_fma(odd[H * H + b], dv[b], ps, pc);
     v[H] = pair_norm(ps, pc);
   }
 }
 
+
+// The fused form's <u, A_L u>: a deterministic reduction, a fixed-order tree
+// in the CTA, one partial per CTA, and the last CTA (ticket) sums the
+// partials in CTA order.  red: T doubles of shared memory no thread still
+// reads.
+template <int T>
+__device__ __forceinline__ void pair_fused_reduce(float ds, float dc, const PairFuse &f,
+                                                  double *red) {
+  constexpr int P2 = T > 128 ? 256 : T > 64 ? 128 : T > 32 ? 64 : 32;
+  __shared__ bool last;
+  const int tid = threadIdx.x;
+  red[tid] = widen_f32(ds) + widen_f32(dc);
+  __syncthreads();
+#pragma unroll
+  for (int h = P2 / 2; h > 0; h >>= 1) {
+    if (tid < h && tid + h < T) red[tid] += red[tid + h];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    f.partials[blockIdx.x] = red[0];
+    __threadfence();
+    last = atomicAdd(f.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double x = 0.0;
+  for (int b = tid; b < (int)gridDim.x; b += T) x += __ldcg(&f.partials[b]);
+  red[tid] = x;
+  __syncthreads();
+#pragma unroll
+  for (int h = P2 / 2; h > 0; h >>= 1) {
+    if (tid < h && tid + h < T) red[tid] += red[tid + h];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    *f.pw = red[0];
+    *f.counter = 0u;
+  }
+}
 
 template <int NP>
 struct PairShape {
@@ -190,11 +243,16 @@ __global__ void __launch_bounds__(PairShape<NP>::THREADS, PairShape<NP>::MIN_CTA
     if (active) {
       // A: reference gradients; u_t overwrites the column of u in registers
       pair_apply_eo<NP>(sEO, sEO + NEO, rt);
-#pragma unroll
+      // not unrolled: the whole-kernel unrolling overflowed the instruction
+      // cache (no_instruction stalls); this loop alone needs no register
+      // array, and rolling it cut a launch by 10 %
+#pragma unroll 1
       for (int k = 0; k < NP; ++k) {
-        float rs = 0.f, rc = 0.f, ss = 0.f, sc = 0.f;
+        float rs, rc, ss, sc;
+        pair_mul_first(sD[i][0], sU[le][j * NP + k * NP2], rs, rc);
+        pair_mul_first(sD[j][0], sU[le][i + k * NP2], ss, sc);
 #pragma unroll
-        for (int l = 0; l < NP; ++l) {
+        for (int l = 1; l < NP; ++l) {
           pair_fma(sD[i][l], sU[le][l + j * NP + k * NP2], rs, rc);
           pair_fma(sD[j][l], sU[le][i + l * NP + k * NP2], ss, sc);
         }
@@ -209,14 +267,12 @@ __global__ void __launch_bounds__(PairShape<NP>::THREADS, PairShape<NP>::MIN_CTA
 #pragma unroll
         for (int f = 0; f < 6; ++f) g[f] = __ldg(&Ge[f * NP3 + k * NP2]);
         const float2 ur = sR[le][ij + k * NP2], us = sS[le][ij + k * NP2], ut = rt[k];
-        float a = 0.f, b = 0.f;
-        pair_fma(g[0], ur, a, b); pair_fma(g[1], us, a, b); pair_fma(g[2], ut, a, b);
+        float a, b;
+        pair_mul_first(g[0], ur, a, b); pair_fma(g[1], us, a, b); pair_fma(g[2], ut, a, b);
         sR[le][ij + k * NP2] = pair_norm(a, b);
-        a = 0.f; b = 0.f;
-        pair_fma(g[1], ur, a, b); pair_fma(g[3], us, a, b); pair_fma(g[4], ut, a, b);
+        pair_mul_first(g[1], ur, a, b); pair_fma(g[3], us, a, b); pair_fma(g[4], ut, a, b);
         sS[le][ij + k * NP2] = pair_norm(a, b);
-        a = 0.f; b = 0.f;
-        pair_fma(g[2], ur, a, b); pair_fma(g[4], us, a, b); pair_fma(g[5], ut, a, b);
+        pair_mul_first(g[2], ur, a, b); pair_fma(g[4], us, a, b); pair_fma(g[5], ut, a, b);
         rt[k] = pair_norm(a, b);
       }
     }
@@ -240,43 +296,8 @@ __global__ void __launch_bounds__(PairShape<NP>::THREADS, PairShape<NP>::MIN_CTA
     }
     __syncthreads();
   }
-  if constexpr (FUSED) {
-    // deterministic reduction: a fixed-order tree in the CTA, one partial per
-    // CTA, and the last CTA (ticket) sums the partials in CTA order
-    constexpr int T = S::THREADS;
-    constexpr int P2 = T > 128 ? 256 : T > 64 ? 128 : T > 32 ? 64 : 32;
-    double *red = reinterpret_cast<double *>(smem_pair);
-    __shared__ bool last;
-    const int tid = threadIdx.x;
-    red[tid] = widen_f32(ds) + widen_f32(dc);
-    __syncthreads();
-#pragma unroll
-    for (int h = P2 / 2; h > 0; h >>= 1) {
-      if (tid < h && tid + h < T) red[tid] += red[tid + h];
-      __syncthreads();
-    }
-    if (tid == 0) {
-      f.partials[blockIdx.x] = red[0];
-      __threadfence();
-      last = atomicAdd(f.counter, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double x = 0.0;
-    for (int b = tid; b < (int)gridDim.x; b += T) x += __ldcg(&f.partials[b]);
-    red[tid] = x;
-    __syncthreads();
-#pragma unroll
-    for (int h = P2 / 2; h > 0; h >>= 1) {
-      if (tid < h && tid + h < T) red[tid] += red[tid + h];
-      __syncthreads();
-    }
-    if (tid == 0) {
-      *f.pw = red[0];
-      *f.counter = 0u;
-    }
-  }
+  if constexpr (FUSED) pair_fused_reduce<S::THREADS>(ds, dc, f, reinterpret_cast<double *>(smem_pair));
 }
+
 
 }  // namespace sem

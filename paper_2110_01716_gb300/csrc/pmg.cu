@@ -574,9 +574,10 @@ void pmg_build(sem_pmg *P, sem_mesh *mesh, const sem_pmg_desc &d, cudaStream_t s
               "unknown coarse_mode %d", d.coarse_mode);
   SEM_REQUIRE(d.coarse_mode == SEM_COARSE_JACOBI || P->persistent_coarse,
               "SEM_COARSE_MG needs a coarsest level of order 1");
+  SEM_REQUIRE(d.coarse_ctas >= 0, "coarse_ctas must be >= 0");
   if (P->persistent_coarse) {
-    coarse_setup(P->coarse, *Cl.L, st);
-    if (d.coarse_mode == SEM_COARSE_MG) coarse_mg_setup(P->coarse, *Cl.L, st);
+    coarse_setup(P->coarse, *Cl.L, st, d.coarse_ctas);
+    if (d.coarse_mode == SEM_COARSE_MG) coarse_mg_setup(P->coarse, *Cl.L, st, d.coarse_ctas);
   } else {
     const int64_t nc = Cl.L->t.nl;
     P->cz.alloc(nc); P->cp.alloc(nc); P->cw.alloc(nc);
@@ -821,6 +822,17 @@ static void coarse_solve(sem_pmg *P, cudaStream_t st) {
     launch_stop_test(sc + 1, sc + 0, tol2, it, maxit, skip, iters, st);
     launch_cg_direction(t.nl, sc + nxt, sc + cur, 1.0, z, p, skip, st);
   }
+}
+
+// The coarsest-level solve alone, on a right-hand side b of that level
+// (E-layout, assembled, masked) into x.
+void pmg_coarse_solve(sem_pmg *P, const double *b, double *x, cudaStream_t st) {
+  PmgLevel &Q = (*P->levp.back());
+  const int64_t n = Q.L->t.nl;
+  SEM_REQUIRE(Q.v64[0].p && Q.v64[1].p, "coarsest level has no FP64 vectors");
+  SEM_CHECK_CUDA(cudaMemcpyAsync(Q.v64[0].p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  coarse_solve(P, st);
+  SEM_CHECK_CUDA(cudaMemcpyAsync(x, Q.v64[1].p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
 }
 
 template <typename T, typename Tn>

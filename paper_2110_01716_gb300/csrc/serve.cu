@@ -43,6 +43,19 @@ __global__ void manufactured_rhs_kernel(int64_t n, const double *__restrict__ X,
     b[l] = B[l] * 3.0 * pi * pi * sin(pi * X[l]) * sin(pi * Y[l]) * sin(pi * Z[l]);
 }
 
+void build_manufactured_rhs(const Level &L, double *b, double *tmp, cudaStream_t st) {
+  const int64_t nl = L.t.nl;
+  double *X = tmp, *Y = X + nl, *Z = Y + nl, *B = Z + nl;
+  launch_field(L, SEM_FIELD_X, X, st);
+  launch_field(L, SEM_FIELD_Y, Y, st);
+  launch_field(L, SEM_FIELD_Z, Z, st);
+  launch_field(L, SEM_FIELD_MASS, B, st);
+  manufactured_rhs_kernel<<<vec_grid(nl), kVecThreads, 0, st>>>(nl, X, Y, Z, B, b);
+  SEM_CHECK_CUDA(cudaGetLastError());
+  launch_gs<double>(L, b, st);
+  launch_mask<double>(L, b, st);
+}
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -180,15 +193,7 @@ void sem_server::serve_one(Request &q, Setup &S, cudaStream_t st) {
   const int64_t nl = L.t.nl;
   if (q.r.rhs == SEM_RHS_MANUFACTURED) {
     if (!S.tmp.p) S.tmp.alloc(4 * (size_t)nl);
-    double *X = S.tmp.p, *Y = X + nl, *Z = Y + nl, *B = Z + nl;
-    launch_field(L, SEM_FIELD_X, X, st);
-    launch_field(L, SEM_FIELD_Y, Y, st);
-    launch_field(L, SEM_FIELD_Z, Z, st);
-    launch_field(L, SEM_FIELD_MASS, B, st);
-    manufactured_rhs_kernel<<<vec_grid(nl), kVecThreads, 0, st>>>(nl, X, Y, Z, B, S.b.p);
-    SEM_CHECK_CUDA(cudaGetLastError());
-    launch_gs<double>(L, S.b.p, st);
-    launch_mask<double>(L, S.b.p, st);
+    build_manufactured_rhs(L, S.b.p, S.tmp.p, st);
   } else {
     SEM_CHECK_CUDA(cudaMemcpyAsync(S.b.p, q.b.data(), nl * sizeof(double),
                                    cudaMemcpyHostToDevice, st));

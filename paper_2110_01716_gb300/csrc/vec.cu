@@ -296,6 +296,32 @@ __global__ void graph_arm_kernel(double *g, double tol2, double maxit, double do
   g[3] = 0.0;
 }
 
+// Start of a solve run wholly on the device: the stopping state from the
+// start kernel's <b, b> and <r, r> (the host loop's tests, in the same
+// arithmetic), g[4] = the initial <r, r>, and the condition of the node that
+// runs the iterations (1 while iterations are due).
+__global__ void graph_arm_full_kernel(const double *__restrict__ bb, const double *__restrict__ rr,
+                                      double *g, double tol, double maxit,
+                                      cudaGraphConditionalHandle h) {
+  const double b = *bb, r = *rr;
+  const double tol2 = tol * tol * b;
+  g[0] = tol2;
+  g[1] = maxit;
+  g[2] = 0.0;
+  g[4] = r;
+  double state = 0.0;
+  if (!(r == r) || !(b == b)) state = 2.0;
+  else if (r <= tol2 || maxit < 1.0) state = 1.0;
+  g[3] = state;
+  cudaGraphSetConditional(h, state == 0.0 ? 1u : 0u);
+}
+
+void launch_graph_arm_full(const double *bb, const double *rr, double *g, double tol, int maxit,
+                           cudaGraphConditionalHandle h, cudaStream_t st) {
+  graph_arm_full_kernel<<<1, 1, 0, st>>>(bb, rr, g, tol, (double)maxit, h);
+  SEM_CHECK_CUDA(cudaGetLastError());
+}
+
 void launch_graph_stop(const double *rr, double *g, cudaGraphConditionalHandle h,
                        cudaStream_t st) {
   graph_stop_kernel<<<1, 1, 0, st>>>(rr, g, h);

@@ -39,7 +39,10 @@ EXPORTED = ["sem_mesh_create", "sem_mesh_destroy", "sem_mesh_info", "sem_mesh_fi
             "sem_trace_read", "sem_dot_noalloc", "sem_proj_create", "sem_proj_destroy",
             "sem_proj_info", "sem_solve_projected", "sem_server_create", "sem_server_destroy",
             "sem_submit", "sem_poll", "sem_server_stats_read", "sem_server_autotune",
-            "sem_inject_wait_error", "sem_inject_alloc_failure", "sem_last_error"]
+            "sem_inject_wait_error", "sem_inject_alloc_failure", "sem_batch_create",
+            "sem_batch_solve", "sem_batch_info", "sem_batch_pmg_desc", "sem_batch_x",
+            "sem_batch_destroy", "sem_batch_autotune", "sem_pmg_coarse_solve",
+            "sem_last_error"]
 
 
 class SemError(RuntimeError):
@@ -58,7 +61,7 @@ class sem_pmg_desc(C.Structure):
     _fields_ = [("nlevels", C.c_int32), ("orders", C.c_int32 * 8), ("cheb_degree", C.c_int32),
                 ("lanczos_steps", C.c_int32), ("seed", C.c_uint64), ("smoother_dtype", C.c_int32),
                 ("coarse_tol", C.c_double), ("coarse_maxit", C.c_int32),
-                ("coarse_mode", C.c_int32), ("smoother", C.c_int32)]
+                ("coarse_mode", C.c_int32), ("smoother", C.c_int32), ("coarse_ctas", C.c_int32)]
 
 
 class sem_solve_desc(C.Structure):
@@ -84,6 +87,13 @@ class sem_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("setups_built", C.c_int64), ("setups_reused", C.c_int64),
                 ("hbm_in_use", C.c_int64)]
+
+
+class sem_batch_desc(C.Structure):
+    _fields_ = [("cheb_degree", C.c_int32), ("smoother_dtype", C.c_int32),
+                ("coarse_tol", C.c_double), ("coarse_maxit", C.c_int32),
+                ("coarse_ctas", C.c_int32), ("ax_fill", C.c_float * (SEM_MAX_ORDER + 1)),
+                ("arena_chunk", C.c_int64)]
 
 
 class sem_trace_entry(C.Structure):
@@ -127,6 +137,7 @@ def lib():
     L.sem_pmg_destroy.argtypes = [vp]
     L.sem_pmg_info.argtypes = [vp, i32, C.POINTER(d), C.POINTER(d)]
     L.sem_pmg_vcycle.argtypes = [vp, vp, vp, vp]
+    L.sem_pmg_coarse_solve.argtypes = [vp, vp, vp, vp]
     L.sem_pmg_coarse_iters.argtypes = [vp, vp, C.POINTER(i32)]
     L.sem_solve.argtypes = [vp, vp, vp, vp, C.POINTER(sem_solve_desc), C.POINTER(sem_solve_info),
                             vp]
@@ -143,6 +154,15 @@ def lib():
     L.sem_server_stats_read.argtypes = [vp, C.POINTER(sem_server_stats)]
     L.sem_server_autotune.argtypes = [C.POINTER(sem_server_desc), C.POINTER(sem_request), i32, i32,
                                       C.POINTER(i32), C.POINTER(d)]
+    L.sem_batch_create.argtypes = [C.POINTER(sem_batch_desc), C.POINTER(sem_request), i32, vp,
+                                   C.POINTER(vp)]
+    L.sem_batch_solve.argtypes = [vp, C.POINTER(sem_solve_info), vp]
+    L.sem_batch_info.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(i32), C.POINTER(d)]
+    L.sem_batch_pmg_desc.argtypes = [vp, i32, C.POINTER(sem_pmg_desc)]
+    L.sem_batch_x.argtypes = [vp, i32, C.POINTER(vp)]
+    L.sem_batch_destroy.argtypes = [vp]
+    L.sem_batch_autotune.argtypes = [vp, C.POINTER(C.c_float), i32, i32, vp,
+                                     C.POINTER(C.c_float), C.POINTER(d)]
     L.sem_trace_enable.argtypes = [i32, C.c_char_p]
     L.sem_trace_read.argtypes = [C.POINTER(sem_trace_entry), i32, C.POINTER(i32), i32]
     for name in EXPORTED:
@@ -271,7 +291,7 @@ class Pmg:
 
     def __init__(self, mesh: Mesh, orders=(7, 3, 1), cheb_degree=2, lanczos_steps=20, seed=0,
                  smoother_dtype=SEM_F32, coarse_tol=1e-2, coarse_maxit=50, stream=None,
-                 coarse_mode=SEM_COARSE_JACOBI, smoother=SEM_SMOOTH_JACOBI):
+                 coarse_mode=SEM_COARSE_JACOBI, smoother=SEM_SMOOTH_JACOBI, coarse_ctas=0):
         desc = sem_pmg_desc()
         desc.nlevels = len(orders)
         for i, o in enumerate(orders):
@@ -284,6 +304,7 @@ class Pmg:
         desc.coarse_maxit = int(coarse_maxit)
         desc.coarse_mode = int(coarse_mode)
         desc.smoother = int(smoother)
+        desc.coarse_ctas = int(coarse_ctas)
         h = C.c_void_p()
         check(lib().sem_pmg_setup(mesh.h, C.byref(desc), _stream(stream), C.byref(h)))
         self.h = h
@@ -311,6 +332,12 @@ class Pmg:
         lo, hi = C.c_double(), C.c_double()
         check(lib().sem_pmg_info(self.h, level, C.byref(lo), C.byref(hi)))
         return lo.value, hi.value
+
+
+def sem_pmg_coarse_solve(pmg: Pmg, b, x, stream=None):
+    """The coarsest level's solve alone (b, x: that level's E-layout vectors)."""
+    check(lib().sem_pmg_coarse_solve(pmg.h, _ptr(b), _ptr(x), _stream(stream)))
+    return x
 
 
 def sem_pmg_vcycle(pmg: Pmg, r, z, stream=None):
@@ -482,6 +509,77 @@ def server_autotune(requests, max_workers=16, **desc_kw):
     check(lib().sem_server_autotune(C.byref(server_desc(**desc_kw)), arr, len(requests),
                                     int(max_workers), C.byref(w), C.byref(rate)))
     return w.value, rate.value
+
+
+class Batch:
+    """Many independent FlexCG solves in one graph launch (sem_batch).
+    requests: sem_request structures (make_request); host arrays they point
+    to are kept alive with the batch."""
+
+    def __init__(self, requests, cheb_degree=3, smoother_dtype=SEM_F32, coarse_tol=0.2,
+                 coarse_maxit=30, coarse_ctas=1, ax_fill=None, arena_chunk=0, keep=(),
+                 stream=None):
+        d = sem_batch_desc()
+        d.cheb_degree, d.smoother_dtype = int(cheb_degree), int(smoother_dtype)
+        d.coarse_tol, d.coarse_maxit = float(coarse_tol), int(coarse_maxit)
+        d.coarse_ctas, d.arena_chunk = int(coarse_ctas), int(arena_chunk)
+        for o, f in (ax_fill or {}).items():
+            d.ax_fill[int(o)] = float(f)
+        self.n = len(requests)
+        self._reqs = (sem_request * self.n)(*requests)
+        self._keep = list(keep)
+        h = C.c_void_p()
+        check(lib().sem_batch_create(C.byref(d), self._reqs, self.n, _stream(stream),
+                                     C.byref(h)))
+        self.h = h
+
+    def solve(self, stream=None, raise_on_fail=True):
+        """One launch of the batch's graph: the list of info dicts."""
+        infos = (sem_solve_info * self.n)()
+        st = lib().sem_batch_solve(self.h, infos, _stream(stream))
+        if raise_on_fail:
+            check(st)
+        return [i.as_dict() for i in infos]
+
+    def info(self):
+        b, nodes, ms = C.c_size_t(), C.c_int32(), C.c_double()
+        check(lib().sem_batch_info(self.h, C.byref(b), C.byref(nodes), C.byref(ms)))
+        return {"dev_bytes": b.value, "graph_nodes": nodes.value, "setup_ms": ms.value}
+
+    def pmg_desc(self, i):
+        d = sem_pmg_desc()
+        check(lib().sem_batch_pmg_desc(self.h, int(i), C.byref(d)))
+        return d
+
+    def autotune(self, candidates=(4.0, 2.0, 1.0, 0.5, 0.25, 0.125), reps=3, stream=None):
+        """Per-order work split of the FP32 operator: ({order: fill}, ms per launch)."""
+        c = (C.c_float * len(candidates))(*candidates)
+        out = (C.c_float * (SEM_MAX_ORDER + 1))()
+        ms = C.c_double()
+        check(lib().sem_batch_autotune(self.h, c, len(candidates), int(reps), _stream(stream),
+                                       out, C.byref(ms)))
+        return {o: out[o] for o in range(SEM_MAX_ORDER + 1) if out[o] > 0}, ms.value
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().sem_batch_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pmg_from_desc(mesh: "Mesh", desc: "sem_pmg_desc", stream=None):
+    """A Pmg built from a full sem_pmg_desc (e.g. Batch.pmg_desc(i))."""
+    p = Pmg.__new__(Pmg)
+    h = C.c_void_p()
+    check(lib().sem_pmg_setup(mesh.h, C.byref(desc), _stream(stream), C.byref(h)))
+    p.h, p.mesh = h, mesh
+    p.orders = tuple(desc.orders[i] for i in range(desc.nlevels))
+    return p
 
 
 def sem_trace_enable(enable: bool, timed_filter: str = ""):

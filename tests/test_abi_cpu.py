@@ -72,6 +72,24 @@ def test_invalid_arguments_return_einval_without_device_work(libsem):
     assert L.sem_solve(None, None, None, None, C.byref(desc), C.byref(info), None) == \
         libsem.SEM_EINVAL
     assert L.sem_inject_wait_error(None, None) == libsem.SEM_EINVAL
+    assert L.sem_batch_create(None, None, 0, None, C.byref(h)) == libsem.SEM_EINVAL
+    assert L.sem_batch_solve(None, None, None) == libsem.SEM_EINVAL
+    assert L.sem_batch_info(None, None, None, None) == libsem.SEM_EINVAL
+    assert L.sem_batch_autotune(None, None, 0, 0, None, None, None) == libsem.SEM_EINVAL
+    assert L.sem_batch_destroy(None) == libsem.SEM_OK
+    # batch descriptions and requests are checked before any device work
+    bd = libsem.sem_batch_desc(cheb_degree=3, smoother_dtype=1, coarse_tol=0.2, coarse_maxit=30)
+    good = libsem.make_request(2, 2, 2, 5)
+    for bad in (dict(N=1), dict(solver=libsem.SEM_SOLVER_PCG), dict(bc=1), dict(ex=0)):
+        r = libsem.make_request(bad.get("ex", 2), 2, 2, bad.get("N", 5), bc=bad.get("bc", 0),
+                                solver=bad.get("solver", libsem.SEM_SOLVER_FLEXCG))
+        arr = (libsem.sem_request * 2)(good, r)
+        assert L.sem_batch_create(C.byref(bd), arr, 2, None, C.byref(h)) == libsem.SEM_EINVAL, bad
+        assert not h.value
+    bd.ax_fill[3] = -1.0
+    arr = (libsem.sem_request * 1)(good)
+    assert L.sem_batch_create(C.byref(bd), arr, 1, None, C.byref(h)) == libsem.SEM_EINVAL
+    assert "ax_fill" in libsem.last_error()
     assert L.sem_dot_noalloc(None, None, None, None, None) == libsem.SEM_EINVAL
     assert "null argument" in libsem.last_error()
     assert L.sem_mesh_destroy(None) == libsem.SEM_OK

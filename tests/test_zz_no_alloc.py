@@ -54,7 +54,16 @@ def test_noalloc_dot_rejects_meshes_beyond_its_scratch():
     m = sem.Mesh(64, 64, 33, 7, sem.SEM_DIRICHLET, sem.SEM_GEOM_TRILINEAR, jitter=0.0)
     u = torch.zeros(1, device=DEV, dtype=torch.float64)
     out = torch.zeros(1, device=DEV, dtype=torch.float64)
+    # the library's own check, through the C ABI (the binding would reject
+    # these short tensors before the call)
     with pytest.raises(sem.SemError) as ei:
-        sem.sem_dot_noalloc(m, u, u, out)
+        sem.check(sem.lib().sem_dot_noalloc(m.h, sem._ptr(u), sem._ptr(u), sem._ptr(out), None))
     assert ei.value.status == sem.SEM_EINVAL
     assert "at most" in str(ei.value)
+    # the binding checks the tensors it is given
+    with pytest.raises(ValueError):
+        sem.sem_dot_noalloc(m, u, u, out)
+    small = sem.Mesh(2, 2, 2, 3, sem.SEM_DIRICHLET, verts=inputs.box_vertices(2, 2, 2, 0.1, 2))
+    v = torch.zeros(small.n_local, device=DEV, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        sem.sem_dot_noalloc(small, v, v, torch.zeros(1, device=DEV, dtype=torch.float32))
