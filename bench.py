@@ -68,8 +68,8 @@ PAIR_PEAK_TFLOPS = 152 * 128 * 2.07e9 / PAIR_INSTR_PER_FMA * 2 / 1e12
 # DRAM traffic of one fine-level FP64 operator launch per local point (the
 # form with the inner product folded in, as in the solve), from an ncu capture
 # of that kernel on a 24^3 case, valid while the kernel source is unchanged.
-AX_TRAFFIC = {"source_sha256": "6be51339915d304430207d3ee5a7908f9bc6ecc41030ae6dba61825fd4488a18",
-              "bytes_per_point": 63.18}
+AX_TRAFFIC = {"source_sha256": "6f621cf46126f8793624c899942980d172260cf55e99fe23ad4980ebe0ee489a",
+              "bytes_per_point": 63.19}
 # The same for the smoother's assembled FP32 operator, per factor storage
 # (ncu capture on a 32^3 case), valid while ax32.cu is unchanged.
 AX32_TRAFFIC = {"f32": {"source_sha256": "a1c86ef6bae402e521ec9400dc4df4087b40792cad358632c0c31adec941b4d2",
@@ -645,7 +645,7 @@ def batch_leg(sem, torch, inputs, dev, count=64, reps=5):
         e1.record(stream)
         e1.synchronize()
         default_ms.append(e0.elapsed_time(e1))
-    chosen, tuned_ms = B.autotune(candidates=(2.0, 1.0, 0.5, 0.25, 0.125, 0.0625), reps=3)
+    chosen, tuned_ms = B.autotune(candidates=(1.0, 0.5, 0.25), reps=3)
     ms = []
     for _ in range(reps):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -670,52 +670,94 @@ def batch_leg(sem, torch, inputs, dev, count=64, reps=5):
             "speedup_vs_fp64_sequential": round(t64 / tb, 2),
             "speedup_vs_fp32_sequential": round(t32 / tb, 2),
             "autotuned_ax_fill_by_order": {str(k): v for k, v in sorted(chosen.items())},
+            "autotune_note": "orders absent keep the default split (2 units per CTA slot)",
             "graph_nodes": info["graph_nodes"], "setup_s": round(setup_s, 2),
             "arena_GB": round(info["dev_bytes"] / 1e9, 2),
             "iters_mean": round(sum(f["iters"] for f in infos) / count, 2),
             "same_iters_as_sequential_fp32": [f["iters"] for f in infos] == its32}
 
 
-def serve_leg(sem, inputs, workers=None, count=200, load=0.8, graph=False):
-    """Config 5: Poisson arrivals at `load` times the measured capacity (the
-    first 32 requests run back to back with the same workers), E log-uniform
-    in [512, 65536], N = 7, tolerance in {1e-6, 1e-8, 1e-10}.  Latency is
-    submit -> completion; the stream is cut to `count` requests (1000 in the
-    full recipe) to keep the bench within minutes."""
+def _serve_stream(sem, S, stream, shapes=None):
+    """Submit the arrival stream (each request at its time) and wait for all;
+    returns (latencies sorted, span seconds).  shapes: replace each request's
+    mesh by shapes[i] (a finite population of meshes)."""
+    tickets = []
+    t0 = time.perf_counter()
+    for i, r in enumerate(stream):
+        now = time.perf_counter() - t0
+        if r["t"] > now:
+            time.sleep(r["t"] - now)
+        m = shapes[i] if shapes is not None else r
+        tickets.append(S.submit(m["ex"], m["ey"], m["ez"], m["N"], sem.SEM_DIRICHLET, 0.1,
+                                m["seed"], tol=r["tol"]))
+    infos = [S.wait(t) for t in tickets]
+    span = time.perf_counter() - t0
+    if any(f["status"] != sem.SEM_OK for f in infos):
+        raise SystemExit("serve leg: a request failed")
+    return sorted(f["time_ms"] for f in infos), span
+
+
+def _capacity(sem, S, reqs):
+    t0 = time.perf_counter()
+    tk = [S.submit(r["ex"], r["ey"], r["ez"], r["N"], sem.SEM_DIRICHLET, 0.1, r["seed"],
+                   tol=r["tol"]) for r in reqs]
+    for t in tk:
+        S.wait(t)
+    return len(reqs) / (time.perf_counter() - t0)
+
+
+def _pct(lat):
+    return {"p50": round(lat[len(lat) // 2], 2),
+            "p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 2)}
+
+
+def serve_leg(sem, inputs, workers=None, count=1000, load=0.8, population=12):
+    """Config 5: Poisson arrivals at `load` times the measured capacity, E
+    log-uniform in [512, 65536], N = 7, tolerance in {1e-6, 1e-8, 1e-10};
+    latency = submit -> completion.  (a) Every request brings its own mesh:
+    setup included, no cache.  (b) The same arrivals and tolerances on a
+    population of `population` meshes drawn from the same distribution, whose
+    setups the server has cached before the stream starts (pre-warmed: every
+    request reuses a resident mesh, hierarchy and workspace).  The capacity
+    of each case is measured first on 32 requests with the same workers."""
     probe = inputs.arrival_stream(5, 32, 1.0)
     if workers is None:
         sample = [sem.make_request(r["ex"], r["ey"], r["ez"], r["N"], sem.SEM_DIRICHLET, 0.1,
                                    r["seed"], tol=r["tol"]) for r in probe[:16]]
         workers, _ = sem.server_autotune(sample, max_workers=8, cache_per_shape=0)
+    out = {"requests": count, "workers": workers,
+           "workload": "config 5: Poisson arrivals, E log-uniform [512, 65536], N=7, "
+                       "tol in {1e-6,1e-8,1e-10}"}
+    # (a) setup included
     S = sem.Server(workers=workers, cache_per_shape=0)
-    t0 = time.perf_counter()
-    tk = [S.submit(r["ex"], r["ey"], r["ez"], r["N"], sem.SEM_DIRICHLET, 0.1, r["seed"],
-                   tol=r["tol"], use_graph=graph) for r in probe]
-    for t in tk:
-        S.wait(t)
-    capacity = len(probe) / (time.perf_counter() - t0)
-    stream = inputs.arrival_stream(5, count, load * capacity)
-    lat, tickets = [], []
-    t0 = time.perf_counter()
-    for r in stream:
-        now = time.perf_counter() - t0
-        if r["t"] > now:
-            time.sleep(r["t"] - now)
-        tickets.append(S.submit(r["ex"], r["ey"], r["ez"], r["N"], sem.SEM_DIRICHLET, 0.1,
-                                r["seed"], tol=r["tol"], use_graph=graph))
-    infos = [S.wait(t) for t in tickets]
-    span = time.perf_counter() - t0
+    cap = _capacity(sem, S, probe)
+    lat, span = _serve_stream(sem, S, inputs.arrival_stream(5, count, load * cap))
+    st = S.stats()
     S.close()
-    lat = sorted(f["time_ms"] for f in infos)
-    if any(f["status"] != sem.SEM_OK for f in infos):
-        raise SystemExit("serve leg: a request failed")
-    return {"requests": count, "workers": workers, "use_graph": graph,
-            "capacity_solves_per_s": round(capacity, 2),
-            "offered_rate": round(load * capacity, 2), "achieved_solves_per_s": round(count / span, 2),
-            "latency_ms": {"p50": round(lat[len(lat) // 2], 2),
-                           "p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 2)},
-            "workload": "config 5 (cut to %d requests): Poisson arrivals, E log-uniform "
-                        "[512, 65536], N=7, tol in {1e-6,1e-8,1e-10}, setup included" % count}
+    out["setup_included"] = {"capacity_solves_per_s": round(cap, 2),
+                             "offered_rate": round(load * cap, 2),
+                             "achieved_solves_per_s": round(count / span, 2),
+                             "latency_ms": _pct(lat), "setups_built": st["setups_built"]}
+    # (b) pre-warmed cache over a finite mesh population
+    shapes = inputs.arrival_stream(55, population, 1.0)
+    rng = __import__("random").Random(56)
+    S = sem.Server(workers=workers, cache_per_shape=1)
+    for m in shapes:  # pre-warm: build and cache every mesh of the population
+        S.wait(S.submit(m["ex"], m["ey"], m["ez"], m["N"], sem.SEM_DIRICHLET, 0.1, m["seed"],
+                        tol=1e-6))
+    pick = [shapes[rng.randrange(population)] for _ in range(count)]
+    cap = _capacity(sem, S, [dict(pick[i], tol=probe[i]["tol"]) for i in range(len(probe))])
+    lat, span = _serve_stream(sem, S, inputs.arrival_stream(5, count, load * cap), shapes=pick)
+    st = S.stats()
+    S.close()
+    out["prewarmed"] = {"population": population, "capacity_solves_per_s": round(cap, 2),
+                        "offered_rate": round(load * cap, 2),
+                        "achieved_solves_per_s": round(count / span, 2),
+                        "latency_ms": _pct(lat), "setups_built": st["setups_built"],
+                        "setups_reused": st["setups_reused"],
+                        "hbm_in_use_GB": round(st["hbm_in_use"] / 1e9, 2)}
+    out["latency_ms"] = out["setup_included"]["latency_ms"]
+    return out
 
 
 def oracle_sample_solve(side=12):
@@ -821,8 +863,9 @@ def summary_of(line):
         out["err_vs_oracle"] = {sm: pe[sm]["rel_err_vs_oracle_1e-12"]
                                 for sm in ("f64", "f32", "f16", "bf16") if sm in pe}
     if "serve" in line:
-        out["serve_p50_p99_ms"] = [line["serve"]["latency_ms"]["p50"],
-                                   line["serve"]["latency_ms"]["p99"]]
+        sv = line["serve"]
+        out["serve_p50_p99_ms"] = {k: [sv[k]["latency_ms"]["p50"], sv[k]["latency_ms"]["p99"]]
+                                   for k in ("setup_included", "prewarmed") if k in sv}
     if "batch" in line:
         out["batch_solves_per_s"] = line["batch"].get("solves_per_s")
     if "config1" in line:

@@ -338,9 +338,13 @@ sem_status sem_solve_projected(sem_mesh *mesh, sem_pmg *pmg, sem_proj *proj, con
  * The paper has no counterpart (it runs one large solve across partitions);
  * this is a service of the library for streams of small and mid-sized
  * problems.  A server owns `workers` host threads, each with its own CUDA
- * stream.  A worker takes the oldest queued request whose estimated device
- * memory fits in what the budget leaves (the oldest request runs anyway when
- * nothing else does), takes an idle setup of the same shape from the cache or
+ * stream.  A worker takes the oldest queued request whose device memory fits
+ * in what the budget leaves (the oldest request runs anyway when nothing else
+ * does); a request's memory is the measured bytes of its shape's earlier
+ * setup, else the largest bytes per local point measured for its order times
+ * its points (+5 %), else, before any setup of its order, 200 bytes per local
+ * point + 64 MiB, and a new setup's reservation is replaced by its measured
+ * bytes after its first solve; takes an idle setup of the same shape from the cache or
  * builds the mesh and pMG hierarchy (orders N, ceil(N/2), 1), solves, copies x
  * back, and records the result; its next request starts as soon as it is done
  * (continuous batching).  Solves of different workers overlap on the GPU.
@@ -376,7 +380,8 @@ typedef struct {
 typedef struct {
   int64_t submitted, completed, failed;
   int64_t setups_built, setups_reused;
-  int64_t hbm_in_use;   /* estimated device bytes of running and cached setups */
+  int64_t hbm_in_use;   /* device bytes of running and cached setups (measured
+                           once a setup has solved) */
 } sem_server_stats;
 
 sem_status sem_server_create(const sem_server_desc *desc, sem_server **out);
@@ -450,13 +455,14 @@ sem_status sem_batch_pmg_desc(const sem_batch *batch, int32_t i, sem_pmg_desc *o
 /* Device address of problem i's solution (owned by the batch). */
 sem_status sem_batch_x(const sem_batch *batch, int32_t i, const double **x_dev);
 sem_status sem_batch_destroy(sem_batch *batch);
-/* Autotuner of the batch's work split: for every fine order present, the
- * graph of that order's problems alone is captured with each candidate
- * ax_fill (for the levels of that order) and timed (median of reps
- * launches, CUDA events); the fastest is kept.  The batch's graph is then
- * captured again with the chosen values, written to chosen[0..SEM_MAX_ORDER]
- * (HOST), and *best_ms is the median time of one launch of the whole batch.
- * Synchronises. */
+/* Autotuner of the batch's work split, by coordinate descent on the whole
+ * batch: starting from the batch's current ax_fill, for one fine order at a
+ * time every candidate value (for the levels of that order) is captured into
+ * the whole batch's graph and timed (median of reps launches, CUDA events),
+ * and the value with the fastest whole-batch time is kept (the current one
+ * unless a candidate beats it).  The batch keeps the graph of the chosen
+ * values; they are written to chosen[0..SEM_MAX_ORDER] (HOST, 0 = the
+ * default) and *best_ms is the median time of one launch.  Synchronises. */
 sem_status sem_batch_autotune(sem_batch *batch, const float *candidates, int32_t ncand,
                               int32_t reps, void *stream, float *chosen, double *best_ms);
 

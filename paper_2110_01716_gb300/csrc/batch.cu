@@ -364,49 +364,45 @@ sem_status sem_batch_autotune(sem_batch *batch, const float *candidates, int32_t
       cudaEvent_t a, b;
       ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
     } guard{e0, e1};
-    // problems grouped by fine order: their levels' orders (N, N/2) are the
-    // split's keys, and every class is timed alone
-    std::map<int, std::vector<int>> classes;
-    for (int i = 0; i < batch->n; ++i) classes[batch->reqs[i].N].push_back(i);
-    for (auto &kv : classes) {
-      const int N = kv.first;
-      const std::vector<int> ord = batch_orders(N);
-      float best_f = 0.f;
-      double best = 1e300;
+    const std::vector<int> everyone = all_of(batch->n);
+    // median time of one launch of the whole batch with the current split
+    auto time_batch = [&]() {
+      batch->capture(everyone);
+      batch->launch(everyone, nullptr, st, false);  // warm-up
+      std::vector<float> t(reps);
+      for (int32_t k = 0; k < reps; ++k) {
+        SEM_CHECK_CUDA(cudaEventRecord(e0, st));
+        SEM_CHECK_CUDA(cudaGraphLaunch(batch->exec, st));
+        SEM_CHECK_CUDA(cudaEventRecord(e1, st));
+        SEM_CHECK_CUDA(cudaEventSynchronize(e1));
+        SEM_CHECK_CUDA(cudaEventElapsedTime(&t[k], e0, e1));
+      }
+      std::sort(t.begin(), t.end());
+      return (double)t[reps / 2];
+    };
+    // problems grouped by fine order: the levels of a class (orders N, N/2)
+    // share one value.  Coordinate descent on the whole batch, the problems
+    // of every class running beside the others as in use: one class at a
+    // time tries every candidate and keeps the fastest whole-batch time.
+    std::set<int> classes;
+    for (int i = 0; i < batch->n; ++i) classes.insert(batch->reqs[i].N);
+    double best = time_batch();
+    for (int N : classes) {
+      const std::vector<int32_t> ord = batch_orders(N);
+      const float keep = batch->d.ax_fill[N];
+      float best_f = keep;
       for (int32_t c = 0; c < ncand; ++c) {
         for (int o : ord) batch->d.ax_fill[o] = candidates[c];
-        batch->capture(kv.second);
-        batch->launch(kv.second, nullptr, st, false);  // warm-up
-        std::vector<float> t(reps);
-        for (int32_t k = 0; k < reps; ++k) {
-          SEM_CHECK_CUDA(cudaEventRecord(e0, st));
-          SEM_CHECK_CUDA(cudaGraphLaunch(batch->exec, st));
-          SEM_CHECK_CUDA(cudaEventRecord(e1, st));
-          SEM_CHECK_CUDA(cudaEventSynchronize(e1));
-          SEM_CHECK_CUDA(cudaEventElapsedTime(&t[k], e0, e1));
-        }
-        std::sort(t.begin(), t.end());
-        const double med = t[reps / 2];
-        if (med < best) {
-          best = med;
+        const double t = time_batch();
+        if (t < best) {
+          best = t;
           best_f = candidates[c];
         }
       }
       for (int o : ord) batch->d.ax_fill[o] = best_f;
     }
     for (int o = 0; o <= SEM_MAX_ORDER; ++o) chosen[o] = batch->d.ax_fill[o];
-    batch->capture(all_of(batch->n));
-    batch->launch(all_of(batch->n), nullptr, st, false);  // warm-up of the final graph
-    std::vector<float> t(reps);
-    for (int32_t k = 0; k < reps; ++k) {
-      SEM_CHECK_CUDA(cudaEventRecord(e0, st));
-      SEM_CHECK_CUDA(cudaGraphLaunch(batch->exec, st));
-      SEM_CHECK_CUDA(cudaEventRecord(e1, st));
-      SEM_CHECK_CUDA(cudaEventSynchronize(e1));
-      SEM_CHECK_CUDA(cudaEventElapsedTime(&t[k], e0, e1));
-    }
-    std::sort(t.begin(), t.end());
-    *best_ms = t[reps / 2];
+    *best_ms = time_batch();
   });
 }
 

@@ -129,9 +129,12 @@ struct CtaBarrier {
 // x = d, r = b; one more step), residual, restriction to level l + 1.  Every
 // phase maps node g to the same thread, so pointwise dependencies need no
 // barrier; a barrier precedes every phase that reads neighbours or another
-// level.
+// level.  The restriction writes node G of level l + 1 from the thread that
+// starts level l + 1's smoothing at G (a pointwise step), so the barrier
+// after it is needed only when level l + 1 is run another way (by another
+// set of threads, or the dense bottom): `last_barrier`.
 template <typename Bar>
-__device__ void mg_down(const MgArgs &A, int l, Bar bar, int tid, int nth) {
+__device__ void mg_down(const MgArgs &A, int l, Bar bar, int tid, int nth, bool last_barrier) {
   const MgLevelT<float> &L = A.V[l];
   const float *b = L.b;
   float *x = L.x;
@@ -195,7 +198,7 @@ __device__ void mg_down(const MgArgs &A, int l, Bar bar, int tid, int nth) {
     }
     C.b[G] = acc;
   }
-  bar();
+  if (last_barrier) bar();
 }
 
 // The bottom: dense inverse, one row per thread.
@@ -212,6 +215,8 @@ __device__ void mg_bottom(const MgArgs &A, Bar bar, int tid, int nth) {
 
 // Up the cycle at level l: prolongation and correction from level l + 1,
 // post-smoothing (r = b - A x; d = Dinv r / theta; x += d; one more step).
+// The first step's x += d waits for the second step, whose phase reads only
+// d's neighbours: one barrier fewer, the same arithmetic.
 template <typename Bar>
 __device__ void mg_up(const MgArgs &A, int l, Bar bar, int tid, int nth) {
   const MgLevelT<float> &L = A.V[l];
@@ -258,19 +263,17 @@ __device__ void mg_up(const MgArgs &A, int l, Bar bar, int tid, int nth) {
     x[g] += acc;
   }
   bar();
-  for (int g = tid; g < L.n; g += nth) L.r[g] = b[g] - mg_apply(L, g, x);
-  bar();
   for (int g = tid; g < L.n; g += nth) {
-    const float d = L.dinv[g] * L.r[g] * L.inv_theta;
-    L.da[g] = d;
-    x[g] += d;
+    const float rg = b[g] - mg_apply(L, g, x);
+    L.r[g] = rg;
+    L.da[g] = L.dinv[g] * rg * L.inv_theta;
   }
   bar();
   for (int g = tid; g < L.n; g += nth) {
     const float rg = L.r[g] - mg_apply(L, g, L.da);
     L.r[g] = rg;
     const float d = L.c1 * L.da[g] + L.c2 * L.dinv[g] * rg;
-    x[g] += d;
+    x[g] = (x[g] + L.da[g]) + d;
   }
   bar();
 }
@@ -287,14 +290,14 @@ __device__ void mg_vcycle(const MgArgs &A, const double *__restrict__ b0, double
   const MgLevelT<float> &V0 = A.V[0];
   for (int g = tid; g < V0.n; g += nth) V0.b[g] = (float)b0[g];
   if (ls == 0) grid.sync();  // CTA 0 reads every node of level 0
-  for (int l = 0; l < ls; ++l) mg_down(A, l, gb, tid, nth);
+  for (int l = 0; l < ls; ++l) mg_down(A, l, gb, tid, nth, l + 1 >= ls);
   if (ls == A.nlev - 1 && A.nbottom > (int)blockDim.x) {
     mg_bottom(A, gb, tid, nth);  // a large bottom: rows across the grid
   } else {
     if (blockIdx.x == 0) {
       const CtaBarrier cb;
       const int t = threadIdx.x, n = blockDim.x;
-      for (int l = ls; l < A.nlev - 1; ++l) mg_down(A, l, cb, t, n);
+      for (int l = ls; l < A.nlev - 1; ++l) mg_down(A, l, cb, t, n, l + 1 == A.nlev - 1);
       mg_bottom(A, cb, t, n);
       for (int l = A.nlev - 2; l >= ls; --l) mg_up(A, l, cb, t, n);
     }

@@ -824,6 +824,27 @@ static void coarse_solve(sem_pmg *P, cudaStream_t st) {
   }
 }
 
+// Device bytes held by the hierarchy (the levels it owns, their vectors,
+// the Schwarz data, the coarse solver and the reduction buffers).
+size_t pmg_device_bytes(const sem_pmg *P) {
+  size_t b = P->red.partials.bytes() + P->red.counter.bytes() + P->scal.bytes() +
+             P->flags.bytes() + P->cz.bytes() + P->cp.bytes() + P->cw.bytes() + P->z64.bytes();
+  for (const auto &q : P->levp) {
+    if (!q) continue;
+    if (q->own) b += q->own->device_bytes();
+    for (int v = 0; v < 5; ++v) b += q->v64[v].bytes() + q->v32[v].bytes();
+    if (q->asmd) {
+      const AsmData &A = *q->asmd;
+      b += A.S64.bytes() + A.lam64.bytes() + A.S32.bytes() + A.lam32.bytes() + A.ext64.bytes() +
+           A.ext32.bytes() + A.mr64.bytes() + A.mr32.bytes();
+    }
+  }
+  const CoarseSolver &C = P->coarse;
+  b += C.S.bytes() + C.dinv.bytes() + C.vec.bytes() + C.part.bytes() + C.iters.bytes();
+  if (C.mg) b += C.mg->fbuf.bytes() + C.mg->ibuf.bytes() + C.mg->kbuf.bytes() + C.mg->part.bytes();
+  return b;
+}
+
 // The coarsest-level solve alone, on a right-hand side b of that level
 // (E-layout, assembled, masked) into x.
 void pmg_coarse_solve(sem_pmg *P, const double *b, double *x, cudaStream_t st) {

@@ -36,6 +36,8 @@ struct VcycleIO {
 VcycleIO pmg_io(sem_pmg *P);
 // One V-cycle from the input buffer to the output buffer.
 void pmg_vcycle_core(sem_pmg *P, cudaStream_t st);
+// Device bytes held by the hierarchy (not the mesh's).
+size_t pmg_device_bytes(const sem_pmg *P);
 // The coarsest-level solve alone (b, x: E-layout vectors of that level).
 void pmg_coarse_solve(sem_pmg *P, const double *b, double *x, cudaStream_t st);
 

