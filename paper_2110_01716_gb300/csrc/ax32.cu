@@ -44,6 +44,51 @@
 
 namespace sem {
 
+// Shared-memory wavefronts per 8-lane phase of the float4 row reads of the
+// unstaged kernel (rows of one plane: row j for the natural copy, row i for
+// the transposed one), averaged over a CTA, for element stride es (floats).
+constexpr double row_read_waves(int NP, int NE, int RS, int es) {
+  const int T = NE * NP * NP;
+  double tot = 0.0;
+  int phases = 0;
+  for (int pat = 0; pat < 2; ++pat)
+    for (int c = 0; c < (NP + 3) / 4; ++c)
+      for (int g0 = 0; g0 < T; g0 += 8) {
+        int addr[8] = {}, n = 0;
+        for (int t = g0; t < g0 + 8 && t < T; ++t) {
+          const int le = t / (NP * NP), ij = t % (NP * NP), i = ij % NP, j = ij / NP;
+          const int a = le * es + (pat == 0 ? j : i) * RS + 4 * c;
+          bool seen = false;
+          for (int q = 0; q < n; ++q) seen = seen || addr[q] == a;
+          if (!seen) addr[n++] = a;
+        }
+        int worst = 0;
+        for (int b = 0; b < 8; ++b) {  // 16-byte bank groups of a 128-byte row
+          int m = 0;
+          for (int q = 0; q < n; ++q) m += ((addr[q] / 4) % 8) == b;
+          worst = m > worst ? m : worst;
+        }
+        tot += worst;
+        ++phases;
+      }
+  return tot / phases;
+}
+// The element stride (floats, a whole number of float4, at least NP planes)
+// with the fewest wavefronts; the first such stride above the minimum.
+constexpr int best_element_stride(int NP, int NE, int RS) {
+  const int base = NP * NP * RS;
+  int best = base;
+  double bw = row_read_waves(NP, NE, RS, base);
+  for (int es = base + 4; es < base + 32; es += 4) {
+    const double w = row_read_waves(NP, NE, RS, es);
+    if (w < bw) {
+      bw = w;
+      best = es;
+    }
+  }
+  return best;
+}
+
 template <int NP>
 struct A32 {
   static constexpr int NP2 = NP * NP;
@@ -53,7 +98,15 @@ struct A32 {
   static constexpr int C4 = (NP + 3) / 4;                            // float4 per row
   static constexpr int RS = (C4 % 2 == 0) ? 4 * C4 + 4 : 4 * C4;     // padded row stride
   static constexpr int PL = NP * RS;                                 // padded plane stride
-  static constexpr int ES = ((NP * PL / 4) % 2 == 0) ? NP * PL + 4 : NP * PL;  // padded element
+#ifndef SEM_AX32_ES_SEARCH
+#define SEM_AX32_ES_SEARCH 1
+#endif
+  // padded element: for the unstaged orders the stride whose rows a warp
+  // reads across two neighbouring elements fall in distinct bank groups
+  // (measured at 48^3: N = 4 0.144 -> 0.139 ms, N = 2 0.040 -> 0.036 ms)
+  static constexpr int ES = (NP % 4 != 0 && SEM_AX32_ES_SEARCH)
+                                ? best_element_stride(NP, NE, RS)
+                                : (((NP * PL / 4) % 2 == 0) ? NP * PL + 4 : NP * PL);
   // Staged variant (NP a multiple of 4): natural-order arrays keep unpadded
   // rows (a warp reads at most four rows of one element, or of two elements
   // 16 banks apart); the element's u and factors arrive by bulk copy.
@@ -62,8 +115,17 @@ struct A32 {
 #ifndef SEM_AX32_MIN_CTAS
 #define SEM_AX32_MIN_CTAS 2
 #endif
-  // the unstaged small orders fit 64 registers (four CTAs, 32 warps per SM)
-  static constexpr int MIN_CTAS = !STAGED && NP <= 5 ? 4 : (NP <= 8 ? SEM_AX32_MIN_CTAS : 1);
+#ifndef SEM_AX32_GPRE
+#define SEM_AX32_GPRE 1
+#endif
+  // unstaged small orders: the element column's factors are loaded into
+  // registers with u, before the barrier, so no load waits inside the k loop
+  // (measured at 48^3: N = 4 0.139 -> 0.131 ms per launch; at N = 2 slower)
+  static constexpr bool GPRE = !STAGED && NP == 5 && SEM_AX32_GPRE;
+  // the unstaged small orders fit 64 registers (four CTAs, 32 warps per SM),
+  // 80 with the factors in registers (three CTAs)
+  static constexpr int MIN_CTAS =
+      !STAGED && NP <= 5 ? (GPRE ? 3 : 4) : (NP <= 8 ? SEM_AX32_MIN_CTAS : 1);
 };
 
 constexpr int round16(int b) { return (b + 15) & ~15; }
@@ -336,6 +398,15 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
         }
       }
     }
+    float gpre[S::GPRE ? 6 : 1][S::GPRE ? NP : 1];
+    if constexpr (S::GPRE) {
+      const GT *Gg = static_cast<const GT *>(a.G) + (active ? e : 0) * 6 * NP3 + ij;
+#pragma unroll
+      for (int f = 0; f < 6; ++f)
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+          gpre[f][k] = active ? factor_value<GK>(__ldg(Gg + f * NP3 + k * NP2)) : 0.f;
+    }
     __syncthreads();
     // ---- gradients, geometric factors, fluxes
     float wt[NP];
@@ -369,6 +440,7 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
           if constexpr (Lay::SG || Lay::SGS) g6[f] = factor_value<GK>(stG[f * NP3 + k * NP2 + ij]);
+          else if constexpr (S::GPRE) g6[f] = gpre[f][k];
           else g6[f] = factor_value<GK>(__ldg(Gg + f * NP3 + k * NP2));
         }
         wR[k * NPL + j * NRS + i] = g6[0] * ur + g6[1] * us + g6[2] * ut;
