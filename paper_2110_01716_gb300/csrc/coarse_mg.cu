@@ -748,7 +748,8 @@ void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st, int max_
   A.div_ey = FastDiv((uint32_t)Lv.t.ey);
   const size_t s0 = C.vec_stride;
   A.x = C.vec.p; A.r = A.x + s0; A.z = A.r + s0; A.p = A.z + s0; A.w = A.p + s0;
-  // grid: one CTA per SM (grid barriers dominate; see coarse.cu)
+  // grid: two CTAs per SM (more warps hide the stencil loads' latency; each
+  // grid barrier costs a little more)
   int dev = 0, sms = 0, per_sm = 0;
   SEM_CHECK_CUDA(cudaGetDevice(&dev));
   SEM_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -756,7 +757,7 @@ void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st, int max_
                                                                kMgThreads, 0));
   SEM_REQUIRE(per_sm >= 1, "multigrid coarse kernel cannot be resident");
 #ifndef SEM_MG_CTAS_PER_SM
-#define SEM_MG_CTAS_PER_SM 1
+#define SEM_MG_CTAS_PER_SM 2  // 1 / 2 / 4 measured 0.47 / 0.44 / 0.44 ms per coarse solve at 48^3
 #endif
   M->grid = std::max(1, std::min(sms * std::min(per_sm, SEM_MG_CTAS_PER_SM),
                                  (n0 + kMgThreads - 1) / kMgThreads));

@@ -175,3 +175,23 @@ def test_graph_requests_equal_host_loop_requests():
                       use_graph=True)
         finally:
             S2.close()
+
+
+def test_admission_counts_measured_setup_bytes():
+    """After a new shape's first solve the server holds that setup's measured
+    device bytes (mesh with its workspaces, hierarchy, b and x), not the
+    first estimate of 200 bytes per local point + 64 MiB; a reuse adds
+    nothing; an unseen shape of a measured order is admitted from the
+    measured bytes per point."""
+    S = sem.Server(workers=1, cache_per_shape=1)
+    ex, ey, ez, N = 3, 3, 2, 5
+    nl = ex * ey * ez * (N + 1) ** 3
+    S.wait(S.submit(ex, ey, ez, N, sem.SEM_DIRICHLET, 0.1, 7, tol=1e-8))
+    st = S.stats()
+    held = st["hbm_in_use"]
+    assert held > 0 and held != 200 * nl + (64 << 20)
+    assert held < 200 * nl + (64 << 20)  # far below the first estimate at this size
+    S.wait(S.submit(ex, ey, ez, N, sem.SEM_DIRICHLET, 0.1, 7, tol=1e-8))
+    st2 = S.stats()
+    assert st2["setups_reused"] == 1 and st2["hbm_in_use"] == held
+    S.close()
