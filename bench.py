@@ -68,8 +68,8 @@ PAIR_PEAK_TFLOPS = 152 * 128 * 2.07e9 / PAIR_INSTR_PER_FMA * 2 / 1e12
 # DRAM traffic of one fine-level FP64 operator launch per local point (the
 # form with the inner product folded in, as in the solve), from an ncu capture
 # of that kernel on a 24^3 case, valid while the kernel source is unchanged.
-AX_TRAFFIC = {"source_sha256": "6f621cf46126f8793624c899942980d172260cf55e99fe23ad4980ebe0ee489a",
-              "bytes_per_point": 63.19}
+AX_TRAFFIC = {"source_sha256": "ca840efb8d892b9000dd5912465d5da7951c30be7b8ed79d1b6c6eb565a0f7d6",
+              "bytes_per_point": 63.54}
 # The same for the smoother's assembled FP32 operator, per factor storage
 # (ncu capture on a 32^3 case), valid while ax32.cu is unchanged.
 AX32_TRAFFIC = {"f32": {"source_sha256": "a1c86ef6bae402e521ec9400dc4df4087b40792cad358632c0c31adec941b4d2",

@@ -2,7 +2,7 @@
 // ("double-float") arithmetic.
 //
 // Same operator as ax.cu (Sec. 2, footnote 1: w^e = sum_d D_d^T sum_f G_df D_f u^e),
-// same thread layout, but every value is carried as an unevaluated sum of two
+// but every value is carried as an unevaluated sum of two
 // floats (hi + lo, about 48 significant bits) and every multiply-add is
 // error-free-transformed on the FP32 pipes:
 //   product  p = fl(a_hi b_hi),  e = fma(a_hi, b_hi, -p)  (exact error, Ogita-Rump-Oishi)
@@ -31,17 +31,18 @@ static void launch_pair_np(const Level &L, const double *u, double *w, cudaStrea
   int64_t blocks = (L.t.E + S::NE - 1) / S::NE;
   const int64_t cap = 152 * 16;
   int grid = (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
+  auto kern = ax_pair_kernel<NP, false>;
   const size_t shm = sizeof(float2) * (size_t)S::SMEM_PAIRS;
   static std::atomic<bool> attr_set[64] = {};  // per function and device (host threads may race)
   int dev = 0;
   SEM_CHECK_CUDA(cudaGetDevice(&dev));
   if (dev >= 64 || !attr_set[dev]) {
-    SEM_CHECK_CUDA(cudaFuncSetAttribute(ax_pair_kernel<NP, false>,
+    SEM_CHECK_CUDA(cudaFuncSetAttribute(kern,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     if (dev < 64) attr_set[dev] = true;
   }
   TraceScope ts("ax_f64pair", L.t.N, st);
-  ax_pair_kernel<NP, false><<<grid, S::THREADS, shm, st>>>(L.t.E, L.basis, u, w, L.G2.p,
+  kern<<<grid, S::THREADS, shm, st>>>(L.t.E, L.basis, u, w, L.G2.p,
                                                                    PairFuse{});
   SEM_CHECK_CUDA(cudaGetLastError());
 }

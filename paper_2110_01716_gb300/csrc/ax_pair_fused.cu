@@ -19,17 +19,18 @@ static void launch_fused_np(const Level &L, const double *u, double *w, const Pa
   int64_t blocks = (L.t.E + S::NE - 1) / S::NE;
   const int64_t cap = 152 * 16;
   int grid = (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
+  auto kern = ax_pair_kernel<NP, true>;
   const size_t shm = sizeof(float2) * (size_t)S::SMEM_PAIRS;
   static std::atomic<bool> attr_set[64] = {};
   int dev = 0;
   SEM_CHECK_CUDA(cudaGetDevice(&dev));
   if (dev >= 64 || !attr_set[dev]) {
-    SEM_CHECK_CUDA(cudaFuncSetAttribute(ax_pair_kernel<NP, true>,
+    SEM_CHECK_CUDA(cudaFuncSetAttribute(kern,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     if (dev < 64) attr_set[dev] = true;
   }
   TraceScope ts("ax_f64pair", L.t.N, st);
-  ax_pair_kernel<NP, true><<<grid, S::THREADS, shm, st>>>(L.t.E, L.basis, u, w, L.G2.p, f);
+  kern<<<grid, S::THREADS, shm, st>>>(L.t.E, L.basis, u, w, L.G2.p, f);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
 
