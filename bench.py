@@ -72,9 +72,9 @@ AX_TRAFFIC = {"source_sha256": "ca840efb8d892b9000dd5912465d5da7951c30be7b8ed79d
               "bytes_per_point": 63.54}
 # The same for the smoother's assembled FP32 operator, per factor storage
 # (ncu capture on a 32^3 case), valid while ax32.cu is unchanged.
-AX32_TRAFFIC = {"f32": {"source_sha256": "a1c86ef6bae402e521ec9400dc4df4087b40792cad358632c0c31adec941b4d2",
-                        "bytes_per_point": 31.29},
-                "f16": {"source_sha256": "a1c86ef6bae402e521ec9400dc4df4087b40792cad358632c0c31adec941b4d2",
+AX32_TRAFFIC = {"f32": {"source_sha256": "a1ec8ef68ef769562e18901d6e5ac4fe3e14479f80e51652bf9318a9ac65cd3b",
+                        "bytes_per_point": 31.28},
+                "f16": {"source_sha256": "a1ec8ef68ef769562e18901d6e5ac4fe3e14479f80e51652bf9318a9ac65cd3b",
                         "bytes_per_point": 18.82}}
 
 

@@ -6,8 +6,13 @@
 //
 // Shared-memory traffic, not HBM, limits a straightforward column kernel in
 // FP32 (each FMA of the r and s contractions re-reads D and u from shared
-// memory).  Here each thread owns one (i, j) column of an element, loops over
-// k, and
+// memory).  At N = 7 (the fine level of the smoother) each thread owns three
+// lines of its element -- an (i, j) column, an r-line and an s-line -- and
+// contracts each whole line in registers through the even/odd halves of D,
+// so a line is read from shared memory once for its eight outputs (about
+// half the shared-memory traffic of the column form; see slot8 for the
+// conflict-free layout).  At the other orders each thread owns one (i, j)
+// column of an element, loops over k, and
 //   * keeps its rows D[i][.], D[j][.] and columns D[.][i], D[.][j] in registers;
 //   * reads the contracted u values as float4 from two shared copies of the
 //     element: natural (i fastest, for the r contraction) and transposed in
@@ -247,6 +252,53 @@ __device__ __forceinline__ int unit_ix0(const Ax32Args &a, int64_t unit) {
   return (int)(unit % a.nseg) * a.seg_len;
 }
 
+// Line form at N = 7: each of an element's 64 threads owns an (i,j) column
+// (t-direction and the pointwise mix), an r-line (j,k) and an s-line (i,k),
+// and applies each contraction to a whole line in registers through the
+// even/odd halves of D.  A line is read from shared memory once for its
+// eight outputs, where the column form re-reads a row for every output.
+// Element-local slot of (i,j,k): 64k + 32(j/4) + 8((j + k) mod 4) + (i ^ k).
+// Its bank, 8((j + k) mod 4) + (i ^ k), is distinct across a warp for column
+// owners (i = 0..7, four j), r-line owners (k = 0..7, four j) and s-line
+// owners (i = 0..7, four k).
+__device__ __forceinline__ int slot8(int i, int j, int k) {
+  return 64 * k + 32 * (j >> 2) + 8 * ((j + k) & 3) + (i ^ k);
+}
+
+// v <- M v for a centro-antisymmetric 8 x 8 matrix M from its halves
+// od[a][b] = (M_ab - M_a,7-b) / 2 and ev[a][b] = (M_ab + M_a,7-b) / 2
+// (a, b < 4): (Mv)_a = P + Q, (Mv)_7-a = P - Q with P = sum_b od[a][b]
+// (v_b - v_7-b) and Q = sum_b ev[a][b] (v_b + v_7-b).
+__device__ __forceinline__ void eo_apply8(const float (&od)[16], const float (&ev)[16],
+                                          float (&v)[8]) {
+  float sv[4], dv[4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    sv[b] = v[b] + v[7 - b];
+    dv[b] = v[b] - v[7 - b];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    float p = od[4 * a] * dv[0], q = ev[4 * a] * sv[0];
+#pragma unroll
+    for (int b = 1; b < 4; ++b) {
+      p = fmaf(od[4 * a + b], dv[b], p);
+      q = fmaf(ev[4 * a + b], sv[b], q);
+    }
+    v[a] = p + q;
+    v[7 - a] = p - q;
+  }
+}
+
+// 16 floats of a 16-byte aligned shared block into registers.
+__device__ __forceinline__ void load16(const float *p, float (&r)[16]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float4 v = *reinterpret_cast<const float4 *>(p + 4 * c);
+    r[4 * c] = v.x; r[4 * c + 1] = v.y; r[4 * c + 2] = v.z; r[4 * c + 3] = v.w;
+  }
+}
+
 template <int NP, int GK, bool ASSEMBLE>
 __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
     ax32_kernel(Ax32Args a, Basis bs) {
@@ -272,10 +324,22 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
   const int le = threadIdx.x / NP2;
   const int ij = threadIdx.x - le * NP2;
   const int i = ij % NP, j = ij / NP;
-  for (int q = threadIdx.x; q < NP * RS; q += blockDim.x) {
-    const int r = q / RS, l = q % RS;
-    sD[q] = l < NP ? bs.D32[r * NP + l] : 0.f;
-    sDT[q] = l < NP ? bs.D32[l * NP + r] : 0.f;
+  constexpr bool LINES = STAGED && NP == 8;
+  if constexpr (LINES) {
+    // even/odd halves of D (od, ev) and of D^T (odT, evT), 16 floats each
+    for (int q = threadIdx.x; q < 64; q += blockDim.x) {
+      const int m = q >> 4, a = (q >> 2) & 3, b = q & 3;
+      const bool tr = m >= 2, ev = (m & 1) != 0;
+      auto Dm = [&](int x, int y) { return tr ? bs.D[y * NP + x] : bs.D[x * NP + y]; };
+      const double v = ev ? 0.5 * (Dm(a, b) + Dm(a, 7 - b)) : 0.5 * (Dm(a, b) - Dm(a, 7 - b));
+      sD[q] = (float)v;
+    }
+  } else {
+    for (int q = threadIdx.x; q < NP * RS; q += blockDim.x) {
+      const int r = q / RS, l = q % RS;
+      sD[q] = l < NP ? bs.D32[r * NP + l] : 0.f;
+      sDT[q] = l < NP ? bs.D32[l * NP + r] : 0.f;
+    }
   }
   if (STAGED && threadIdx.x == 0) {
     mbar_init(smem_addr(&mbar[0]), 1);
@@ -377,113 +441,201 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
     }
     const float *uN = STAGED ? stU : sU + le * ES;
 
-    // ---- u: registers along k, transposed copy (and padded natural copy)
-    float ru[NP];
-    if (active) {
-      if constexpr (STAGED) {
+    if constexpr (LINES) {
+      float *sUs = reinterpret_cast<float *>(smem + Lay::UT) + le * NP3;
+      float *sR = reinterpret_cast<float *>(smem + Lay::WR) + le * NP3;
+      float *sS = reinterpret_cast<float *>(smem + Lay::WS) + le * NP3;
+      // column (i, j); r-line (j, k) = (j, i); s-line (i, k) = (i, j)
+      float ru[NP];
+      if (active) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
           const float v = stU[k * NP2 + ij];
           ru[k] = v;
-          uT[k * PL + i * RS + j] = v;
+          sUs[slot8(i, j, k)] = v;
         }
-      } else {
-        const float *ue = a.u + e * NP3 + ij;
+      }
+      __syncthreads();
+      // ---- gradients: u_r on the r-line, u_s on the s-line, u_t on the column
+      if (active) {
+        float od[16], ev[16], v[NP];
+        load16(sD, od);
+        load16(sD + 16, ev);
+#pragma unroll
+        for (int l = 0; l < NP; ++l) v[l] = sUs[slot8(l, j, i)];
+        eo_apply8(od, ev, v);
+#pragma unroll
+        for (int l = 0; l < NP; ++l) sR[slot8(l, j, i)] = v[l];
+#pragma unroll
+        for (int l = 0; l < NP; ++l) v[l] = sUs[slot8(i, l, j)];
+        eo_apply8(od, ev, v);
+#pragma unroll
+        for (int l = 0; l < NP; ++l) sS[slot8(i, l, j)] = v[l];
+        eo_apply8(od, ev, ru);
+      }
+      __syncthreads();
+      // ---- geometric factors at the column's points, in place
+      if (active) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-          const float v = __ldg(ue + k * NP2);
-          ru[k] = v;
-          sU[le * ES + k * PL + j * RS + i] = v;
-          uT[k * PL + i * RS + j] = v;
+          const int sl = slot8(i, j, k);
+          const float ur = sR[sl], us = sS[sl], ut = ru[k];
+          float g6[6];
+#pragma unroll
+          for (int f = 0; f < 6; ++f) {
+            if constexpr (Lay::SG || Lay::SGS) g6[f] = factor_value<GK>(stG[f * NP3 + k * NP2 + ij]);
+            else g6[f] = factor_value<GK>(__ldg(static_cast<const GT *>(a.G) + e * 6 * NP3 +
+                                                f * NP3 + k * NP2 + ij));
+          }
+          sR[sl] = g6[0] * ur + g6[1] * us + g6[2] * ut;
+          sS[sl] = g6[1] * ur + g6[3] * us + g6[4] * ut;
+          ru[k] = g6[2] * ur + g6[4] * us + g6[5] * ut;
         }
       }
-    }
-    float gpre[S::GPRE ? 6 : 1][S::GPRE ? NP : 1];
-    if constexpr (S::GPRE) {
-      const GT *Gg = static_cast<const GT *>(a.G) + (active ? e : 0) * 6 * NP3 + ij;
+      __syncthreads();
+      // the factor stage is free: bring in the next chunk's factors
+      if constexpr (Lay::SGS)
+        if (threadIdx.x == 0 && nunit < units) issue_g(nunit, ncx);
+      // ---- divergence: D^T on the r-line and the s-line (in place), on the column
+      if (active) {
+        float od[16], ev[16], v[NP];
+        load16(sD + 32, od);
+        load16(sD + 48, ev);
 #pragma unroll
-      for (int f = 0; f < 6; ++f)
+        for (int l = 0; l < NP; ++l) v[l] = sR[slot8(l, j, i)];
+        eo_apply8(od, ev, v);
 #pragma unroll
-        for (int k = 0; k < NP; ++k)
-          gpre[f][k] = active ? factor_value<GK>(__ldg(Gg + f * NP3 + k * NP2)) : 0.f;
-    }
-    __syncthreads();
-    // ---- gradients, geometric factors, fluxes
-    float wt[NP];
-    if (active) {
-      float Dr[NP], Ds[NP];
-      load_row<NP>(sD + i * RS, Dr);
-      load_row<NP>(sD + j * RS, Ds);
-      const GT *Gg = static_cast<const GT *>(a.G) + e * 6 * NP3 + ij;
+        for (int l = 0; l < NP; ++l) sR[slot8(l, j, i)] = v[l];
 #pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        // two partial sums per contraction (even and odd l) halve the chains
-        float ur2[2] = {0.f, 0.f}, us2[2] = {0.f, 0.f}, ut2[2] = {0.f, 0.f};
-        const float *pa = uN + k * NPL + j * NRS, *pb = uT + k * PL + i * RS, *pd = sD + k * RS;
+        for (int l = 0; l < NP; ++l) v[l] = sS[slot8(i, l, j)];
+        eo_apply8(od, ev, v);
 #pragma unroll
-        for (int c = 0; c < C4; ++c) {
-          const float4 va = *reinterpret_cast<const float4 *>(pa + 4 * c);
-          const float4 vb = *reinterpret_cast<const float4 *>(pb + 4 * c);
-          const float4 vd = *reinterpret_cast<const float4 *>(pd + 4 * c);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int l = 4 * c + q;
-            if (l < NP) {
-              ur2[q & 1] = fmaf(Dr[l], f4get(va, q), ur2[q & 1]);
-              us2[q & 1] = fmaf(Ds[l], f4get(vb, q), us2[q & 1]);
-              ut2[q & 1] = fmaf(f4get(vd, q), ru[l], ut2[q & 1]);
-            }
-          }
-        }
-        const float ur = ur2[0] + ur2[1], us = us2[0] + us2[1], ut = ut2[0] + ut2[1];
-        float g6[6];
-#pragma unroll
-        for (int f = 0; f < 6; ++f) {
-          if constexpr (Lay::SG || Lay::SGS) g6[f] = factor_value<GK>(stG[f * NP3 + k * NP2 + ij]);
-          else if constexpr (S::GPRE) g6[f] = gpre[f][k];
-          else g6[f] = factor_value<GK>(__ldg(Gg + f * NP3 + k * NP2));
-        }
-        wR[k * NPL + j * NRS + i] = g6[0] * ur + g6[1] * us + g6[2] * ut;
-        wS[k * PL + i * RS + j] = g6[1] * ur + g6[3] * us + g6[4] * ut;
-        wt[k] = g6[2] * ur + g6[4] * us + g6[5] * ut;
+        for (int l = 0; l < NP; ++l) sS[slot8(i, l, j)] = v[l];
+        eo_apply8(od, ev, ru);
       }
-    }
-    __syncthreads();
-    // the factor stage is free: bring in the next chunk's factors
-    if constexpr (Lay::SGS)
-      if (threadIdx.x == 0 && nunit < units) issue_g(nunit, ncx);
-    // ---- divergence: w = scale * (D_r^T wr + D_s^T ws + D_t^T wt)
-    if (active) {
-      float DTr[NP], DTs[NP];
-      load_row<NP>(sDT + i * RS, DTr);
-      load_row<NP>(sDT + j * RS, DTs);
-      const float sc = GK == 0 ? 1.f : __ldg(a.scale + e);
-      float *we = a.w + e * NP3 + ij;
+      __syncthreads();
+      if (active) {
+        const float sc = GK == 0 ? 1.f : __ldg(a.scale + e);
+        float *we = a.w + e * NP3 + ij;
 #pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        // one partial sum per direction (three independent chains)
-        float ar = 0.f, as = 0.f, at = 0.f;
-        const float *pa = wR + k * NPL + j * NRS, *pb = wS + k * PL + i * RS, *pd = sDT + k * RS;
-#pragma unroll
-        for (int c = 0; c < C4; ++c) {
-          const float4 va = *reinterpret_cast<const float4 *>(pa + 4 * c);
-          const float4 vb = *reinterpret_cast<const float4 *>(pb + 4 * c);
-          const float4 vd = *reinterpret_cast<const float4 *>(pd + 4 * c);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int l = 4 * c + q;
-            if (l < NP) {
-              ar = fmaf(DTr[l], f4get(va, q), ar);
-              as = fmaf(DTs[l], f4get(vb, q), as);
-              at = fmaf(f4get(vd, q), wt[l], at);
-            }
+        for (int k = 0; k < NP; ++k) {
+          const int sl = slot8(i, j, k);
+          float acc = (sR[sl] + sS[sl]) + ru[k];
+          if (GK != 0) acc *= sc;
+          if (!ASSEMBLE || (i != 0 && i != N)) we[k * NP2] = acc;
+          else if (i == 0) sFL[le * NP2 + k * NP + j] = acc;
+          else sFR[le * NP2 + k * NP + j] = acc;
+        }
+      }
+    } else {
+      // ---- u: registers along k, transposed copy (and padded natural copy)
+      float ru[NP];
+      if (active) {
+        if constexpr (STAGED) {
+  #pragma unroll
+          for (int k = 0; k < NP; ++k) {
+            const float v = stU[k * NP2 + ij];
+            ru[k] = v;
+            uT[k * PL + i * RS + j] = v;
+          }
+        } else {
+          const float *ue = a.u + e * NP3 + ij;
+  #pragma unroll
+          for (int k = 0; k < NP; ++k) {
+            const float v = __ldg(ue + k * NP2);
+            ru[k] = v;
+            sU[le * ES + k * PL + j * RS + i] = v;
+            uT[k * PL + i * RS + j] = v;
           }
         }
-        float acc = (ar + as) + at;
-        if (GK != 0) acc *= sc;
-        if (!ASSEMBLE || (i != 0 && i != N)) we[k * NP2] = acc;
-        else if (i == 0) sFL[le * NP2 + k * NP + j] = acc;
-        else sFR[le * NP2 + k * NP + j] = acc;
+      }
+      float gpre[S::GPRE ? 6 : 1][S::GPRE ? NP : 1];
+      if constexpr (S::GPRE) {
+        const GT *Gg = static_cast<const GT *>(a.G) + (active ? e : 0) * 6 * NP3 + ij;
+  #pragma unroll
+        for (int f = 0; f < 6; ++f)
+  #pragma unroll
+          for (int k = 0; k < NP; ++k)
+            gpre[f][k] = active ? factor_value<GK>(__ldg(Gg + f * NP3 + k * NP2)) : 0.f;
+      }
+      __syncthreads();
+      // ---- gradients, geometric factors, fluxes
+      float wt[NP];
+      if (active) {
+        float Dr[NP], Ds[NP];
+        load_row<NP>(sD + i * RS, Dr);
+        load_row<NP>(sD + j * RS, Ds);
+        const GT *Gg = static_cast<const GT *>(a.G) + e * 6 * NP3 + ij;
+  #pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          // two partial sums per contraction (even and odd l) halve the chains
+          float ur2[2] = {0.f, 0.f}, us2[2] = {0.f, 0.f}, ut2[2] = {0.f, 0.f};
+          const float *pa = uN + k * NPL + j * NRS, *pb = uT + k * PL + i * RS, *pd = sD + k * RS;
+  #pragma unroll
+          for (int c = 0; c < C4; ++c) {
+            const float4 va = *reinterpret_cast<const float4 *>(pa + 4 * c);
+            const float4 vb = *reinterpret_cast<const float4 *>(pb + 4 * c);
+            const float4 vd = *reinterpret_cast<const float4 *>(pd + 4 * c);
+  #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int l = 4 * c + q;
+              if (l < NP) {
+                ur2[q & 1] = fmaf(Dr[l], f4get(va, q), ur2[q & 1]);
+                us2[q & 1] = fmaf(Ds[l], f4get(vb, q), us2[q & 1]);
+                ut2[q & 1] = fmaf(f4get(vd, q), ru[l], ut2[q & 1]);
+              }
+            }
+          }
+          const float ur = ur2[0] + ur2[1], us = us2[0] + us2[1], ut = ut2[0] + ut2[1];
+          float g6[6];
+  #pragma unroll
+          for (int f = 0; f < 6; ++f) {
+            if constexpr (Lay::SG || Lay::SGS) g6[f] = factor_value<GK>(stG[f * NP3 + k * NP2 + ij]);
+            else if constexpr (S::GPRE) g6[f] = gpre[f][k];
+            else g6[f] = factor_value<GK>(__ldg(Gg + f * NP3 + k * NP2));
+          }
+          wR[k * NPL + j * NRS + i] = g6[0] * ur + g6[1] * us + g6[2] * ut;
+          wS[k * PL + i * RS + j] = g6[1] * ur + g6[3] * us + g6[4] * ut;
+          wt[k] = g6[2] * ur + g6[4] * us + g6[5] * ut;
+        }
+      }
+      __syncthreads();
+      // the factor stage is free: bring in the next chunk's factors
+      if constexpr (Lay::SGS)
+        if (threadIdx.x == 0 && nunit < units) issue_g(nunit, ncx);
+      // ---- divergence: w = scale * (D_r^T wr + D_s^T ws + D_t^T wt)
+      if (active) {
+        float DTr[NP], DTs[NP];
+        load_row<NP>(sDT + i * RS, DTr);
+        load_row<NP>(sDT + j * RS, DTs);
+        const float sc = GK == 0 ? 1.f : __ldg(a.scale + e);
+        float *we = a.w + e * NP3 + ij;
+  #pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          // one partial sum per direction (three independent chains)
+          float ar = 0.f, as = 0.f, at = 0.f;
+          const float *pa = wR + k * NPL + j * NRS, *pb = wS + k * PL + i * RS, *pd = sDT + k * RS;
+  #pragma unroll
+          for (int c = 0; c < C4; ++c) {
+            const float4 va = *reinterpret_cast<const float4 *>(pa + 4 * c);
+            const float4 vb = *reinterpret_cast<const float4 *>(pb + 4 * c);
+            const float4 vd = *reinterpret_cast<const float4 *>(pd + 4 * c);
+  #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int l = 4 * c + q;
+              if (l < NP) {
+                ar = fmaf(DTr[l], f4get(va, q), ar);
+                as = fmaf(DTs[l], f4get(vb, q), as);
+                at = fmaf(f4get(vd, q), wt[l], at);
+              }
+            }
+          }
+          float acc = (ar + as) + at;
+          if (GK != 0) acc *= sc;
+          if (!ASSEMBLE || (i != 0 && i != N)) we[k * NP2] = acc;
+          else if (i == 0) sFL[le * NP2 + k * NP + j] = acc;
+          else sFR[le * NP2 + k * NP + j] = acc;
+        }
       }
     }
     if constexpr (ASSEMBLE) {
