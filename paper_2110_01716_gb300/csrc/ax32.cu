@@ -6,11 +6,12 @@
 //
 // Shared-memory traffic, not HBM, limits a straightforward column kernel in
 // FP32 (each FMA of the r and s contractions re-reads D and u from shared
-// memory).  At N = 7 (the fine level of the smoother) each thread owns three
-// lines of its element -- an (i, j) column, an r-line and an s-line -- and
-// contracts each whole line in registers through the even/odd halves of D,
-// so a line is read from shared memory once for its eight outputs (about
-// half the shared-memory traffic of the column form; see slot8 for the
+// memory).  At N = 7 and N = 4 (the smoother's fine and second levels) each
+// thread owns three lines of its element -- an (i, j) column, an r-line and
+// an s-line -- and contracts each whole line in registers through the
+// even/odd halves of D, so a line is read from shared memory once for its
+// NP outputs (about
+// half the shared-memory traffic of the column form; see line_slot for the
 // conflict-free layout).  At the other orders each thread owns one (i, j)
 // column of an element, loops over k, and
 //   * keeps its rows D[i][.], D[j][.] and columns D[.][i], D[.][j] in registers;
@@ -252,51 +253,70 @@ __device__ __forceinline__ int unit_ix0(const Ax32Args &a, int64_t unit) {
   return (int)(unit % a.nseg) * a.seg_len;
 }
 
-// Line form at N = 7: each of an element's 64 threads owns an (i,j) column
-// (t-direction and the pointwise mix), an r-line (j,k) and an s-line (i,k),
-// and applies each contraction to a whole line in registers through the
-// even/odd halves of D.  A line is read from shared memory once for its
-// eight outputs, where the column form re-reads a row for every output.
-// Element-local slot of (i,j,k): 64k + 32(j/4) + 8((j + k) mod 4) + (i ^ k).
-// Its bank, 8((j + k) mod 4) + (i ^ k), is distinct across a warp for column
-// owners (i = 0..7, four j), r-line owners (k = 0..7, four j) and s-line
-// owners (i = 0..7, four k).
-__device__ __forceinline__ int slot8(int i, int j, int k) {
-  return 64 * k + 32 * (j >> 2) + 8 * ((j + k) & 3) + (i ^ k);
+// Line form (N = 7 and N = 4): each of an element's NP^2 threads owns an
+// (i,j) column (t-direction and the pointwise mix), an r-line (j,k) and an
+// s-line (i,k), and applies each contraction to a whole line in registers
+// through the even/odd halves of D.  A line is read from shared memory once
+// for its NP outputs, where the column form re-reads a row for every output.
+//
+// Element-local slot of (i,j,k) and element stride of the line buffers.
+// NP = 8: 64k + 32(j/4) + 8((j + k) mod 4) + (i ^ k); its bank,
+// 8((j + k) mod 4) + (i ^ k), is distinct across a warp for column owners
+// (i = 0..7, four j), r-line owners (k = 0..7, four j) and s-line owners
+// (i = 0..7, four k).  NP = 5 (25 threads per element, warps straddle
+// elements): i + 5j + 26k with elements 153 floats apart, the layout with
+// the fewest wavefronts per warp access (1.6 on average, at most 2) found by
+// enumerating row, plane and element strides.
+template <int NP>
+__device__ __forceinline__ int line_slot(int i, int j, int k) {
+  if constexpr (NP == 8) return 64 * k + 32 * (j >> 2) + 8 * ((j + k) & 3) + (i ^ k);
+  else return i + 5 * j + 26 * k;
 }
+template <int NP>
+constexpr int line_stride() { return NP == 8 ? 512 : 153; }
 
-// v <- M v for a centro-antisymmetric 8 x 8 matrix M from its halves
-// od[a][b] = (M_ab - M_a,7-b) / 2 and ev[a][b] = (M_ab + M_a,7-b) / 2
-// (a, b < 4): (Mv)_a = P + Q, (Mv)_7-a = P - Q with P = sum_b od[a][b]
-// (v_b - v_7-b) and Q = sum_b ev[a][b] (v_b + v_7-b).
-__device__ __forceinline__ void eo_apply8(const float (&od)[16], const float (&ev)[16],
-                                          float (&v)[8]) {
-  float sv[4], dv[4];
+// v <- M v for a centro-antisymmetric NP x NP matrix M (the GLL D and D^T)
+// from its halves in registers: with b' = NP-1-b and H = NP/2,
+// od[a][b] = (M_ab - M_ab') / 2 ((H + NP%2) x H) and ev[a][b] =
+// (M_ab + M_ab') / 2 (H x (H + NP%2), for odd NP the last column M_a,mid):
+// (Mv)_a = P + Q, (Mv)_a' = P - Q with P = sum_b od[a][b] (v_b - v_b') and
+// Q = sum_b ev[a][b] (v_b + v_b') (v_mid alone in the last column); for odd
+// NP the middle row is sum_b od[H][b] (v_b - v_b').
+template <int NP>
+__device__ __forceinline__ void eo_apply(const float (&od)[(NP / 2) * (NP / 2 + (NP & 1))],
+                                         const float (&ev)[(NP / 2) * (NP / 2 + (NP & 1))],
+                                         float (&v)[NP]) {
+  constexpr int H = NP / 2, HO = H + (NP & 1);
+  float sv[HO], dv[H];
 #pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    sv[b] = v[b] + v[7 - b];
-    dv[b] = v[b] - v[7 - b];
+  for (int b = 0; b < H; ++b) {
+    sv[b] = v[b] + v[NP - 1 - b];
+    dv[b] = v[b] - v[NP - 1 - b];
   }
+  if constexpr (HO > H) sv[H] = v[H];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    float p = od[4 * a] * dv[0], q = ev[4 * a] * sv[0];
+  for (int a = 0; a < H; ++a) {
+    float p = od[a * H] * dv[0], q = ev[a * HO] * sv[0];
 #pragma unroll
-    for (int b = 1; b < 4; ++b) {
-      p = fmaf(od[4 * a + b], dv[b], p);
-      q = fmaf(ev[4 * a + b], sv[b], q);
-    }
+    for (int b = 1; b < H; ++b) p = fmaf(od[a * H + b], dv[b], p);
+#pragma unroll
+    for (int b = 1; b < HO; ++b) q = fmaf(ev[a * HO + b], sv[b], q);
     v[a] = p + q;
-    v[7 - a] = p - q;
+    v[NP - 1 - a] = p - q;
+  }
+  if constexpr (HO > H) {
+    float p = od[H * H] * dv[0];
+#pragma unroll
+    for (int b = 1; b < H; ++b) p = fmaf(od[H * H + b], dv[b], p);
+    v[H] = p;
   }
 }
 
-// 16 floats of a 16-byte aligned shared block into registers.
-__device__ __forceinline__ void load16(const float *p, float (&r)[16]) {
+// n floats of shared memory into registers (warp-uniform addresses).
+template <int n>
+__device__ __forceinline__ void load_coef(const float *p, float (&r)[n]) {
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const float4 v = *reinterpret_cast<const float4 *>(p + 4 * c);
-    r[4 * c] = v.x; r[4 * c + 1] = v.y; r[4 * c + 2] = v.z; r[4 * c + 3] = v.w;
-  }
+  for (int q = 0; q < n; ++q) r[q] = p[q];
 }
 
 template <int NP, int GK, bool ASSEMBLE>
@@ -324,14 +344,19 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
   const int le = threadIdx.x / NP2;
   const int ij = threadIdx.x - le * NP2;
   const int i = ij % NP, j = ij / NP;
-  constexpr bool LINES = STAGED && NP == 8;
+  constexpr bool LINES = (STAGED && NP == 8) || (!STAGED && NP == 5);
+  constexpr int LH = NP / 2, LHO = LH + (NP & 1), NEO = LH * LHO;
   if constexpr (LINES) {
-    // even/odd halves of D (od, ev) and of D^T (odT, evT), 16 floats each
-    for (int q = threadIdx.x; q < 64; q += blockDim.x) {
-      const int m = q >> 4, a = (q >> 2) & 3, b = q & 3;
+    // even/odd halves of D (od, ev) and of D^T (odT, evT), NEO floats each
+    for (int q = threadIdx.x; q < 4 * NEO; q += blockDim.x) {
+      const int m = q / NEO, r = q - m * NEO;
       const bool tr = m >= 2, ev = (m & 1) != 0;
+      const int cols = ev ? LHO : LH;
+      const int a = r / cols, b = r - a * cols;
       auto Dm = [&](int x, int y) { return tr ? bs.D[y * NP + x] : bs.D[x * NP + y]; };
-      const double v = ev ? 0.5 * (Dm(a, b) + Dm(a, 7 - b)) : 0.5 * (Dm(a, b) - Dm(a, 7 - b));
+      double v;
+      if (!ev) v = 0.5 * (Dm(a, b) - Dm(a, NP - 1 - b));
+      else v = b < LH ? 0.5 * (Dm(a, b) + Dm(a, NP - 1 - b)) : Dm(a, LH);
       sD[q] = (float)v;
     }
   } else {
@@ -442,48 +467,59 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
     const float *uN = STAGED ? stU : sU + le * ES;
 
     if constexpr (LINES) {
-      float *sUs = reinterpret_cast<float *>(smem + Lay::UT) + le * NP3;
-      float *sR = reinterpret_cast<float *>(smem + Lay::WR) + le * NP3;
-      float *sS = reinterpret_cast<float *>(smem + Lay::WS) + le * NP3;
+      constexpr int LS = line_stride<NP>();
+      float *sUs = reinterpret_cast<float *>(smem + Lay::UT) + le * LS;
+      float *sR = reinterpret_cast<float *>(smem + Lay::WR) + le * LS;
+      float *sS = reinterpret_cast<float *>(smem + Lay::WS) + le * LS;
       // column (i, j); r-line (j, k) = (j, i); s-line (i, k) = (i, j)
       float ru[NP];
+      float gpre[S::GPRE ? 6 : 1][S::GPRE ? NP : 1];
       if (active) {
+        const float *ue = a.u + e * NP3 + ij;
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-          const float v = stU[k * NP2 + ij];
+          const float v = STAGED ? stU[k * NP2 + ij] : __ldg(ue + k * NP2);
           ru[k] = v;
-          sUs[slot8(i, j, k)] = v;
+          sUs[line_slot<NP>(i, j, k)] = v;
+        }
+        if constexpr (S::GPRE) {
+          const GT *Gg = static_cast<const GT *>(a.G) + e * 6 * NP3 + ij;
+#pragma unroll
+          for (int f = 0; f < 6; ++f)
+#pragma unroll
+            for (int k = 0; k < NP; ++k) gpre[f][k] = factor_value<GK>(__ldg(Gg + f * NP3 + k * NP2));
         }
       }
       __syncthreads();
       // ---- gradients: u_r on the r-line, u_s on the s-line, u_t on the column
       if (active) {
-        float od[16], ev[16], v[NP];
-        load16(sD, od);
-        load16(sD + 16, ev);
+        float od[NEO], ev[NEO], v[NP];
+        load_coef(sD, od);
+        load_coef(sD + NEO, ev);
 #pragma unroll
-        for (int l = 0; l < NP; ++l) v[l] = sUs[slot8(l, j, i)];
-        eo_apply8(od, ev, v);
+        for (int l = 0; l < NP; ++l) v[l] = sUs[line_slot<NP>(l, j, i)];
+        eo_apply<NP>(od, ev, v);
 #pragma unroll
-        for (int l = 0; l < NP; ++l) sR[slot8(l, j, i)] = v[l];
+        for (int l = 0; l < NP; ++l) sR[line_slot<NP>(l, j, i)] = v[l];
 #pragma unroll
-        for (int l = 0; l < NP; ++l) v[l] = sUs[slot8(i, l, j)];
-        eo_apply8(od, ev, v);
+        for (int l = 0; l < NP; ++l) v[l] = sUs[line_slot<NP>(i, l, j)];
+        eo_apply<NP>(od, ev, v);
 #pragma unroll
-        for (int l = 0; l < NP; ++l) sS[slot8(i, l, j)] = v[l];
-        eo_apply8(od, ev, ru);
+        for (int l = 0; l < NP; ++l) sS[line_slot<NP>(i, l, j)] = v[l];
+        eo_apply<NP>(od, ev, ru);
       }
       __syncthreads();
       // ---- geometric factors at the column's points, in place
       if (active) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-          const int sl = slot8(i, j, k);
+          const int sl = line_slot<NP>(i, j, k);
           const float ur = sR[sl], us = sS[sl], ut = ru[k];
           float g6[6];
 #pragma unroll
           for (int f = 0; f < 6; ++f) {
             if constexpr (Lay::SG || Lay::SGS) g6[f] = factor_value<GK>(stG[f * NP3 + k * NP2 + ij]);
+            else if constexpr (S::GPRE) g6[f] = gpre[f][k];
             else g6[f] = factor_value<GK>(__ldg(static_cast<const GT *>(a.G) + e * 6 * NP3 +
                                                 f * NP3 + k * NP2 + ij));
           }
@@ -498,20 +534,20 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
         if (threadIdx.x == 0 && nunit < units) issue_g(nunit, ncx);
       // ---- divergence: D^T on the r-line and the s-line (in place), on the column
       if (active) {
-        float od[16], ev[16], v[NP];
-        load16(sD + 32, od);
-        load16(sD + 48, ev);
+        float od[NEO], ev[NEO], v[NP];
+        load_coef(sD + 2 * NEO, od);
+        load_coef(sD + 3 * NEO, ev);
 #pragma unroll
-        for (int l = 0; l < NP; ++l) v[l] = sR[slot8(l, j, i)];
-        eo_apply8(od, ev, v);
+        for (int l = 0; l < NP; ++l) v[l] = sR[line_slot<NP>(l, j, i)];
+        eo_apply<NP>(od, ev, v);
 #pragma unroll
-        for (int l = 0; l < NP; ++l) sR[slot8(l, j, i)] = v[l];
+        for (int l = 0; l < NP; ++l) sR[line_slot<NP>(l, j, i)] = v[l];
 #pragma unroll
-        for (int l = 0; l < NP; ++l) v[l] = sS[slot8(i, l, j)];
-        eo_apply8(od, ev, v);
+        for (int l = 0; l < NP; ++l) v[l] = sS[line_slot<NP>(i, l, j)];
+        eo_apply<NP>(od, ev, v);
 #pragma unroll
-        for (int l = 0; l < NP; ++l) sS[slot8(i, l, j)] = v[l];
-        eo_apply8(od, ev, ru);
+        for (int l = 0; l < NP; ++l) sS[line_slot<NP>(i, l, j)] = v[l];
+        eo_apply<NP>(od, ev, ru);
       }
       __syncthreads();
       if (active) {
@@ -519,7 +555,7 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
         float *we = a.w + e * NP3 + ij;
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-          const int sl = slot8(i, j, k);
+          const int sl = line_slot<NP>(i, j, k);
           float acc = (sR[sl] + sS[sl]) + ru[k];
           if (GK != 0) acc *= sc;
           if (!ASSEMBLE || (i != 0 && i != N)) we[k * NP2] = acc;
