@@ -280,6 +280,20 @@ __global__ void __launch_bounds__(TrShape<NF>::THREADS)
   const int i = ij % NF, j = ij / NF;
   for (int q = threadIdx.x; q < NF * NC; q += blockDim.x) sJ[q] = (R)tp.J[q];
   __syncthreads();
+  // the inputs of this thread's next batch are loaded into registers while
+  // the current batch is contracted (the loads' latency overlaps the barriers)
+  Tf bn[NF], wn[NF];
+  auto load = [&](int64_t e) {
+    if (e < t.E) {
+#pragma unroll
+      for (int k = 0; k < NF; ++k) {
+        const int64_t l = e * NF3 + k * NF2 + ij;
+        bn[k] = b[l];
+        wn[k] = w[l];
+      }
+    }
+  };
+  load((int64_t)blockIdx.x * NE + le);
   for (int64_t e0 = (int64_t)blockIdx.x * NE; e0 < t.E; e0 += (int64_t)gridDim.x * NE) {
     const int64_t e = e0 + le;
     const bool active = e < t.E;
@@ -290,10 +304,10 @@ __global__ void __launch_bounds__(TrShape<NF>::THREADS)
       R v[NF];
 #pragma unroll
       for (int k = 0; k < NF; ++k) {
-        const int64_t l = e * NF3 + k * NF2 + ij;
         const int sd = shared_dirs(i, j, k, N, ix, iy, iz, t);
-        v[k] = ((R)b[l] - (R)w[l]) * (R)(1.0f / (float)(1 << sd));
+        v[k] = ((R)bn[k] - (R)wn[k]) * (R)(1.0f / (float)(1 << sd));
       }
+      load(e + (int64_t)gridDim.x * NE);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         R y = 0;
@@ -303,23 +317,36 @@ __global__ void __launch_bounds__(TrShape<NF>::THREADS)
       }
     }
     __syncthreads();
+    // the j and i contractions one line per thread: a line is read once for
+    // its NC outputs, and J is read at warp-uniform addresses (broadcast)
     if (active) {
-      for (int q = ij; q < NC2 * NF; q += NF2) {
-        const int ii = q % NF, bc = q / NF, bb = bc % NC, c = bc / NC;
-        R z = 0;
+      for (int q = ij; q < NF * NC; q += NF2) {
+        const int ii = q % NF, c = q / NF;  // line (ii, ., c) of y
+        R yl[NF];
 #pragma unroll
-        for (int jj = 0; jj < NF; ++jj) z += sJ[jj * NC + bb] * s1[le][c * NF2 + jj * NF + ii];
-        s2[le][q] = z;
+        for (int jj = 0; jj < NF; ++jj) yl[jj] = s1[le][c * NF2 + jj * NF + ii];
+#pragma unroll
+        for (int bb = 0; bb < NC; ++bb) {
+          R z = 0;
+#pragma unroll
+          for (int jj = 0; jj < NF; ++jj) z += sJ[jj * NC + bb] * yl[jj];
+          s2[le][(c * NC + bb) * NF + ii] = z;
+        }
       }
     }
     __syncthreads();
     if (active) {
-      for (int q = ij; q < NC3; q += NF2) {
-        const int a = q % NC, bc = q / NC;
-        R o = 0;
+      for (int bc = ij; bc < NC2; bc += NF2) {  // line (., b, c) of z
+        R zl[NF];
 #pragma unroll
-        for (int ii = 0; ii < NF; ++ii) o += sJ[ii * NC + a] * s2[le][bc * NF + ii];
-        out[e * NC3 + q] = (Tc)o;
+        for (int ii = 0; ii < NF; ++ii) zl[ii] = s2[le][bc * NF + ii];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+          R o = 0;
+#pragma unroll
+          for (int ii = 0; ii < NF; ++ii) o += sJ[ii * NC + a] * zl[ii];
+          out[e * NC3 + bc * NC + a] = (Tc)o;
+        }
       }
     }
   }
@@ -338,11 +365,35 @@ __global__ void __launch_bounds__(TrShape<NF>::THREADS)
   const int le = threadIdx.x / NF2, ij = threadIdx.x - le * NF2;
   const int i = ij % NF, j = ij / NF;
   for (int q = threadIdx.x; q < NF * NC; q += blockDim.x) sJ[q] = (R)tp.J[q];
+  // the coarse values and the fine column of this thread's next batch are
+  // loaded into registers while the current batch is interpolated (the
+  // loads' latency overlaps the barriers; the fine values were read only
+  // after them before, which left the kernel waiting on memory)
+  constexpr int QC = (NC3 + NF2 - 1) / NF2;
+  Tc cn[QC];
+  Tf fn[NF];
+  auto load = [&](int64_t e) {
+    if (e < t.E) {
+#pragma unroll
+      for (int r = 0; r < QC; ++r)
+        if (ij + r * NF2 < NC3) cn[r] = xc[e * NC3 + ij + r * NF2];
+#pragma unroll
+      for (int k = 0; k < NF; ++k) fn[k] = xf[e * NF3 + k * NF2 + ij];
+    }
+  };
+  load((int64_t)blockIdx.x * NE + le);
   for (int64_t e0 = (int64_t)blockIdx.x * NE; e0 < t.E; e0 += (int64_t)gridDim.x * NE) {
     const int64_t e = e0 + le;
     const bool active = e < t.E;
-    if (active)
-      for (int q = ij; q < NC3; q += NF2) s0[le][q] = (R)xc[e * NC3 + q];
+    R fc[NF];
+    if (active) {
+#pragma unroll
+      for (int r = 0; r < QC; ++r)
+        if (ij + r * NF2 < NC3) s0[le][ij + r * NF2] = (R)cn[r];
+#pragma unroll
+      for (int k = 0; k < NF; ++k) fc[k] = (R)fn[k];
+      load(e + (int64_t)gridDim.x * NE);
+    }
     __syncthreads();
     if (active) {
       for (int q = ij; q < NF * NC2; q += NF2) {
@@ -368,8 +419,7 @@ __global__ void __launch_bounds__(TrShape<NF>::THREADS)
         R s = 0;
 #pragma unroll
         for (int c = 0; c < NC; ++c) s += sJ[k * NC + c] * z2[c];
-        const int64_t l = e * NF3 + k * NF2 + ij;
-        xf[l] = (Tf)((R)xf[l] + s);
+        xf[e * NF3 + k * NF2 + ij] = (Tf)(fc[k] + s);
       }
     }
   }
