@@ -99,7 +99,18 @@ template <int NP>
 struct A32 {
   static constexpr int NP2 = NP * NP;
   static constexpr int NP3 = NP2 * NP;
-  static constexpr int NE = (256 / NP2) < 1 ? 1 : (256 / NP2);
+  // elements per CTA: two at N = 7 (128 threads, four CTAs per SM) and five
+  // at N = 4 (125 threads, six per SM) measured faster than four and ten at
+  // 48^3 (0.336 -> 0.322 and 0.107 -> 0.104 ms per launch); one at N = 7 was
+  // slower (0.331)
+#ifndef SEM_AX32_NE8
+#define SEM_AX32_NE8 2
+#endif
+#ifndef SEM_AX32_NE5
+#define SEM_AX32_NE5 5
+#endif
+  static constexpr int NE = NP == 8 ? SEM_AX32_NE8 : NP == 5 ? SEM_AX32_NE5
+                          : (256 / NP2) < 1 ? 1 : (256 / NP2);
   static constexpr int THREADS = NE * NP2;
   static constexpr int C4 = (NP + 3) / 4;                            // float4 per row
   static constexpr int RS = (C4 % 2 == 0) ? 4 * C4 + 4 : 4 * C4;     // padded row stride
@@ -131,7 +142,8 @@ struct A32 {
   // the unstaged small orders fit 64 registers (four CTAs, 32 warps per SM),
   // 80 with the factors in registers (three CTAs)
   static constexpr int MIN_CTAS =
-      !STAGED && NP <= 5 ? (GPRE ? 3 : 4) : (NP <= 8 ? SEM_AX32_MIN_CTAS : 1);
+      NP == 8 && NE <= 2 ? 8 / NE : NP == 5 && NE == 5 ? 6
+      : !STAGED && NP <= 5 ? (GPRE ? 3 : 4) : (NP <= 8 ? SEM_AX32_MIN_CTAS : 1);
 };
 
 constexpr int round16(int b) { return (b + 15) & ~15; }
