@@ -72,10 +72,10 @@ AX_TRAFFIC = {"source_sha256": "ca840efb8d892b9000dd5912465d5da7951c30be7b8ed79d
               "bytes_per_point": 63.54}
 # The same for the smoother's assembled FP32 operator, per factor storage
 # (ncu capture on a 32^3 case), valid while ax32.cu is unchanged.
-AX32_TRAFFIC = {"f32": {"source_sha256": "a1ec8ef68ef769562e18901d6e5ac4fe3e14479f80e51652bf9318a9ac65cd3b",
-                        "bytes_per_point": 31.28},
-                "f16": {"source_sha256": "a1ec8ef68ef769562e18901d6e5ac4fe3e14479f80e51652bf9318a9ac65cd3b",
-                        "bytes_per_point": 18.82}}
+AX32_TRAFFIC = {"f32": {"source_sha256": "c09633532b5ddf1453647455ea5886b74bf84f5f250779299a116f69725304c8",
+                        "bytes_per_point": 31.29},
+                "f16": {"source_sha256": "c09633532b5ddf1453647455ea5886b74bf84f5f250779299a116f69725304c8",
+                        "bytes_per_point": 18.80}}
 
 
 def parse_args():
