@@ -60,7 +60,11 @@ enum { SEM_DIRICHLET = 0, SEM_NEUMANN = 1 };
 enum { SEM_GEOM_STORED = 0, SEM_GEOM_TRILINEAR = 1 };
 /* How FP64 operator applications are computed (results agree to ~1e-14):
  * SEM_ARITH_PAIR   FP32-pair ("double-float") arithmetic on the FP32 pipes,
- *                  geometric factors stored as hi/lo float pairs (default);
+ *                  geometric factors stored as hi/lo float pairs (default).
+ *                  It covers the FP32 exponent range: input values, factors
+ *                  and partial sums of magnitude about 1e-38 to 3e38 keep
+ *                  FP64-level relative accuracy; values outside it are
+ *                  taken as zero.  Scale the data into that range or use
  * SEM_ARITH_NATIVE native FP64 instructions, factors stored as doubles.
  * Recomputed (trilinear) geometry always uses native FP64. */
 enum { SEM_ARITH_PAIR = 0, SEM_ARITH_NATIVE = 1 };
