@@ -64,18 +64,9 @@ __device__ __forceinline__ float2 pair_norm(float s, float c) {
   return make_float2(t, __fsub_rn(c, __fsub_rn(t, s)));
 }
 
-// a + b for pairs: TwoSum of the heads, the tails and its error added, then
-// renormalised.  The error is a few units of 2^-46 of |a| + |b|, the same
-// scale as the rounding of the sums it feeds.
-__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
-  const float t = __fadd_rn(a.x, b.x);
-  const float z = __fsub_rn(t, a.x);
-  const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(t, z)), __fsub_rn(b.x, z));
-  return pair_norm(t, __fadd_rn(err, __fadd_rn(a.y, b.y)));
-}
-
-// a + b for pairs without the final renormalisation: (t, c) with |c| a few
-// units of 2^-24 |t| or below (a product operand needs no more).
+// a + b for pairs: TwoSum of the heads, the tails and its error added,
+// without renormalisation.  The error is a few units of 2^-46 of |a| + |b|,
+// the same scale as the rounding of the sums it feeds.
 __device__ __forceinline__ float2 pair_add_nn(float2 a, float2 b) {
   const float t = __fadd_rn(a.x, b.x);
   const float z = __fsub_rn(t, a.x);
@@ -105,8 +96,10 @@ __device__ __forceinline__ float2 lds_pair(const float2 *p) {
 //   ((Mv)_a - (Mv)_a') / 2 = sum_b even[a][b] s_b,  even[a][b] = (M_ab + M_ab') / 2,
 // with, for odd NP, the extra column even[a][H] = M_a,mid taken against
 // v_mid, and the middle row (Mv)_mid = sum_b odd[H][b] d_b.  The NP^2
-// products become about NP^2 / 2 plus 2 NP pair additions.  s_b and d_b
-// are product operands only and stay unnormalised.
+// products become about NP^2 / 2 plus 2 NP pair additions.  Neither s_b,
+// d_b nor the results are renormalised: every consumer (a product, or a
+// TwoSum of heads) takes an unnormalised pair, and the tail's own rounding
+// stays at the 2^-48 scale of the sums it came from.
 // odd is (H + NP%2) x H, even is H x (H + NP%2), both row-major, in shared
 // memory.
 template <int NP>
@@ -129,15 +122,15 @@ __device__ __forceinline__ void pair_apply_eo(const float2 *odd, const float2 *e
     pair_mul_first(lds_pair(&even[a * HO]), sv[0], ms, mc);
 #pragma unroll
     for (int b = 1; b < HO; ++b) pair_fma(lds_pair(&even[a * HO + b]), sv[b], ms, mc);
-    v[a] = pair_add(make_float2(ps, pc), make_float2(ms, mc));
-    v[NP - 1 - a] = pair_add(make_float2(ps, pc), make_float2(-ms, -mc));
+    v[a] = pair_add_nn(make_float2(ps, pc), make_float2(ms, mc));
+    v[NP - 1 - a] = pair_add_nn(make_float2(ps, pc), make_float2(-ms, -mc));
   }
   if constexpr (HO > H) {
     float ps, pc;
     pair_mul_first(lds_pair(&odd[H * H]), dv[0], ps, pc);
 #pragma unroll
     for (int b = 1; b < H; ++b) pair_fma(lds_pair(&odd[H * H + b]), dv[b], ps, pc);
-    v[H] = pair_norm(ps, pc);
+    v[H] = make_float2(ps, pc);
   }
 }
 
@@ -312,11 +305,11 @@ __global__ void __launch_bounds__(PairShape<NP>::THREADS, PairShape<NP>::MIN_CTA
         const float2 ur = sR[le][sl], us = sS[le][sl], ut = rt[k];
         float a, b;
         pair_mul_first(g[0], ur, a, b); pair_fma(g[1], us, a, b); pair_fma(g[2], ut, a, b);
-        sR[le][sl] = pair_norm(a, b);
+        sR[le][sl] = make_float2(a, b);
         pair_mul_first(g[1], ur, a, b); pair_fma(g[3], us, a, b); pair_fma(g[4], ut, a, b);
-        sS[le][sl] = pair_norm(a, b);
+        sS[le][sl] = make_float2(a, b);
         pair_mul_first(g[2], ur, a, b); pair_fma(g[4], us, a, b); pair_fma(g[5], ut, a, b);
-        rt[k] = pair_norm(a, b);
+        rt[k] = make_float2(a, b);
       }
     }
     __syncthreads();
