@@ -6,7 +6,7 @@
 //
 // Shared-memory traffic, not HBM, limits a straightforward column kernel in
 // FP32 (each FMA of the r and s contractions re-reads D and u from shared
-// memory).  At N = 7 and N = 4 (the smoother's fine and second levels) each
+// memory).  At N = 7, 4 and 2 (the levels of the smoother) each
 // thread owns three lines of its element -- an (i, j) column, an r-line and
 // an s-line -- and contracts each whole line in registers through the
 // even/odd halves of D, so a line is read from shared memory once for its
@@ -95,6 +95,9 @@ constexpr int best_element_stride(int NP, int NE, int RS) {
   return best;
 }
 
+// Element stride (floats) of the line form's shared copies (see line_slot).
+constexpr int line_stride_of(int NP) { return NP == 8 ? 512 : NP == 5 ? 153 : NP == 3 ? 41 : 0; }
+
 template <int NP>
 struct A32 {
   static constexpr int NP2 = NP * NP;
@@ -124,6 +127,9 @@ struct A32 {
   static constexpr int ES = (NP % 4 != 0 && SEM_AX32_ES_SEARCH)
                                 ? best_element_stride(NP, NE, RS)
                                 : (((NP * PL / 4) % 2 == 0) ? NP * PL + 4 : NP * PL);
+  // element stride of the shared regions: the column form's, or the line
+  // form's where that is larger
+  static constexpr int ESB = ES < line_stride_of(NP) ? line_stride_of(NP) : ES;
   // Staged variant (NP a multiple of 4): natural-order arrays keep unpadded
   // rows (a warp reads at most four rows of one element, or of two elements
   // 16 banks apart); the element's u and factors arrive by bulk copy.
@@ -176,10 +182,10 @@ struct L32 {
   static constexpr int UN = DTAB + round16(2 * NP * S::RS * 4);       // direct: padded natural u
   static constexpr int UN_END = S::STAGED ? UN : UN + S::NE * S::ES * 4;
   static constexpr int UT = UN_END;                                   // transposed u
-  static constexpr int WR = UT + S::NE * S::ES * 4;                   // natural r flux
-  static constexpr int WR_END = WR + S::NE * (S::STAGED ? S::ESN : S::ES) * 4;
+  static constexpr int WR = UT + S::NE * S::ESB * 4;                  // natural r flux
+  static constexpr int WR_END = WR + S::NE * (S::STAGED ? S::ESN : S::ESB) * 4;
   static constexpr int WS = WR_END;                                   // transposed s flux
-  static constexpr int FACES = WS + S::NE * S::ES * 4;                // sFL, sFR, sCarry
+  static constexpr int FACES = WS + S::NE * S::ESB * 4;               // sFL, sFR, sCarry
   static constexpr int BYTES = FACES + (2 * S::NE + 2) * S::NP2 * 4;
 };
 
@@ -278,14 +284,16 @@ __device__ __forceinline__ int unit_ix0(const Ax32Args &a, int64_t unit) {
 // (i = 0..7, four k).  NP = 5 (25 threads per element, warps straddle
 // elements): i + 5j + 26k with elements 153 floats apart, the layout with
 // the fewest wavefronts per warp access (1.6 on average, at most 2) found by
-// enumerating row, plane and element strides.
+// enumerating row, plane and element strides.  NP = 3 likewise: i + 3j + 11k,
+// elements 41 floats apart (1.7 wavefronts per access, at most 2).
 template <int NP>
 __device__ __forceinline__ int line_slot(int i, int j, int k) {
   if constexpr (NP == 8) return 64 * k + 32 * (j >> 2) + 8 * ((j + k) & 3) + (i ^ k);
-  else return i + 5 * j + 26 * k;
+  else if constexpr (NP == 5) return i + 5 * j + 26 * k;
+  else return i + 3 * j + 11 * k;
 }
 template <int NP>
-constexpr int line_stride() { return NP == 8 ? 512 : 153; }
+constexpr int line_stride() { return line_stride_of(NP); }
 
 // v <- M v for a centro-antisymmetric NP x NP matrix M (the GLL D and D^T)
 // from its halves in registers: with b' = NP-1-b and H = NP/2,
@@ -356,7 +364,7 @@ __global__ void __launch_bounds__(A32<NP>::THREADS, A32<NP>::MIN_CTAS)
   const int le = threadIdx.x / NP2;
   const int ij = threadIdx.x - le * NP2;
   const int i = ij % NP, j = ij / NP;
-  constexpr bool LINES = (STAGED && NP == 8) || (!STAGED && NP == 5);
+  constexpr bool LINES = (STAGED && NP == 8) || (!STAGED && (NP == 5 || NP == 3));
   constexpr int LH = NP / 2, LHO = LH + (NP & 1), NEO = LH * LHO;
   if constexpr (LINES) {
     // even/odd halves of D (od, ev) and of D^T (odT, evT), NEO floats each
