@@ -72,10 +72,10 @@ AX_TRAFFIC = {"source_sha256": "2c501da0dc26ea66228f2a74a4e74d7a574e1eeb4a3a83b5
               "bytes_per_point": 63.72}
 # The same for the smoother's assembled FP32 operator, per factor storage
 # (ncu capture on a 32^3 case), valid while ax32.cu is unchanged.
-AX32_TRAFFIC = {"f32": {"source_sha256": "c09633532b5ddf1453647455ea5886b74bf84f5f250779299a116f69725304c8",
-                        "bytes_per_point": 31.29},
-                "f16": {"source_sha256": "c09633532b5ddf1453647455ea5886b74bf84f5f250779299a116f69725304c8",
-                        "bytes_per_point": 18.80}}
+AX32_TRAFFIC = {"f32": {"source_sha256": "a797ec83846c77963b93140f5d48cb141371698a98aac0655e34ba1e0aeb1190",
+                        "bytes_per_point": 31.26},
+                "f16": {"source_sha256": "a797ec83846c77963b93140f5d48cb141371698a98aac0655e34ba1e0aeb1190",
+                        "bytes_per_point": 18.63}}
 
 
 def parse_args():
