@@ -253,6 +253,14 @@ struct TrShape {
   static constexpr int NF2 = NF * NF;
   static constexpr int NE = (256 / NF2) < 1 ? 1 : (256 / NF2);
   static constexpr int THREADS = NE * NF2;
+  // six CTAs per SM (40 registers): at 48^3 the transfers between N = 7 and
+  // N = 4 took 0.176 -> 0.141 ms (restriction) and 0.146 -> 0.130 ms
+  // (prolongation) against the compiler's choice of four; eight spilled
+  // and lost
+#ifndef SEM_TR_MIN_CTAS
+#define SEM_TR_MIN_CTAS 6
+#endif
+  static constexpr int MIN_CTAS = SEM_TR_MIN_CTAS;
 };
 
 // 2^-(number of elements sharing fine point (i, j, k) besides its own) as the
@@ -266,7 +274,7 @@ __device__ __forceinline__ int shared_dirs(int i, int j, int k, int N, int ix, i
 }
 
 template <int NF, int NC, typename Tf, typename Tc>
-__global__ void __launch_bounds__(TrShape<NF>::THREADS)
+__global__ void __launch_bounds__(TrShape<NF>::THREADS, TrShape<NF>::MIN_CTAS)
     restrict_fast_kernel(TransferParams tp, const Tf *__restrict__ b, const Tf *__restrict__ w,
                          Tc *__restrict__ out) {
   using R = typename TransferCompute<Tf, Tc>::type;
@@ -353,7 +361,7 @@ __global__ void __launch_bounds__(TrShape<NF>::THREADS)
 }
 
 template <int NF, int NC, typename Tc, typename Tf>
-__global__ void __launch_bounds__(TrShape<NF>::THREADS)
+__global__ void __launch_bounds__(TrShape<NF>::THREADS, TrShape<NF>::MIN_CTAS)
     prolong_fast_kernel(TransferParams tp, const Tc *__restrict__ xc, Tf *__restrict__ xf) {
   using R = typename TransferCompute<Tf, Tc>::type;
   constexpr int NF2 = NF * NF, NF3 = NF2 * NF, NC2 = NC * NC, NC3 = NC2 * NC;
