@@ -464,8 +464,10 @@ sem_status sem_batch_destroy(sem_batch *batch);
  * time every candidate value (for the levels of that order) is captured into
  * the whole batch's graph and timed (median of reps launches, CUDA events),
  * and the value with the fastest whole-batch time is kept (the current one
- * unless a candidate beats it).  The batch keeps the graph of the chosen
- * values; they are written to chosen[0..SEM_MAX_ORDER] (HOST, 0 = the
+ * unless a candidate beats it by more than 2 %).  The tuned values are then
+ * timed twice more, alternately with the starting ones, and kept only if
+ * they are still faster by that margin.  The batch keeps the graph of the
+ * chosen values; they are written to chosen[0..SEM_MAX_ORDER] (HOST, 0 = the
  * default) and *best_ms is the median time of one launch.  Synchronises. */
 sem_status sem_batch_autotune(sem_batch *batch, const float *candidates, int32_t ncand,
                               int32_t reps, void *stream, float *chosen, double *best_ms);

@@ -384,22 +384,43 @@ sem_status sem_batch_autotune(sem_batch *batch, const float *candidates, int32_t
     // share one value.  Coordinate descent on the whole batch, the problems
     // of every class running beside the others as in use: one class at a
     // time tries every candidate and keeps the fastest whole-batch time.
+    // A candidate replaces the current value only when it is faster by more
+    // than the margin (launch-to-launch variation of a batch is a few per
+    // cent), and the tuned split must beat the starting one again, timed
+    // alternately with it, or the starting split is kept.
+    constexpr double kMargin = 0.02;
     std::set<int> classes;
     for (int i = 0; i < batch->n; ++i) classes.insert(batch->reqs[i].N);
+    float start[SEM_MAX_ORDER + 1];
+    std::copy(batch->d.ax_fill, batch->d.ax_fill + SEM_MAX_ORDER + 1, start);
     double best = time_batch();
     for (int N : classes) {
       const std::vector<int32_t> ord = batch_orders(N);
       const float keep = batch->d.ax_fill[N];
       float best_f = keep;
       for (int32_t c = 0; c < ncand; ++c) {
+        if (candidates[c] == keep) continue;
         for (int o : ord) batch->d.ax_fill[o] = candidates[c];
         const double t = time_batch();
-        if (t < best) {
+        if (t < best * (1.0 - kMargin)) {
           best = t;
           best_f = candidates[c];
         }
       }
       for (int o : ord) batch->d.ax_fill[o] = best_f;
+    }
+    if (!std::equal(start, start + SEM_MAX_ORDER + 1, batch->d.ax_fill)) {
+      float tuned[SEM_MAX_ORDER + 1];
+      std::copy(batch->d.ax_fill, batch->d.ax_fill + SEM_MAX_ORDER + 1, tuned);
+      double t_tuned = 0.0, t_start = 0.0;
+      for (int r = 0; r < 2; ++r) {
+        std::copy(tuned, tuned + SEM_MAX_ORDER + 1, batch->d.ax_fill);
+        t_tuned += time_batch();
+        std::copy(start, start + SEM_MAX_ORDER + 1, batch->d.ax_fill);
+        t_start += time_batch();
+      }
+      const float *keep_fill = t_tuned < t_start * (1.0 - kMargin) ? tuned : start;
+      std::copy(keep_fill, keep_fill + SEM_MAX_ORDER + 1, batch->d.ax_fill);
     }
     for (int o = 0; o <= SEM_MAX_ORDER; ++o) chosen[o] = batch->d.ax_fill[o];
     *best_ms = time_batch();
