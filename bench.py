@@ -89,6 +89,8 @@ def parse_args():
                    help="skip the operator sweep, e2e and CPU-baseline legs")
     p.add_argument("--no-serve", action="store_true",
                    help="skip the batched (config 4) and serving (config 5) legs")
+    p.add_argument("--host-loop", action="store_true",
+                   help="time FlexCG's host-driven loop instead of the CUDA-graph loop")
     p.add_argument("--breakdown", action="store_true",
                    help="after the timed region, time every kernel class of one more solve")
     p.add_argument("--coarse-maxit", type=int, default=COARSE_MAXIT)
@@ -963,9 +965,16 @@ def main():
 
     solver = sem.SEM_SOLVER_FGMRES if args.solver == "fgmres" else sem.SEM_SOLVER_FLEXCG
 
-    def step():  # from x = 0 (the solver zeroes x and skips the product with it)
+    # FlexCG runs its iterations 2.. as one CUDA-graph launch with the stopping
+    # test on the device (use_graph; the same kernels and bits as the host
+    # loop): the initial V-cycle and iteration 1 stay host-launched, so the
+    # kernels of the roofline entry are event-timed there, and the graph's
+    # launches are counted per class from the tally taken at its capture
+    use_graph = solver == sem.SEM_SOLVER_FLEXCG and not args.host_loop
+
+    def step(graph=use_graph):  # from x = 0 (the solver zeroes x and skips the product with it)
         return sem.sem_solve(mesh, pmg, b, x, solver, tol=TOL, max_iter=200, check_every=1,
-                             restart=args.restart, zero_guess=True)
+                             restart=args.restart, zero_guess=True, use_graph=graph)
 
     for _ in range(max(args.warmup, 0)):
         info = step()
@@ -1005,9 +1014,12 @@ def main():
     launches = sum(v["launches"] for v in trace.values())
 
     def timed(key):
+        # average event-timed launch; share of the step from every launch of
+        # the class (graph replays included)
         ent = trace.get(key, {"launches": 0, "timed": 0, "total_ms": 0.0})
         per = ent["total_ms"] / max(ent["timed"], 1)
-        return per, (ent["total_ms"] / total_ms if total_ms > 0 else None), ent["timed"]
+        share = per * ent["launches"] / total_ms if total_ms > 0 else None
+        return per, share, ent["timed"]
 
     # FP64 operator in FP32-pair arithmetic (FP32-pipe bound)
     key64 = f"ax_f64pair_N{ORDER}"
@@ -1063,6 +1075,8 @@ def main():
                        "coarse_tol": args.coarse_tol,
                        "coarse_maxit": args.coarse_maxit, "coarse_mode": args.coarse_mode,
                        "n_global": ng, "parallelism": "replicas" if world > 1 else "single",
+                       "loop": ("cuda graph: iterations 2.. in one launch, stopping test on "
+                                "the device" if use_graph else "host-driven"),
                        "l2": "inputs larger than L2 (working set ~6 GB), no flush"},
             "iters": [inf["iters"] for inf in infos],
             "final_rel_res": max(inf["res"] / inf["bnorm"] for inf in infos),
@@ -1080,7 +1094,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step()
+        step(graph=False)  # host-launched, so that every kernel is timed
         e1.record(stream)
         torch.cuda.synchronize()
         bd = sem.sem_trace_read(reset=True)
@@ -1095,23 +1109,27 @@ def main():
     if not args.no_extras and rank == 0:
         ex = {}
         if solver == sem.SEM_SOLVER_FLEXCG:
-            # the same solves with iterations 2.. as one CUDA-graph launch
-            # (device-side stopping test, one host read per solve), right
-            # after the timed region so that both see the same GPU state
+            # the same solves with the other loop (host-driven when the
+            # timed region ran the graph, and the other way round), right
+            # after the timed region so that both see the same GPU state: the
+            # host-driven loop reads <r, r> after every iteration
             gt = []
             for i in range(args.warmup + args.steps):
                 ge0 = torch.cuda.Event(enable_timing=True)
                 ge1 = torch.cuda.Event(enable_timing=True)
                 ge0.record(stream)
-                ginf = sem.sem_solve(mesh, pmg, b, x, solver, tol=TOL, max_iter=200,
-                                     stream=stream, use_graph=True, zero_guess=True)
+                ginf = step(graph=not use_graph)
                 ge1.record(stream)
                 torch.cuda.synchronize()
                 if i >= args.warmup:
                     gt.append(ge0.elapsed_time(ge1))
-            ex["graph"] = {"ms_per_solve": statistics.mean(gt), "iters": ginf["iters"],
-                           "host_loop_ms_per_solve": ms_per_step,
-                           "value": ng / (statistics.mean(gt) / 1e3) / 1e9, "unit": "GDOF/s"}
+            other = statistics.mean(gt)
+            ex["graph"] = {"ms_per_solve": ms_per_step if use_graph else other,
+                           "host_loop_ms_per_solve": other if use_graph else ms_per_step,
+                           "timed_region_loop": "graph" if use_graph else "host",
+                           "iters": ginf["iters"],
+                           "value": ng / ((ms_per_step if use_graph else other) / 1e3) / 1e9,
+                           "unit": "GDOF/s"}
         # end to end through the host-buffer entry point: host b in, host x
         # out (pinned host memory), from x = 0 (x's input is neither read nor
         # copied)
@@ -1119,12 +1137,12 @@ def main():
         xh = torch.zeros(nl, dtype=torch.float64).pin_memory()
         for _ in range(1):
             sem.sem_solve_host(mesh, pmg, bh, xh, solver, tol=TOL, max_iter=200,
-                               restart=args.restart, zero_guess=True)
+                               restart=args.restart, zero_guess=True, use_graph=use_graph)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             sem.sem_solve_host(mesh, pmg, bh, xh, solver, tol=TOL, max_iter=200,
-                               restart=args.restart, zero_guess=True)
+                               restart=args.restart, zero_guess=True, use_graph=use_graph)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
         line["e2e"] = {"value": ng / e2e_s / 1e9, "unit": "GDOF/s",

@@ -9,6 +9,7 @@
 
 #include <atomic>
 #include <cstdarg>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -328,4 +329,5 @@ struct sem_mesh {
   uint64_t graph_pmg = 0;          // serial of the pMG captured
   const double *graph_x = nullptr; // solution vector captured
   int graph_kernels = 0;           // kernels per loop pass
+  std::map<std::string, int64_t> graph_tally;  // of them, per trace class
 };

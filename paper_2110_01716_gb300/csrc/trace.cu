@@ -66,15 +66,27 @@ static bool filter_matches(const std::string &filter, const char *name) {
   return false;
 }
 
+namespace {
+// Kernels per class captured by this thread while a tally is open.
+thread_local std::map<std::string, int64_t> *t_tally = nullptr;
+}  // namespace
+
+void trace_tally_begin(std::map<std::string, int64_t> *tally) { t_tally = tally; }
+void trace_tally_end() { t_tally = nullptr; }
+
 TraceScope::TraceScope(const char *name, int N, cudaStream_t st, int kernels) : st_(st) {
   Tracer &T = tracer();
-  if (!T.on.load(std::memory_order_relaxed)) return;
-  // launches captured into a CUDA graph run later, once per replay: the
-  // graph's owner counts them
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return;
+  if (!T.on.load(std::memory_order_relaxed) && !t_tally) return;
   char buf[64];
   snprintf(buf, sizeof(buf), "%s_N%d", name, N);
+  // launches captured into a CUDA graph run later, once per replay: the
+  // capture's tally holds them and the graph's owner counts the replays
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+    if (t_tally) (*t_tally)[buf] += kernels;
+    return;
+  }
+  if (!T.on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lock(T.mu);
   ClassStats &c = T.cls[buf];
   c.launches += kernels;
@@ -96,12 +108,16 @@ TraceScope::~TraceScope() {
 }
 
 void trace_count(const char *name, int N, int64_t launches) {
-  Tracer &T = tracer();
-  if (!T.on.load(std::memory_order_relaxed)) return;
   char buf[64];
   snprintf(buf, sizeof(buf), "%s_N%d", name, N);
+  trace_count_key(buf, launches);
+}
+
+void trace_count_key(const std::string &key, int64_t launches) {
+  Tracer &T = tracer();
+  if (!T.on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lock(T.mu);
-  T.cls[buf].launches += launches;
+  T.cls[key].launches += launches;
 }
 
 void trace_enable(bool on, const char *filter) {

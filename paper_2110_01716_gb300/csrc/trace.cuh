@@ -1,6 +1,7 @@
 // trace.cuh -- per-class launch counters and event timers (see trace.cu).
 #pragma once
 
+#include <map>
 #include <string>
 
 #include "common.cuh"
@@ -25,8 +26,15 @@ class TraceScope {
   std::string key_;
 };
 
-// Adds `launches` kernel launches to class "<name>_N<order>" without timing
-// (kernels that ran inside a graph launch).
+// Adds `launches` kernel launches to class "<name>_N<order>" (or to the class
+// named `key`) without timing (kernels that ran inside a graph launch).
 void trace_count(const char *name, int N, int64_t launches);
+void trace_count_key(const std::string &key, int64_t launches);
+
+// While a tally is open, the TraceScopes this thread meets on a capturing
+// stream add their kernels to (*tally)[class] instead of counting them: the
+// per-class kernels of a captured graph, for trace_count_key per replay.
+void trace_tally_begin(std::map<std::string, int64_t> *tally);
+void trace_tally_end();
 
 }  // namespace sem

@@ -318,17 +318,20 @@ __global__ void graph_arm_full_kernel(const double *__restrict__ bb, const doubl
 
 void launch_graph_arm_full(const double *bb, const double *rr, double *g, double tol, int maxit,
                            cudaGraphConditionalHandle h, cudaStream_t st) {
+  TraceScope ts("graph_ctl", 0, st);
   graph_arm_full_kernel<<<1, 1, 0, st>>>(bb, rr, g, tol, (double)maxit, h);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
 
 void launch_graph_stop(const double *rr, double *g, cudaGraphConditionalHandle h,
                        cudaStream_t st) {
+  TraceScope ts("graph_ctl", 0, st);
   graph_stop_kernel<<<1, 1, 0, st>>>(rr, g, h);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
 
 void launch_graph_arm(double *g, double tol2, int maxit, int done, cudaStream_t st) {
+  TraceScope ts("graph_ctl", 0, st);
   graph_arm_kernel<<<1, 1, 0, st>>>(g, tol2, (double)maxit, (double)done);
   SEM_CHECK_CUDA(cudaGetLastError());
 }

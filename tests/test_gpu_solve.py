@@ -597,6 +597,32 @@ def test_graph_flexcg_matches_host_loop_bitwise(bc, orders, cmode, smoother, dty
     assert residual(L, b, xg.cpu().numpy()) <= 1.05e-8
 
 
+def test_graph_launches_are_counted_per_kernel_class():
+    """A graph solve's kernels are counted under their own classes (from the
+    tally taken at capture, times the replays): the same per-class launch
+    counts as the host-driven loop, which launches the same kernels."""
+    m, L, b = _graph_problem(1, (7, 3, 1))
+    P = sem.Pmg(m, orders=(7, 3, 1), coarse_tol=1e-2, coarse_maxit=60, coarse_mode=sem.SEM_COARSE_MG)
+    bd = torch.tensor(b, device=DEV)
+    counts = []
+    for g in (False, True, True):
+        x = torch.zeros_like(bd)
+        sem.sem_solve(m, P, bd, x, sem.SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=100, use_graph=g,
+                      zero_guess=True)  # warm-up (and the capture)
+        sem.sem_trace_enable(True, "")
+        sem.sem_trace_read(reset=True)
+        info = sem.sem_solve(m, P, bd, x, sem.SEM_SOLVER_FLEXCG, tol=1e-8, max_iter=100,
+                             use_graph=g, zero_guess=True)
+        tr = sem.sem_trace_read(reset=True)
+        sem.sem_trace_enable(False, "")
+        assert info["iters"] >= 3
+        # the loop's own control kernels (arm, stop) exist only in the graph
+        counts.append({k: v["launches"] for k, v in tr.items()
+                       if v["launches"] and not k.startswith("graph_ctl")})
+    assert counts[1] == counts[0], (counts[0], counts[1])
+    assert counts[2] == counts[0]
+
+
 @pytest.mark.parametrize("max_iter", [1, 2, 3, 5])
 def test_graph_flexcg_stops_at_max_iter(max_iter):
     m, L, b = _graph_problem(0, (7, 3, 1))
