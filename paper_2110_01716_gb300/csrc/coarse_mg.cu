@@ -9,7 +9,7 @@
 // cycle per iteration, inside one persistent cooperative kernel:
 //  * levels: lattice coarsened by two per direction (even indices plus the
 //    last), index-space trilinear prolongation P = Pz x Py x Px, restriction
-//    P^T, Galerkin operators P^T A P (27-point stencils, built on the host in
+//    P^T, Galerkin operators P^T A P (27-point stencils, built on the device in
 //    FP64, in a fixed order);
 //  * smoother: degree-2 Chebyshev-Jacobi on [lambda/10, lambda], lambda =
 //    1.1 x a power-iteration estimate of lambda_max(D^-1 A);
@@ -25,6 +25,8 @@
 #include <vector>
 
 #include "coarse.cuh"
+#include "kernels.cuh"
+#include "reduce.cuh"
 #include "trace.cuh"
 
 namespace cg = cooperative_groups;
@@ -392,15 +394,146 @@ __global__ void __launch_bounds__(kMgThreads) coarse_mgcg_kernel(MgArgs A) {
   if (tid == 0) *A.iters = it;
 }
 
+// ------------------------------------------------------------------ device setup
+// The hierarchy is built on the device: Galerkin stencils by a gather over
+// each coarse point's fine support, keep masks and Jacobi inverses, and the
+// power iterations of the Chebyshev bounds.  The host keeps the 1D transfer
+// tables and inverts the dense bottom (at most kMgMaxBottom unknowns).
+
+// 1D transfer tables of one level pair (device), per direction.
+struct GalerkinTables {
+  const int *pi[3];     // [2 nf]: coarse indices of fine point i (-1: none)
+  const double *pw[3];  // [2 nf]: their weights
+  const int *ri[3];     // [3 nc]: fine indices of coarse point k (-1: none)
+  const double *rw[3];  // [3 nc]: their weights (the transposed prolongation)
+};
+
+// keep = not on the Dirichlet boundary; dinv = 1 / diagonal (0 where not
+// kept or where the diagonal is zero).
+__global__ void mg_finish_kernel(int nx, int ny, int nz, int dirichlet, const double *__restrict__ S,
+                                 unsigned char *__restrict__ keep, double *__restrict__ dinv) {
+  const int n = nx * ny * nz;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+    const int x = g % nx, y = (g / nx) % ny, z = g / (nx * ny);
+    const bool bnd = dirichlet && (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 ||
+                                   z == nz - 1);
+    keep[g] = bnd ? 0 : 1;
+    const double dg = S[(size_t)13 * n + g];
+    dinv[g] = !bnd && dg != 0.0 ? 1.0 / dg : 0.0;
+  }
+}
+
+// A_c = P^T A P over the fine unknowns, one coarse point I per thread:
+// A_c[I][J] = sum_f R[I][f] sum_g A[f][g] P[g][J] over kept fine f in I's
+// support and kept stencil neighbours g of f.  Each term is formed as
+// (w_I a) w_J with w = w_z w_y w_x, the factors in the host's order.
+__global__ void mg_galerkin_kernel(int fnx, int fny, int fnz, const double *__restrict__ SF,
+                                   const unsigned char *__restrict__ keepF, int cnx, int cny, int cnz,
+                                   GalerkinTables T, double *__restrict__ SC, int *bad) {
+  const int fn = fnx * fny * fnz, cn = cnx * cny * cnz;
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < cn; I += gridDim.x * blockDim.x) {
+    const int Ix = I % cnx, Iy = (I / cnx) % cny, Iz = I / (cnx * cny);
+    double acc[27];
+    for (int q = 0; q < 27; ++q) acc[q] = 0.0;
+    for (int c1 = 0; c1 < 3; ++c1) {
+      const int fz = T.ri[2][3 * Iz + c1];
+      if (fz < 0) continue;
+      for (int b1 = 0; b1 < 3; ++b1) {
+        const int fy = T.ri[1][3 * Iy + b1];
+        if (fy < 0) continue;
+        for (int a1 = 0; a1 < 3; ++a1) {
+          const int fx = T.ri[0][3 * Ix + a1];
+          if (fx < 0) continue;
+          const int f = fx + fnx * (fy + fny * fz);
+          if (!keepF[f]) continue;
+          const double wI = T.rw[2][3 * Iz + c1] * T.rw[1][3 * Iy + b1] * T.rw[0][3 * Ix + a1];
+          for (int d = 0; d < 27; ++d) {
+            const int gx = fx + d % 3 - 1, gy = fy + (d / 3) % 3 - 1, gz = fz + d / 9 - 1;
+            if (gx < 0 || gy < 0 || gz < 0 || gx >= fnx || gy >= fny || gz >= fnz) continue;
+            if (!keepF[gx + fnx * (gy + fny * gz)]) continue;
+            const double a = SF[(size_t)d * fn + f];
+            if (a == 0.0) continue;
+            const double wa = wI * a;
+            for (int c2 = 0; c2 < 2; ++c2) {
+              const int Jz = T.pi[2][2 * gz + c2];
+              if (Jz < 0) continue;
+              for (int b2 = 0; b2 < 2; ++b2) {
+                const int Jy = T.pi[1][2 * gy + b2];
+                if (Jy < 0) continue;
+                for (int a2 = 0; a2 < 2; ++a2) {
+                  const int Jx = T.pi[0][2 * gx + a2];
+                  if (Jx < 0) continue;
+                  const int ox = Jx - Ix, oy = Jy - Iy, oz = Jz - Iz;
+                  if (ox < -1 || ox > 1 || oy < -1 || oy > 1 || oz < -1 || oz > 1) {
+                    atomicExch(bad, 1);
+                    continue;
+                  }
+                  const double wJ = T.pw[2][2 * gz + c2] * T.pw[1][2 * gy + b2] * T.pw[0][2 * gx + a2];
+                  acc[(ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)] += wa * wJ;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    for (int q = 0; q < 27; ++q) SC[(size_t)q * cn + I] = acc[q];
+  }
+}
+
+// Start vector of the power iterations: 1 + sin(0.7 g + 0.3) / 2 on kept nodes.
+__global__ void mg_power_start_kernel(int n, const unsigned char *__restrict__ keep,
+                                      double *__restrict__ v) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x)
+    v[g] = keep[g] ? 1.0 + 0.5 * sin(0.7 * g + 0.3) : 0.0;
+}
+
+// One power step: w = D^-1 A v over kept nodes, and <v, v>, <v, w> (the
+// Rayleigh quotient of v is the second over the first).
+__global__ void __launch_bounds__(kVecThreads)
+    mg_power_step_kernel(int nx, int ny, int nz, const double *__restrict__ S,
+                         const unsigned char *__restrict__ keep, const double *__restrict__ dinv,
+                         const double *__restrict__ v, double *__restrict__ w, double *partials,
+                         unsigned int *counter, OutPtrs<2> out) {
+  const int n = nx * ny * nz;
+  double acc[2] = {0.0, 0.0};
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+    double a = 0.0;
+    if (keep[g]) {
+      const int gx = g % nx, gy = (g / nx) % ny, gz = g / (nx * ny);
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int x = gx + dx, y = gy + dy, z = gz + dz;
+            if (x < 0 || y < 0 || z < 0 || x >= nx || y >= ny || z >= nz) continue;
+            const int nb = x + nx * (y + ny * z);
+            if (!keep[nb]) continue;
+            a += S[(size_t)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)) * n + g] * v[nb];
+          }
+    }
+    const double wg = dinv[g] * a;
+    w[g] = wg;
+    acc[0] = fma(v[g], v[g], acc[0]);
+    acc[1] = fma(v[g], wg, acc[1]);
+  }
+  grid_reduce<2>(acc, partials, counter, out.p);
+}
+
+// FP64 -> FP32, rounded to nearest (the V-cycle's copies of the operators).
+__global__ void mg_narrow_kernel(size_t n, const double *__restrict__ a, float *__restrict__ b) {
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (size_t)gridDim.x * blockDim.x)
+    b[q] = (float)a[q];
+}
+
 // ------------------------------------------------------------------ host setup
 namespace {
 
+// The dense bottom level on the host.
 struct HostLevel {
   int nx, ny, nz, n;
   std::vector<double> S;            // [27][n]
   std::vector<unsigned char> keep;  // unknowns
-  std::vector<double> dinv;
-  double lam_hi = 0.0;
 };
 
 // Coarse points of a 1D lattice of n points: the even indices and the last.
@@ -460,126 +593,136 @@ double apply_host(const HostLevel &L, int g, const std::vector<double> &v) {
   return acc;
 }
 
-// lambda_max(D^-1 A) by 30 power iterations from a fixed start vector.
-double power_lambda(const HostLevel &L) {
-  std::vector<double> v(L.n), w(L.n);
-  for (int g = 0; g < L.n; ++g) v[g] = L.keep[g] ? 1.0 + 0.5 * std::sin(0.7 * g + 0.3) : 0.0;
-  double lam = 0.0;
-  for (int it = 0; it < 30; ++it) {
-    double nv = 0.0;
-    for (double a : v) nv += a * a;
-    nv = std::sqrt(nv);
-    if (nv == 0.0) return 1.0;
-    for (double &a : v) a /= nv;
-    for (int g = 0; g < L.n; ++g) w[g] = L.dinv[g] * apply_host(L, g, v);
-    double num = 0.0;
-    for (int g = 0; g < L.n; ++g) num += v[g] * w[g];
-    lam = num;
-    v.swap(w);
-  }
-  return lam;
-}
-
 }  // namespace
 
 void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st, int max_ctas) {
   const int nx0 = Lv.t.ex + 1, ny0 = Lv.t.ey + 1, nz0 = Lv.t.ez + 1;
   const int n0 = nx0 * ny0 * nz0;
   std::unique_ptr<CoarseMg> M(new CoarseMg());
-  std::vector<HostLevel> H(1);
-  H[0].nx = nx0; H[0].ny = ny0; H[0].nz = nz0; H[0].n = n0;
-  H[0].S.resize((size_t)27 * n0);
-  SEM_CHECK_CUDA(cudaMemcpyAsync(H[0].S.data(), C.S.p, H[0].S.size() * sizeof(double),
-                                 cudaMemcpyDeviceToHost, st));
-  SEM_CHECK_CUDA(cudaStreamSynchronize(st));
   const bool dir = Lv.t.bc == SEM_DIRICHLET;
-  auto boundary = [&](int x, int y, int z, int nx, int ny, int nz) {
-    return dir && (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1);
+  // FP64 operators of the levels, on the device: level 0 is the coarse
+  // solver's own stencil; the others are Galerkin products of their finer
+  // level.  Every level gets its keep mask and Jacobi inverse.
+  struct DevLevel {
+    int nx = 0, ny = 0, nz = 0, n = 0;
+    const double *S = nullptr;
+    DevBuf<double> Sbuf, dinv;
+    DevBuf<unsigned char> keep;
+    double lam_hi = 0.0;
   };
-  auto finish_level = [&](HostLevel &L) {
-    L.keep.assign(L.n, 1);
-    L.dinv.assign(L.n, 0.0);
-    for (int g = 0; g < L.n; ++g) {
-      const int x = g % L.nx, y = (g / L.nx) % L.ny, z = g / (L.nx * L.ny);
-      if (boundary(x, y, z, L.nx, L.ny, L.nz)) L.keep[g] = 0;
-    }
-    for (int g = 0; g < L.n; ++g) {
-      const double dg = L.S[(size_t)13 * L.n + g];
-      L.dinv[g] = L.keep[g] && dg != 0.0 ? 1.0 / dg : 0.0;
-    }
+  std::vector<std::unique_ptr<DevLevel>> H;
+  auto finish = [&](DevLevel &L) {
+    L.keep.alloc(L.n);
+    L.dinv.alloc(L.n);
+    const int g = (int)std::min<int64_t>((L.n + 255) / 256, 152 * 8);
+    mg_finish_kernel<<<g, 256, 0, st>>>(L.nx, L.ny, L.nz, dir ? 1 : 0, L.S, L.keep.p, L.dinv.p);
+    SEM_CHECK_CUDA(cudaGetLastError());
   };
-  finish_level(H[0]);
-  // transfer tables and Galerkin operators
+  H.emplace_back(new DevLevel());
+  H[0]->nx = nx0; H[0]->ny = ny0; H[0]->nz = nz0; H[0]->n = n0;
+  H[0]->S = C.S.p;
+  finish(*H[0]);
+  // transfer tables (host) and Galerkin operators (device)
   std::vector<std::vector<int>> PI[3], RI[3];
   std::vector<std::vector<double>> PW[3], RW[3];
-  while ((int)H.size() < kMgMaxLevels && H.back().n > kMgMaxBottom &&
-         std::min({H.back().nx, H.back().ny, H.back().nz}) > 3) {
-    const HostLevel &F = H.back();
+  DevBuf<int> bad;
+  bad.alloc(1);
+  SEM_CHECK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+  std::vector<std::unique_ptr<DevBuf<int>>> tab_i;
+  std::vector<std::unique_ptr<DevBuf<double>>> tab_d;
+  auto to_dev_i = [&](const std::vector<int> &v) {
+    tab_i.emplace_back(new DevBuf<int>());
+    tab_i.back()->alloc(v.size());
+    SEM_CHECK_CUDA(cudaMemcpyAsync(tab_i.back()->p, v.data(), v.size() * sizeof(int),
+                                   cudaMemcpyHostToDevice, st));
+    return (const int *)tab_i.back()->p;
+  };
+  auto to_dev_d = [&](const std::vector<double> &v) {
+    tab_d.emplace_back(new DevBuf<double>());
+    tab_d.back()->alloc(v.size());
+    SEM_CHECK_CUDA(cudaMemcpyAsync(tab_d.back()->p, v.data(), v.size() * sizeof(double),
+                                   cudaMemcpyHostToDevice, st));
+    return (const double *)tab_d.back()->p;
+  };
+  while ((int)H.size() < kMgMaxLevels && H.back()->n > kMgMaxBottom &&
+         std::min({H.back()->nx, H.back()->ny, H.back()->nz}) > 3) {
+    const DevLevel &F = *H.back();
     int ncd[3];
     std::vector<int> pi[3], ri[3];
     std::vector<double> pw[3], rw[3];
     const int nf[3] = {F.nx, F.ny, F.nz};
-    for (int d = 0; d < 3; ++d) prolong_1d(nf[d], pi[d], pw[d], ri[d], rw[d], ncd[d]);
-    HostLevel Cl;
-    Cl.nx = ncd[0]; Cl.ny = ncd[1]; Cl.nz = ncd[2];
-    Cl.n = Cl.nx * Cl.ny * Cl.nz;
-    Cl.S.assign((size_t)27 * Cl.n, 0.0);
-    // A_c[I][J] = sum_f sum_g P[f][I] A[f][g] P[g][J], fine unknowns only
-    for (int f = 0; f < F.n; ++f) {
-      if (!F.keep[f]) continue;
-      const int fx = f % F.nx, fy = (f / F.nx) % F.ny, fz = f / (F.nx * F.ny);
-      for (int d = 0; d < 27; ++d) {
-        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-        const int gx = fx + dx, gy = fy + dy, gz = fz + dz;
-        if (gx < 0 || gy < 0 || gz < 0 || gx >= F.nx || gy >= F.ny || gz >= F.nz) continue;
-        const int gidx = gx + F.nx * (gy + F.ny * gz);
-        if (!F.keep[gidx]) continue;
-        const double a = F.S[(size_t)d * F.n + f];
-        if (a == 0.0) continue;
-        for (int c1 = 0; c1 < 2; ++c1) {
-          const int Iz = pi[2][2 * fz + c1];
-          if (Iz < 0) continue;
-          for (int b1 = 0; b1 < 2; ++b1) {
-            const int Iy = pi[1][2 * fy + b1];
-            if (Iy < 0) continue;
-            for (int a1 = 0; a1 < 2; ++a1) {
-              const int Ix = pi[0][2 * fx + a1];
-              if (Ix < 0) continue;
-              const double wI = pw[2][2 * fz + c1] * pw[1][2 * fy + b1] * pw[0][2 * fx + a1];
-              const int I = Ix + Cl.nx * (Iy + Cl.ny * Iz);
-              for (int c2 = 0; c2 < 2; ++c2) {
-                const int Jz = pi[2][2 * gz + c2];
-                if (Jz < 0) continue;
-                for (int b2 = 0; b2 < 2; ++b2) {
-                  const int Jy = pi[1][2 * gy + b2];
-                  if (Jy < 0) continue;
-                  for (int a2 = 0; a2 < 2; ++a2) {
-                    const int Jx = pi[0][2 * gx + a2];
-                    if (Jx < 0) continue;
-                    const double wJ = pw[2][2 * gz + c2] * pw[1][2 * gy + b2] * pw[0][2 * gx + a2];
-                    const int od = (Jx - Ix + 1) + 3 * (Jy - Iy + 1) + 9 * (Jz - Iz + 1);
-                    SEM_REQUIRE(Jx - Ix >= -1 && Jx - Ix <= 1 && Jy - Iy >= -1 && Jy - Iy <= 1 &&
-                                    Jz - Iz >= -1 && Jz - Iz <= 1,
-                                "coarse stencil exceeds 27 points");
-                    Cl.S[(size_t)od * Cl.n + I] += wI * a * wJ;
-                  }
-                }
-              }
-            }
-          }
-        }
-      }
+    GalerkinTables T;
+    for (int d = 0; d < 3; ++d) {
+      prolong_1d(nf[d], pi[d], pw[d], ri[d], rw[d], ncd[d]);
+      T.pi[d] = to_dev_i(pi[d]);
+      T.pw[d] = to_dev_d(pw[d]);
+      T.ri[d] = to_dev_i(ri[d]);
+      T.rw[d] = to_dev_d(rw[d]);
     }
-    finish_level(Cl);
+    std::unique_ptr<DevLevel> Cl(new DevLevel());
+    Cl->nx = ncd[0]; Cl->ny = ncd[1]; Cl->nz = ncd[2];
+    Cl->n = Cl->nx * Cl->ny * Cl->nz;
+    Cl->Sbuf.alloc((size_t)27 * Cl->n);
+    Cl->S = Cl->Sbuf.p;
+    const int g = (int)std::min<int64_t>((Cl->n + 127) / 128, 152 * 8);
+    mg_galerkin_kernel<<<g, 128, 0, st>>>(F.nx, F.ny, F.nz, F.S, F.keep.p, Cl->nx, Cl->ny, Cl->nz,
+                                          T, Cl->Sbuf.p, bad.p);
+    SEM_CHECK_CUDA(cudaGetLastError());
+    finish(*Cl);
     for (int d = 0; d < 3; ++d) {
       PI[d].push_back(pi[d]); PW[d].push_back(pw[d]);
       RI[d].push_back(ri[d]); RW[d].push_back(rw[d]);
     }
     H.push_back(std::move(Cl));
   }
-  SEM_REQUIRE(H.back().n <= kMgMaxBottom, "coarse lattice too elongated for the multigrid mode");
-  // bottom: dense (Dirichlet rows -> identity; Neumann: + c 1 1^T)
-  const HostLevel &B = H.back();
+  SEM_REQUIRE(H.back()->n <= kMgMaxBottom, "coarse lattice too elongated for the multigrid mode");
+  // Chebyshev bounds (smoothed levels): 30 power steps each on the device
+  {
+    Reducer R;
+    R.init(kVecMaxBlocks, 2);
+    DevBuf<double> pv, slots;
+    size_t nmax = 0;
+    for (size_t l = 0; l + 1 < H.size(); ++l) nmax = std::max(nmax, (size_t)H[l]->n);
+    pv.alloc(2 * std::max<size_t>(nmax, 1));
+    slots.alloc(2 * std::max<size_t>(H.size(), 1));
+    for (size_t l = 0; l + 1 < H.size(); ++l) {
+      const DevLevel &L = *H[l];
+      double *v = pv.p, *w = pv.p + nmax;
+      const int g = vec_grid(L.n);
+      mg_power_start_kernel<<<g, kVecThreads, 0, st>>>(L.n, L.keep.p, v);
+      SEM_CHECK_CUDA(cudaGetLastError());
+      OutPtrs<2> o{{slots.p + 2 * l, slots.p + 2 * l + 1}};
+      for (int it = 0; it < 30; ++it) {
+        mg_power_step_kernel<<<g, kVecThreads, 0, st>>>(L.nx, L.ny, L.nz, L.S, L.keep.p, L.dinv.p, v,
+                                                         w, R.partials.p, R.counter.p, o);
+        SEM_CHECK_CUDA(cudaGetLastError());
+        std::swap(v, w);
+      }
+    }
+    std::vector<double> hs(2 * H.size(), 0.0);
+    SEM_CHECK_CUDA(cudaMemcpyAsync(hs.data(), slots.p, hs.size() * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
+    int hbad = 0;
+    SEM_CHECK_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+    SEM_REQUIRE(hbad == 0, "coarse stencil exceeds 27 points");
+    for (size_t l = 0; l + 1 < H.size(); ++l)
+      H[l]->lam_hi = 1.1 * (hs[2 * l] > 0.0 ? hs[2 * l + 1] / hs[2 * l] : 1.0);
+  }
+  // bottom: dense (Dirichlet rows -> identity; Neumann: + c 1 1^T), from the
+  // last level's stencil and mask brought to the host
+  HostLevel B;
+  {
+    const DevLevel &D = *H.back();
+    B.nx = D.nx; B.ny = D.ny; B.nz = D.nz; B.n = D.n;
+    B.S.resize((size_t)27 * D.n);
+    B.keep.resize(D.n);
+    SEM_CHECK_CUDA(cudaMemcpyAsync(B.S.data(), D.S, B.S.size() * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
+    SEM_CHECK_CUDA(cudaMemcpyAsync(B.keep.data(), D.keep.p, B.keep.size(), cudaMemcpyDeviceToHost,
+                                   st));
+    SEM_CHECK_CUDA(cudaStreamSynchronize(st));
+  }
   const int nb = B.n;
   std::vector<double> Ad((size_t)nb * nb, 0.0), inv((size_t)nb * nb, 0.0);
   {
@@ -631,8 +774,6 @@ void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st, int max_
       if (!B.keep[i])
         for (int j = 0; j < nb; ++j) inv[(size_t)i * nb + j] = 0.0;
   }
-  // Chebyshev bounds (smoothed levels)
-  for (size_t l = 0; l + 1 < H.size(); ++l) H[l].lam_hi = 1.1 * power_lambda(H[l]);
   // Device buffers of the FP32 V-cycle.  Every array carved out of the three
   // buffers starts on a 256-byte boundary: the unrolled gathers read
   // neighbouring table entries, which the compiler may merge into vector
@@ -641,7 +782,7 @@ void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st, int max_
   const int nlev = (int)H.size();
   size_t flt = up((size_t)nb * nb, 64), ints = 0;
   for (int l = 0; l < nlev; ++l) {
-    flt += up((size_t)27 * H[l].n, 64) + 6 * up(H[l].n, 64);
+    flt += up((size_t)27 * H[l]->n, 64) + 6 * up(H[l]->n, 64);
     if (l + 1 < nlev)
       for (int d = 0; d < 3; ++d) {
         flt += up(PW[d][l].size(), 64) + up(RW[d][l].size(), 64);
@@ -649,7 +790,7 @@ void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st, int max_
       }
   }
   size_t keeps = 0;
-  for (int l = 0; l < nlev; ++l) keeps += up(H[l].n, 256);
+  for (int l = 0; l < nlev; ++l) keeps += up(H[l]->n, 256);
   M->fbuf.alloc(flt);
   M->ibuf.alloc(ints > 0 ? ints : 1);
   M->kbuf.alloc(keeps);
@@ -663,23 +804,44 @@ void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st, int max_
     of += up(v.size(), 64);
     return dst;
   };
-  auto vec = [&](int n) {
+  auto vec = [&](size_t n) {
     float *dst = M->fbuf.p + of;
     of += up(n, 64);
     return dst;
   };
+  // FP32 copies of the levels' operators made on the device once the host
+  // part of the buffers has been copied (dst, FP64 src, count), and the keep
+  // masks copied likewise
+  struct Narrow {
+    float *dst;
+    const double *src;
+    size_t n;
+  };
+  struct KeepCopy {
+    unsigned char *dst;
+    const unsigned char *src;
+    size_t n;
+  };
+  std::vector<Narrow> narrows;
+  std::vector<KeepCopy> keepcopies;
   MgArgs &A = M->args;
   std::memset(&A, 0, sizeof(A));
   A.nlev = nlev;
   for (int l = 0; l < nlev; ++l) {
-    const HostLevel &L = H[l];
+    const DevLevel &L = *H[l];
     MgLevelT<float> &D = A.V[l];
     D.nx = L.nx; D.ny = L.ny; D.nz = L.nz; D.n = L.n;
     D.div_nx = FastDiv((uint32_t)L.nx);
     D.div_nxy = FastDiv((uint32_t)(L.nx * L.ny));
-    D.S = put(L.S);
-    D.dinv = put(L.dinv);
-    std::copy(L.keep.begin(), L.keep.end(), hk.begin() + ok);
+    {
+      float *dS = vec((size_t)27 * L.n);
+      narrows.push_back({dS, L.S, (size_t)27 * L.n});
+      D.S = dS;
+      float *dD = vec(L.n);
+      narrows.push_back({dD, L.dinv.p, (size_t)L.n});
+      D.dinv = dD;
+    }
+    keepcopies.push_back({M->kbuf.p + ok, L.keep.p, (size_t)L.n});
     D.keep = M->kbuf.p + ok; ok += up(L.n, 256);
     D.x = vec(L.n);
     D.b = vec(L.n);
@@ -743,6 +905,13 @@ void coarse_mg_setup(CoarseSolver &C, const Level &Lv, cudaStream_t st, int max_
   SEM_CHECK_CUDA(cudaMemcpyAsync(M->ibuf.p, hi.data(), hi.size() * sizeof(int),
                                  cudaMemcpyHostToDevice, st));
   SEM_CHECK_CUDA(cudaMemcpyAsync(M->kbuf.p, hk.data(), hk.size(), cudaMemcpyHostToDevice, st));
+  for (const Narrow &q : narrows) {
+    const int g = (int)std::min<size_t>((q.n + 255) / 256, 152 * 8);
+    mg_narrow_kernel<<<g, 256, 0, st>>>(q.n, q.src, q.dst);
+    SEM_CHECK_CUDA(cudaGetLastError());
+  }
+  for (const KeepCopy &q : keepcopies)
+    SEM_CHECK_CUDA(cudaMemcpyAsync(q.dst, q.src, q.n, cudaMemcpyDeviceToDevice, st));
   A.ex = Lv.t.ex; A.ey = Lv.t.ey; A.ez = Lv.t.ez; A.bc = Lv.t.bc;
   A.div_ex = FastDiv((uint32_t)Lv.t.ex);
   A.div_ey = FastDiv((uint32_t)Lv.t.ey);
