@@ -149,7 +149,15 @@ struct sem_batch {
       cudaGraph_t g;
       ~GraphGuard() { if (g) cudaGraphDestroy(g); }
     } gg{g};
-    for (int i : which) {
+    // largest problems first: the graph's independent branches start in about
+    // the order they were added, and the batch ends with its slowest solve
+    std::vector<int> order(which);
+    auto work = [&](int i) {
+      const sem_request &r = reqs[i];
+      return (double)r.ex * r.ey * r.ez * std::pow((double)(r.N + 1), 3);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+    for (int i : order) {
       apply_fill(i);
       const sem_solve_desc &s = reqs[i].solve;
       cudaGraphNode_t end =
