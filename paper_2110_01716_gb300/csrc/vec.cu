@@ -22,6 +22,9 @@ void Reducer::init(int blocks, int max_sums) {
   partials.alloc(capacity);
   counter.alloc(1);
   SEM_CHECK_CUDA(cudaMemset(counter.p, 0, sizeof(unsigned int)));
+  // the memset runs on the legacy stream, which kernels on non-blocking
+  // streams (server workers, batch captures) do not wait for: finish it here
+  SEM_CHECK_CUDA(cudaStreamSynchronize(0));
 }
 
 int vec_grid(int64_t n) {
