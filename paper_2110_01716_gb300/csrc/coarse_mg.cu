@@ -357,21 +357,27 @@ __global__ void __launch_bounds__(kMgThreads) coarse_mgcg_kernel(MgArgs A) {
       mg_sum<1>(v, A.partA, grid);
       const double pw = v[0];
       const double alpha = rho / pw;
+      // the update with (r,r): the stopping test comes before the
+      // preconditioner, whose output the last iteration would not use (the
+      // reduction's grid barrier is also the one the V-cycle needs first)
+      double q[1] = {0.0};
       for (int g = tid; g < L0.n; g += nth) {
         A.x[g] = fma(alpha, A.p[g], A.x[g]);
-        A.r[g] = fma(-alpha, A.w[g], A.r[g]);
+        const double rg = fma(-alpha, A.w[g], A.r[g]);
+        A.r[g] = rg;
+        q[0] = fma(rg, rg, q[0]);
       }
-      grid.sync();
+      mg_sum<1>(q, A.partM, grid);
+      if (!(q[0] > A.tol2 * bb) || it >= A.maxit || !(q[0] == q[0])) break;
       mg_vcycle(A, A.r, A.z, grid, tid, nth);
-      double u[3] = {0.0, 0.0, 0.0};  // (r,z), (z,w), (r,r)
+      double u[2] = {0.0, 0.0};  // (r,z), (z,w)
       for (int g = tid; g < L0.n; g += nth) {
-        const double rg = A.r[g], zg = A.z[g];
-        u[0] = fma(rg, zg, u[0]);
+        const double zg = A.z[g];
+        u[0] = fma(A.r[g], zg, u[0]);
         u[1] = fma(zg, A.w[g], u[1]);
-        u[2] = fma(rg, rg, u[2]);
       }
-      mg_sum<3>(u, A.partK, grid);
-      if (!(u[2] > A.tol2 * bb) || it >= A.maxit || !(u[2] == u[2]) || u[0] == 0.0) break;
+      mg_sum<2>(u, A.partK, grid);
+      if (u[0] == 0.0) break;
       // flexible (Polak-Ribiere) coefficient: (z_new, r_new - r_old) / rho
       const double beta = -alpha * u[1] / rho;
       rho = u[0];
