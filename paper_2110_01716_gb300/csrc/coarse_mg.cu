@@ -53,7 +53,9 @@ __device__ __forceinline__ void mg_coords(const MgLevelT<T> &L, int g, int &gx, 
 // flight together (a load is issued only for a neighbour inside the lattice).
 template <typename T>
 __device__ __forceinline__ T mg_apply(const MgLevelT<T> &L, int g, const T *__restrict__ v) {
-  if (!L.keep[g]) return (T)0;
+  // the keep flag is read beside the stencil's loads, not before them (every
+  // node has a stencil row, so the loads are in bounds either way)
+  const bool kept = L.keep[g] != 0;
   int gx, gy, gz;
   mg_coords(L, g, gx, gy, gz);
   const bool in_x[3] = {gx > 0, true, gx < L.nx - 1};
@@ -74,7 +76,7 @@ __device__ __forceinline__ T mg_apply(const MgLevelT<T> &L, int g, const T *__re
   T acc = 0;
 #pragma unroll
   for (int d = 0; d < 27; ++d) acc = fma(sv[d], vv[d], acc);
-  return acc;
+  return kept ? acc : (T)0;
 }
 
 // Grid-wide sums identical in every CTA (warp 0 reduces; see coarse.cu).
@@ -161,7 +163,8 @@ __device__ void mg_down(const MgArgs &A, int l, Bar bar, int tid, int nth, bool 
   const MgLevelT<float> &C = A.V[l + 1];
   for (int G = tid; G < C.n; G += nth) {
     float acc = 0.f;
-    if (C.keep[G]) {
+    const bool kept = C.keep[G] != 0;  // applied at the end, not waited for
+    {
       int Gx, Gy, Gz;
       mg_coords(C, G, Gx, Gy, Gz);
       // table rows first (index -1: no fine point), then guarded loads
@@ -198,7 +201,7 @@ __device__ void mg_down(const MgArgs &A, int l, Bar bar, int tid, int nth, bool 
           }
         }
     }
-    C.b[G] = acc;
+    C.b[G] = kept ? acc : 0.f;
   }
   if (last_barrier) bar();
 }
@@ -226,7 +229,7 @@ __device__ void mg_up(const MgArgs &A, int l, Bar bar, int tid, int nth) {
   const float *b = L.b;
   float *x = L.x;
   for (int g = tid; g < L.n; g += nth) {
-    if (!L.keep[g]) continue;
+    const bool kept = L.keep[g] != 0;  // applied at the end, not waited for
     int gx, gy, gz;
     mg_coords(L, g, gx, gy, gz);
     int ci[3][2];
@@ -262,7 +265,7 @@ __device__ void mg_up(const MgArgs &A, int l, Bar bar, int tid, int nth) {
           if (ok) acc = fma(wyz * cw[0][a], xv[a + 2 * (b2 + 2 * c)], acc);
         }
       }
-    x[g] += acc;
+    if (kept) x[g] += acc;
   }
   bar();
   for (int g = tid; g < L.n; g += nth) {
