@@ -198,13 +198,57 @@ __global__ void __launch_bounds__(kVecThreads)
   grid_reduce<2>(acc, partials, counter, out.p);
 }
 
+// The same two sums for an FP32 z whose element rows are whole float4s
+// (Np % 4 == 0): four points per iteration, one index decode for the four
+// (they share an element, j and k), and 16-byte loads of z, r and w.
+__global__ void __launch_bounds__(kVecThreads)
+    flex_dots4_kernel(Topo t, const float4 *__restrict__ z, const double2 *__restrict__ r,
+                      const double2 *__restrict__ w, double *partials, unsigned int *counter,
+                      OutPtrs<2> out) {
+  double acc[2] = {0.0, 0.0};
+  const uint32_t n4 = (uint32_t)t.nl / 4;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
+    const float4 zv = z[q];
+    const double2 r0 = r[2 * q], r1 = r[2 * q + 1], w0 = w[2 * q], w1 = w[2 * q + 1];
+    const uint32_t l = q * 4;
+    const uint32_t e = t.div_np3.div(l);
+    const uint32_t jk = t.div_np.div(l - e * (uint32_t)t.Np3);
+    const int i0 = (int)(l - e * (uint32_t)t.Np3 - jk * (uint32_t)t.Np);
+    const int k = (int)t.div_np.div(jk);
+    const int j = (int)(jk - (uint32_t)k * t.Np);
+    const uint32_t yz = t.div_ex.div(e);
+    const int ix = (int)(e - yz * (uint32_t)t.ex);
+    const int iz = (int)t.div_ey.div(yz);
+    const int iy = (int)(yz - (uint32_t)iz * t.ey);
+    const uint32_t ef = elem_face_bits(ix, iy, iz, t);
+    const float zc[4] = {zv.x, zv.y, zv.z, zv.w};
+    const double rc[4] = {r0.x, r0.y, r1.x, r1.y}, wc[4] = {w0.x, w0.y, w1.x, w1.y};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int lm = __popc(point_face_bits(i0 + c, j, k, t.N) & ~ef);
+      const double zl = scale_pow2_down(widen_f32(zc[c]), lm);
+      acc[0] = fma(zl, rc[c], acc[0]);
+      acc[1] = fma(zl, wc[c], acc[1]);
+    }
+  }
+  grid_reduce<2>(acc, partials, counter, out.p);
+}
+
 template <typename Tz>
 void launch_flex_dots(const Topo &t, Reducer &R, const Tz *z, const double *r, const double *w,
                       double *zr, double *zw, cudaStream_t st) {
   OutPtrs<2> o{{zr, zw}};
   TraceScope ts("flex_dots", t.N, st);
-  flex_dots_kernel<Tz><<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, z, r, w, R.partials.p,
-                                                               R.counter.p, o);
+  auto a16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (sizeof(Tz) == 4 && t.Np % 4 == 0 && (uint64_t)t.nl < (1ull << 32) && a16(z) && a16(r) &&
+      a16(w)) {
+    flex_dots4_kernel<<<vec_grid(t.nl / 4), kVecThreads, 0, st>>>(
+        t, reinterpret_cast<const float4 *>(z), reinterpret_cast<const double2 *>(r),
+        reinterpret_cast<const double2 *>(w), R.partials.p, R.counter.p, o);
+  } else {
+    flex_dots_kernel<Tz><<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, z, r, w, R.partials.p,
+                                                                 R.counter.p, o);
+  }
   SEM_CHECK_CUDA(cudaGetLastError());
 }
 template void launch_flex_dots<double>(const Topo &, Reducer &, const double *, const double *,
