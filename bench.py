@@ -1146,8 +1146,26 @@ def main():
                                restart=args.restart, zero_guess=True, use_graph=use_graph)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
+        # the host link's rate on these very buffers, after the timed region:
+        # the part of the end-to-end time the copies take
+        db = torch.empty(nl, dtype=torch.float64, device=dev)
+        rates = {}
+        for name, dst, src in (("h2d_GBps", db, bh), ("d2h_GBps", xh, db)):
+            best = None
+            for _ in range(3):
+                c0 = torch.cuda.Event(enable_timing=True)
+                c1 = torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                dst.copy_(src, non_blocking=True)
+                c1.record(stream)
+                c1.synchronize()
+                t = c0.elapsed_time(c1)
+                best = t if best is None else min(best, t)
+            rates[name] = round(nl * 8 / (best / 1e3) / 1e9, 1)
+        del db
         line["e2e"] = {"value": ng / e2e_s / 1e9, "unit": "GDOF/s",
-                       "h2d_bytes_per_step": nl * 8, "d2h_bytes_per_step": nl * 8}
+                       "h2d_bytes_per_step": nl * 8, "d2h_bytes_per_step": nl * 8,
+                       "ms_per_step": round(e2e_s * 1e3, 2), **rates}
         del bh, xh
         if solver == sem.SEM_SOLVER_FLEXCG:
             ex["named_config"] = named_config_leg(sem, torch, mesh, b, x, args, ng)
