@@ -240,15 +240,17 @@ void launch_flex_dots(const Topo &t, Reducer &R, const Tz *z, const double *r, c
   OutPtrs<2> o{{zr, zw}};
   TraceScope ts("flex_dots", t.N, st);
   auto a16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-  if (sizeof(Tz) == 4 && t.Np % 4 == 0 && (uint64_t)t.nl < (1ull << 32) && a16(z) && a16(r) &&
-      a16(w)) {
-    flex_dots4_kernel<<<vec_grid(t.nl / 4), kVecThreads, 0, st>>>(
-        t, reinterpret_cast<const float4 *>(z), reinterpret_cast<const double2 *>(r),
-        reinterpret_cast<const double2 *>(w), R.partials.p, R.counter.p, o);
-  } else {
-    flex_dots_kernel<Tz><<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, z, r, w, R.partials.p,
-                                                                 R.counter.p, o);
+  if constexpr (sizeof(Tz) == 4) {
+    if (t.Np % 4 == 0 && (uint64_t)t.nl < (1ull << 32) && a16(z) && a16(r) && a16(w)) {
+      flex_dots4_kernel<<<vec_grid(t.nl / 4), kVecThreads, 0, st>>>(
+          t, reinterpret_cast<const float4 *>(z), reinterpret_cast<const double2 *>(r),
+          reinterpret_cast<const double2 *>(w), R.partials.p, R.counter.p, o);
+      SEM_CHECK_CUDA(cudaGetLastError());
+      return;
+    }
   }
+  flex_dots_kernel<Tz><<<vec_grid(t.nl), kVecThreads, 0, st>>>(t, z, r, w, R.partials.p,
+                                                               R.counter.p, o);
   SEM_CHECK_CUDA(cudaGetLastError());
 }
 template void launch_flex_dots<double>(const Topo &, Reducer &, const double *, const double *,
